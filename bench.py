@@ -1,0 +1,430 @@
+"""Benchmark of the BN254 prover hot path on B300.
+
+One step = one pass over the plain single ops at scale: KZG commitment MSMs
+of n = 2^20 points (scalars uniform in F_r, and quantised int8 * 2^16 values),
+and F_r NTT + INTT of lengths 2^20 and 2^22, all inputs resident in HBM.
+The headline value is MSM throughput (Mpts/s) at 2^20 with uniform scalars;
+the JSON line also carries every op's throughput, the batched-vs-plain
+comparisons (256-polynomial CNN commitment batch, 1024-leaf fold tree), the
+roofline of the dominant kernel, the end-to-end number through the C ABI
+with host buffers, and the CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import zkinputs as Z  # noqa: E402
+
+METRIC = "BN254 MSM Mpts/s & Fr NTT Melem/s at 2^20; batched folds/s vs plain; % roofline"
+UNIT = "Mpts/s"
+WORKLOAD = "plain single ops at scale: MSM 2^20 (uniform F_r; int8*2^16), NTT/INTT 2^20 and 2^22"
+L2_FLUSH_BYTES = 512 << 20
+SRS_LOG = 22
+# Per mixed addition (madd-2008-s): 8 multiplications + 2 squarings in F_q;
+# per Montgomery product 264 32-bit IMADs (8 x (16 product + 16 reduction + 1)).
+FQ_MUL_PER_MADD = 10
+IMAD_PER_MUL = 264
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip batch / fold-tree comparisons")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for name, v in zip(names, s[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_msm_rate(sample_n: int):
+    """The oracle's affine double-and-add MSM timed on sample_n points."""
+    import oracle as orc
+    orc.lib()
+    tau = Z.tau(0)
+    srs = orc.srs_gen(tau, sample_n)
+    c = Z.fr_uniform(3, sample_n)
+    t0 = time.perf_counter()
+    orc.msm(srs, c)
+    dt = time.perf_counter() - t0
+    return sample_n / dt / 1e6, dt, orc.threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    import oracle as orc
+    orc.lib()
+    sample = 1 << 9
+    rates, times = [], []
+    for _ in range(args.warmup):
+        oracle_msm_rate(sample)
+    for _ in range(args.steps):
+        r, dt, cores = oracle_msm_rate(sample)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact F_q/F_r)",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "MSM of %d points" % sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "affine double-and-add MSM, %d points, SRS from seeded tau" % sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2507_07031_b300 as zk
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+    ctx = zk.zk_init(local)
+    zk.zk_srs_generate(ctx, Z.tau(0), 1 << SRS_LOG)
+    n20, n22 = 1 << 20, 1 << 22
+    sc_uni = dev(Z.fr_uniform(3, n20))
+    sc_q = dev(Z.zkml_scalars(4, n20))
+    x20 = dev(Z.fr_uniform(5, n20))
+    x22 = dev(Z.fr_uniform(6, n22))
+    out = torch.zeros((2, 8), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    ops = [
+        ("msm_2^20_uniform", n20, lambda: zk.zk_commit(ctx, sc_uni, out[0])),
+        ("msm_2^20_int8x2^16", n20, lambda: zk.zk_commit(ctx, sc_q, out[1])),
+        ("ntt_2^20", n20, lambda: zk.zk_ntt(ctx, x20)),
+        ("intt_2^20", n20, lambda: zk.zk_intt(ctx, x20)),
+        ("ntt_2^22", n22, lambda: zk.zk_ntt(ctx, x22)),
+        ("intt_2^22", n22, lambda: zk.zk_intt(ctx, x22)),
+    ]
+    ev = {name: [] for name, _, _ in ops}
+
+    def step(record):
+        for name, _, fn in ops:
+            flush.fill_(1)  # evict L2 (512 MiB > 126 MB) between ops
+            if record:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                ev[name].append((a, b))
+            else:
+                fn()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    zk.zk_timing_read(ctx)  # discard
+    zk.zk_timing_enable(ctx, True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = zk.zk_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = zk.zk_kernel_launches() - launches0
+    sampler.stop()
+    phases = zk.zk_timing_read(ctx)
+    zk.zk_timing_enable(ctx, False)
+    total_ms = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    per_op = {}
+    for name, n, _ in ops:
+        ms = [a.elapsed_time(b) for a, b in ev[name]]
+        med = statistics.median(ms)
+        unit = "Mpts/s" if name.startswith("msm") else "Melem/s"
+        per_op[name] = {"ms": med, unit: n / (med * 1e-3) / 1e6}
+    msm_ms = statistics.median([a.elapsed_time(b) for a, b in ev["msm_2^20_uniform"]])
+    value_per_gpu = n20 / (msm_ms * 1e-3) / 1e6
+    value = value_per_gpu * world
+
+    # Roofline of the dominant kernel class: MSM bucket accumulation.
+    imad_peak, fq_mul_peak = zk.zk_probe_rates(local)
+    acc_ms, acc_cnt = phases["msm_accum"]
+    W = 16
+    # Mixed additions per step: W nonzero digits per uniform scalar, one per
+    # recentred int8 * 2^16 scalar (its only nonzero 16-bit window).
+    madds = (n20 * W + n20 * 1) * args.steps
+    achieved = madds * FQ_MUL_PER_MADD * IMAD_PER_MUL / (acc_ms * 1e-3) / 1e12 if acc_ms else None
+    roofline = {
+        "bound": "alu", "kernel": "k_pieces_first/k_pieces_next/k_buckets_final (MSM accumulation)",
+        "achieved": achieved, "peak": imad_peak / 1e12, "unit": "TIMAD/s",
+        "frac": (achieved / (imad_peak / 1e12)) if achieved else None,
+        "peak_source": "measured live: independent 32-bit mad.lo issue rate (zk_probe_rates)",
+        "fq_mul_peak_per_s": fq_mul_peak, "traffic": None,
+        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+    }
+
+    # End to end through the C ABI with host buffers (pinned): H2D of the
+    # scalars and D2H of the commitment inside the timed region.
+    h_sc = torch.from_numpy(Z.fr_uniform(3, n20).view(np.int64)).pin_memory()
+    h_out = torch.zeros(8, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        zk.zk_commit(ctx, h_sc, h_out)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        zk.zk_commit(ctx, h_sc, h_out)
+        e2e_t.append(time.perf_counter() - s0)
+    e2e = {"value": n20 / statistics.median(e2e_t) / 1e6 * world, "unit": UNIT,
+           "h2d_bytes_per_step": n20 * 32, "d2h_bytes_per_step": 64,
+           "call": "zk_commit(host scalars, host out)"}
+
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(zk, ctx, dev, torch)
+
+    cpu = None
+    if rank == 0:
+        r, dt, cores = oracle_msm_rate(1 << 9)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "affine double-and-add MSM of 512 points (SRS from seeded tau), %.1f s" % dt}
+
+    zk.zk_destroy(ctx)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact F_q/F_r)",
+        "data": "synthetic (seeded SplitMix64; SRS from seeded tau)",
+        "config": {"workload": WORKLOAD, "srs": "2^22 points, window tables c=16",
+                   "l2": "flushed (512 MiB write) before every op", "parallelism": "replicas" if world > 1 else "single"},
+        "ops": per_op, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": sampler.summary(), **extras,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_extras(zk, ctx, dev, torch):
+    """Batched vs plain: the 256-polynomial CNN commitment batch and the
+    1024-leaf fold tree."""
+    res = {}
+    # CNN batch: 256 evaluation vectors (int8 * 2^16), INTT + commit each.
+    sizes = Z.cnn_poly_sizes(8)
+    vecs = [dev(Z.zkml_scalars(7_000_000 + i, int(s))) for i, s in enumerate(sizes)]
+    outb = torch.zeros((len(vecs), 8), dtype=torch.int64, device="cuda")
+    outp = torch.zeros((len(vecs), 8), dtype=torch.int64, device="cuda")
+
+    def batched():
+        zk.zk_commit_batch(ctx, vecs, outb, flags=zk.ZK_EVALS)
+
+    def plain():
+        for i, v in enumerate(vecs):
+            zk.zk_commit_batch(ctx, [v], outp[i:i + 1], flags=zk.ZK_EVALS)
+
+    for f in (batched, plain):
+        f()
+    torch.cuda.synchronize()
+    tb = _time(torch, batched, 3)
+    tp = _time(torch, plain, 3)
+    res["cnn_batch_commit"] = {"polys": len(vecs), "coeffs": int(sizes.sum()),
+                               "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb,
+                               "identical": bool(torch.equal(outb, outp))}
+    del vecs
+    # Fold tree: 1024 leaves of 2^16 (config: matmul block, 4 witness vectors).
+    count, n = 1024, 1 << 16
+    accs = []
+    for j in range(count):
+        m = torch.zeros((4, n, 4), dtype=torch.int64, device="cuda")
+        base = (9 << 20) + 4 * j
+        m[0].copy_(dev(Z.zkml_scalars(base, n)))
+        m[1].copy_(dev(Z.zkml_scalars(base + 1, n)))
+        m[3].copy_(dev(Z.zkml_scalars(base + 3, n)))
+        e = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+        x = torch.zeros(44, dtype=torch.int64, device="cuda")
+        accs.append((m, e, x))
+    descs = [zk.make_acc(*a) for a in accs]
+    t_leaf = _time(torch, lambda: zk.zk_leaf_init(ctx, descs), 1)
+    leaf_state = [(a[0].clone(), a[1].clone(), a[2].clone()) for a in accs]
+    gam = dev(np.concatenate([Z.gammas(l, count >> l) for l in range(1, 11)]))
+    root = (torch.zeros((4, n, 4), dtype=torch.int64, device="cuda"),
+            torch.zeros((n, 4), dtype=torch.int64, device="cuda"),
+            torch.zeros(44, dtype=torch.int64, device="cuda"))
+    rdesc = zk.make_acc(*root)
+
+    def restore():
+        for a, s in zip(accs, leaf_state):
+            for t, u in zip(a, s):
+                t.copy_(u)
+
+    def tree():
+        zk.zk_fold_tree(ctx, descs, gam, rdesc)
+
+    def plain_tree():
+        width, goff, span = count, 0, 2
+        while span <= count:
+            for j in range(width // 2):
+                L = descs[j * span + span // 2 - 1]
+                R = descs[j * span + span - 1]
+                zk.zk_fold(ctx, L, R, gam[goff + j], R)
+            goff += width // 2
+            width //= 2
+            span *= 2
+
+    restore()
+    tree()  # warm-up (sizes workspaces)
+    restore()
+    torch.cuda.synchronize()
+    tt = _time(torch, tree, 1)
+    root_batched = [r.clone() for r in root]
+    restore()
+    plain_tree()  # warm-up
+    restore()
+    torch.cuda.synchronize()
+    tp = _time(torch, plain_tree, 1)
+    same = all(torch.equal(a, b) for a, b in zip(accs[count - 1], root_batched))
+    res["fold_tree"] = {"leaves": count, "n": n, "folds": count - 1,
+                        "batched_folds_per_s": (count - 1) / (tt * 1e-3),
+                        "plain_folds_per_s": (count - 1) / (tp * 1e-3),
+                        "batched_ms": tt, "plain_ms": tp, "speedup": tp / tt,
+                        "leaf_commit_ms": t_leaf, "identical": bool(same)}
+    return res
+
+
+def _time(torch, fn, reps):
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * zk_b300.h -- C ABI of the B300 (sm_103a) prover hot path for ZKTorch-style
+ * proofs of ML inference over BN254 (Chen, Tang, Kang, "ZKTorch: Compiling ML
+ * Inference to Zero-Knowledge Proofs via Parallel Proof Accumulation").
+ *
+ * The library computes, on one GPU:
+ *   - KZG commitments com = [f(tau)]_1 = sum_i c_i [tau^i]_1 as multi-scalar
+ *     multiplications over a device-resident SRS (paper Sec. 2.1);
+ *   - the F_r NTT / inverse NTT that maps a witness vector of evaluations over
+ *     H = <omega> to polynomial coefficients (Sec. 3, "witness generation and
+ *     encoding"; Sec. 4.4, f|_H);
+ *   - generalised-Mira accumulation folds and the parallel fold tree
+ *     (Sec. 4.2, accumulation prover steps 2-7, tree reduction).
+ *
+ * Encodings (all little endian, canonical):
+ *   zk_fr  -- an element of F_r (r = BN254 group order) as 4 x uint64, value < r.
+ *   zk_g1  -- an affine G1 point (y^2 = x^3 + 3 over F_q), x then y, each
+ *             4 x uint64 < q.  The point at infinity is 64 zero bytes.
+ *   NTT root of unity: omega_n = 5^((r-1)/n) mod r, n a power of two <= 2^28.
+ *
+ * Memory: unless stated otherwise a buffer argument may be a device pointer
+ * (cudaMalloc / torch) or a host pointer; host buffers are staged through the
+ * context's device workspace inside the call, and a call with any host output
+ * synchronises the stream before it returns.  Device results are valid once
+ * the stream has reached the call.  The caller owns every buffer it passes.
+ * A context's workspace is not safe for concurrent calls on different
+ * streams: use one lane (zk_lane_create) per concurrent stream.
+ *
+ * Errors: every function returns ZK_OK (0) or one of the codes below; no
+ * function aborts the process.  zk_strerror() gives a static description.
+ */
+#ifndef ZK_B300_H
+#define ZK_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZK_OK 0
+#define ZK_EINVAL 1   /* null pointer, bad size, non-canonical or off-curve input */
+#define ZK_ESRS 2     /* no SRS loaded, or the request is longer than the SRS */
+#define ZK_ENOMEM 3   /* allocation would exceed the context's HBM budget */
+#define ZK_ECUDA 4    /* a CUDA runtime call failed */
+#define ZK_ETIMEOUT 5 /* a bounded wait on the device or in the job queue expired */
+#define ZK_EBUSY 6    /* the serving queue is full */
+
+/* Opaque context: device, HBM budget, SRS and its window tables, NTT twiddle
+ * tables and scratch workspace.  A stream handle is a cudaStream_t; NULL is
+ * the legacy default stream. */
+typedef struct zk_ctx zk_ctx;
+typedef struct CUstream_st *zk_stream;
+
+typedef struct { uint64_t l[4]; } zk_fr;
+typedef struct { uint64_t x[4]; uint64_t y[4]; } zk_g1;
+
+/* Accumulator instance of the generalised Mira scheme for the degree-2
+ * relation m1 o m2 - mu m3 = e over H (Sec. 4.2: acc.x = {C_i, E, mu}; the
+ * relation has no public input or verifier challenges, so pi and r_i are
+ * absent).  352 bytes; lives in device memory. */
+typedef struct {
+    zk_g1 C[4]; /* commitments to the interpolants of m_1..m_4 */
+    zk_g1 E;    /* commitment to the interpolant of the error vector e */
+    zk_fr mu;   /* slack scalar */
+} zk_acc_inst;
+
+/* Accumulator (Sec. 4.2: acc.w = {m_i, e} and acc.x).  All pointers are
+ * DEVICE pointers: m[i] and e hold n evaluations over H each; x points to one
+ * zk_acc_inst.  n is a power of two, 2 <= n <= 2^26. */
+typedef struct {
+    size_t n;
+    zk_fr *m[4];
+    zk_fr *e;
+    zk_acc_inst *x;
+} zk_acc;
+
+/* Create a context on CUDA device `device` that may allocate at most
+ * `hbm_budget_bytes` of device memory (0 = no limit).  *out receives the
+ * context.  ZK_EINVAL for a null out or a bad device. */
+int zk_init(zk_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Release a context (or a lane) and everything it allocated.  Waits for the
+ * device first.  A context must outlive its lanes. */
+int zk_destroy(zk_ctx *ctx);
+
+/* A lane shares the parent's SRS, window tables and twiddles (read only) and
+ * owns its own scratch workspace, so calls on different lanes may overlap on
+ * different streams.  Used by the serving loop. */
+int zk_lane_create(zk_ctx *parent, zk_ctx **out);
+
+/* Load the SRS [tau^0]_1 .. [tau^(n-1)]_1 (Sec. 2.1; the powers-of-tau
+ * ceremony output).  Every point is checked to be canonical and on the curve
+ * (cofactor 1, so on the curve means in the group); infinity is rejected.
+ * ZK_EINVAL on a bad point, n == 0 or n > 2^26; the previous SRS is then
+ * dropped.  Builds the window tables the MSM uses.  Synchronous. */
+int zk_srs_load(zk_ctx *ctx, const zk_g1 *pts, size_t n);
+
+/* Test-and-benchmark set-up: build the SRS [tau^i]_1, i < n, on the device
+ * from a known trapdoor tau (host pointer).  A real deployment loads the
+ * ceremony output with zk_srs_load instead; this exists because the paper's
+ * workloads need SRSs up to 2^22 points and only the commitment, not its
+ * setup, is on the prover's hot path.  Synchronous. */
+int zk_srs_generate(zk_ctx *ctx, const zk_fr *tau, size_t n);
+
+/* Number of SRS points loaded (0 if none). */
+int zk_srs_size(const zk_ctx *ctx, size_t *n);
+
+/* Copy SRS points [first, first + count) out in canonical affine form. */
+int zk_srs_export(zk_ctx *ctx, zk_g1 *out, size_t first, size_t count, zk_stream stream);
+
+/* KZG commitment of the polynomial with coefficients coeffs[0..n-1]:
+ * *out = sum_i coeffs[i] * SRS[i] = [f(tau)]_1 (Sec. 2.1), by a signed-window
+ * Pippenger MSM.  1 <= n <= SRS size (ZK_ESRS otherwise).  Coefficients must
+ * be canonical (< r). */
+int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream);
+
+/* Flags of zk_commit_batch. */
+#define ZK_EVALS 1u /* vectors are evaluations over H: INTT each one first (in place, on
+                       a workspace copy -- the caller's vectors are not modified) */
+
+/* Commit `count` vectors in one batched pass: out[k] = commitment of vecs[k]
+ * (lens[k] elements).  `vecs` is a host array of pointers (each device or
+ * host) and `out` points to count zk_g1.  With ZK_EVALS a vector whose length
+ * is not a power of two is zero-padded to the next power of two before the
+ * INTT (Sec. 3 encodes each tensor's last axis as one polynomial). */
+int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, size_t count,
+                    unsigned flags, zk_g1 *out, zk_stream stream);
+
+/* In-place natural-order NTT: data[k] <- sum_j data[j] omega_n^{jk}.  n a power
+ * of two, 1 <= n <= 2^28 (ZK_EINVAL otherwise). */
+int zk_ntt(zk_ctx *ctx, zk_fr *data, size_t n, zk_stream stream);
+
+/* In-place natural-order inverse NTT: data[j] <- n^{-1} sum_k data[k] omega_n^{-jk}
+ * (evaluations over H to coefficients). */
+int zk_intt(zk_ctx *ctx, zk_fr *data, size_t n, zk_stream stream);
+
+/* Batched NTT / INTT of `count` device vectors of power-of-two lengths. */
+int zk_ntt_batch(zk_ctx *ctx, zk_fr *const *data, const size_t *lens, size_t count, int inverse,
+                 zk_stream stream);
+
+/* Leaf accumulators from NARK witnesses (Sec. 4.2: a NARK proof is the
+ * accumulator with mu = 1 and e = 0): for each of the `count` accumulators
+ * (host array; all of one length n), given m1, m2, m4 in acc->m, writes
+ * m3 = m1 o m2, e = 0, and acc->x = {C_i = Commit(INTT(m_i)), E = infinity,
+ * mu = 1}.  The commitments of all leaves run as batched INTTs and MSMs. */
+int zk_leaf_init(zk_ctx *ctx, const zk_acc *accs, size_t count, zk_stream stream);
+
+/* One fold acc'' = fold(L, R, gamma) (Sec. 4.2, prover steps 2-7, d = 2, L in
+ * the role of acc and R of acc'):
+ *   e1  = m1 o m2' + m1' o m2 - mu m3' - mu' m3          (step 2)
+ *   E1  = Commit(INTT(e1))                                 (step 3)
+ *   m_i'' = gamma m_i + m_i',  e'' = e' + gamma e1 + gamma^2 e   (step 5)
+ *   C_i'' = gamma C_i + C_i',  E'' = E' + gamma E1 + gamma^2 E,  mu'' = gamma mu + mu'.
+ * `gamma` may be a host or device pointer; `out` may alias R (not L).  If
+ * E1_out is not NULL it receives E1 (the correction term pf, step 7). */
+int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
+            zk_g1 *E1_out, zk_stream stream);
+
+/* Parallel fold tree (Sec. 4.2, tree reduction): count = 2^levels leaves; at
+ * level l = 1..levels fold j combines the two level-(l-1) accumulators 2j (as
+ * L) and 2j+1 (as R) with gammas[(count - count/2^(l-1)) + j] (level-major,
+ * count - 1 challenges; host or device pointer).  All folds of one level run
+ * as one batch.  The leaves' buffers are overwritten (used as the tree's
+ * storage); the root is copied into *root (which must not alias a leaf). */
+int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
+                 zk_stream stream);
+
+/* Static description of an error code. */
+const char *zk_strerror(int code);
+
+/* Diagnostics (not part of the paper's method).
+ * zk_kernel_launches: number of kernels this library has launched in the
+ * process so far (every launch site counts itself).
+ * zk_probe_rates: measures, on `device`, the issue rate of independent 32-bit
+ * integer multiply-adds (IMAD/s, the integer roofline's ceiling) and the
+ * throughput of this library's F_q Montgomery multiplication (products/s).
+ * Takes a few milliseconds; synchronous. */
+unsigned long long zk_kernel_launches(void);
+int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s);
+
+/* Phase timing: with timing on, each call brackets its phases with CUDA events
+ * on its stream; zk_timing_read waits for them, adds up the device time (ms)
+ * and interval count per phase since the last read, and clears the record. */
+#define ZK_PHASE_MSM_SORT 0       /* recode + counting sort of bucket entries */
+#define ZK_PHASE_MSM_ACCUM 1      /* bucket accumulation (mixed additions) */
+#define ZK_PHASE_MSM_REDUCE 2     /* weighted bucket sums and output */
+#define ZK_PHASE_NTT 3            /* all NTT / INTT passes */
+#define ZK_PHASE_FOLD_WITNESS 4   /* cross term and witness RLC */
+#define ZK_PHASE_FOLD_INSTANCE 5  /* instance RLC (G1 scalar multiplications) */
+#define ZK_NPHASES 6
+int zk_timing_enable(zk_ctx *ctx, int on);
+int zk_timing_read(zk_ctx *ctx, double ms[ZK_NPHASES], unsigned long long count[ZK_NPHASES]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZK_B300_H */

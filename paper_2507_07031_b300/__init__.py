@@ -1,0 +1,251 @@
+"""Python binding of libzkb300 (the C ABI in include/zk_b300.h).
+
+Argument marshalling only: every function below forwards to the C entry
+point of the same name, passing raw device/host pointers and the current
+torch CUDA stream.  Field elements travel as (n, 4) int64 tensors or uint64
+numpy arrays (little-endian limbs, canonical); G1 points as (n, 8).  PyTorch
+provides device memory and streams; all arithmetic runs in the library's
+CUDA kernels.  Importing this module fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzkb300.so")
+
+ZK_OK, ZK_EINVAL, ZK_ESRS, ZK_ENOMEM, ZK_ECUDA, ZK_ETIMEOUT, ZK_EBUSY = range(7)
+ZK_EVALS = 1
+
+
+class ZkError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (where, zk_strerror(code), code))
+
+
+class ZkAcc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_size_t), ("m", ctypes.c_void_p * 4), ("e", ctypes.c_void_p),
+                ("x", ctypes.c_void_p)]
+
+
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_SZP = ctypes.POINTER(ctypes.c_size_t)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libzkb300.so not built: run `python paper_2507_07031_b300/build.py` "
+                          "(or __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "zk_init": [ctypes.POINTER(_VP), ctypes.c_int, _SZ],
+        "zk_destroy": [_VP],
+        "zk_lane_create": [_VP, ctypes.POINTER(_VP)],
+        "zk_srs_load": [_VP, _VP, _SZ],
+        "zk_srs_generate": [_VP, _VP, _SZ],
+        "zk_srs_size": [_VP, _SZP],
+        "zk_srs_export": [_VP, _VP, _SZ, _SZ, _VP],
+        "zk_commit": [_VP, _VP, _SZ, _VP, _VP],
+        "zk_commit_batch": [_VP, _VP, _VP, _SZ, ctypes.c_uint, _VP, _VP],
+        "zk_ntt": [_VP, _VP, _SZ, _VP],
+        "zk_intt": [_VP, _VP, _SZ, _VP],
+        "zk_ntt_batch": [_VP, _VP, _VP, _SZ, ctypes.c_int, _VP],
+        "zk_leaf_init": [_VP, _VP, _SZ, _VP],
+        "zk_fold": [_VP, _VP, _VP, _VP, _VP, _VP, _VP],
+        "zk_fold_tree": [_VP, _VP, _SZ, _VP, _VP, _VP],
+        "zk_timing_enable": [_VP, ctypes.c_int],
+        "zk_timing_read": [_VP, _VP, _VP],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.zk_strerror.argtypes = [ctypes.c_int]
+    L.zk_strerror.restype = ctypes.c_char_p
+    L.zk_kernel_launches.argtypes = []
+    L.zk_kernel_launches.restype = ctypes.c_ulonglong
+    L.zk_probe_rates.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    L.zk_probe_rates.restype = ctypes.c_int
+    return L
+
+
+lib = _load()
+
+EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_generate",
+            "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_batch", "zk_ntt", "zk_intt",
+            "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_strerror",
+            "zk_kernel_launches", "zk_probe_rates", "zk_timing_enable", "zk_timing_read"]
+
+PHASES = ["msm_sort", "msm_accum", "msm_reduce", "ntt", "fold_witness", "fold_instance"]
+
+
+def zk_strerror(code: int) -> str:
+    return lib.zk_strerror(int(code)).decode()
+
+
+def zk_kernel_launches() -> int:
+    return int(lib.zk_kernel_launches())
+
+
+def zk_probe_rates(device: int = 0):
+    """(IMAD/s, F_q Montgomery products/s) measured on `device`."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.zk_probe_rates(int(device), ctypes.byref(a), ctypes.byref(b)), "zk_probe_rates")
+    return a.value, b.value
+
+
+def zk_timing_enable(ctx: int, on: bool = True) -> None:
+    _check(lib.zk_timing_enable(ctx, int(bool(on))), "zk_timing_enable")
+
+
+def zk_timing_read(ctx: int) -> dict:
+    """{phase: (device ms, intervals)} since the last read."""
+    ms = (ctypes.c_double * len(PHASES))()
+    cnt = (ctypes.c_ulonglong * len(PHASES))()
+    _check(lib.zk_timing_read(ctx, ms, cnt), "zk_timing_read")
+    return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+
+def _check(rc: int, where: str):
+    if rc != ZK_OK:
+        raise ZkError(rc, where)
+
+
+# ---------------------------------------------------------------------------
+# Pointer / stream marshalling
+# ---------------------------------------------------------------------------
+
+def _ptr(buf) -> int:
+    """Address of a torch tensor (device or host) or a numpy array (host)."""
+    if buf is None:
+        return 0
+    if isinstance(buf, np.ndarray):
+        assert buf.flags["C_CONTIGUOUS"], "numpy buffers must be contiguous"
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        assert buf.is_contiguous(), "tensors must be contiguous"
+        return buf.data_ptr()
+    return int(buf)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return 0
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _nelem(buf, width: int) -> int:
+    n = buf.numel() if hasattr(buf, "numel") else buf.size
+    assert n % width == 0
+    return n // width
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def zk_init(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    h = _VP()
+    _check(lib.zk_init(ctypes.byref(h), int(device), int(hbm_budget_bytes)), "zk_init")
+    return h.value
+
+
+def zk_destroy(ctx: int) -> None:
+    _check(lib.zk_destroy(ctx), "zk_destroy")
+
+
+def zk_lane_create(ctx: int) -> int:
+    h = _VP()
+    _check(lib.zk_lane_create(ctx, ctypes.byref(h)), "zk_lane_create")
+    return h.value
+
+
+def zk_srs_load(ctx: int, pts, n: int | None = None) -> None:
+    n = _nelem(pts, 8) if n is None else n
+    _check(lib.zk_srs_load(ctx, _ptr(pts), n), "zk_srs_load")
+
+
+def zk_srs_generate(ctx: int, tau, n: int) -> None:
+    t = np.ascontiguousarray(np.asarray(tau, dtype=np.uint64).reshape(4))
+    _check(lib.zk_srs_generate(ctx, t.ctypes.data, int(n)), "zk_srs_generate")
+
+
+def zk_srs_size(ctx: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.zk_srs_size(ctx, ctypes.byref(n)), "zk_srs_size")
+    return n.value
+
+
+def zk_srs_export(ctx: int, out, first: int, count: int, stream=None) -> None:
+    _check(lib.zk_srs_export(ctx, _ptr(out), first, count, _stream(stream)), "zk_srs_export")
+
+
+def zk_commit(ctx: int, coeffs, out, n: int | None = None, stream=None) -> None:
+    n = _nelem(coeffs, 4) if n is None else n
+    _check(lib.zk_commit(ctx, _ptr(coeffs), n, _ptr(out), _stream(stream)), "zk_commit")
+
+
+def zk_commit_batch(ctx: int, vecs, out, flags: int = 0, lens=None, stream=None) -> None:
+    count = len(vecs)
+    ptrs = (ctypes.c_void_p * max(count, 1))(*[_ptr(v) for v in vecs])
+    lens = [(_nelem(v, 4)) for v in vecs] if lens is None else list(lens)
+    ls = (ctypes.c_size_t * max(count, 1))(*lens)
+    _check(lib.zk_commit_batch(ctx, ptrs, ls, count, int(flags), _ptr(out), _stream(stream)),
+           "zk_commit_batch")
+
+
+def zk_ntt(ctx: int, data, n: int | None = None, stream=None) -> None:
+    n = _nelem(data, 4) if n is None else n
+    _check(lib.zk_ntt(ctx, _ptr(data), n, _stream(stream)), "zk_ntt")
+
+
+def zk_intt(ctx: int, data, n: int | None = None, stream=None) -> None:
+    n = _nelem(data, 4) if n is None else n
+    _check(lib.zk_intt(ctx, _ptr(data), n, _stream(stream)), "zk_intt")
+
+
+def zk_ntt_batch(ctx: int, vecs, inverse: bool, stream=None) -> None:
+    count = len(vecs)
+    ptrs = (ctypes.c_void_p * max(count, 1))(*[_ptr(v) for v in vecs])
+    ls = (ctypes.c_size_t * max(count, 1))(*[_nelem(v, 4) for v in vecs])
+    _check(lib.zk_ntt_batch(ctx, ptrs, ls, count, int(bool(inverse)), _stream(stream)), "zk_ntt_batch")
+
+
+def make_acc(m, e, x) -> ZkAcc:
+    """Accumulator descriptor from device tensors: m = four (n, 4) tensors (or
+    one (4, n, 4) tensor), e (n, 4), x (44,) int64 (zk_acc_inst)."""
+    a = ZkAcc()
+    ms = [m[i] for i in range(4)]
+    a.n = _nelem(e, 4)
+    for i in range(4):
+        a.m[i] = _ptr(ms[i])
+    a.e = _ptr(e)
+    a.x = _ptr(x)
+    return a
+
+
+def zk_leaf_init(ctx: int, accs, stream=None) -> None:
+    arr = (ZkAcc * len(accs))(*accs)
+    _check(lib.zk_leaf_init(ctx, arr, len(accs), _stream(stream)), "zk_leaf_init")
+
+
+def zk_fold(ctx: int, L: ZkAcc, R: ZkAcc, gamma, out: ZkAcc, E1_out=None, stream=None) -> None:
+    _check(lib.zk_fold(ctx, ctypes.byref(L), ctypes.byref(R), _ptr(gamma), ctypes.byref(out),
+                       _ptr(E1_out), _stream(stream)), "zk_fold")
+
+
+def zk_fold_tree(ctx: int, leaves, gammas, root: ZkAcc, stream=None) -> None:
+    arr = (ZkAcc * len(leaves))(*leaves)
+    _check(lib.zk_fold_tree(ctx, arr, len(leaves), _ptr(gammas), ctypes.byref(root), _stream(stream)),
+           "zk_fold_tree")

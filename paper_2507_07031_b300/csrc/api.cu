@@ -1,0 +1,397 @@
+// api.cu -- the extern "C" entry points of zk_b300.h, context management,
+// budget-checked allocation and host-buffer staging.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace zk {
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+Shared::~Shared() {
+    for (auto &t : tables)
+        if (t.buf.p) cudaFree(t.buf.p);
+    if (srs.p) cudaFree(srs.p);
+    for (auto &b : tw)
+        if (b.p) cudaFree(b.p);
+}
+
+int dev_alloc(Shared &sh, DevBuf &b, size_t bytes) {
+    std::lock_guard<std::mutex> g(sh.alloc_mu);
+    if (b.p) {
+        cudaFree(b.p);
+        sh.used -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) return ZK_OK;
+    if (sh.budget && sh.used + bytes > sh.budget) return ZK_ENOMEM;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return ZK_ENOMEM;
+    }
+    b.p = p;
+    b.bytes = bytes;
+    sh.used += bytes;
+    return ZK_OK;
+}
+
+void dev_free(Shared &sh, DevBuf &b) {
+    std::lock_guard<std::mutex> g(sh.alloc_mu);
+    if (b.p) {
+        cudaFree(b.p);
+        sh.used -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err) {
+    DevBuf &b = ctx->scratch[name];
+    if (b.p && b.bytes >= bytes) return b.p;
+    // Grow by at least 25% so that slowly growing requests do not reallocate
+    // (cudaFree waits for the device) on every call.
+    size_t want = std::max(bytes, b.bytes + b.bytes / 4);
+    want = (want + 255) & ~(size_t)255;
+    int r = dev_alloc(*ctx->sh, b, want);
+    if (r != ZK_OK) {
+        r = dev_alloc(*ctx->sh, b, (bytes + 255) & ~(size_t)255);
+        if (r != ZK_OK) {
+            *err = r;
+            return nullptr;
+        }
+    }
+    return b.p;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(const zk_ctx *ctx) {
+        cudaGetDevice(&prev);
+        if (ctx && ctx->sh && prev != ctx->sh->device) cudaSetDevice(ctx->sh->device);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Stages `bytes` of a host buffer into the named scratch (or passes a device
+// pointer through).
+int stage_in(zk_ctx *ctx, const void *src, size_t bytes, const char *name, const void **dev,
+             cudaStream_t s) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return ZK_OK;
+    }
+    int err = ZK_OK;
+    void *d = scratch(ctx, name, std::max<size_t>(bytes, 32), &err);
+    if (!d) return err;
+    ZK_CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+    *dev = d;
+    return ZK_OK;
+}
+
+__global__ void k_zero_pad(uint4 *dst, size_t from16, size_t to16) {
+    for (size_t i = from16 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < to16;
+         i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = make_uint4(0, 0, 0, 0);
+}
+
+size_t next_pow2(size_t n) {
+    size_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+}  // namespace zk
+
+using namespace zk;
+
+extern "C" {
+
+unsigned long long zk_kernel_launches(void) { return g_launches.load(); }
+
+const char *zk_strerror(int code) {
+    switch (code) {
+        case ZK_OK: return "ok";
+        case ZK_EINVAL: return "invalid argument (null pointer, bad size, non-canonical or off-curve input)";
+        case ZK_ESRS: return "no SRS loaded, or request longer than the SRS";
+        case ZK_ENOMEM: return "device allocation would exceed the HBM budget";
+        case ZK_ECUDA: return "CUDA runtime error";
+        case ZK_ETIMEOUT: return "bounded wait expired";
+        case ZK_EBUSY: return "queue full";
+        default: return "unknown error";
+    }
+}
+
+int zk_init(zk_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) return ZK_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return ZK_EINVAL;
+    zk_ctx *c = new (std::nothrow) zk_ctx();
+    if (!c) return ZK_ENOMEM;
+    c->sh = std::make_shared<Shared>();
+    c->sh->device = device;
+    c->sh->budget = hbm_budget_bytes;
+    DeviceGuard g(c);
+    if (cudaFree(nullptr) != cudaSuccess) {  // create the primary context
+        delete c;
+        return ZK_ECUDA;
+    }
+    *out = c;
+    return ZK_OK;
+}
+
+int zk_timing_enable(zk_ctx *ctx, int on) {
+    if (!ctx) return ZK_EINVAL;
+    ctx->timing = on != 0;
+    return ZK_OK;
+}
+
+int zk_timing_read(zk_ctx *ctx, double ms[ZK_NPHASES], unsigned long long count[ZK_NPHASES]) {
+    if (!ctx || !ms || !count) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    for (int i = 0; i < ZK_NPHASES; i++) {
+        ms[i] = 0;
+        count[i] = 0;
+    }
+    int rc = ZK_OK;
+    for (auto &m : ctx->marks) {
+        float t = 0;
+        if (cudaEventSynchronize(m.b) != cudaSuccess || cudaEventElapsedTime(&t, m.a, m.b) != cudaSuccess) {
+            cudaGetLastError();
+            rc = ZK_ECUDA;
+        }
+        if (m.phase >= 0 && m.phase < ZK_NPHASES) {
+            ms[m.phase] += t;
+            count[m.phase] += 1;
+        }
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    ctx->marks.clear();
+    return rc;
+}
+
+int zk_lane_create(zk_ctx *parent, zk_ctx **out) {
+    if (!parent || !out) return ZK_EINVAL;
+    zk_ctx *c = new (std::nothrow) zk_ctx();
+    if (!c) return ZK_ENOMEM;
+    c->sh = parent->sh;
+    c->is_lane = true;
+    *out = c;
+    return ZK_OK;
+}
+
+int zk_destroy(zk_ctx *ctx) {
+    if (!ctx) return ZK_EINVAL;
+    {
+        DeviceGuard g(ctx);
+        cudaDeviceSynchronize();
+        for (auto &m : ctx->marks) {
+            cudaEventDestroy(m.a);
+            cudaEventDestroy(m.b);
+        }
+        ctx->marks.clear();
+        for (auto &kv : ctx->scratch) dev_free(*ctx->sh, kv.second);
+        ctx->scratch.clear();
+        ctx->sh.reset();  // frees SRS and tables with the last owner
+    }
+    delete ctx;
+    return ZK_OK;
+}
+
+int zk_srs_load(zk_ctx *ctx, const zk_g1 *pts, size_t n) {
+    if (!ctx) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return srs_load_impl(ctx, pts, n, 0);
+}
+
+int zk_srs_generate(zk_ctx *ctx, const zk_fr *tau, size_t n) {
+    if (!ctx) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return srs_generate_impl(ctx, tau, n, 0);
+}
+
+int zk_srs_size(const zk_ctx *ctx, size_t *n) {
+    if (!ctx || !n) return ZK_EINVAL;
+    *n = ctx->sh->srs_n;
+    return ZK_OK;
+}
+
+int zk_srs_export(zk_ctx *ctx, zk_g1 *out, size_t first, size_t count, zk_stream stream) {
+    if (!ctx) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return srs_export_impl(ctx, out, first, count, (cudaStream_t)stream);
+}
+
+int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream) {
+    if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
+    const size_t lens[1] = {n};
+    const zk_fr *const vecs[1] = {coeffs};
+    return zk_commit_batch(ctx, vecs, lens, 1, 0, out, stream);
+}
+
+int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, size_t count,
+                    unsigned flags, zk_g1 *out, zk_stream stream) {
+    if (!ctx || !vecs || !lens || !out) return ZK_EINVAL;
+    if (count == 0) return ZK_OK;
+    if (flags & ~ZK_EVALS) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool evals = flags & ZK_EVALS;
+    Shared &sh = *ctx->sh;
+    if (sh.srs_n == 0) return ZK_ESRS;
+    std::vector<size_t> padded(count);
+    size_t total = 0;
+    for (size_t k = 0; k < count; k++) {
+        if (!vecs[k] && lens[k]) return ZK_EINVAL;
+        padded[k] = evals ? next_pow2(std::max<size_t>(lens[k], 1)) : lens[k];
+        if (lens[k] == 0) padded[k] = 0;
+        if (padded[k] > sh.srs_n) return ZK_ESRS;
+        if (evals && padded[k] > ((size_t)1 << kMaxLogN)) return ZK_EINVAL;
+        total += padded[k];
+    }
+    // Inputs: staged (host sources, or a workspace copy for the INTT).
+    int err = ZK_OK;
+    bool any_host = false;
+    std::vector<bool> dev_in(count);
+    for (size_t k = 0; k < count; k++) {
+        dev_in[k] = !lens[k] || is_device_ptr(vecs[k]);
+        any_host |= !dev_in[k];
+    }
+    uint32_t *ws = nullptr;
+    if (evals || any_host) {
+        ws = (uint32_t *)scratch(ctx, "commit.ws", std::max<size_t>(total, 1) * 32, &err);
+        if (!ws) return err;
+    }
+    std::vector<MsmJob> jobs(count);
+    std::vector<uint32_t *> ntt_vecs;
+    std::vector<size_t> ntt_lens;
+    size_t off = 0;
+    for (size_t k = 0; k < count; k++) {
+        const uint32_t *src = (const uint32_t *)vecs[k];
+        if (evals || !dev_in[k]) {
+            uint32_t *dst = ws + off * 8;
+            if (lens[k]) {
+                cudaMemcpyKind kind = dev_in[k] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+                ZK_CUDA_TRY(cudaMemcpyAsync(dst, src, lens[k] * 32, kind, s));
+            }
+            if (padded[k] > lens[k]) {
+                k_zero_pad<<<64, 256, 0, s>>>((uint4 *)dst, lens[k] * 2, padded[k] * 2);
+                ZK_LAUNCHED();
+            }
+            if (evals && padded[k]) {
+                ntt_vecs.push_back(dst);
+                ntt_lens.push_back(padded[k]);
+            }
+            src = dst;
+        }
+        jobs[k].scalars = src;
+        jobs[k].n = (uint32_t)padded[k];
+        off += padded[k];
+    }
+    if (!ntt_vecs.empty())
+        ZK_TRY(ntt_batch_impl(ctx, ntt_vecs.data(), ntt_lens.data(), ntt_vecs.size(), true, s));
+    // Outputs.
+    const bool dev_out = is_device_ptr(out);
+    uint32_t *obuf = (uint32_t *)out;
+    if (!dev_out) {
+        obuf = (uint32_t *)scratch(ctx, "commit.out", count * 64, &err);
+        if (!obuf) return err;
+    }
+    size_t maxn = 1;
+    for (size_t k = 0; k < count; k++) {
+        jobs[k].out = obuf + 16 * k;
+        maxn = std::max(maxn, (size_t)jobs[k].n);
+    }
+    ZK_TRY(msm_batch_impl(ctx, jobs.data(), count, msm_pick_window(ctx, maxn, count), s));
+    if (!dev_out) {
+        ZK_CUDA_TRY(cudaMemcpyAsync(out, obuf, count * 64, cudaMemcpyDeviceToHost, s));
+        ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return ZK_OK;
+}
+
+static int ntt_entry(zk_ctx *ctx, zk_fr *data, size_t n, bool inverse, zk_stream stream) {
+    if (!ctx || !data) return ZK_EINVAL;
+    if (!n || (n & (n - 1)) || n > ((size_t)1 << kMaxLogN)) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (is_device_ptr(data)) return ntt_impl(ctx, (uint32_t *)data, n, inverse, s);
+    const void *d = nullptr;
+    ZK_TRY(stage_in(ctx, data, n * 32, "ntt.stage", &d, s));
+    ZK_TRY(ntt_impl(ctx, (uint32_t *)d, n, inverse, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(data, d, n * 32, cudaMemcpyDeviceToHost, s));
+    ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    return ZK_OK;
+}
+
+int zk_ntt(zk_ctx *ctx, zk_fr *data, size_t n, zk_stream stream) {
+    return ntt_entry(ctx, data, n, false, stream);
+}
+
+int zk_intt(zk_ctx *ctx, zk_fr *data, size_t n, zk_stream stream) {
+    return ntt_entry(ctx, data, n, true, stream);
+}
+
+int zk_ntt_batch(zk_ctx *ctx, zk_fr *const *data, const size_t *lens, size_t count, int inverse,
+                 zk_stream stream) {
+    if (!ctx || (count && (!data || !lens))) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    for (size_t k = 0; k < count; k++)
+        if (!is_device_ptr(data[k])) return ZK_EINVAL;
+    return ntt_batch_impl(ctx, (uint32_t *const *)data, lens, count, inverse != 0,
+                          (cudaStream_t)stream);
+}
+
+int zk_leaf_init(zk_ctx *ctx, const zk_acc *accs, size_t count, zk_stream stream) {
+    if (!ctx) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return leaf_init_impl(ctx, accs, count, (cudaStream_t)stream);
+}
+
+int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
+            zk_g1 *E1_out, zk_stream stream) {
+    if (!ctx) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return fold_impl(ctx, L, R, gamma, out, E1_out, (cudaStream_t)stream);
+}
+
+int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
+                 zk_stream stream) {
+    if (!ctx) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return fold_tree_impl(ctx, leaves, count, gammas, root, (cudaStream_t)stream);
+}
+
+}  // extern "C"

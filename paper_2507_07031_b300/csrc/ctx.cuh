@@ -1,0 +1,165 @@
+// ctx.cuh -- library context: device, HBM budget, resident SRS tables,
+// twiddle tables and grow-only scratch buffers (host-side C++).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/zk_b300.h"
+
+namespace zk {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Precomputed window table for window width c: entry (w, i) holds
+// 2^(c w) * SRS[i] as an affine point in Montgomery form (64 bytes), for
+// w < W = ceil(254 / c) and i < n.  With one table per c every window of a
+// scalar adds into the same bucket set, so the bucket reduction is done once
+// per MSM instead of once per window, and no Horner pass over windows is
+// needed.
+struct WindowTable {
+    int c = 0;
+    int W = 0;
+    size_t n = 0;
+    DevBuf buf;
+};
+
+// State shared by a context and its lanes: the SRS and the tables derived
+// from it never change after loading, so lanes read them concurrently.
+struct Shared {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::mutex mu;        // SRS / tables / twiddles
+    std::mutex alloc_mu;  // budget accounting
+    size_t srs_n = 0;
+    DevBuf srs;  // affine Montgomery, srs_n points
+    std::deque<WindowTable> tables;  // deque: references stay valid as tables are added
+    DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg
+    ~Shared();
+};
+
+}  // namespace zk
+
+namespace zk {
+// One timed interval of a phase, recorded on the launching stream.
+struct PhaseMark {
+    int phase;
+    cudaEvent_t a, b;
+};
+}  // namespace zk
+
+struct zk_ctx {
+    std::shared_ptr<zk::Shared> sh;
+    bool is_lane = false;
+    bool timing = false;                  // record phase intervals (zk_timing_enable)
+    std::vector<zk::PhaseMark> marks;
+    std::map<std::string, zk::DevBuf> scratch;  // per context (per lane)
+    zk::DevBuf host_stage;                       // device staging for host buffers
+    int last_error = 0;
+};
+
+namespace zk {
+
+constexpr int kMaxLogN = 28;      // 2-adicity of r - 1
+constexpr int kMaxSrsLog = 26;    // window-table index must fit 31 bits at c >= 16
+constexpr int kScalarBits = 254;  // |recentred scalar| < r / 2 < 2^253, one spare bit for carries
+
+inline int ceil_div_int(int a, int b) { return (a + b - 1) / b; }
+inline int windows_for(int c) { return ceil_div_int(kScalarBits, c); }
+
+// Budget-checked device allocation owned by the shared state.
+int dev_alloc(Shared &sh, DevBuf &b, size_t bytes);
+void dev_free(Shared &sh, DevBuf &b);
+// Grow-only named scratch of a context.
+void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err);
+
+bool is_device_ptr(const void *p);
+
+#define ZK_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return ZK_ECUDA;             \
+    } while (0)
+
+// Every kernel launch site counts itself (zk_kernel_launches) and checks the
+// launch status.
+void count_launches(unsigned k);
+#define ZK_LAUNCHED()                                       \
+    do {                                                    \
+        count_launches(1);                                  \
+        ZK_CUDA_TRY(cudaGetLastError());                    \
+    } while (0)
+
+#define ZK_TRY(expr)                                        \
+    do {                                                    \
+        int _r = (expr);                                    \
+        if (_r != ZK_OK) return _r;                         \
+    } while (0)
+
+// Brackets one phase of a call with CUDA events on its stream when the
+// context's timing is on (kernel durations for the roofline report).
+struct PhaseScope {
+    zk_ctx *ctx;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(zk_ctx *c, int ph, cudaStream_t st) : ctx(c), phase(ph), s(st) {
+        if (ctx->timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    }
+    void end() {
+        if (!a) return;
+        cudaEvent_t b;
+        if (cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, s);
+            ctx->marks.push_back({phase, a, b});
+        } else {
+            cudaEventDestroy(a);
+        }
+        a = nullptr;
+    }
+    ~PhaseScope() { end(); }
+};
+
+// --- internal entry points between translation units ----------------------
+
+// SRS (srs.cu)
+int srs_load_impl(zk_ctx *ctx, const zk_g1 *pts, size_t n, cudaStream_t s);
+int srs_generate_impl(zk_ctx *ctx, const zk_fr *tau, size_t n, cudaStream_t s);
+int srs_export_impl(zk_ctx *ctx, zk_g1 *out, size_t first, size_t count, cudaStream_t s);
+int table_get(zk_ctx *ctx, int c, size_t n, const WindowTable **out, cudaStream_t s);
+
+// NTT (ntt.cu)
+int ntt_impl(zk_ctx *ctx, uint32_t *data, size_t n, bool inverse, cudaStream_t s);
+int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_t count,
+                   bool inverse, cudaStream_t s);
+int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s);
+
+// MSM (msm.cu).  Each job: scalars (device, canonical, 32 B each), length n,
+// output 64-byte canonical affine point (device).
+struct MsmJob {
+    const uint32_t *scalars;
+    uint32_t n;
+    void *out;
+};
+int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStream_t s);
+int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count);
+
+// Fold (fold.cu)
+int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
+              zk_g1 *E1_out, cudaStream_t s);
+int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
+                   cudaStream_t s);
+int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s);
+
+}  // namespace zk

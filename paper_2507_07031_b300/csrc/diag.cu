@@ -1,0 +1,113 @@
+// diag.cu -- measurement helpers for the roofline: the integer multiply-add
+// issue rate of the device (independent 32-bit mad.lo chains) and the
+// sustained Montgomery-multiplication rate of this library's F_q multiply.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "ctx.cuh"
+#include "field.cuh"
+
+namespace zk {
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kUnroll = 16;
+
+// Each iteration issues kChains * kUnroll independent 32-bit IMADs per thread.
+__global__ void k_probe_imad(uint32_t *sink, uint32_t iters, uint32_t seed) {
+    uint32_t a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) a[j] = seed + threadIdx.x * 7u + j * 131u;
+    const uint32_t b = seed ^ 0x9e3779b9u;
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+#pragma unroll
+            for (int j = 0; j < kChains; j++)
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[j]) : "r"(b), "r"(a[(j + 1) % kChains]));
+        }
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) x ^= a[j];
+    if (x == 0x12345678u) sink[0] = x;  // keep the chains alive
+}
+
+// Each thread runs `iters` rounds of 4 independent F_q Montgomery products.
+__global__ void k_probe_mont(uint32_t *sink, uint32_t iters, uint32_t seed) {
+    Fq x[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        x[j] = fe_mont_one<FqP>();
+        x[j].v[0] ^= seed + threadIdx.x + 17u * j;
+        x[j].v[7] &= 0x0fffffffu;
+    }
+    Fq y = x[1];
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) x[j] = fe_mul<FqP>(x[j], y);
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc ^= x[j].v[0];
+    if (acc == 0x12345678u) sink[0] = acc;
+}
+
+template <class K>
+double time_kernel(K kern, int blocks, int threads, uint32_t iters, uint32_t *sink) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0);
+        kern<<<blocks, threads>>>(sink, iters, 12345u + rep);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best * 1e-3;
+}
+
+}  // namespace
+
+}  // namespace zk
+
+using namespace zk;
+
+extern "C" int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s) {
+    if (!imad_per_s || !fq_mul_per_s) return ZK_EINVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return ZK_EINVAL;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    uint32_t *sink = nullptr;
+    if (cudaMalloc(&sink, 64) != cudaSuccess) {
+        cudaGetLastError();
+        cudaSetDevice(prev);
+        return ZK_ENOMEM;
+    }
+    const int blocks = sms * 8, threads = 256;
+    const uint32_t it1 = 2048;
+    double t1 = time_kernel(k_probe_imad, blocks, threads, it1, sink);
+    *imad_per_s = (double)blocks * threads * it1 * kChains * kUnroll / t1;
+    const int mblocks = sms * 4, mthreads = 256;
+    const uint32_t it2 = 256;
+    double t2 = time_kernel(k_probe_mont, mblocks, mthreads, it2, sink);
+    *fq_mul_per_s = (double)mblocks * mthreads * it2 * 4 / t2;
+    count_launches(8);
+    cudaError_t e = cudaGetLastError();
+    cudaFree(sink);
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? ZK_OK : ZK_ECUDA;
+}

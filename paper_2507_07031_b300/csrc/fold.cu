@@ -1,0 +1,320 @@
+// fold.cu -- generalised Mira accumulation (paper Sec. 4.2, prover steps 2-7)
+// for the degree-2 relation m1 o m2 - mu m3 = e over H, batched over all folds
+// of a tree level.
+//
+// For fold(L, R, gamma) (L plays acc, scaled by gamma; R plays acc'):
+//   K4  per element k (one pass over both accumulators, in place on R allowed):
+//         e1  = m1 m2' + m1' m2 - mu m3' - mu' m3            (step 2)
+//         m_i'' = gamma m_i + m_i'  (i = 1..4),  e'' = e' + gamma e1 + gamma^2 e
+//   INTT of every e1, then one batched MSM: E1 = Commit(e1)  (step 3)
+//   K5  per fold: C_i'' = gamma C_i + C_i', E'' = E' + gamma E1 + gamma^2 E,
+//       mu'' = gamma mu + mu'                                (step 5)
+// Field vectors are canonical; gamma and mu are moved into Montgomery form
+// once per thread so that mont(x, gamma R) = gamma x stays canonical.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ctx.cuh"
+#include "curve.cuh"
+
+namespace zk {
+
+namespace {
+
+struct FoldDesc {
+    const uint32_t *Lm[4];
+    const uint32_t *Le;
+    const uint32_t *Lx;  // zk_acc_inst
+    const uint32_t *Rm[4];
+    const uint32_t *Re;
+    const uint32_t *Rx;
+    uint32_t *Om[4];
+    uint32_t *Oe;
+    uint32_t *Ox;
+    const uint32_t *gamma;  // canonical F_r, device
+    uint32_t *e1;           // n elements (workspace)
+    uint32_t *E1;           // one canonical affine point (workspace or caller)
+};
+
+constexpr int kInstMu = 40 * 2;  // word offset of mu in zk_acc_inst (5 points x 16 words)
+
+// K4: cross term and witness RLC, grid (elements, folds).
+__global__ void __launch_bounds__(256) k_fold_witness(const FoldDesc *__restrict__ descs, uint32_t n) {
+    const FoldDesc &d = descs[blockIdx.y];
+    const Fr r2 = fe_r2<FrP>();
+    const Fr g = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
+    const Fr g2 = fe_mul<FrP>(g, g);
+    const Fr muL = fe_to_mont<FrP>(fe_load<FrP>(d.Lx + kInstMu));
+    const Fr muR = fe_to_mont<FrP>(fe_load<FrP>(d.Rx + kInstMu));
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t o = 8 * (size_t)k;
+        Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
+        Fr a3 = fe_load<FrP>(d.Lm[2] + o), a4 = fe_load<FrP>(d.Lm[3] + o);
+        Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
+        Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
+        Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
+        // (m1 m2' + m1' m2) R^-1, then * R^2 R^-1 -> canonical
+        Fr x = fe_add<FrP>(fe_mul<FrP>(a1, b2), fe_mul<FrP>(b1, a2));
+        x = fe_mul<FrP>(x, r2);
+        Fr y = fe_add<FrP>(fe_mul<FrP>(b3, muL), fe_mul<FrP>(a3, muR));
+        Fr e1 = fe_sub<FrP>(x, y);
+        fe_store<FrP>(d.e1 + o, e1);
+        fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
+        fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
+        fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
+        fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+        Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(eL, g2)));
+        fe_store<FrP>(d.Oe + o, eo);
+    }
+}
+
+__device__ __forceinline__ void load_bits(const uint32_t *p, uint32_t (&k)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) k[i] = p[i];
+}
+
+// K5: instance RLC; 5 threads per fold (C_1..C_4, and E'' with mu'').
+__global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t folds) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 5 * folds) return;
+    const FoldDesc &d = descs[t / 5];
+    const uint32_t task = t % 5;
+    uint32_t g[8];
+    load_bits(d.gamma, g);
+    if (task < 4) {
+        Xyzz cl = xyzz_load_canonical(d.Lx + 16 * task);
+        Xyzz cr = xyzz_load_canonical(d.Rx + 16 * task);
+        Xyzz r = xyzz_add(xyzz_mul(cl, g), cr);
+        xyzz_store_canonical(d.Ox + 16 * task, r);
+        return;
+    }
+    // E'' = E' + gamma E1 + gamma^2 E (joint double-and-add), mu'' = gamma mu + mu'.
+    Fr gm = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
+    Fr g2 = fe_from_mont<FrP>(fe_mul<FrP>(gm, gm));
+    Xyzz e1 = xyzz_load_canonical(d.E1);
+    Xyzz eL = xyzz_load_canonical(d.Lx + 64);
+    Xyzz eR = xyzz_load_canonical(d.Rx + 64);
+    Fr muL = fe_load<FrP>(d.Lx + kInstMu);
+    Fr muR = fe_load<FrP>(d.Rx + kInstMu);
+    Xyzz acc = xyzz_inf();
+    for (int i = 253; i >= 0; i--) {
+        acc = xyzz_dbl(acc);
+        if ((g[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, e1);
+        if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, eL);
+    }
+    acc = xyzz_add(acc, eR);
+    Fr mu = fe_add<FrP>(fe_mul<FrP>(muL, gm), muR);
+    xyzz_store_canonical(d.Ox + 64, acc);
+    fe_store<FrP>(d.Ox + kInstMu, mu);
+}
+
+// Leaf: m3 = m1 o m2, e = 0, mu = 1, E = infinity (C_i are written by the MSM).
+__global__ void k_leaf(const uint32_t *m1, const uint32_t *m2, uint32_t *m3, uint32_t *e,
+                       uint32_t *x, uint32_t n) {
+    const Fr r2 = fe_r2<FrP>();
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t o = 8 * (size_t)k;
+        Fr a = fe_to_mont<FrP>(fe_load<FrP>(m1 + o));
+        (void)r2;
+        fe_store<FrP>(m3 + o, fe_mul<FrP>(a, fe_load<FrP>(m2 + o)));
+        fe_store<FrP>(e + o, fe_zero<FrP>());
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 16) {
+        x[64 + threadIdx.x] = 0;                        // E = infinity
+        if (threadIdx.x < 8) x[kInstMu + threadIdx.x] = threadIdx.x == 0 ? 1u : 0u;  // mu = 1
+    }
+}
+
+// Copy one vector (workspace staging for INTT before a commitment).
+__global__ void k_copy(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+bool pow2(size_t n) { return n && !(n & (n - 1)); }
+
+bool acc_ok(const zk_acc *a, size_t n) {
+    if (!a || a->n != n || !a->e || !a->x) return false;
+    for (int i = 0; i < 4; i++)
+        if (!a->m[i]) return false;
+    return true;
+}
+
+unsigned elem_blocks(uint32_t n) { return std::min<unsigned>((n + 255) / 256, 1024u); }
+
+// Runs a batch of folds that share the length n.  `gam_dev` holds one
+// canonical gamma per fold (device).
+int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, cudaStream_t s) {
+    const size_t F = descs.size();
+    if (F == 0) return ZK_OK;
+    int err = ZK_OK;
+    uint32_t *e1 = (uint32_t *)scratch(ctx, "fold.e1", F * (size_t)n * 32, &err);
+    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.E1", F * 64, &err);
+    FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.descs", F * sizeof(FoldDesc), &err);
+    if (!e1 || !E1 || !dd) return err;
+    std::vector<uint32_t *> vecs(F);
+    std::vector<size_t> lens(F, n);
+    std::vector<MsmJob> jobs(F);
+    for (size_t f = 0; f < F; f++) {
+        descs[f].e1 = e1 + f * (size_t)n * 8;
+        if (!descs[f].E1) descs[f].E1 = E1 + 16 * f;
+        vecs[f] = descs[f].e1;
+        jobs[f].scalars = descs[f].e1;
+        jobs[f].n = n;
+        jobs[f].out = descs[f].E1;
+    }
+    ZK_CUDA_TRY(cudaMemcpyAsync(dd, descs.data(), F * sizeof(FoldDesc), cudaMemcpyHostToDevice, s));
+    dim3 g(elem_blocks(n), (unsigned)F);
+    {
+        PhaseScope ph(ctx, ZK_PHASE_FOLD_WITNESS, s);
+        k_fold_witness<<<g, 256, 0, s>>>(dd, n);
+        ZK_LAUNCHED();
+    }
+    ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), F, true, s));
+    ZK_TRY(msm_batch_impl(ctx, jobs.data(), F, msm_pick_window(ctx, n, F), s));
+    {
+        PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s);
+        k_fold_instance<<<(unsigned)((5 * F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
+        ZK_LAUNCHED();
+    }
+    return ZK_OK;
+}
+
+FoldDesc make_desc(const zk_acc *L, const zk_acc *R, const zk_acc *O, const uint32_t *gamma) {
+    FoldDesc d;
+    for (int i = 0; i < 4; i++) {
+        d.Lm[i] = (const uint32_t *)L->m[i];
+        d.Rm[i] = (const uint32_t *)R->m[i];
+        d.Om[i] = (uint32_t *)O->m[i];
+    }
+    d.Le = (const uint32_t *)L->e;
+    d.Re = (const uint32_t *)R->e;
+    d.Oe = (uint32_t *)O->e;
+    d.Lx = (const uint32_t *)L->x;
+    d.Rx = (const uint32_t *)R->x;
+    d.Ox = (uint32_t *)O->x;
+    d.gamma = gamma;
+    d.e1 = nullptr;
+    d.E1 = nullptr;
+    return d;
+}
+
+}  // namespace
+
+int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
+              zk_g1 *E1_out, cudaStream_t s) {
+    if (!L || !R || !out || !gamma) return ZK_EINVAL;
+    const size_t n = L->n;
+    if (!pow2(n) || n < 2 || n > ((size_t)1 << kMaxSrsLog)) return ZK_EINVAL;
+    if (!acc_ok(L, n) || !acc_ok(R, n) || !acc_ok(out, n)) return ZK_EINVAL;
+    if (out->x == L->x || out->e == L->e) return ZK_EINVAL;
+    if (n > ctx->sh->srs_n) return ZK_ESRS;
+    int err = ZK_OK;
+    const uint32_t *g = (const uint32_t *)gamma;
+    if (!is_device_ptr(gamma)) {
+        uint32_t *gd = (uint32_t *)scratch(ctx, "fold.gamma", 32, &err);
+        if (!gd) return err;
+        ZK_CUDA_TRY(cudaMemcpyAsync(gd, gamma, 32, cudaMemcpyHostToDevice, s));
+        g = gd;
+    }
+    std::vector<FoldDesc> d(1, make_desc(L, R, out, g));
+    ZK_TRY(fold_batch(ctx, d, (uint32_t)n, s));
+    if (E1_out) {
+        if (is_device_ptr(E1_out)) {
+            ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, 64, cudaMemcpyDeviceToDevice, s));
+        } else {
+            ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, 64, cudaMemcpyDeviceToHost, s));
+            ZK_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    }
+    return ZK_OK;
+}
+
+int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
+                   cudaStream_t s) {
+    if (!leaves || !gammas || !root || !pow2(count) || count < 2) return ZK_EINVAL;
+    const size_t n = leaves[0].n;
+    if (!pow2(n) || n < 2 || n > ((size_t)1 << kMaxSrsLog)) return ZK_EINVAL;
+    for (size_t i = 0; i < count; i++)
+        if (!acc_ok(&leaves[i], n)) return ZK_EINVAL;
+    if (!acc_ok(root, n)) return ZK_EINVAL;
+    if (n > ctx->sh->srs_n) return ZK_ESRS;
+    int err = ZK_OK;
+    const uint32_t *g = (const uint32_t *)gammas;
+    if (!is_device_ptr(gammas)) {
+        uint32_t *gd = (uint32_t *)scratch(ctx, "fold.gammas", (count - 1) * 32, &err);
+        if (!gd) return err;
+        ZK_CUDA_TRY(cudaMemcpyAsync(gd, gammas, (count - 1) * 32, cudaMemcpyHostToDevice, s));
+        g = gd;
+    }
+    // Level l accumulator j lives in leaf slot j 2^l + 2^l - 1 (the fold
+    // output overwrites its R operand).
+    size_t width = count, goff = 0;
+    for (size_t span = 2; span <= count; span <<= 1) {
+        std::vector<FoldDesc> d;
+        d.reserve(width / 2);
+        for (size_t j = 0; j < width / 2; j++) {
+            const zk_acc *Lp = &leaves[j * span + span / 2 - 1];
+            zk_acc *Rp = &leaves[j * span + span - 1];
+            d.push_back(make_desc(Lp, Rp, Rp, g + 8 * (goff + j)));
+        }
+        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, s));
+        goff += width / 2;
+        width /= 2;
+    }
+    const zk_acc &top = leaves[count - 1];
+    for (int i = 0; i < 4; i++)
+        ZK_CUDA_TRY(cudaMemcpyAsync(root->m[i], top.m[i], n * 32, cudaMemcpyDeviceToDevice, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(root->e, top.e, n * 32, cudaMemcpyDeviceToDevice, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(root->x, top.x, sizeof(zk_acc_inst), cudaMemcpyDeviceToDevice, s));
+    return ZK_OK;
+}
+
+int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s) {
+    if (!accs || count == 0) return ZK_EINVAL;
+    const size_t n = accs[0].n;
+    if (!pow2(n) || n < 2 || n > ((size_t)1 << kMaxSrsLog)) return ZK_EINVAL;
+    for (size_t i = 0; i < count; i++)
+        if (!acc_ok(&accs[i], n)) return ZK_EINVAL;
+    if (n > ctx->sh->srs_n) return ZK_ESRS;
+    // Commit in groups so the INTT and MSM workspace stays near 2^24 elements.
+    const size_t group = std::max<size_t>(1, ((size_t)1 << 24) / (4 * n));
+    int err = ZK_OK;
+    for (size_t a0 = 0; a0 < count; a0 += group) {
+        const size_t a1 = std::min(count, a0 + group);
+        const size_t G = a1 - a0;
+        uint32_t *ws = (uint32_t *)scratch(ctx, "leaf.ws", 4 * G * n * 32, &err);
+        if (!ws) return err;
+        std::vector<uint32_t *> vecs;
+        std::vector<size_t> lens;
+        std::vector<MsmJob> jobs;
+        for (size_t a = a0; a < a1; a++) {
+            const zk_acc &A = accs[a];
+            k_leaf<<<elem_blocks((uint32_t)n), 256, 0, s>>>((const uint32_t *)A.m[0],
+                                                            (const uint32_t *)A.m[1],
+                                                            (uint32_t *)A.m[2], (uint32_t *)A.e,
+                                                            (uint32_t *)A.x, (uint32_t)n);
+            ZK_LAUNCHED();
+            for (int i = 0; i < 4; i++) {
+                uint32_t *dst = ws + ((a - a0) * 4 + i) * n * 8;
+                k_copy<<<elem_blocks((uint32_t)n), 256, 0, s>>>((const uint4 *)A.m[i], (uint4 *)dst,
+                                                                n * 2);
+                ZK_LAUNCHED();
+                vecs.push_back(dst);
+                lens.push_back(n);
+                MsmJob j;
+                j.scalars = dst;
+                j.n = (uint32_t)n;
+                j.out = (char *)A.x + 64 * i;
+                jobs.push_back(j);
+            }
+        }
+        ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), vecs.size(), true, s));
+        ZK_TRY(msm_batch_impl(ctx, jobs.data(), jobs.size(), msm_pick_window(ctx, n, jobs.size()), s));
+    }
+    return ZK_OK;
+}
+
+}  // namespace zk

@@ -1,0 +1,481 @@
+// msm.cu -- KZG commitment as a multi-scalar multiplication over the SRS
+// (paper Sec. 2.1: com = [f(tau)]_1 = sum_i c_i [tau^i]_1), batched.
+//
+// Pippenger's bucket method with signed windows of c bits, in five phases:
+//   1. recode: every scalar is recentred (s > (r-1)/2 becomes r - s with the
+//      point negated) and split into W = ceil(254/c) signed digits in
+//      [-2^(c-1), 2^(c-1)]; digit d of window w of scalar i contributes
+//      sign(d) * 2^(c w) SRS[i], a point read from the precomputed window
+//      table, to bucket |d| - 1 of its MSM.  A warp-aggregated counting pass
+//      builds the bucket histogram;
+//   2. sort: an exclusive scan gives bucket offsets and a warp-aggregated
+//      scatter writes the (table index, sign) words bucket by bucket;
+//   3. accumulate: each bucket's list is cut into pieces of kPiece entries,
+//      one thread per piece adds them in XYZZ coordinates (mixed additions);
+//      piece sums are combined again in rounds of kPiece until every bucket
+//      is a single point, so skewed buckets (quantised ML values put 2^20
+//      points into 128 buckets) keep the whole GPU busy;
+//   4. reduce: sum_b (b + 1) S_b per MSM by block-level suffix scans
+//      (256 threads x 4 buckets per block), then one warp per MSM combines the
+//      block results;
+//   5. normalise the result to canonical affine coordinates.
+// Every MSM of a batch (uneven lengths) goes through the same launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ctx.cuh"
+#include "curve.cuh"
+#include "scan.cuh"
+
+namespace zk {
+
+namespace {
+
+constexpr uint32_t kInvalid = 0xffffffffu;
+constexpr int kPiece = 32;        // entries (or partial sums) per thread per round
+constexpr int kRedThreads = 256;  // bucket-reduction block
+constexpr int kRedPer = 4;        // buckets per thread
+constexpr int kRedSpan = kRedThreads * kRedPer;
+
+struct DevJobs {
+    const uint32_t *const *scalars;  // per job
+    const uint32_t *base;            // prefix sums of n, count + 1 entries
+    void *const *out;                // per job
+    uint32_t count;
+};
+
+__device__ __forceinline__ uint32_t find_job(const uint32_t *base, uint32_t count, uint32_t gid) {
+    uint32_t lo = 0, hi = count;  // base[lo] <= gid < base[hi]
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (base[mid] <= gid) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Largest b with off[b] <= x, for off nondecreasing with off[0] = 0.
+__device__ __forceinline__ uint32_t upper_index(const uint32_t *off, uint32_t nb, uint32_t x) {
+    uint32_t lo = 0, hi = nb;  // off[lo] <= x < off[hi] (off[nb] > x assumed)
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int C>
+__device__ __forceinline__ uint32_t window_bits(const uint32_t (&s)[8], int w) {
+    const int pos = w * C;
+    const int word = pos >> 5;
+    const int off = pos & 31;
+    uint32_t lo = word < 8 ? (s[word] >> off) : 0u;
+    uint32_t hi = (off + C > 32 && word + 1 < 8) ? (s[word + 1] << (32 - off)) : 0u;
+    return (lo | hi) & ((1u << C) - 1u);
+}
+
+// Loads scalar i of its job, recentres it, and returns the negation flag.
+__device__ __forceinline__ bool load_recentred(const uint32_t *p, uint32_t (&s)[8]) {
+    Fr x = fe_load<FrP>(p);
+    bool neg = fe_gt_half<FrP>(x);
+    if (neg) x = fe_neg<FrP>(x);
+#pragma unroll
+    for (int j = 0; j < 8; j++) s[j] = x.v[j];
+    return neg;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+// Phase 1: bucket histogram.
+template <int C>
+__global__ void k_count(DevJobs jobs, uint32_t total, uint32_t *__restrict__ counts) {
+    constexpr int W = (kScalarBits + C - 1) / C;
+    constexpr uint32_t B = 1u << (C - 1);
+    uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    bool live = gid < total;
+    uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t job = 0;
+    bool neg = false;
+    if (live) {
+        job = find_job(jobs.base, jobs.count, gid);
+        neg = load_recentred(jobs.scalars[job] + 8 * (gid - jobs.base[job]), s);
+    }
+    (void)neg;
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        uint32_t d = window_bits<C>(s, w) + carry;
+        carry = d > (1u << (C - 1)) ? 1u : 0u;
+        int sd = carry ? (int)d - (1 << C) : (int)d;
+        uint32_t key = (live && sd != 0) ? job * B + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
+        uint32_t group = __match_any_sync(0xffffffffu, key);
+        if (key != kInvalid && lane_id() == (uint32_t)(__ffs(group) - 1))
+            atomicAdd(&counts[key], (uint32_t)__popc(group));
+    }
+}
+
+// Phase 2: scatter (table index << 1 | sign) into bucket order.
+template <int C>
+__global__ void k_scatter(DevJobs jobs, uint32_t total, uint32_t table_n,
+                          uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted) {
+    constexpr int W = (kScalarBits + C - 1) / C;
+    constexpr uint32_t B = 1u << (C - 1);
+    uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    bool live = gid < total;
+    uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t job = 0, i = 0;
+    bool neg = false;
+    if (live) {
+        job = find_job(jobs.base, jobs.count, gid);
+        i = gid - jobs.base[job];
+        neg = load_recentred(jobs.scalars[job] + 8 * i, s);
+    }
+    const uint32_t lt_mask = (1u << lane_id()) - 1u;
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        uint32_t d = window_bits<C>(s, w) + carry;
+        carry = d > (1u << (C - 1)) ? 1u : 0u;
+        int sd = carry ? (int)d - (1 << C) : (int)d;
+        uint32_t key = (live && sd != 0) ? job * B + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
+        uint32_t group = __match_any_sync(0xffffffffu, key);
+        uint32_t leader = (uint32_t)(__ffs(group) - 1);
+        uint32_t base = 0;
+        if (key != kInvalid && lane_id() == leader)
+            base = atomicAdd(&cursor[key], (uint32_t)__popc(group));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (key != kInvalid) {
+            uint32_t sign = ((sd < 0) ? 1u : 0u) ^ (neg ? 1u : 0u);
+            sorted[base + __popc(group & lt_mask)] = (((uint32_t)w * table_n + i) << 1) | sign;
+        }
+    }
+}
+
+// Phase 3a: first round of piece sums over the sorted table indices.
+// off0: entry offsets per bucket (nb + 1); off1: piece offsets (nb + 1).
+__global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32_t *__restrict__ off0,
+                               const uint32_t *__restrict__ off1, uint32_t nb,
+                               const Affine *__restrict__ table, Xyzz *__restrict__ pieces) {
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= off1[nb]) return;
+    uint32_t b = upper_index(off1, nb, p);
+    uint32_t k = p - off1[b];
+    uint32_t lo = off0[b] + k * kPiece;
+    uint32_t hi = min(lo + kPiece, off0[b + 1]);
+    Xyzz acc = xyzz_inf();
+    for (uint32_t j = lo; j < hi; j++) {
+        uint32_t v = sorted[j];
+        Affine a = affine_ldg(table + (v >> 1));
+        if (v & 1) a = affine_neg(a);
+        acc = xyzz_add_affine(acc, a);
+    }
+    pieces[p] = acc;
+}
+
+// Phase 3b: further rounds over partial sums.
+__global__ void k_pieces_next(const Xyzz *__restrict__ in, const uint32_t *__restrict__ off_in,
+                              const uint32_t *__restrict__ off_out, uint32_t nb,
+                              Xyzz *__restrict__ out) {
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= off_out[nb]) return;
+    uint32_t b = upper_index(off_out, nb, p);
+    uint32_t k = p - off_out[b];
+    uint32_t lo = off_in[b] + k * kPiece;
+    uint32_t hi = min(lo + kPiece, off_in[b + 1]);
+    Xyzz acc = xyzz_inf();
+    for (uint32_t j = lo; j < hi; j++) acc = xyzz_add(acc, in[j]);
+    out[p] = acc;
+}
+
+// Phase 3c: one thread per bucket sums its (at most kPiece) remaining items;
+// `first` selects table entries (no piece round ran) or partial sums.
+__global__ void k_buckets_final(const uint32_t *__restrict__ sorted, const Affine *__restrict__ table,
+                                const Xyzz *__restrict__ in, const uint32_t *__restrict__ off,
+                                uint32_t nb, int first, Xyzz *__restrict__ buckets) {
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    Xyzz acc = xyzz_inf();
+    for (uint32_t j = off[b]; j < off[b + 1]; j++) {
+        if (first) {
+            uint32_t v = sorted[j];
+            Affine a = affine_ldg(table + (v >> 1));
+            if (v & 1) a = affine_neg(a);
+            acc = xyzz_add_affine(acc, a);
+        } else {
+            acc = xyzz_add(acc, in[j]);
+        }
+    }
+    buckets[b] = acc;
+}
+
+// Warp shuffle of a whole point.
+__device__ __forceinline__ Xyzz shfl_down_pt(const Xyzz &p, int d) {
+    Xyzz r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        r.X.v[i] = __shfl_down_sync(0xffffffffu, p.X.v[i], d);
+        r.Y.v[i] = __shfl_down_sync(0xffffffffu, p.Y.v[i], d);
+        r.ZZ.v[i] = __shfl_down_sync(0xffffffffu, p.ZZ.v[i], d);
+        r.ZZZ.v[i] = __shfl_down_sync(0xffffffffu, p.ZZZ.v[i], d);
+    }
+    return r;
+}
+
+// Inclusive suffix sum over the lanes of a warp: lane l gets sum_{l' >= l} x_l'.
+__device__ __forceinline__ Xyzz warp_suffix(Xyzz x) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        Xyzz y = shfl_down_pt(x, d);
+        if (lane_id() + d < 32) x = xyzz_add(x, y);
+    }
+    return x;
+}
+
+// Sum over the lanes of a warp (valid in lane 0).
+__device__ __forceinline__ Xyzz warp_sum(Xyzz x) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        Xyzz y = shfl_down_pt(x, d);
+        x = xyzz_add(x, y);
+    }
+    return x;
+}
+
+// Phase 4a: for block k of 1024 buckets of MSM j, val = sum_b (b - b0 + 1) S_b
+// and sum = sum_b S_b (b0 = first bucket of the block).
+__global__ void __launch_bounds__(kRedThreads, 1)
+    k_reduce_blocks(const Xyzz *__restrict__ buckets, uint32_t B, Xyzz *__restrict__ blk_val,
+                    Xyzz *__restrict__ blk_sum) {
+    __shared__ Xyzz sh[kRedThreads / 32];
+    const uint32_t nblk = B / kRedSpan;
+    const uint32_t job = blockIdx.y;
+    const uint32_t t = threadIdx.x;
+    const Xyzz *S = buckets + (size_t)job * B + (size_t)blockIdx.x * kRedSpan + kRedPer * t;
+    // thread-local: l = sum_i (i + 1) S_i, r = sum_i S_i
+    Xyzz r = S[kRedPer - 1];
+    Xyzz l = r;
+#pragma unroll
+    for (int i = kRedPer - 2; i >= 0; i--) {
+        r = xyzz_add(r, S[i]);
+        l = xyzz_add(l, r);
+    }
+    // block suffix sums of r
+    Xyzz x = warp_suffix(r);
+    const uint32_t warp = t >> 5;
+    if (lane_id() == 0) sh[warp] = x;
+    __syncthreads();
+    Xyzz later = xyzz_inf();
+    for (uint32_t w = warp + 1; w < kRedThreads / 32; w++) later = xyzz_add(later, sh[w]);
+    x = xyzz_add(x, later);  // x = sum_{t' >= t} r_t'
+    // contrib_t = l_t + 4 t r_t summed over t == sum_t l_t + 4 sum_{t >= 1} suffix_t
+    Xyzz c = l;
+    if (t >= 1) c = xyzz_add(c, xyzz_dbl(xyzz_dbl(x)));
+    Xyzz tot_sum = x;  // suffix at t = 0 is the block sum
+    __syncthreads();
+    c = warp_sum(c);
+    if (lane_id() == 0) sh[warp] = c;
+    __syncthreads();
+    if (t == 0) {
+        Xyzz v = sh[0];
+        for (uint32_t w = 1; w < kRedThreads / 32; w++) v = xyzz_add(v, sh[w]);
+        blk_val[(size_t)job * nblk + blockIdx.x] = v;
+        blk_sum[(size_t)job * nblk + blockIdx.x] = tot_sum;
+    }
+}
+
+// Phase 4b + 5: one warp per MSM: total = sum_k val_k + 1024 sum_k k sum_k.
+__global__ void k_reduce_final(const Xyzz *__restrict__ blk_val, const Xyzz *__restrict__ blk_sum,
+                               uint32_t nblk, DevJobs jobs) {
+    const uint32_t job = blockIdx.x;
+    const uint32_t l = lane_id();
+    const uint32_t q = nblk >= 32 ? nblk / 32 : 1;  // blocks per lane (power of two)
+    const Xyzz *V = blk_val + (size_t)job * nblk;
+    const Xyzz *Sm = blk_sum + (size_t)job * nblk;
+    Xyzz lv = xyzz_inf(), lw = xyzz_inf(), ls = xyzz_inf();
+    uint32_t lo = l * q, hi = min(lo + q, nblk);
+    // lw = sum_k (k - lo) sum_k over the lane's blocks, by a running sum from the top
+    for (uint32_t k = hi; k-- > lo;) {
+        lv = xyzz_add(lv, V[k]);
+        ls = xyzz_add(ls, Sm[k]);
+        if (k > lo) lw = xyzz_add(lw, ls);
+    }
+    // sum_k k sum_k = sum_l lw_l + q sum_l l ls_l, and sum_l l ls_l = sum_{l >= 1} suffix_l
+    Xyzz suf = warp_suffix(ls);
+    Xyzz term = lw;
+    if (l >= 1) {
+        Xyzz qs = suf;
+        for (uint32_t m = q; m > 1; m >>= 1) qs = xyzz_dbl(qs);
+        term = xyzz_add(term, qs);
+    }
+    Xyzz wsum = warp_sum(term);
+    Xyzz vsum = warp_sum(lv);
+    if (l == 0) {
+        Xyzz tot = wsum;
+        for (int k = 0; k < 10; k++) tot = xyzz_dbl(tot);  // x 1024
+        tot = xyzz_add(tot, vsum);
+        xyzz_store_canonical(jobs.out[job], tot);
+    }
+}
+
+// Empty MSM (n = 0) or all-zero output: write infinity.
+template <int C>
+int launch_recode(const DevJobs &dj, uint32_t total, uint32_t table_n, uint32_t *counts,
+                  uint32_t *cursor, uint32_t *sorted, bool scatter, cudaStream_t s) {
+    unsigned blocks = (total + 255) / 256;
+    if (!scatter) k_count<C><<<blocks, 256, 0, s>>>(dj, total, counts);
+    else k_scatter<C><<<blocks, 256, 0, s>>>(dj, total, table_n, cursor, sorted);
+    ZK_LAUNCHED();
+    return ZK_OK;
+}
+
+int recode(int c, const DevJobs &dj, uint32_t total, uint32_t table_n, uint32_t *counts,
+           uint32_t *cursor, uint32_t *sorted, bool scatter, cudaStream_t s) {
+    switch (c) {
+        case 11: return launch_recode<11>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 12: return launch_recode<12>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 13: return launch_recode<13>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 14: return launch_recode<14>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 15: return launch_recode<15>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 16: return launch_recode<16>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 17: return launch_recode<17>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        case 18: return launch_recode<18>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        default: return ZK_EINVAL;
+    }
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count) {
+    (void)ctx;
+    (void)max_n;
+    (void)count;
+    return 16;
+}
+
+int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStream_t s) {
+    if (count == 0) return ZK_OK;
+    if (c < 11 || c > 18) return ZK_EINVAL;
+    Shared &sh = *ctx->sh;
+    size_t total64 = 0, max_n = 0;
+    for (size_t k = 0; k < count; k++) {
+        total64 += jobs[k].n;
+        max_n = std::max(max_n, (size_t)jobs[k].n);
+        if (!jobs[k].out) return ZK_EINVAL;
+        if (jobs[k].n && !jobs[k].scalars) return ZK_EINVAL;
+    }
+    if (max_n > sh.srs_n) return ZK_ESRS;
+    const int W = windows_for(c);
+    const uint32_t B = 1u << (c - 1);
+    const size_t nb64 = count * (size_t)B;
+    const size_t entries_max = total64 * (size_t)W;
+    if (total64 >= (1ull << 32) || nb64 >= (1ull << 31) || entries_max >= (1ull << 32))
+        return ZK_EINVAL;
+    const WindowTable *tab;
+    ZK_TRY(table_get(ctx, c, max_n ? max_n : 1, &tab, s));
+    const uint32_t total = (uint32_t)total64;
+    const uint32_t nb = (uint32_t)nb64;
+
+    // Piece rounds: after R rounds a bucket with at most max_n W entries holds
+    // ceil(max_n W / kPiece^R) items; stop once that is <= kPiece.
+    int rounds = 0;
+    {
+        size_t m = std::max<size_t>(max_n * (size_t)W, 1);
+        while (m > (size_t)kPiece) {
+            m = (m + kPiece - 1) / kPiece;
+            rounds++;
+        }
+    }
+    const size_t piece_cap = entries_max / kPiece + nb + 1;
+
+    // Workspace.
+    int err = ZK_OK;
+    const size_t job_bytes = align_up(count * sizeof(void *), 256);
+    char *jt = (char *)scratch(ctx, "msm.jobs", 3 * job_bytes + 256, &err);
+    uint32_t *counts = (uint32_t *)scratch(ctx, "msm.counts", (nb + 1) * 4, &err);
+    uint32_t *off0 = (uint32_t *)scratch(ctx, "msm.off0", (nb + 1) * 4, &err);
+    uint32_t *offa = (uint32_t *)scratch(ctx, "msm.offa", (nb + 1) * 4, &err);
+    uint32_t *offb = (uint32_t *)scratch(ctx, "msm.offb", (nb + 1) * 4, &err);
+    uint32_t *cursor = (uint32_t *)scratch(ctx, "msm.cursor", (nb + 1) * 4, &err);
+    uint32_t *sorted = (uint32_t *)scratch(ctx, "msm.sorted", std::max<size_t>(entries_max, 1) * 4, &err);
+    Xyzz *pa = (Xyzz *)scratch(ctx, "msm.piecea", piece_cap * sizeof(Xyzz), &err);
+    Xyzz *pb = (Xyzz *)scratch(ctx, "msm.pieceb", piece_cap * sizeof(Xyzz), &err);
+    Xyzz *buckets = (Xyzz *)scratch(ctx, "msm.buckets", nb64 * sizeof(Xyzz), &err);
+    const uint32_t nblk = B / kRedSpan;
+    Xyzz *bval = (Xyzz *)scratch(ctx, "msm.bval", count * nblk * sizeof(Xyzz), &err);
+    Xyzz *bsum = (Xyzz *)scratch(ctx, "msm.bsum", count * nblk * sizeof(Xyzz), &err);
+    void *scan_tmp = scratch(ctx, "msm.scantmp", scan_temp_bytes(nb), &err);
+    if (!jt || !counts || !off0 || !offa || !offb || !cursor || !sorted || !pa || !pb || !buckets ||
+        !bval || !bsum || !scan_tmp)
+        return err;
+
+    // Job table (device copy of scalars pointers, length prefix, outputs).
+    std::vector<uint64_t> hjt(3 * job_bytes / 8 + 32, 0);
+    const uint32_t **h_sc = (const uint32_t **)hjt.data();
+    uint32_t *h_base = (uint32_t *)((char *)hjt.data() + job_bytes);
+    void **h_out = (void **)((char *)hjt.data() + 2 * job_bytes);
+    uint32_t acc = 0;
+    for (size_t k = 0; k < count; k++) {
+        h_sc[k] = jobs[k].scalars;
+        h_base[k] = acc;
+        acc += jobs[k].n;
+        h_out[k] = jobs[k].out;
+    }
+    h_base[count] = acc;
+    ZK_CUDA_TRY(cudaMemcpyAsync(jt, hjt.data(), 3 * job_bytes, cudaMemcpyHostToDevice, s));
+    DevJobs dj;
+    dj.scalars = (const uint32_t *const *)jt;
+    dj.base = (const uint32_t *)(jt + job_bytes);
+    dj.out = (void *const *)(jt + 2 * job_bytes);
+    dj.count = (uint32_t)count;
+
+    // 1-2: histogram, offsets, scatter.
+    PhaseScope ph_sort(ctx, ZK_PHASE_MSM_SORT, s);
+    ZK_CUDA_TRY(cudaMemsetAsync(counts, 0, (nb + 1) * 4, s));
+    if (total) ZK_TRY(recode(c, dj, total, (uint32_t)tab->n, counts, nullptr, nullptr, false, s));
+    ZK_TRY(scan_exclusive(counts, off0, nb, 0, scan_tmp, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (total)
+        ZK_TRY(recode(c, dj, total, (uint32_t)tab->n, nullptr, cursor, sorted, true, s));
+
+    ph_sort.end();
+
+    // 3: piece rounds, then one point per bucket.
+    PhaseScope ph_accum(ctx, ZK_PHASE_MSM_ACCUM, s);
+    const uint32_t *off_prev = off0;
+    Xyzz *cur = pa, *nxt = pb;
+    size_t cap = piece_cap;
+    for (int rd = 0; rd < rounds; rd++) {
+        uint32_t *off_new = (rd % 2 == 0) ? offa : offb;
+        ZK_TRY(scan_exclusive(off_prev, off_new, nb, kPiece, scan_tmp, s));
+        unsigned blocks = (unsigned)((cap + 127) / 128);
+        if (rd == 0)
+            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb,
+                                                  (const Affine *)tab->buf.p, cur);
+        else
+            k_pieces_next<<<blocks, 128, 0, s>>>(nxt, off_prev, off_new, nb, cur);
+        ZK_LAUNCHED();
+        std::swap(cur, nxt);  // nxt now holds this round's output
+        off_prev = off_new;
+        cap = cap / kPiece + nb + 1;
+    }
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, (const Affine *)tab->buf.p, nxt,
+                                                      off_prev, nb, rounds == 0 ? 1 : 0, buckets);
+    ZK_LAUNCHED();
+
+    ph_accum.end();
+
+    // 4-5: bucket reduction and output.
+    PhaseScope ph_reduce(ctx, ZK_PHASE_MSM_REDUCE, s);
+    dim3 g(nblk, (unsigned)count);
+    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, B, bval, bsum);
+    ZK_LAUNCHED();
+    k_reduce_final<<<(unsigned)count, 32, 0, s>>>(bval, bsum, nblk, dj);
+    ZK_LAUNCHED();
+    return ZK_OK;
+}
+
+}  // namespace zk

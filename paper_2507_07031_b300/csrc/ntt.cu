@@ -1,0 +1,319 @@
+// ntt.cu -- natural-order NTT / inverse NTT over F_r (the interpolation of a
+// witness vector of evaluations over H = <omega_n> into coefficients, paper
+// Sec. 3 and Sec. 4.4), n = 2^L <= 2^28.
+//
+// Stockham autosort formulation in P = ceil(L / 10) passes of radix R_p = 2^s_p
+// (s_p <= 10): pass p computes, for each of the n / R sub-transforms j,
+//   v_r = x[j + r n/R] * omega_{Ns R}^{r (j mod Ns)},  r < R,
+//   V   = R-point DFT of v,
+//   y[(j / Ns) Ns R + (j mod Ns) + r Ns] = V_r,
+// with Ns = prod_{p' < p} R_p'.  A CTA stages J = min(4, n/R) consecutive
+// sub-transforms (J R elements, up to 128 KiB) in shared memory in a
+// limb-planar, sub-transform-interleaved layout (word l of element r of
+// sub-transform jj at l J R + r J + jj, so consecutive threads touch
+// consecutive banks), runs the R-point DFT as log2 R
+// radix-2 decimation-in-frequency stages, and writes the bit-reversed
+// positions back in natural order.  Global loads and stores move runs of J
+// consecutive 32-byte elements (J R contiguous ones in the first pass).
+//
+// Data stay canonical: twiddles are stored in Montgomery form, so
+// mont(x, w R) = x w is already canonical and no conversion pass is needed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "ctx.cuh"
+#include "field.cuh"
+
+namespace zk {
+
+namespace {
+
+constexpr int kMaxRadixLog = 10;
+constexpr int kMaxJ = 4;
+
+// w = 5^((r - 1) / 2^lg), the primitive 2^lg-th root of unity (5 generates
+// the 2-Sylow subgroup of F_r^*: it is a quadratic non-residue).
+__global__ void k_root(uint32_t lg, Fr *out) {
+    if (threadIdx.x || blockIdx.x) return;
+    uint32_t e[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) e[i] = FrP::p(i);
+    e[0] -= 1;  // r - 1 (r is odd)
+    for (uint32_t k = 0; k < lg; k++) {
+#pragma unroll
+        for (int i = 0; i < 7; i++) e[i] = (e[i] >> 1) | (e[i + 1] << 31);
+        e[7] >>= 1;
+    }
+    Fr five = fe_zero<FrP>();
+    five.v[0] = 5;
+    *out = fe_pow<FrP>(fe_to_mont<FrP>(five), e);
+}
+
+// tw[k] = w^k for k < n (chunks of 64 per thread); tw[n] = n^{-1}.
+__global__ void k_twiddles(const Fr *__restrict__ root, uint32_t lg, Fr *__restrict__ tw) {
+    const uint64_t n = 1ull << lg;
+    uint64_t lo = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 64;
+    if (lo == 0 && threadIdx.x == 0 && blockIdx.x == 0) {
+        Fr nn = fe_zero<FrP>();
+        nn.v[0] = (uint32_t)n;
+        nn.v[1] = (uint32_t)(n >> 32);
+        tw[n] = fe_to_mont<FrP>(fe_inv_canonical<FrP>(nn));
+    }
+    if (lo >= n) return;
+    uint64_t hi = lo + 64 < n ? lo + 64 : n;
+    uint32_t e[8] = {(uint32_t)lo, (uint32_t)(lo >> 32), 0, 0, 0, 0, 0, 0};
+    Fr w = *root;
+    Fr acc = fe_pow<FrP>(w, e);
+    for (uint64_t k = lo; k < hi; k++) {
+        tw[k] = acc;
+        acc = fe_mul<FrP>(acc, w);
+    }
+}
+
+struct PassArgs {
+    const uint32_t *const *in_tab;  // per vector (blockIdx.y)
+    uint32_t *const *out_tab;
+    uint32_t logn, logR, logNs, J;
+    const Fr *tw_n;  // size-n table (+ n^{-1} at index n)
+    const Fr *tw_R;  // size-R table
+    int inverse;
+    int scale;  // multiply outputs by n^{-1}
+};
+
+__global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
+    extern __shared__ uint32_t sm[];
+    const uint32_t R = 1u << a.logR;
+    const uint32_t J = a.J;
+    const uint32_t JR = J * R;
+    const uint64_t n = 1ull << a.logn;
+    const uint32_t Ns = 1u << a.logNs;
+    const uint64_t stride = n >> a.logR;  // n / R
+    const uint32_t *in = a.in_tab[blockIdx.y];
+    uint32_t *out = a.out_tab[blockIdx.y];
+    const uint64_t j0 = (uint64_t)blockIdx.x * J;
+    const uint32_t tshift = a.logn - a.logNs - a.logR;
+
+    // Load, apply the inter-pass twiddle omega_{Ns R}^{r (j mod Ns)}.
+    for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
+        uint32_t r = e / J, jj = e % J;
+        uint64_t j = j0 + jj;
+        Fr x = fe_load<FrP>(in + 8 * (j + (uint64_t)r * stride));
+        uint64_t m = j & (Ns - 1);
+        uint64_t ex = ((uint64_t)r * m) << tshift;
+        if (ex) {
+            uint64_t idx = a.inverse ? n - ex : ex;
+            x = fe_mul<FrP>(x, fe_ldg<FrP>(a.tw_n + idx));
+        }
+#pragma unroll
+        for (int l = 0; l < 8; l++) sm[l * JR + r * J + jj] = x.v[l];
+    }
+    __syncthreads();
+
+    // R-point DIF radix-2: (a, b) -> (a + b, (a - b) omega_{2h}^pos).
+    const uint32_t half = R >> 1;
+    (void)half;
+    for (uint32_t lh = a.logR; lh >= 1; lh--) {
+        const uint32_t h = 1u << (lh - 1);
+        for (uint32_t bf = threadIdx.x; bf < J * half; bf += blockDim.x) {
+            uint32_t jj = bf % J, k = bf / J;
+            uint32_t pos = k & (h - 1);
+            uint32_t i0 = ((((k >> (lh - 1)) << lh) + pos) * J) + jj;
+            uint32_t i1 = i0 + h * J;
+            Fr x, y;
+#pragma unroll
+            for (int l = 0; l < 8; l++) {
+                x.v[l] = sm[l * JR + i0];
+                y.v[l] = sm[l * JR + i1];
+            }
+            Fr s = fe_add<FrP>(x, y);
+            Fr d = fe_sub<FrP>(x, y);
+            if (pos) {
+                uint32_t idx = pos << (a.logR - lh);
+                if (a.inverse) idx = R - idx;
+                d = fe_mul<FrP>(d, fe_ldg<FrP>(a.tw_R + idx));
+            }
+#pragma unroll
+            for (int l = 0; l < 8; l++) {
+                sm[l * JR + i0] = s.v[l];
+                sm[l * JR + i1] = d.v[l];
+            }
+        }
+        __syncthreads();
+    }
+
+    // Store V_r (at bit-reversed position r) to its natural-order place.
+    Fr sc;
+    if (a.scale) sc = fe_ldg<FrP>(a.tw_n + n);
+    for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
+        uint32_t r, jj;
+        if (Ns >= J) {
+            r = e / J;
+            jj = e % J;
+        } else {
+            uint32_t q = e >> (a.logNs + a.logR);
+            uint32_t rem = e & ((Ns << a.logR) - 1);
+            r = rem >> a.logNs;
+            jj = q * Ns + (rem & (Ns - 1));
+        }
+        uint64_t j = j0 + jj;
+        uint32_t src = a.logR ? (__brev(r) >> (32 - a.logR)) : 0;
+        Fr x;
+#pragma unroll
+        for (int l = 0; l < 8; l++) x.v[l] = sm[l * JR + src * J + jj];
+        if (a.scale) x = fe_mul<FrP>(x, sc);
+        uint64_t dst = (j / Ns) * ((uint64_t)Ns << a.logR) + (j & (Ns - 1)) + (uint64_t)r * Ns;
+        fe_store<FrP>(out + 8 * dst, x);
+    }
+}
+
+// Radix split of L into passes of at most kMaxRadixLog.
+std::vector<int> plan_passes(int L) {
+    std::vector<int> s;
+    if (L == 0) return s;
+    int P = (L + kMaxRadixLog - 1) / kMaxRadixLog;
+    for (int p = 0; p < P; p++) s.push_back(L / P + (p < L % P ? 1 : 0));
+    return s;
+}
+
+int ilog2(size_t n) {
+    int l = 0;
+    while (((size_t)1 << l) < n) l++;
+    return l;
+}
+
+bool is_pow2(size_t n) { return n && !(n & (n - 1)); }
+
+}  // namespace
+
+int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
+    Shared &sh = *ctx->sh;
+    std::lock_guard<std::mutex> g(sh.mu);
+    DevBuf &b = sh.tw[lg];
+    if (!b.p) {
+        const size_t n = (size_t)1 << lg;
+        ZK_TRY(dev_alloc(sh, b, (n + 1) * sizeof(Fr)));
+        int err = ZK_OK;
+        Fr *root = (Fr *)scratch(ctx, "ntt.root", sizeof(Fr), &err);
+        if (!root) return err;
+        k_root<<<1, 1, 0, s>>>((uint32_t)lg, root);
+        count_launches(1);
+        size_t threads = (n + 63) / 64;
+        k_twiddles<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(root, (uint32_t)lg, (Fr *)b.p);
+        ZK_LAUNCHED();
+        // Shared read-only with lanes on other streams: finish before use.
+        ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    *out = (const uint32_t *)b.p;
+    return ZK_OK;
+}
+
+// Workspace of one group: ping-pong buffers and per-pass pointer tables.
+static size_t group_buf_bytes(size_t count, size_t n) {
+    int P = (int)plan_passes(ilog2(n)).size();
+    return P > 1 ? (size_t)(P > 2 ? 2 : 1) * count * n * 32 : 0;
+}
+static size_t group_tab_words(size_t count, size_t n) {
+    return plan_passes(ilog2(n)).size() * 2 * count;
+}
+
+// Runs every pass for `count` vectors of the same length n.  `buf` and
+// `tabs` are this group's workspace (sizes from the two functions above).
+static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t n, bool inverse,
+                     uint32_t *buf, uint64_t *tabs, cudaStream_t s) {
+    const int L = ilog2(n);
+    if (L == 0) return ZK_OK;  // a length-1 transform is the identity
+    std::vector<int> passes = plan_passes(L);
+    const int P = (int)passes.size();
+    const size_t tab_words = 2 * count;
+    std::vector<uint64_t> h((size_t)P * tab_words);
+    for (int p = 0; p < P; p++) {
+        for (size_t v = 0; v < count; v++) {
+            uint64_t src = p == 0 ? (uint64_t)data_h[v]
+                                  : (uint64_t)(buf + (((p - 1) % 2) * count + v) * n * 8);
+            uint64_t dst = p == P - 1 ? (uint64_t)data_h[v]
+                                      : (uint64_t)(buf + ((p % 2) * count + v) * n * 8);
+            h[p * tab_words + v] = src;
+            h[p * tab_words + count + v] = dst;
+        }
+    }
+    ZK_CUDA_TRY(cudaMemcpyAsync(tabs, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s));
+    const uint32_t *tw_n;
+    ZK_TRY(twiddles(ctx, L, &tw_n, s));
+    int logNs = 0;
+    PhaseScope ph(ctx, ZK_PHASE_NTT, s);
+    for (int p = 0; p < P; p++) {
+        const int logR = passes[p];
+        const uint32_t *tw_R;
+        ZK_TRY(twiddles(ctx, logR, &tw_R, s));
+        PassArgs a;
+        a.in_tab = (const uint32_t *const *)(tabs + p * tab_words);
+        a.out_tab = (uint32_t *const *)(tabs + p * tab_words + count);
+        a.logn = (uint32_t)L;
+        a.logR = (uint32_t)logR;
+        a.logNs = (uint32_t)logNs;
+        const uint64_t subs = (uint64_t)n >> logR;
+        a.J = (uint32_t)std::min<uint64_t>(kMaxJ, subs);
+        a.tw_n = (const Fr *)tw_n;
+        a.tw_R = (const Fr *)tw_R;
+        a.inverse = inverse ? 1 : 0;
+        a.scale = (inverse && p == P - 1) ? 1 : 0;
+        const uint32_t JR = a.J << logR;
+        const uint32_t threads = std::min<uint32_t>(512, std::max<uint32_t>(32, JR / 2));
+        const size_t smem = (size_t)JR * 32;
+        static bool attr_set = false;
+        if (!attr_set) {
+            ZK_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((size_t)kMaxJ << kMaxRadixLog) * 32));
+            attr_set = true;
+        }
+        dim3 grid((unsigned)(subs / a.J), (unsigned)count);
+        k_ntt_pass<<<grid, threads, smem, s>>>(a);
+        ZK_LAUNCHED();
+        logNs += logR;
+    }
+    return ZK_OK;
+}
+
+int ntt_impl(zk_ctx *ctx, uint32_t *data, size_t n, bool inverse, cudaStream_t s) {
+    if (!data || !is_pow2(n) || n > ((size_t)1 << kMaxLogN)) return ZK_EINVAL;
+    size_t lens[1] = {n};
+    uint32_t *const v[1] = {data};
+    return ntt_batch_impl(ctx, v, lens, 1, inverse, s);
+}
+
+int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_t count,
+                   bool inverse, cudaStream_t s) {
+    if (count == 0) return ZK_OK;
+    if (!data || !lens) return ZK_EINVAL;
+    std::map<size_t, std::vector<uint32_t *>> groups;
+    for (size_t k = 0; k < count; k++) {
+        if (!data[k] || !is_pow2(lens[k]) || lens[k] > ((size_t)1 << kMaxLogN)) return ZK_EINVAL;
+        groups[lens[k]].push_back(data[k]);
+    }
+    // Size the whole batch's workspace first so that no buffer is reallocated
+    // while an earlier group's passes are still queued.
+    size_t buf_bytes = 0, tab_words = 0;
+    for (auto &g : groups) {
+        buf_bytes += group_buf_bytes(g.second.size(), g.first);
+        tab_words += group_tab_words(g.second.size(), g.first);
+    }
+    int err = ZK_OK;
+    uint32_t *buf = nullptr;
+    if (buf_bytes) {
+        buf = (uint32_t *)scratch(ctx, "ntt.buf", buf_bytes, &err);
+        if (!buf) return err;
+    }
+    uint64_t *tabs = (uint64_t *)scratch(ctx, "ntt.tabs", std::max<size_t>(tab_words, 1) * 8, &err);
+    if (!tabs) return err;
+    for (auto &g : groups) {
+        ZK_TRY(ntt_group(ctx, g.second.data(), g.second.size(), g.first, inverse, buf, tabs, s));
+        buf += group_buf_bytes(g.second.size(), g.first) / 4;
+        tabs += group_tab_words(g.second.size(), g.first);
+    }
+    return ZK_OK;
+}
+
+}  // namespace zk

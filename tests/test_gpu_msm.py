@@ -1,0 +1,156 @@
+"""GPU parity of the SRS and the KZG commitment MSM against the oracle.
+
+Bit-exact throughout (finite-field arithmetic is exact; points are compared
+in canonical affine form).  Small sizes compare with the oracle's affine
+double-and-add MSM; sizes the oracle cannot run in seconds (2^20, 2^22)
+compare with the commitment's closed form [f(tau)]_1 for the known tau."""
+import numpy as np
+import pytest
+
+import zkinputs as Z
+from _util import pts_equal, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+R = Z.R_MOD
+
+
+def _commit(zk, ctx, c):
+    import torch
+    out = torch.zeros(8, dtype=torch.int64, device="cuda")
+    zk.zk_commit(ctx, to_dev(c), out)
+    torch.cuda.synchronize()
+    return to_host(out)
+
+
+def test_generated_srs_matches_oracle(zk, ctx_small, srs_small):
+    import torch
+    n = srs_small.shape[0]
+    out = torch.zeros((n, 8), dtype=torch.int64, device="cuda")
+    zk.zk_srs_export(ctx_small, out, 0, n)
+    torch.cuda.synchronize()
+    assert pts_equal(to_host(out), srs_small)
+
+
+def test_loaded_srs_validation_and_use(zk, orc, srs_small):
+    ctx = zk.zk_init(0)
+    try:
+        pts = np.ascontiguousarray(srs_small[:256])
+        zk.zk_srs_load(ctx, pts)            # host pointer
+        assert zk.zk_srs_size(ctx) == 256
+        c = Z.fr_uniform(41, 256)
+        assert pts_equal(_commit(zk, ctx, c), orc.msm(pts, c))
+        zk.zk_srs_load(ctx, to_dev(pts))    # device pointer
+        assert pts_equal(_commit(zk, ctx, c), orc.msm(pts, c))
+        for bad in ("off", "noncanon", "inf"):
+            p = pts.copy()
+            if bad == "off":
+                p[7, 4] ^= np.uint64(1)
+            elif bad == "noncanon":
+                p[9, :4] = orc.from_int(Z.Q_MOD + 1)
+            else:
+                p[11] = 0
+            with pytest.raises(zk.ZkError) as ei:
+                zk.zk_srs_load(ctx, p)
+            assert ei.value.code == zk.ZK_EINVAL
+            assert zk.zk_srs_size(ctx) == 0
+    finally:
+        zk.zk_destroy(ctx)
+
+
+def test_msm_full_oracle_2_12(zk, orc, ctx_small, srs_small, tau):
+    n = 1 << 12
+    c = Z.fr_uniform(1, n)
+    got = _commit(zk, ctx_small, c)
+    assert pts_equal(got, orc.msm(srs_small, c))
+    assert pts_equal(got, orc.commit_coeffs_tau(c, tau))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 1000, 4095])
+def test_msm_ragged_lengths(zk, orc, ctx_small, tau, n):
+    c = Z.fr_uniform(100 + n, n)
+    assert pts_equal(_commit(zk, ctx_small, c), orc.commit_coeffs_tau(c, tau))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "gauss"])
+def test_msm_quantised_scalars(zk, orc, ctx_small, srs_small, dist):
+    n = 1 << 12
+    c = Z.zkml_scalars(4, n, dist)
+    assert pts_equal(_commit(zk, ctx_small, c), orc.msm(srs_small, c))
+
+
+def test_msm_edge_cases(zk, orc, ctx_small, srs_small, tau):
+    n = 512
+    inf = np.zeros(8, dtype=np.uint64)
+    assert pts_equal(_commit(zk, ctx_small, np.zeros((n, 4), np.uint64)), inf)
+    c = np.zeros((n, 4), np.uint64)
+    c[17] = Z.int_to_fr(R - 1)
+    assert pts_equal(_commit(zk, ctx_small, c), orc.g1_neg(srs_small[17]))
+    # Recentring boundary (r-1)/2 and (r+1)/2, the largest digits, powers of two.
+    specials = [(R - 1) // 2, (R + 1) // 2, R - 2, 1, 2, (1 << 253) - 1, 1 << 252, (1 << 16) - 1,
+                1 << 15, (1 << 15) + 1, 3 << 240]
+    c = np.stack([Z.int_to_fr(v % R) for v in specials])
+    assert pts_equal(_commit(zk, ctx_small, c), orc.commit_coeffs_tau(c, tau))
+    # Every scalar equal: all points land in the same buckets (maximal skew).
+    c = np.tile(Z.fr_uniform(7, 1)[0], (4096, 1))
+    assert pts_equal(_commit(zk, ctx_small, c), orc.commit_coeffs_tau(c, tau))
+    c = np.tile(Z.int_to_fr(5), (4096, 1))
+    assert pts_equal(_commit(zk, ctx_small, c), orc.commit_coeffs_tau(c, tau))
+
+
+def test_msm_host_buffers(zk, orc, ctx_small, tau):
+    n = 777
+    c = Z.fr_uniform(55, n)
+    out = np.zeros(8, dtype=np.uint64)
+    zk.zk_commit(ctx_small, np.ascontiguousarray(c), out)
+    assert pts_equal(out, orc.commit_coeffs_tau(c, tau))
+
+
+def test_commit_batch_ragged_and_evals(zk, orc, ctx_small, tau):
+    import torch
+    lens = [1, 5, 64, 100, 1024, 3000, 4096, 2]
+    vecs = [Z.fr_uniform(200 + i, l) for i, l in enumerate(lens)]
+    out = torch.zeros((len(lens), 8), dtype=torch.int64, device="cuda")
+    zk.zk_commit_batch(ctx_small, [to_dev(v) for v in vecs], out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    for k, v in enumerate(vecs):
+        assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), k
+    # Evaluation form: INTT then MSM, padded to a power of two.
+    evals = [Z.zkml_scalars(300 + i, l) for i, l in enumerate([4, 64, 1000, 4096])]
+    out2 = np.zeros((len(evals), 8), dtype=np.uint64)
+    zk.zk_commit_batch(ctx_small, [np.ascontiguousarray(v) for v in evals], out2, flags=zk.ZK_EVALS)
+    for k, v in enumerate(evals):
+        n2 = 1 << (len(v) - 1).bit_length()
+        vp = np.zeros((n2, 4), np.uint64)
+        vp[:len(v)] = v
+        assert pts_equal(out2[k], orc.commit_evals_tau(vp, tau)), k
+
+
+@pytest.mark.parametrize("dist", ["fr", "zkml", "zkml_gauss"])
+def test_msm_at_scale_2_20(zk, orc, ctx_big, tau, dist):
+    n = 1 << 20
+    c = {"fr": lambda: Z.fr_uniform(3, n),
+         "zkml": lambda: Z.zkml_scalars(4, n),
+         "zkml_gauss": lambda: Z.zkml_scalars(4, n, "gauss")}[dist]()
+    assert pts_equal(_commit(zk, ctx_big, c), orc.commit_coeffs_tau(c, tau))
+
+
+def test_msm_at_scale_2_22(zk, orc, ctx_big, tau):
+    n = 1 << 22
+    c = Z.fr_uniform(12, n)
+    assert pts_equal(_commit(zk, ctx_big, c), orc.commit_coeffs_tau(c, tau))
+
+
+def test_big_srs_samples(zk, orc, ctx_big, tau):
+    import torch
+    n = 1 << 22
+    out = torch.zeros((n, 8), dtype=torch.int64, device="cuda")
+    zk.zk_srs_export(ctx_big, out, 0, n)
+    torch.cuda.synchronize()
+    pts = to_host(out)
+    assert orc.count_off_curve(pts[:: 64]) == 0
+    G = orc.g1_generator()
+    t = Z.fr_to_int(tau)
+    rng = np.random.default_rng(0)
+    for i in [0, 1, 2, n - 1] + rng.integers(0, n, 16).tolist():
+        assert pts_equal(pts[i], orc.g1_mul(G, Z.int_to_fr(pow(t, int(i), R)))), i
