@@ -116,6 +116,26 @@ int zk_srs_export(zk_ctx *ctx, zk_g1 *out, size_t first, size_t count, zk_stream
  * be canonical (< r). */
 int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream);
 
+/* Allocation-free variant of zk_commit, for callers that cannot call
+ * cudaMalloc (a host thread that must never block on the device-wide
+ * synchronisation that cudaFree implies, or a process whose device memory is
+ * all owned by another allocator).  The paper has no counterpart: this is a
+ * deployment variant of the same commitment.
+ *   coeffs, out : DEVICE pointers (ZK_EINVAL for host pointers); 1 <= n <= 4096
+ *                 (ZK_EINVAL above that), n <= SRS size (ZK_ESRS otherwise).
+ *   Workspace   : one fixed 14 MiB device array inside the library, shared by
+ *                 every call; each GPU that loads the library holds it until
+ *                 the process exits.  The call allocates nothing (no
+ *                 cudaMalloc, cudaFree or allocating library routine) and
+ *                 uses the window table built by zk_srs_load/zk_srs_generate.
+ *   First call  : on each device, the first call looks up the array's device
+ *                 address (cudaGetSymbolAddress); make that first call before
+ *                 any stream capture.
+ *   Concurrency : calls that overlap on the GPU (other streams, other host
+ *                 threads) race on the shared array; serialise them.
+ * The result equals zk_commit's bit for bit. */
+int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream);
+
 /* Flags of zk_commit_batch. */
 #define ZK_EVALS 1u /* vectors are evaluations over H: INTT each one first (in place, on
                        a workspace copy -- the caller's vectors are not modified) */

@@ -51,6 +51,7 @@ def _load():
         "zk_srs_size": [_VP, _SZP],
         "zk_srs_export": [_VP, _VP, _SZ, _SZ, _VP],
         "zk_commit": [_VP, _VP, _SZ, _VP, _VP],
+        "zk_commit_noalloc": [_VP, _VP, _SZ, _VP, _VP],
         "zk_commit_batch": [_VP, _VP, _VP, _SZ, ctypes.c_uint, _VP, _VP],
         "zk_ntt": [_VP, _VP, _SZ, _VP],
         "zk_intt": [_VP, _VP, _SZ, _VP],
@@ -78,7 +79,7 @@ def _load():
 lib = _load()
 
 EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_generate",
-            "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_batch", "zk_ntt", "zk_intt",
+            "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_noalloc", "zk_commit_batch", "zk_ntt", "zk_intt",
             "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_strerror",
             "zk_kernel_launches", "zk_probe_rates", "zk_timing_enable", "zk_timing_read"]
 
@@ -194,6 +195,13 @@ def zk_srs_export(ctx: int, out, first: int, count: int, stream=None) -> None:
 def zk_commit(ctx: int, coeffs, out, n: int | None = None, stream=None) -> None:
     n = _nelem(coeffs, 4) if n is None else n
     _check(lib.zk_commit(ctx, _ptr(coeffs), n, _ptr(out), _stream(stream)), "zk_commit")
+
+
+def zk_commit_noalloc(ctx: int, coeffs, out, n: int | None = None, stream=None) -> None:
+    """zk_commit without any device allocation (device buffers, n <= 4096)."""
+    n = _nelem(coeffs, 4) if n is None else n
+    _check(lib.zk_commit_noalloc(ctx, _ptr(coeffs), n, _ptr(out), _stream(stream)),
+           "zk_commit_noalloc")
 
 
 def zk_commit_batch(ctx: int, vecs, out, flags: int = 0, lens=None, stream=None) -> None:

@@ -479,3 +479,175 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStr
 }
 
 }  // namespace zk
+
+// ---------------------------------------------------------------------------
+// Allocation-free commitment (zk_commit_noalloc).
+//
+// Some callers cannot call cudaMalloc: a host thread that must never block on
+// the device-wide synchronisation cudaFree implies, or a process whose device
+// memory is all owned by another allocator (a framework's caching allocator
+// that reserved the HBM up front).  For them the MSM below runs the same
+// kernels as msm_batch_impl with its whole workspace in one fixed device
+// array compiled into this library, sized for one MSM of at most
+// kNoAllocMaxN points at window width 16.  Every GPU that loads the library
+// holds the array until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace zk {
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxN = 1u << 12;
+constexpr int kNoAllocC = 16;
+constexpr uint32_t kNoAllocB = 1u << (kNoAllocC - 1);
+constexpr uint32_t kNoAllocW = (kScalarBits + kNoAllocC - 1) / kNoAllocC;
+constexpr size_t kNoAllocEntries = (size_t)kNoAllocMaxN * kNoAllocW;
+constexpr size_t kNoAllocPieces = kNoAllocEntries / kPiece + kNoAllocB + 1;
+constexpr size_t kNoAllocBlk = kNoAllocB / kRedSpan;
+
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+// Workspace layout (byte offsets).
+constexpr size_t kNaJobs = 0;                                          // 3 x 256 B
+constexpr size_t kNaCounts = kNaJobs + 3 * 256;
+constexpr size_t kNaOff0 = kNaCounts + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaOffA = kNaOff0 + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaOffB = kNaOffA + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaCursor = kNaOffB + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaSorted = kNaCursor + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaPieceA = kNaSorted + na_align(kNoAllocEntries * 4);
+constexpr size_t kNaPieceB = kNaPieceA + na_align(kNoAllocPieces * sizeof(Xyzz));
+constexpr size_t kNaBuckets = kNaPieceB + na_align(kNoAllocPieces * sizeof(Xyzz));
+constexpr size_t kNaBval = kNaBuckets + na_align(kNoAllocB * sizeof(Xyzz));
+constexpr size_t kNaBsum = kNaBval + na_align(kNoAllocBlk * sizeof(Xyzz));
+constexpr size_t kNaScan = kNaBsum + na_align(kNoAllocBlk * sizeof(Xyzz));
+constexpr size_t kNoAllocBytes = kNaScan + na_align(((size_t)kNoAllocB / 2048 + 2) * 4);
+
+// The workspace.  Host code must not use this name as an address: it is a
+// host-side stand-in.  The device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices];
+
+// Device address of g_noalloc_ws on the current device (looked up once per
+// device, with that device current).
+int noalloc_workspace(int device, unsigned char **out) {
+    if (device < 0 || device >= kNoAllocMaxDevices) return ZK_EINVAL;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ZK_ECUDA;
+        }
+        g_noalloc_addr[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_addr[device];
+    return ZK_OK;
+}
+
+// Writes the one-job table (scalars pointer, length prefix, output) that the
+// recode kernels read, without a host-to-device copy.
+__global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint32_t n, void *out) {
+    if (threadIdx.x || blockIdx.x) return;
+    reinterpret_cast<const uint32_t **>(ws + kNaJobs)[0] = scalars;
+    uint32_t *base = reinterpret_cast<uint32_t *>(ws + kNaJobs + 256);
+    base[0] = 0;
+    base[1] = n;
+    reinterpret_cast<void **>(ws + kNaJobs + 512)[0] = out;
+}
+
+}  // namespace
+
+}  // namespace zk
+
+extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out,
+                                 zk_stream stream) {
+    using namespace zk;
+    if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
+    if (n > kNoAllocMaxN) return ZK_EINVAL;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    const int device = ctx->sh->device;
+    if (prev != device && cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    struct Restore {
+        int prev, dev;
+        ~Restore() {
+            if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+        }
+    } restore{prev, device};
+    if (!is_device_ptr(coeffs) || !is_device_ptr(out)) return ZK_EINVAL;
+    Shared &sh = *ctx->sh;
+    if (sh.srs_n == 0 || n > sh.srs_n) return ZK_ESRS;
+    const WindowTable *tab = nullptr;
+    {
+        std::lock_guard<std::mutex> g(sh.mu);
+        for (auto &t : sh.tables)
+            if (t.c == kNoAllocC && t.n >= n) tab = &t;
+    }
+    if (!tab) return ZK_ESRS;  // the c = 16 table is built when the SRS is loaded
+    unsigned char *ws = nullptr;
+    ZK_TRY(noalloc_workspace(device, &ws));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t nb = kNoAllocB;
+    uint32_t *counts = (uint32_t *)(ws + kNaCounts);
+    uint32_t *off0 = (uint32_t *)(ws + kNaOff0);
+    uint32_t *offa = (uint32_t *)(ws + kNaOffA);
+    uint32_t *offb = (uint32_t *)(ws + kNaOffB);
+    uint32_t *cursor = (uint32_t *)(ws + kNaCursor);
+    uint32_t *sorted = (uint32_t *)(ws + kNaSorted);
+    Xyzz *pa = (Xyzz *)(ws + kNaPieceA);
+    Xyzz *pb = (Xyzz *)(ws + kNaPieceB);
+    Xyzz *buckets = (Xyzz *)(ws + kNaBuckets);
+    Xyzz *bval = (Xyzz *)(ws + kNaBval);
+    Xyzz *bsum = (Xyzz *)(ws + kNaBsum);
+    void *scan_tmp = ws + kNaScan;
+
+    k_noalloc_jobs<<<1, 1, 0, s>>>(ws, (const uint32_t *)coeffs, (uint32_t)n, out);
+    ZK_LAUNCHED();
+    DevJobs dj;
+    dj.scalars = (const uint32_t *const *)(ws + kNaJobs);
+    dj.base = (const uint32_t *)(ws + kNaJobs + 256);
+    dj.out = (void *const *)(ws + kNaJobs + 512);
+    dj.count = 1;
+    const uint32_t total = (uint32_t)n;
+    // The workspace keeps the previous call's contents: the histogram must
+    // start at zero; every other region is fully written before it is read.
+    ZK_CUDA_TRY(cudaMemsetAsync(counts, 0, (nb + 1) * 4, s));
+    ZK_TRY(launch_recode<kNoAllocC>(dj, total, (uint32_t)tab->n, counts, nullptr, nullptr, false, s));
+    ZK_TRY(scan_exclusive(counts, off0, nb, 0, scan_tmp, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    ZK_TRY(launch_recode<kNoAllocC>(dj, total, (uint32_t)tab->n, nullptr, cursor, sorted, true, s));
+    int rounds = 0;
+    for (size_t m = (size_t)n * kNoAllocW; m > (size_t)kPiece; m = (m + kPiece - 1) / kPiece) rounds++;
+    const uint32_t *off_prev = off0;
+    Xyzz *cur = pa, *nxt = pb;
+    size_t cap = kNoAllocPieces;
+    for (int rd = 0; rd < rounds; rd++) {
+        uint32_t *off_new = (rd % 2 == 0) ? offa : offb;
+        ZK_TRY(scan_exclusive(off_prev, off_new, nb, kPiece, scan_tmp, s));
+        unsigned blocks = (unsigned)((cap + 127) / 128);
+        if (rd == 0)
+            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb,
+                                                  (const Affine *)tab->buf.p, cur);
+        else
+            k_pieces_next<<<blocks, 128, 0, s>>>(nxt, off_prev, off_new, nb, cur);
+        ZK_LAUNCHED();
+        std::swap(cur, nxt);
+        off_prev = off_new;
+        cap = cap / kPiece + nb + 1;
+    }
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, (const Affine *)tab->buf.p, nxt,
+                                                      off_prev, nb, rounds == 0 ? 1 : 0, buckets);
+    ZK_LAUNCHED();
+    dim3 g((unsigned)kNoAllocBlk, 1);
+    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, nb, bval, bsum);
+    ZK_LAUNCHED();
+    k_reduce_final<<<1, 32, 0, s>>>(bval, bsum, (uint32_t)kNoAllocBlk, dj);
+    ZK_LAUNCHED();
+    return ZK_OK;
+}
