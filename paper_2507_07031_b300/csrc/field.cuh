@@ -273,7 +273,7 @@ ZK_DEV void mont_row(uint32_t (&t)[17], const uint32_t (&a)[8], uint32_t bi) {
 
 }  // namespace detail
 
-template <class P> ZK_DEV Fe<P> fe_mul(const Fe<P> &a, const Fe<P> &b) {
+template <class P> ZK_DEV Fe<P> fe_mul_inline(const Fe<P> &a, const Fe<P> &b) {
     uint32_t t[17];
 #pragma unroll
     for (int i = 0; i < 17; i++) t[i] = 0;
@@ -307,6 +307,32 @@ template <class P> ZK_DEV Fe<P> fe_mul(const Fe<P> &a, const Fe<P> &b) {
 #pragma unroll
     for (int i = 0; i < 8; i++) r.v[i] = (s.v[i] & borrow) | (r.v[i] & ~borrow);
     return r;
+}
+
+// One out-of-line copy of the product per field: the curve formulas call it
+// ten to fourteen times per point operation, and inlining every call makes
+// the kernels' hot code larger than the instruction cache.
+template <class P>
+__device__ __noinline__ Fe<P> fe_mul_call(const Fe<P> a, const Fe<P> b) {
+    return fe_mul_inline<P>(a, b);
+}
+
+template <class P> ZK_DEV Fe<P> fe_mul(const Fe<P> &a, const Fe<P> &b);
+
+template <> ZK_DEV Fe<FqP> fe_mul<FqP>(const Fe<FqP> &a, const Fe<FqP> &b) {
+#ifdef ZK_INLINE_MUL_FQ
+    return fe_mul_inline<FqP>(a, b);
+#else
+    return fe_mul_call<FqP>(a, b);
+#endif
+}
+
+template <> ZK_DEV Fe<FrP> fe_mul<FrP>(const Fe<FrP> &a, const Fe<FrP> &b) {
+#ifdef ZK_NOINLINE_MUL_FR
+    return fe_mul_call<FrP>(a, b);
+#else
+    return fe_mul_inline<FrP>(a, b);
+#endif
 }
 
 template <class P> ZK_DEV Fe<P> fe_sqr(const Fe<P> &a) { return fe_mul<P>(a, a); }
