@@ -187,6 +187,22 @@ int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, z
 int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
                  zk_stream stream);
 
+/* Autotuning (the window width of the MSM and the largest NTT pass radix, per
+ * length).  op = ZK_TUNE_MSM_WINDOW: value = window width c in [9, 20] for
+ * MSMs of length in (2^(log2n-1), 2^log2n]; op = ZK_TUNE_NTT_RADIX: value =
+ * log2 of the largest pass radix in [1, 11] for transforms of length 2^log2n.
+ * value 0 restores the built-in choice (a cost model for the window; radix
+ * 2^10).  zk_tune_measure times one candidate on synthetic device data (median
+ * of `reps` runs, ms) without changing the setting; the first use of a new
+ * window width builds its window table (about W x 64 bytes per SRS point).
+ * paper_2507_07031_b300/autotune.py sweeps the candidates and stores the
+ * winners in a JSON table. */
+#define ZK_TUNE_MSM_WINDOW 0
+#define ZK_TUNE_NTT_RADIX 1
+int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value);
+int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value);
+int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double *ms);
+
 /* Static description of an error code. */
 const char *zk_strerror(int code);
 

@@ -61,6 +61,10 @@ def _load():
         "zk_fold": [_VP, _VP, _VP, _VP, _VP, _VP, _VP],
         "zk_fold_tree": [_VP, _VP, _SZ, _VP, _VP, _VP],
         "zk_timing_enable": [_VP, ctypes.c_int],
+        "zk_tune_set": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "zk_tune_get": [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "zk_tune_measure": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_double)],
         "zk_timing_read": [_VP, _VP, _VP],
     }
     for name, args in sig.items():
@@ -82,7 +86,10 @@ lib = _load()
 EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_generate",
             "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_noalloc", "zk_commit_batch", "zk_ntt", "zk_intt",
             "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_strerror",
-            "zk_kernel_launches", "zk_probe_rates", "zk_timing_enable", "zk_timing_read"]
+            "zk_kernel_launches", "zk_probe_rates", "zk_timing_enable", "zk_timing_read",
+            "zk_tune_set", "zk_tune_get", "zk_tune_measure"]
+
+ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 
 PHASES = ["msm_sort", "msm_accum", "msm_reduce", "ntt", "fold_witness", "fold_instance"]
 
@@ -112,6 +119,23 @@ def zk_timing_read(ctx: int) -> dict:
     cnt = (ctypes.c_ulonglong * len(PHASES))()
     _check(lib.zk_timing_read(ctx, ms, cnt), "zk_timing_read")
     return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+
+def zk_tune_set(ctx: int, op: int, log2n: int, value: int) -> None:
+    _check(lib.zk_tune_set(ctx, int(op), int(log2n), int(value)), "zk_tune_set")
+
+
+def zk_tune_get(ctx: int, op: int, log2n: int) -> int:
+    v = ctypes.c_int()
+    _check(lib.zk_tune_get(ctx, int(op), int(log2n), ctypes.byref(v)), "zk_tune_get")
+    return v.value
+
+
+def zk_tune_measure(ctx: int, op: int, log2n: int, value: int, reps: int = 3) -> float:
+    ms = ctypes.c_double()
+    _check(lib.zk_tune_measure(ctx, int(op), int(log2n), int(value), int(reps), ctypes.byref(ms)),
+           "zk_tune_measure")
+    return ms.value
 
 
 def _check(rc: int, where: str):

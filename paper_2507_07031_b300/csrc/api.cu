@@ -119,6 +119,21 @@ __global__ void k_zero_pad(uint4 *dst, size_t from16, size_t to16) {
         dst[i] = make_uint4(0, 0, 0, 0);
 }
 
+// Synthetic canonical F_r elements (253-bit values, so always < r) for
+// tuning runs: a SplitMix64-style hash of the index.
+__global__ void k_fill_random(uint64_t *out, size_t n, uint64_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        for (int l = 0; l < 4; l++) {
+            uint64_t z = seed + (4 * i + l + 1) * 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            out[4 * i + l] = l == 3 ? (z & ((1ull << 61) - 1)) : z;
+        }
+    }
+}
+
 size_t next_pow2(size_t n) {
     size_t p = 1;
     while (p < n) p <<= 1;
@@ -168,6 +183,81 @@ int zk_init(zk_ctx **out, int device, size_t hbm_budget_bytes) {
         return ZK_ECUDA;
     }
     *out = c;
+    return ZK_OK;
+}
+
+int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value) {
+    if (!ctx || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
+    Shared &sh = *ctx->sh;
+    std::lock_guard<std::mutex> g(sh.mu);
+    if (op == ZK_TUNE_MSM_WINDOW) {
+        if (value != 0 && (value < kMinWindow || value > kMaxWindow)) return ZK_EINVAL;
+        sh.tuned_window[log2n] = value;
+    } else if (op == ZK_TUNE_NTT_RADIX) {
+        if (value < 0 || value > 11) return ZK_EINVAL;
+        sh.tuned_radix[log2n] = value;
+    } else {
+        return ZK_EINVAL;
+    }
+    return ZK_OK;
+}
+
+int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value) {
+    if (!ctx || !value || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
+    const Shared &sh = *ctx->sh;
+    if (op == ZK_TUNE_MSM_WINDOW) *value = sh.tuned_window[log2n];
+    else if (op == ZK_TUNE_NTT_RADIX) *value = sh.tuned_radix[log2n];
+    else return ZK_EINVAL;
+    return ZK_OK;
+}
+
+int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double *ms) {
+    if (!ctx || !ms || reps < 1 || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    const size_t n = (size_t)1 << log2n;
+    int err = ZK_OK;
+    uint64_t *data = (uint64_t *)scratch(ctx, "tune.data", n * 32, &err);
+    uint32_t *out = (uint32_t *)scratch(ctx, "tune.out", 64, &err);
+    if (!data || !out) return err;
+    cudaStream_t s = 0;
+    k_fill_random<<<1024, 256, 0, s>>>(data, n, 0x5eed0000ull + (uint64_t)log2n);
+    ZK_LAUNCHED();
+    std::vector<float> t;
+    cudaEvent_t e0, e1;
+    ZK_CUDA_TRY(cudaEventCreate(&e0));
+    ZK_CUDA_TRY(cudaEventCreate(&e1));
+    int rc = ZK_OK;
+    int saved = 0;
+    if (op == ZK_TUNE_NTT_RADIX) {
+        if (value < 1 || value > 11) rc = ZK_EINVAL;
+        saved = ctx->sh->tuned_radix[log2n];
+        ctx->sh->tuned_radix[log2n] = value;
+    } else if (op != ZK_TUNE_MSM_WINDOW || value < kMinWindow || value > kMaxWindow) {
+        rc = ZK_EINVAL;
+    }
+    for (int r = 0; rc == ZK_OK && r <= reps; r++) {  // run 0 warms up (tables, twiddles)
+        cudaEventRecord(e0, s);
+        if (op == ZK_TUNE_MSM_WINDOW) {
+            MsmJob j;
+            j.scalars = (const uint32_t *)data;
+            j.n = (uint32_t)n;
+            j.out = out;
+            rc = msm_batch_impl(ctx, &j, 1, value, s);
+        } else {
+            rc = ntt_impl(ctx, (uint32_t *)data, n, false, s);
+        }
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float x = 0;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (r > 0) t.push_back(x);
+    }
+    if (op == ZK_TUNE_NTT_RADIX) ctx->sh->tuned_radix[log2n] = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ZK_OK) return rc;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
     return ZK_OK;
 }
 
@@ -334,7 +424,7 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
         jobs[k].out = obuf + 16 * k;
         maxn = std::max(maxn, (size_t)jobs[k].n);
     }
-    ZK_TRY(msm_batch_impl(ctx, jobs.data(), count, msm_pick_window(ctx, maxn, count), s));
+    ZK_TRY(msm_batch_impl(ctx, jobs.data(), count, 0, s));
     if (!dev_out) {
         ZK_CUDA_TRY(cudaMemcpyAsync(out, obuf, count * 64, cudaMemcpyDeviceToHost, s));
         ZK_CUDA_TRY(cudaStreamSynchronize(s));

@@ -46,6 +46,8 @@ struct Shared {
     DevBuf srs;  // affine Montgomery, srs_n points
     std::deque<WindowTable> tables;  // deque: references stay valid as tables are added
     DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg
+    int tuned_window[29] = {};   // MSM window width per log2 length (0 = cost model)
+    int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = default)
     ~Shared();
 };
 
@@ -74,6 +76,8 @@ namespace zk {
 constexpr int kMaxLogN = 28;      // 2-adicity of r - 1
 constexpr int kMaxSrsLog = 26;    // window-table index must fit 31 bits at c >= 16
 constexpr int kScalarBits = 254;  // |recentred scalar| < r / 2 < 2^253, one spare bit for carries
+constexpr int kMinWindow = 9;     // MSM window widths with a recode kernel
+constexpr int kMaxWindow = 20;
 
 inline int ceil_div_int(int a, int b) { return (a + b - 1) / b; }
 inline int windows_for(int c) { return ceil_div_int(kScalarBits, c); }
@@ -146,7 +150,9 @@ int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_
 int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s);
 
 // MSM (msm.cu).  Each job: scalars (device, canonical, 32 B each), length n,
-// output 64-byte canonical affine point (device).
+// output 64-byte canonical affine point (device).  c > 0 fixes the window
+// width of every job; c = 0 takes the tuned (or modelled) width per length.
+
 struct MsmJob {
     const uint32_t *scalars;
     uint32_t n;

@@ -173,7 +173,7 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, cudaStream
         ZK_LAUNCHED();
     }
     ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), F, true, s));
-    ZK_TRY(msm_batch_impl(ctx, jobs.data(), F, msm_pick_window(ctx, n, F), s));
+    ZK_TRY(msm_batch_impl(ctx, jobs.data(), F, 0, s));
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s);
         k_fold_instance<<<(unsigned)((5 * F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
@@ -312,7 +312,7 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
             }
         }
         ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), vecs.size(), true, s));
-        ZK_TRY(msm_batch_impl(ctx, jobs.data(), jobs.size(), msm_pick_window(ctx, n, jobs.size()), s));
+        ZK_TRY(msm_batch_impl(ctx, jobs.data(), jobs.size(), 0, s));
     }
     return ZK_OK;
 }

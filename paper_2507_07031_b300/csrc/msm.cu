@@ -35,35 +35,43 @@ namespace zk {
 namespace {
 
 constexpr uint32_t kInvalid = 0xffffffffu;
-constexpr int kPiece = 32;        // entries (or partial sums) per thread per round
-constexpr int kRedThreads = 256;  // bucket-reduction block
-constexpr int kRedPer = 4;        // buckets per thread
+constexpr int kPiece = 32;       // entries (or partial sums) per thread per round
+constexpr int kRedThreads = 64;  // bucket-reduction block
+constexpr int kRedPer = 4;       // buckets per thread
 constexpr int kRedSpan = kRedThreads * kRedPer;
+constexpr int kRedSpanLog = 8;
+static_assert(kRedSpan == 1 << kRedSpanLog, "reduction span");
+
+// One MSM of a batch.  Jobs are ordered by window width so that each width's
+// scalars form one contiguous range for its recode launch.
+struct JobDesc {
+    const uint32_t *scalars;  // n canonical scalars (device)
+    void *out;                // canonical affine result (device)
+    const Affine *table;      // window table of this job's width
+    uint32_t n;
+    uint32_t logB;            // buckets: B = 2^logB = 2^(c - 1)
+    uint32_t pad[2];
+};
 
 struct DevJobs {
-    const uint32_t *const *scalars;  // per job
-    const uint32_t *base;            // prefix sums of n, count + 1 entries
-    void *const *out;                // per job
+    const JobDesc *jobs;     // count entries
+    const uint32_t *sbase;   // scalar prefix over jobs, count + 1
+    const uint32_t *bbase;   // first global bucket of each job, count + 1
+    const uint32_t *kbase;   // first reduction block of each job, count + 1
     uint32_t count;
 };
 
-__device__ __forceinline__ uint32_t find_job(const uint32_t *base, uint32_t count, uint32_t gid) {
-    uint32_t lo = 0, hi = count;  // base[lo] <= gid < base[hi]
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (base[mid] <= gid) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-// Largest b with off[b] <= x, for off nondecreasing with off[0] = 0.
-__device__ __forceinline__ uint32_t upper_index(const uint32_t *off, uint32_t nb, uint32_t x) {
-    uint32_t lo = 0, hi = nb;  // off[lo] <= x < off[hi] (off[nb] > x assumed)
+// Largest i in [lo, hi) with off[i] <= x (off nondecreasing, off[lo] <= x < off[hi]).
+__device__ __forceinline__ uint32_t search(const uint32_t *off, uint32_t lo, uint32_t hi, uint32_t x) {
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         if (off[mid] <= x) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+__device__ __forceinline__ uint32_t upper_index(const uint32_t *off, uint32_t nb, uint32_t x) {
+    return search(off, 0, nb, x);
 }
 
 template <int C>
@@ -76,7 +84,7 @@ __device__ __forceinline__ uint32_t window_bits(const uint32_t (&s)[8], int w) {
     return (lo | hi) & ((1u << C) - 1u);
 }
 
-// Loads scalar i of its job, recentres it, and returns the negation flag.
+// Loads a scalar, recentres it, and returns the negation flag.
 __device__ __forceinline__ bool load_recentred(const uint32_t *p, uint32_t (&s)[8]) {
     Fr x = fe_load<FrP>(p);
     bool neg = fe_gt_half<FrP>(x);
@@ -88,49 +96,26 @@ __device__ __forceinline__ bool load_recentred(const uint32_t *p, uint32_t (&s)[
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-// Phase 1: bucket histogram.
-template <int C>
-__global__ void k_count(DevJobs jobs, uint32_t total, uint32_t *__restrict__ counts) {
+// Phases 1 and 2 for the jobs [g0, g1) of window width C: with SCATTER false,
+// the bucket histogram; with SCATTER true, the (table index << 1 | sign)
+// words written bucket by bucket.  Lanes with equal keys are aggregated into
+// one atomic per warp (skewed scalar distributions hit few buckets).
+template <int C, bool SCATTER>
+__global__ void k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n,
+                         uint32_t *__restrict__ counts, uint32_t *__restrict__ cursor,
+                         uint32_t *__restrict__ sorted) {
     constexpr int W = (kScalarBits + C - 1) / C;
-    constexpr uint32_t B = 1u << (C - 1);
-    uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    bool live = gid < total;
+    const uint32_t s0 = dj.sbase[g0];
+    const uint32_t gid = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = gid < dj.sbase[g1];
     uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t job = 0;
+    uint32_t job = g0, i = 0, bb = 0;
     bool neg = false;
     if (live) {
-        job = find_job(jobs.base, jobs.count, gid);
-        neg = load_recentred(jobs.scalars[job] + 8 * (gid - jobs.base[job]), s);
-    }
-    (void)neg;
-    uint32_t carry = 0;
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        uint32_t d = window_bits<C>(s, w) + carry;
-        carry = d > (1u << (C - 1)) ? 1u : 0u;
-        int sd = carry ? (int)d - (1 << C) : (int)d;
-        uint32_t key = (live && sd != 0) ? job * B + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
-        uint32_t group = __match_any_sync(0xffffffffu, key);
-        if (key != kInvalid && lane_id() == (uint32_t)(__ffs(group) - 1))
-            atomicAdd(&counts[key], (uint32_t)__popc(group));
-    }
-}
-
-// Phase 2: scatter (table index << 1 | sign) into bucket order.
-template <int C>
-__global__ void k_scatter(DevJobs jobs, uint32_t total, uint32_t table_n,
-                          uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted) {
-    constexpr int W = (kScalarBits + C - 1) / C;
-    constexpr uint32_t B = 1u << (C - 1);
-    uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    bool live = gid < total;
-    uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t job = 0, i = 0;
-    bool neg = false;
-    if (live) {
-        job = find_job(jobs.base, jobs.count, gid);
-        i = gid - jobs.base[job];
-        neg = load_recentred(jobs.scalars[job] + 8 * i, s);
+        job = search(dj.sbase, g0, g1, gid);
+        i = gid - dj.sbase[job];
+        bb = dj.bbase[job];
+        neg = load_recentred(dj.jobs[job].scalars + 8 * (size_t)i, s);
     }
     const uint32_t lt_mask = (1u << lane_id()) - 1u;
     uint32_t carry = 0;
@@ -139,31 +124,43 @@ __global__ void k_scatter(DevJobs jobs, uint32_t total, uint32_t table_n,
         uint32_t d = window_bits<C>(s, w) + carry;
         carry = d > (1u << (C - 1)) ? 1u : 0u;
         int sd = carry ? (int)d - (1 << C) : (int)d;
-        uint32_t key = (live && sd != 0) ? job * B + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
+        uint32_t key = (live && sd != 0) ? bb + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
         uint32_t group = __match_any_sync(0xffffffffu, key);
         uint32_t leader = (uint32_t)(__ffs(group) - 1);
-        uint32_t base = 0;
-        if (key != kInvalid && lane_id() == leader)
-            base = atomicAdd(&cursor[key], (uint32_t)__popc(group));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (key != kInvalid) {
-            uint32_t sign = ((sd < 0) ? 1u : 0u) ^ (neg ? 1u : 0u);
-            sorted[base + __popc(group & lt_mask)] = (((uint32_t)w * table_n + i) << 1) | sign;
+        if (!SCATTER) {
+            if (key != kInvalid && lane_id() == leader) atomicAdd(&counts[key], (uint32_t)__popc(group));
+        } else {
+            uint32_t base = 0;
+            if (key != kInvalid && lane_id() == leader)
+                base = atomicAdd(&cursor[key], (uint32_t)__popc(group));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (key != kInvalid) {
+                uint32_t sign = ((sd < 0) ? 1u : 0u) ^ (neg ? 1u : 0u);
+                sorted[base + __popc(group & lt_mask)] = (((uint32_t)w * table_n + i) << 1) | sign;
+            }
         }
     }
+}
+
+__device__ __forceinline__ Affine table_point(const DevJobs &dj, uint32_t b, uint32_t v) {
+    uint32_t job = search(dj.bbase, 0, dj.count, b);
+    Affine a = affine_ldg(dj.jobs[job].table + (v >> 1));
+    if (v & 1) a = affine_neg(a);
+    return a;
 }
 
 // Phase 3a: first round of piece sums over the sorted table indices.
 // off0: entry offsets per bucket (nb + 1); off1: piece offsets (nb + 1).
 __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32_t *__restrict__ off0,
-                               const uint32_t *__restrict__ off1, uint32_t nb,
-                               const Affine *__restrict__ table, Xyzz *__restrict__ pieces) {
+                               const uint32_t *__restrict__ off1, uint32_t nb, DevJobs dj,
+                               Xyzz *__restrict__ pieces) {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= off1[nb]) return;
     uint32_t b = upper_index(off1, nb, p);
     uint32_t k = p - off1[b];
     uint32_t lo = off0[b] + k * kPiece;
     uint32_t hi = min(lo + kPiece, off0[b + 1]);
+    const Affine *table = dj.jobs[search(dj.bbase, 0, dj.count, b)].table;
     Xyzz acc = xyzz_inf();
     for (uint32_t j = lo; j < hi; j++) {
         uint32_t v = sorted[j];
@@ -191,21 +188,15 @@ __global__ void k_pieces_next(const Xyzz *__restrict__ in, const uint32_t *__res
 
 // Phase 3c: one thread per bucket sums its (at most kPiece) remaining items;
 // `first` selects table entries (no piece round ran) or partial sums.
-__global__ void k_buckets_final(const uint32_t *__restrict__ sorted, const Affine *__restrict__ table,
+__global__ void k_buckets_final(const uint32_t *__restrict__ sorted, DevJobs dj,
                                 const Xyzz *__restrict__ in, const uint32_t *__restrict__ off,
                                 uint32_t nb, int first, Xyzz *__restrict__ buckets) {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     Xyzz acc = xyzz_inf();
     for (uint32_t j = off[b]; j < off[b + 1]; j++) {
-        if (first) {
-            uint32_t v = sorted[j];
-            Affine a = affine_ldg(table + (v >> 1));
-            if (v & 1) a = affine_neg(a);
-            acc = xyzz_add_affine(acc, a);
-        } else {
-            acc = xyzz_add(acc, in[j]);
-        }
+        if (first) acc = xyzz_add_affine(acc, table_point(dj, b, sorted[j]));
+        else acc = xyzz_add(acc, in[j]);
     }
     buckets[b] = acc;
 }
@@ -243,16 +234,17 @@ __device__ __forceinline__ Xyzz warp_sum(Xyzz x) {
     return x;
 }
 
-// Phase 4a: for block k of 1024 buckets of MSM j, val = sum_b (b - b0 + 1) S_b
-// and sum = sum_b S_b (b0 = first bucket of the block).
-__global__ void __launch_bounds__(kRedThreads, 1)
-    k_reduce_blocks(const Xyzz *__restrict__ buckets, uint32_t B, Xyzz *__restrict__ blk_val,
+// Phase 4a: for block k of kRedSpan buckets of MSM j (b0 = its first bucket),
+// val = sum_b (b - b0 + 1) S_b and sum = sum_b S_b.  Grid (max blocks, jobs).
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce_blocks(const Xyzz *__restrict__ buckets, DevJobs dj, Xyzz *__restrict__ blk_val,
                     Xyzz *__restrict__ blk_sum) {
     __shared__ Xyzz sh[kRedThreads / 32];
-    const uint32_t nblk = B / kRedSpan;
     const uint32_t job = blockIdx.y;
+    const uint32_t nblk = dj.kbase[job + 1] - dj.kbase[job];
+    if (blockIdx.x >= nblk) return;
     const uint32_t t = threadIdx.x;
-    const Xyzz *S = buckets + (size_t)job * B + (size_t)blockIdx.x * kRedSpan + kRedPer * t;
+    const Xyzz *S = buckets + dj.bbase[job] + (size_t)blockIdx.x * kRedSpan + kRedPer * t;
     // thread-local: l = sum_i (i + 1) S_i, r = sum_i S_i
     Xyzz r = S[kRedPer - 1];
     Xyzz l = r;
@@ -280,19 +272,20 @@ __global__ void __launch_bounds__(kRedThreads, 1)
     if (t == 0) {
         Xyzz v = sh[0];
         for (uint32_t w = 1; w < kRedThreads / 32; w++) v = xyzz_add(v, sh[w]);
-        blk_val[(size_t)job * nblk + blockIdx.x] = v;
-        blk_sum[(size_t)job * nblk + blockIdx.x] = tot_sum;
+        blk_val[dj.kbase[job] + blockIdx.x] = v;
+        blk_sum[dj.kbase[job] + blockIdx.x] = tot_sum;
     }
 }
 
-// Phase 4b + 5: one warp per MSM: total = sum_k val_k + 1024 sum_k k sum_k.
+// Phase 4b + 5: one warp per MSM: total = sum_k val_k + kRedSpan sum_k k sum_k.
 __global__ void k_reduce_final(const Xyzz *__restrict__ blk_val, const Xyzz *__restrict__ blk_sum,
-                               uint32_t nblk, DevJobs jobs) {
+                               DevJobs dj) {
     const uint32_t job = blockIdx.x;
     const uint32_t l = lane_id();
+    const uint32_t nblk = dj.kbase[job + 1] - dj.kbase[job];
     const uint32_t q = nblk >= 32 ? nblk / 32 : 1;  // blocks per lane (power of two)
-    const Xyzz *V = blk_val + (size_t)job * nblk;
-    const Xyzz *Sm = blk_sum + (size_t)job * nblk;
+    const Xyzz *V = blk_val + dj.kbase[job];
+    const Xyzz *Sm = blk_sum + dj.kbase[job];
     Xyzz lv = xyzz_inf(), lw = xyzz_inf(), ls = xyzz_inf();
     uint32_t lo = l * q, hi = min(lo + q, nblk);
     // lw = sum_k (k - lo) sum_k over the lane's blocks, by a running sum from the top
@@ -313,77 +306,112 @@ __global__ void k_reduce_final(const Xyzz *__restrict__ blk_val, const Xyzz *__r
     Xyzz vsum = warp_sum(lv);
     if (l == 0) {
         Xyzz tot = wsum;
-        for (int k = 0; k < 10; k++) tot = xyzz_dbl(tot);  // x 1024
+        for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl(tot);  // x kRedSpan
         tot = xyzz_add(tot, vsum);
-        xyzz_store_canonical(jobs.out[job], tot);
+        xyzz_store_canonical(dj.jobs[job].out, tot);
     }
 }
 
-// Empty MSM (n = 0) or all-zero output: write infinity.
-template <int C>
-int launch_recode(const DevJobs &dj, uint32_t total, uint32_t table_n, uint32_t *counts,
-                  uint32_t *cursor, uint32_t *sorted, bool scatter, cudaStream_t s) {
-    unsigned blocks = (total + 255) / 256;
-    if (!scatter) k_count<C><<<blocks, 256, 0, s>>>(dj, total, counts);
-    else k_scatter<C><<<blocks, 256, 0, s>>>(dj, total, table_n, cursor, sorted);
+template <int C, bool SCATTER>
+int launch_recode_c(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscalars,
+                    uint32_t table_n, uint32_t *counts, uint32_t *cursor, uint32_t *sorted,
+                    cudaStream_t s) {
+    if (nscalars == 0) return ZK_OK;
+    k_recode<C, SCATTER><<<(nscalars + 255) / 256, 256, 0, s>>>(dj, g0, g1, table_n, counts, cursor,
+                                                               sorted);
     ZK_LAUNCHED();
     return ZK_OK;
 }
 
-int recode(int c, const DevJobs &dj, uint32_t total, uint32_t table_n, uint32_t *counts,
-           uint32_t *cursor, uint32_t *sorted, bool scatter, cudaStream_t s) {
+template <bool SCATTER>
+int recode(int c, const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscalars, uint32_t table_n,
+           uint32_t *counts, uint32_t *cursor, uint32_t *sorted, cudaStream_t s) {
+#define ZK_RECODE_CASE(C) \
+    case C: return launch_recode_c<C, SCATTER>(dj, g0, g1, nscalars, table_n, counts, cursor, sorted, s);
     switch (c) {
-        case 11: return launch_recode<11>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 12: return launch_recode<12>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 13: return launch_recode<13>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 14: return launch_recode<14>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 15: return launch_recode<15>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 16: return launch_recode<16>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 17: return launch_recode<17>(dj, total, table_n, counts, cursor, sorted, scatter, s);
-        case 18: return launch_recode<18>(dj, total, table_n, counts, cursor, sorted, scatter, s);
+        ZK_RECODE_CASE(9) ZK_RECODE_CASE(10) ZK_RECODE_CASE(11) ZK_RECODE_CASE(12)
+        ZK_RECODE_CASE(13) ZK_RECODE_CASE(14) ZK_RECODE_CASE(15) ZK_RECODE_CASE(16)
+        ZK_RECODE_CASE(17) ZK_RECODE_CASE(18) ZK_RECODE_CASE(19) ZK_RECODE_CASE(20)
         default: return ZK_EINVAL;
     }
+#undef ZK_RECODE_CASE
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-}  // namespace
-
-int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count) {
-    (void)ctx;
-    (void)max_n;
-    (void)count;
-    return 16;
+// Cost model used when no tuned window is recorded: mixed additions n W(c)
+// plus about 2.8 addition-equivalents per bucket for the reduction.
+int model_window(size_t n) {
+    int best = 16;
+    double best_cost = 1e300;
+    for (int c = kMinWindow; c <= kMaxWindow; c++) {
+        double cost = (double)n * windows_for(c) + 2.8 * (double)(1u << (c - 1));
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
 }
 
-int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStream_t s) {
+}  // namespace
+
+int msm_pick_window(zk_ctx *ctx, size_t n, size_t count) {
+    (void)count;
+    int lg = 0;
+    while (((size_t)1 << lg) < n) lg++;
+    const Shared &sh = *ctx->sh;
+    if (lg <= kMaxLogN && sh.tuned_window[lg]) return sh.tuned_window[lg];
+    return model_window(n);
+}
+
+int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed, cudaStream_t s) {
     if (count == 0) return ZK_OK;
-    if (c < 11 || c > 18) return ZK_EINVAL;
     Shared &sh = *ctx->sh;
-    size_t total64 = 0, max_n = 0;
+    // Window width per job (fixed by the caller, or tuned / modelled per size).
+    struct J {
+        MsmJob job;
+        int c;
+    };
+    std::vector<J> jv(count);
+    size_t total64 = 0, entries64 = 0, nb64 = 0, nblk64 = 0;
     for (size_t k = 0; k < count; k++) {
-        total64 += jobs[k].n;
-        max_n = std::max(max_n, (size_t)jobs[k].n);
-        if (!jobs[k].out) return ZK_EINVAL;
-        if (jobs[k].n && !jobs[k].scalars) return ZK_EINVAL;
+        const MsmJob &m = jobs_in[k];
+        if (!m.out || (m.n && !m.scalars)) return ZK_EINVAL;
+        if (m.n > sh.srs_n) return ZK_ESRS;
+        int c = c_fixed > 0 ? c_fixed : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
+        if (c < kMinWindow || c > kMaxWindow) return ZK_EINVAL;
+        jv[k] = {m, c};
+        total64 += m.n;
+        entries64 += (size_t)m.n * windows_for(c);
+        nb64 += (size_t)1 << (c - 1);
+        nblk64 += ((size_t)1 << (c - 1)) / kRedSpan;
     }
-    if (max_n > sh.srs_n) return ZK_ESRS;
-    const int W = windows_for(c);
-    const uint32_t B = 1u << (c - 1);
-    const size_t nb64 = count * (size_t)B;
-    const size_t entries_max = total64 * (size_t)W;
-    if (total64 >= (1ull << 32) || nb64 >= (1ull << 31) || entries_max >= (1ull << 32))
-        return ZK_EINVAL;
-    const WindowTable *tab;
-    ZK_TRY(table_get(ctx, c, max_n ? max_n : 1, &tab, s));
+    if (total64 >= (1ull << 32) || nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
+    std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) { return a.c < b.c; });
+    // Window tables (built on first use of a width, outside any timed loop).
+    std::vector<const WindowTable *> tabs(count);
+    size_t max_n = 1;
+    for (size_t k = 0; k < count; k++) max_n = std::max(max_n, (size_t)jv[k].job.n);
+    for (size_t k = 0; k < count; k++) {
+        if (k == 0 || jv[k].c != jv[k - 1].c) {
+            size_t need = 1;
+            for (size_t j = k; j < count && jv[j].c == jv[k].c; j++) need = std::max(need, (size_t)jv[j].job.n);
+            ZK_TRY(table_get(ctx, jv[k].c, need, &tabs[k], s));
+        } else {
+            tabs[k] = tabs[k - 1];
+        }
+    }
     const uint32_t total = (uint32_t)total64;
     const uint32_t nb = (uint32_t)nb64;
+    const size_t entries_max = entries64;
 
     // Piece rounds: after R rounds a bucket with at most max_n W entries holds
     // ceil(max_n W / kPiece^R) items; stop once that is <= kPiece.
     int rounds = 0;
     {
-        size_t m = std::max<size_t>(max_n * (size_t)W, 1);
+        size_t m = 1;
+        for (size_t k = 0; k < count; k++) m = std::max(m, (size_t)jv[k].job.n * windows_for(jv[k].c));
         while (m > (size_t)kPiece) {
             m = (m + kPiece - 1) / kPiece;
             rounds++;
@@ -393,8 +421,9 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStr
 
     // Workspace.
     int err = ZK_OK;
-    const size_t job_bytes = align_up(count * sizeof(void *), 256);
-    char *jt = (char *)scratch(ctx, "msm.jobs", 3 * job_bytes + 256, &err);
+    const size_t jd_bytes = align_up(count * sizeof(JobDesc), 256);
+    const size_t pre_bytes = align_up((count + 1) * 4, 256);
+    char *jt = (char *)scratch(ctx, "msm.jobs", jd_bytes + 3 * pre_bytes, &err);
     uint32_t *counts = (uint32_t *)scratch(ctx, "msm.counts", (nb + 1) * 4, &err);
     uint32_t *off0 = (uint32_t *)scratch(ctx, "msm.off0", (nb + 1) * 4, &err);
     uint32_t *offa = (uint32_t *)scratch(ctx, "msm.offa", (nb + 1) * 4, &err);
@@ -404,43 +433,63 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStr
     Xyzz *pa = (Xyzz *)scratch(ctx, "msm.piecea", piece_cap * sizeof(Xyzz), &err);
     Xyzz *pb = (Xyzz *)scratch(ctx, "msm.pieceb", piece_cap * sizeof(Xyzz), &err);
     Xyzz *buckets = (Xyzz *)scratch(ctx, "msm.buckets", nb64 * sizeof(Xyzz), &err);
-    const uint32_t nblk = B / kRedSpan;
-    Xyzz *bval = (Xyzz *)scratch(ctx, "msm.bval", count * nblk * sizeof(Xyzz), &err);
-    Xyzz *bsum = (Xyzz *)scratch(ctx, "msm.bsum", count * nblk * sizeof(Xyzz), &err);
+    Xyzz *bval = (Xyzz *)scratch(ctx, "msm.bval", std::max<size_t>(nblk64, 1) * sizeof(Xyzz), &err);
+    Xyzz *bsum = (Xyzz *)scratch(ctx, "msm.bsum", std::max<size_t>(nblk64, 1) * sizeof(Xyzz), &err);
     void *scan_tmp = scratch(ctx, "msm.scantmp", scan_temp_bytes(nb), &err);
     if (!jt || !counts || !off0 || !offa || !offb || !cursor || !sorted || !pa || !pb || !buckets ||
         !bval || !bsum || !scan_tmp)
         return err;
 
-    // Job table (device copy of scalars pointers, length prefix, outputs).
-    std::vector<uint64_t> hjt(3 * job_bytes / 8 + 32, 0);
-    const uint32_t **h_sc = (const uint32_t **)hjt.data();
-    uint32_t *h_base = (uint32_t *)((char *)hjt.data() + job_bytes);
-    void **h_out = (void **)((char *)hjt.data() + 2 * job_bytes);
-    uint32_t acc = 0;
+    // Job table: descriptors and the three prefix arrays.
+    std::vector<char> h(jd_bytes + 3 * pre_bytes, 0);
+    JobDesc *hd = (JobDesc *)h.data();
+    uint32_t *hs = (uint32_t *)(h.data() + jd_bytes);
+    uint32_t *hb = (uint32_t *)(h.data() + jd_bytes + pre_bytes);
+    uint32_t *hk = (uint32_t *)(h.data() + jd_bytes + 2 * pre_bytes);
+    uint32_t maxblk = 1;
     for (size_t k = 0; k < count; k++) {
-        h_sc[k] = jobs[k].scalars;
-        h_base[k] = acc;
-        acc += jobs[k].n;
-        h_out[k] = jobs[k].out;
+        hd[k].scalars = jv[k].job.scalars;
+        hd[k].out = jv[k].job.out;
+        hd[k].table = (const Affine *)tabs[k]->buf.p;
+        hd[k].n = jv[k].job.n;
+        hd[k].logB = (uint32_t)(jv[k].c - 1);
+        hs[k + 1] = hs[k] + jv[k].job.n;
+        hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
+        uint32_t kb = (1u << (jv[k].c - 1)) / kRedSpan;
+        hk[k + 1] = hk[k] + kb;
+        maxblk = std::max(maxblk, kb);
     }
-    h_base[count] = acc;
-    ZK_CUDA_TRY(cudaMemcpyAsync(jt, hjt.data(), 3 * job_bytes, cudaMemcpyHostToDevice, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(jt, h.data(), h.size(), cudaMemcpyHostToDevice, s));
     DevJobs dj;
-    dj.scalars = (const uint32_t *const *)jt;
-    dj.base = (const uint32_t *)(jt + job_bytes);
-    dj.out = (void *const *)(jt + 2 * job_bytes);
+    dj.jobs = (const JobDesc *)jt;
+    dj.sbase = (const uint32_t *)(jt + jd_bytes);
+    dj.bbase = (const uint32_t *)(jt + jd_bytes + pre_bytes);
+    dj.kbase = (const uint32_t *)(jt + jd_bytes + 2 * pre_bytes);
     dj.count = (uint32_t)count;
 
-    // 1-2: histogram, offsets, scatter.
+    // 1-2: histogram, offsets, scatter (one recode launch per window width).
     PhaseScope ph_sort(ctx, ZK_PHASE_MSM_SORT, s);
     ZK_CUDA_TRY(cudaMemsetAsync(counts, 0, (nb + 1) * 4, s));
-    if (total) ZK_TRY(recode(c, dj, total, (uint32_t)tab->n, counts, nullptr, nullptr, false, s));
-    ZK_TRY(scan_exclusive(counts, off0, nb, 0, scan_tmp, s));
-    ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
-    if (total)
-        ZK_TRY(recode(c, dj, total, (uint32_t)tab->n, nullptr, cursor, sorted, true, s));
-
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            ZK_TRY(scan_exclusive(counts, off0, nb, 0, scan_tmp, s));
+            ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        for (size_t g0 = 0; g0 < count;) {
+            size_t g1 = g0;
+            while (g1 < count && jv[g1].c == jv[g0].c) g1++;
+            const uint32_t ns = hs[g1] - hs[g0];
+            const uint32_t tn = (uint32_t)tabs[g0]->n;
+            if (pass == 0)
+                ZK_TRY(recode<false>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, counts, nullptr,
+                                     nullptr, s));
+            else
+                ZK_TRY(recode<true>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, nullptr, cursor,
+                                    sorted, s));
+            g0 = g1;
+        }
+    }
+    (void)total;
     ph_sort.end();
 
     // 3: piece rounds, then one point per bucket.
@@ -453,8 +502,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStr
         ZK_TRY(scan_exclusive(off_prev, off_new, nb, kPiece, scan_tmp, s));
         unsigned blocks = (unsigned)((cap + 127) / 128);
         if (rd == 0)
-            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb,
-                                                  (const Affine *)tab->buf.p, cur);
+            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb, dj, cur);
         else
             k_pieces_next<<<blocks, 128, 0, s>>>(nxt, off_prev, off_new, nb, cur);
         ZK_LAUNCHED();
@@ -462,18 +510,17 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStr
         off_prev = off_new;
         cap = cap / kPiece + nb + 1;
     }
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, (const Affine *)tab->buf.p, nxt,
-                                                      off_prev, nb, rounds == 0 ? 1 : 0, buckets);
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, dj, nxt, off_prev, nb, rounds == 0 ? 1 : 0,
+                                                      buckets);
     ZK_LAUNCHED();
-
     ph_accum.end();
 
     // 4-5: bucket reduction and output.
     PhaseScope ph_reduce(ctx, ZK_PHASE_MSM_REDUCE, s);
-    dim3 g(nblk, (unsigned)count);
-    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, B, bval, bsum);
+    dim3 g(maxblk, (unsigned)count);
+    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, dj, bval, bsum);
     ZK_LAUNCHED();
-    k_reduce_final<<<(unsigned)count, 32, 0, s>>>(bval, bsum, nblk, dj);
+    k_reduce_final<<<(unsigned)count, 32, 0, s>>>(bval, bsum, dj);
     ZK_LAUNCHED();
     return ZK_OK;
 }
@@ -504,11 +551,12 @@ constexpr uint32_t kNoAllocW = (kScalarBits + kNoAllocC - 1) / kNoAllocC;
 constexpr size_t kNoAllocEntries = (size_t)kNoAllocMaxN * kNoAllocW;
 constexpr size_t kNoAllocPieces = kNoAllocEntries / kPiece + kNoAllocB + 1;
 constexpr size_t kNoAllocBlk = kNoAllocB / kRedSpan;
+constexpr size_t kNoAllocPre = 256;  // one prefix array of the job table
 
 constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 // Workspace layout (byte offsets).
-constexpr size_t kNaJobs = 0;                                          // 3 x 256 B
-constexpr size_t kNaCounts = kNaJobs + 3 * 256;
+constexpr size_t kNaJobs = 0;                                          // JobDesc + 3 prefixes
+constexpr size_t kNaCounts = kNaJobs + 256 + 3 * kNoAllocPre;
 constexpr size_t kNaOff0 = kNaCounts + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaOffA = kNaOff0 + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaOffB = kNaOffA + na_align((kNoAllocB + 1) * 4);
@@ -547,15 +595,26 @@ int noalloc_workspace(int device, unsigned char **out) {
     return ZK_OK;
 }
 
-// Writes the one-job table (scalars pointer, length prefix, output) that the
-// recode kernels read, without a host-to-device copy.
-__global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint32_t n, void *out) {
+// Writes the one-job table (descriptor and prefix arrays) that the MSM
+// kernels read, without a host-to-device copy.
+__global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint32_t n, void *out,
+                               const Affine *table) {
     if (threadIdx.x || blockIdx.x) return;
-    reinterpret_cast<const uint32_t **>(ws + kNaJobs)[0] = scalars;
-    uint32_t *base = reinterpret_cast<uint32_t *>(ws + kNaJobs + 256);
-    base[0] = 0;
-    base[1] = n;
-    reinterpret_cast<void **>(ws + kNaJobs + 512)[0] = out;
+    JobDesc *d = reinterpret_cast<JobDesc *>(ws + kNaJobs);
+    d->scalars = scalars;
+    d->out = out;
+    d->table = table;
+    d->n = n;
+    d->logB = kNoAllocC - 1;
+    uint32_t *sb = reinterpret_cast<uint32_t *>(ws + kNaJobs + 256);
+    uint32_t *bb = sb + kNoAllocPre / 4;
+    uint32_t *kb = bb + kNoAllocPre / 4;
+    sb[0] = 0;
+    sb[1] = n;
+    bb[0] = 0;
+    bb[1] = kNoAllocB;
+    kb[0] = 0;
+    kb[1] = (uint32_t)kNoAllocBlk;
 }
 
 }  // namespace
@@ -607,21 +666,25 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     Xyzz *bsum = (Xyzz *)(ws + kNaBsum);
     void *scan_tmp = ws + kNaScan;
 
-    k_noalloc_jobs<<<1, 1, 0, s>>>(ws, (const uint32_t *)coeffs, (uint32_t)n, out);
+    k_noalloc_jobs<<<1, 1, 0, s>>>(ws, (const uint32_t *)coeffs, (uint32_t)n, out,
+                                   (const Affine *)tab->buf.p);
     ZK_LAUNCHED();
     DevJobs dj;
-    dj.scalars = (const uint32_t *const *)(ws + kNaJobs);
-    dj.base = (const uint32_t *)(ws + kNaJobs + 256);
-    dj.out = (void *const *)(ws + kNaJobs + 512);
+    dj.jobs = (const JobDesc *)(ws + kNaJobs);
+    dj.sbase = (const uint32_t *)(ws + kNaJobs + 256);
+    dj.bbase = dj.sbase + kNoAllocPre / 4;
+    dj.kbase = dj.bbase + kNoAllocPre / 4;
     dj.count = 1;
     const uint32_t total = (uint32_t)n;
     // The workspace keeps the previous call's contents: the histogram must
     // start at zero; every other region is fully written before it is read.
     ZK_CUDA_TRY(cudaMemsetAsync(counts, 0, (nb + 1) * 4, s));
-    ZK_TRY(launch_recode<kNoAllocC>(dj, total, (uint32_t)tab->n, counts, nullptr, nullptr, false, s));
+    ZK_TRY((launch_recode_c<kNoAllocC, false>(dj, 0, 1, total, (uint32_t)tab->n, counts, nullptr,
+                                               nullptr, s)));
     ZK_TRY(scan_exclusive(counts, off0, nb, 0, scan_tmp, s));
     ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
-    ZK_TRY(launch_recode<kNoAllocC>(dj, total, (uint32_t)tab->n, nullptr, cursor, sorted, true, s));
+    ZK_TRY((launch_recode_c<kNoAllocC, true>(dj, 0, 1, total, (uint32_t)tab->n, nullptr, cursor,
+                                              sorted, s)));
     int rounds = 0;
     for (size_t m = (size_t)n * kNoAllocW; m > (size_t)kPiece; m = (m + kPiece - 1) / kPiece) rounds++;
     const uint32_t *off_prev = off0;
@@ -632,8 +695,7 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
         ZK_TRY(scan_exclusive(off_prev, off_new, nb, kPiece, scan_tmp, s));
         unsigned blocks = (unsigned)((cap + 127) / 128);
         if (rd == 0)
-            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb,
-                                                  (const Affine *)tab->buf.p, cur);
+            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb, dj, cur);
         else
             k_pieces_next<<<blocks, 128, 0, s>>>(nxt, off_prev, off_new, nb, cur);
         ZK_LAUNCHED();
@@ -641,13 +703,13 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
         off_prev = off_new;
         cap = cap / kPiece + nb + 1;
     }
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, (const Affine *)tab->buf.p, nxt,
-                                                      off_prev, nb, rounds == 0 ? 1 : 0, buckets);
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, dj, nxt, off_prev, nb,
+                                                      rounds == 0 ? 1 : 0, buckets);
     ZK_LAUNCHED();
     dim3 g((unsigned)kNoAllocBlk, 1);
-    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, nb, bval, bsum);
+    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, dj, bval, bsum);
     ZK_LAUNCHED();
-    k_reduce_final<<<1, 32, 0, s>>>(bval, bsum, (uint32_t)kNoAllocBlk, dj);
+    k_reduce_final<<<1, 32, 0, s>>>(bval, bsum, dj);
     ZK_LAUNCHED();
     return ZK_OK;
 }

@@ -2,12 +2,12 @@
 // witness vector of evaluations over H = <omega_n> into coefficients, paper
 // Sec. 3 and Sec. 4.4), n = 2^L <= 2^28.
 //
-// Stockham autosort formulation in P = ceil(L / 10) passes of radix R_p = 2^s_p
-// (s_p <= 10): pass p computes, for each of the n / R sub-transforms j,
+// Stockham autosort formulation in P = ceil(L / m) passes of radix R_p = 2^s_p
+// (s_p <= m, m = 10 unless tuned, at most 11): pass p computes, for each of the n / R sub-transforms j,
 //   v_r = x[j + r n/R] * omega_{Ns R}^{r (j mod Ns)},  r < R,
 //   V   = R-point DFT of v,
 //   y[(j / Ns) Ns R + (j mod Ns) + r Ns] = V_r,
-// with Ns = prod_{p' < p} R_p'.  A CTA stages J = min(4, n/R) consecutive
+// with Ns = prod_{p' < p} R_p'.  A CTA stages J = min(4, n/R, 4096/R) consecutive
 // sub-transforms (J R elements, up to 128 KiB) in shared memory in a
 // limb-planar, sub-transform-interleaved layout (word l of element r of
 // sub-transform jj at l J R + r J + jj, so consecutive threads touch
@@ -31,8 +31,10 @@ namespace zk {
 
 namespace {
 
-constexpr int kMaxRadixLog = 10;
+constexpr int kDefaultRadixLog = 10;  // largest pass radix unless tuned
+constexpr int kMaxRadixLog = 11;
 constexpr int kMaxJ = 4;
+constexpr size_t kMaxSmem = (size_t)128 << 10;  // J R 32 bytes per CTA
 
 // w = 5^((r - 1) / 2^lg), the primitive 2^lg-th root of unity (5 generates
 // the 2-Sylow subgroup of F_r^*: it is a quadratic non-residue).
@@ -169,11 +171,11 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     }
 }
 
-// Radix split of L into passes of at most kMaxRadixLog.
-std::vector<int> plan_passes(int L) {
+// Radix split of L into the fewest passes of at most maxlog, as even as possible.
+std::vector<int> plan_passes(int L, int maxlog) {
     std::vector<int> s;
     if (L == 0) return s;
-    int P = (L + kMaxRadixLog - 1) / kMaxRadixLog;
+    int P = (L + maxlog - 1) / maxlog;
     for (int p = 0; p < P; p++) s.push_back(L / P + (p < L % P ? 1 : 0));
     return s;
 }
@@ -210,13 +212,20 @@ int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
     return ZK_OK;
 }
 
+static int radix_for(const Shared &sh, int L) {
+    int r = sh.tuned_radix[L];
+    return (r >= 1 && r <= kMaxRadixLog) ? r : kDefaultRadixLog;
+}
+
 // Workspace of one group: ping-pong buffers and per-pass pointer tables.
-static size_t group_buf_bytes(size_t count, size_t n) {
-    int P = (int)plan_passes(ilog2(n)).size();
+static size_t group_buf_bytes(const Shared &sh, size_t count, size_t n) {
+    int L = ilog2(n);
+    int P = (int)plan_passes(L, radix_for(sh, L)).size();
     return P > 1 ? (size_t)(P > 2 ? 2 : 1) * count * n * 32 : 0;
 }
-static size_t group_tab_words(size_t count, size_t n) {
-    return plan_passes(ilog2(n)).size() * 2 * count;
+static size_t group_tab_words(const Shared &sh, size_t count, size_t n) {
+    int L = ilog2(n);
+    return plan_passes(L, radix_for(sh, L)).size() * 2 * count;
 }
 
 // Runs every pass for `count` vectors of the same length n.  `buf` and
@@ -225,7 +234,7 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
                      uint32_t *buf, uint64_t *tabs, cudaStream_t s) {
     const int L = ilog2(n);
     if (L == 0) return ZK_OK;  // a length-1 transform is the identity
-    std::vector<int> passes = plan_passes(L);
+    std::vector<int> passes = plan_passes(L, radix_for(*ctx->sh, L));
     const int P = (int)passes.size();
     const size_t tab_words = 2 * count;
     std::vector<uint64_t> h((size_t)P * tab_words);
@@ -255,7 +264,8 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         a.logR = (uint32_t)logR;
         a.logNs = (uint32_t)logNs;
         const uint64_t subs = (uint64_t)n >> logR;
-        a.J = (uint32_t)std::min<uint64_t>(kMaxJ, subs);
+        a.J = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(kMaxJ, subs),
+                                           kMaxSmem / ((size_t)32 << logR));
         a.tw_n = (const Fr *)tw_n;
         a.tw_R = (const Fr *)tw_R;
         a.inverse = inverse ? 1 : 0;
@@ -266,7 +276,7 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         static bool attr_set = false;
         if (!attr_set) {
             ZK_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((size_t)kMaxJ << kMaxRadixLog) * 32));
+                                             (int)kMaxSmem));
             attr_set = true;
         }
         dim3 grid((unsigned)(subs / a.J), (unsigned)count);
@@ -297,8 +307,8 @@ int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_
     // while an earlier group's passes are still queued.
     size_t buf_bytes = 0, tab_words = 0;
     for (auto &g : groups) {
-        buf_bytes += group_buf_bytes(g.second.size(), g.first);
-        tab_words += group_tab_words(g.second.size(), g.first);
+        buf_bytes += group_buf_bytes(*ctx->sh, g.second.size(), g.first);
+        tab_words += group_tab_words(*ctx->sh, g.second.size(), g.first);
     }
     int err = ZK_OK;
     uint32_t *buf = nullptr;
@@ -310,8 +320,8 @@ int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_
     if (!tabs) return err;
     for (auto &g : groups) {
         ZK_TRY(ntt_group(ctx, g.second.data(), g.second.size(), g.first, inverse, buf, tabs, s));
-        buf += group_buf_bytes(g.second.size(), g.first) / 4;
-        tabs += group_tab_words(g.second.size(), g.first);
+        buf += group_buf_bytes(*ctx->sh, g.second.size(), g.first) / 4;
+        tabs += group_tab_words(*ctx->sh, g.second.size(), g.first);
     }
     return ZK_OK;
 }

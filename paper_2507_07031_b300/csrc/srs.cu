@@ -152,9 +152,8 @@ __global__ void k_shift_window(const Affine *__restrict__ src, Xyzz *__restrict_
     dst[i] = p;
 }
 
-int build_table(zk_ctx *ctx, WindowTable &t, int c, cudaStream_t s) {
+int build_table(zk_ctx *ctx, WindowTable &t, int c, size_t n, cudaStream_t s) {
     Shared &sh = *ctx->sh;
-    const size_t n = sh.srs_n;
     const int W = windows_for(c);
     ZK_TRY(dev_alloc(sh, t.buf, (size_t)W * n * sizeof(Affine)));
     t.c = c;
@@ -195,8 +194,14 @@ int table_get(zk_ctx *ctx, int c, size_t n, const WindowTable **out, cudaStream_
             return ZK_OK;
         }
     }
+    // A table covers the next power of two of the request (at most the SRS);
+    // a smaller table of the same width stays alive for work still queued.
+    size_t tn = 1;
+    while (tn < n) tn <<= 1;
+    tn = std::min(tn, sh.srs_n);
+    if ((size_t)windows_for(c) * tn >= ((size_t)1 << 31)) return ZK_EINVAL;
     sh.tables.emplace_back();
-    int r = build_table(ctx, sh.tables.back(), c, s);
+    int r = build_table(ctx, sh.tables.back(), c, tn, s);
     if (r != ZK_OK) {
         dev_free(sh, sh.tables.back().buf);
         sh.tables.pop_back();

@@ -154,3 +154,33 @@ def test_big_srs_samples(zk, orc, ctx_big, tau):
     rng = np.random.default_rng(0)
     for i in [0, 1, 2, n - 1] + rng.integers(0, n, 16).tolist():
         assert pts_equal(pts[i], orc.g1_mul(G, Z.int_to_fr(pow(t, int(i), R)))), i
+
+
+@pytest.fixture(scope="module")
+def window_case(tau):
+    c = Z.fr_uniform(77, 4096)
+    return c
+
+
+@pytest.mark.parametrize("c", list(range(9, 21)))
+def test_msm_every_window_width(zk, orc, ctx_small, tau, window_case, c):
+    try:
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_MSM_WINDOW, 12, c)
+        got = _commit(zk, ctx_small, window_case)
+    finally:
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_MSM_WINDOW, 12, 0)
+    assert pts_equal(got, orc.commit_coeffs_tau(window_case, tau))
+
+
+def test_autotune_table(zk, ctx_small, tmp_path):
+    from paper_2507_07031_b300 import autotune
+    path = str(tmp_path / "tune.json")
+    table = autotune.tune(ctx_small, msm_logs=[10, 12], ntt_logs=[10, 12], reps=1,
+                          windows=range(10, 14), radices=range(5, 12), path=path)
+    assert set(table["msm_window"]) == {"10", "12"} and set(table["ntt_radix"]) == {"10", "12"}
+    for lg, e in table["msm_window"].items():
+        assert zk.zk_tune_get(ctx_small, zk.ZK_TUNE_MSM_WINDOW, int(lg)) == e["best"]
+    autotune.apply(ctx_small, path)
+    for lg in (10, 12):
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_MSM_WINDOW, lg, 0)
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, lg, 0)

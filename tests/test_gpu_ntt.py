@@ -68,3 +68,33 @@ def test_ntt_rejects_bad_sizes(zk, ctx_small):
     assert ei.value.code == zk.ZK_EINVAL
     with pytest.raises(zk.ZkError):
         zk.zk_ntt(ctx_small, t, n=1 << 29)
+
+
+@pytest.fixture(scope="module")
+def ntt_case_2_11(orc):
+    x = Z.fr_uniform(801, 1 << 11)
+    return x, orc.ntt(x), orc.intt(x)
+
+
+@pytest.mark.parametrize("radix", list(range(1, 12)))
+def test_ntt_every_pass_radix(zk, ctx_small, ntt_case_2_11, radix):
+    x, f, b = ntt_case_2_11
+    try:
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, 11, radix)
+        assert np.array_equal(_run(zk, ctx_small, x, False), f)
+        assert np.array_equal(_run(zk, ctx_small, x, True), b)
+    finally:
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, 11, 0)
+
+
+def test_ntt_two_pass_radix_2_11_at_2_22(zk, orc, ctx_small):
+    n = 1 << 22
+    x = Z.fr_uniform(802, n)
+    rows = np.array([0, 1, 12345, n - 1])
+    try:
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, 22, 11)
+        f = _run(zk, ctx_small, x, False)
+        assert np.array_equal(f[rows], orc.dft_rows(x, rows, False))
+        assert np.array_equal(_run(zk, ctx_small, f, True), x)
+    finally:
+        zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, 22, 0)
