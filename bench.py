@@ -312,13 +312,17 @@ def main():
     # Roofline of the dominant kernel class: MSM bucket accumulation.
     imad_peak, fq_mul_peak = zk.zk_probe_rates(local)
     acc_ms, acc_cnt = phases["msm_accum"]
-    W = 16
-    # Mixed additions per step: W nonzero digits per uniform scalar, one per
-    # recentred int8 * 2^16 scalar (its only nonzero 16-bit window).
-    madds = (n20 * W + n20 * 1) * args.steps
+    c = zk.zk_tune_get(ctx, zk.ZK_TUNE_MSM_WINDOW, 20)
+    W = -(-254 // c)
+    # Mixed additions per step: W nonzero digits per uniform scalar; a
+    # recentred int8 * 2^16 scalar has |q| 2^16 < 2^23, i.e. its nonzero bits
+    # fall into 1 window (c >= 16, window-aligned) or 2 (c = 17 splits bit 16).
+    q_digits = 1 if (c == 16 or 16 % c == 0) else 2
+    madds = (n20 * W + n20 * q_digits) * args.steps
     achieved = madds * FQ_MUL_PER_MADD * IMAD_PER_MUL / (acc_ms * 1e-3) / 1e12 if acc_ms else None
     roofline = {
         "bound": "alu", "kernel": "k_pieces_first/k_pieces_next/k_buckets_final (MSM accumulation)",
+        "window_c": c,
         "achieved": achieved, "peak": imad_peak / 1e12, "unit": "TIMAD/s",
         "frac": (achieved / (imad_peak / 1e12)) if achieved else None,
         "peak_source": "measured live: independent 32-bit mad.lo issue rate (zk_probe_rates)",
@@ -392,11 +396,17 @@ def run_extras(zk, ctx, dev, torch):
     for f in (batched, plain):
         f()
     torch.cuda.synchronize()
+    zk.zk_timing_read(ctx)
+    zk.zk_timing_enable(ctx, True)
     tb = _time(torch, batched, 3)
+    ph_b = {k: round(v[0] / 3, 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
     tp = _time(torch, plain, 3)
+    ph_p = {k: round(v[0] / 3, 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
+    zk.zk_timing_enable(ctx, False)
     res["cnn_batch_commit"] = {"polys": len(vecs), "coeffs": int(sizes.sum()),
                                "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb,
-                               "identical": bool(torch.equal(outb, outp))}
+                               "identical": bool(torch.equal(outb, outp)),
+                               "batched_phase_ms": ph_b, "plain_phase_ms": ph_p}
     del vecs
     # Fold tree: 1024 leaves of 2^16 (config: matmul block, 4 witness vectors).
     count, n = 1024, 1 << 16
@@ -442,7 +452,11 @@ def run_extras(zk, ctx, dev, torch):
     tree()  # warm-up (sizes workspaces)
     restore()
     torch.cuda.synchronize()
+    zk.zk_timing_read(ctx)
+    zk.zk_timing_enable(ctx, True)
     tt = _time(torch, tree, 1)
+    ph_tree = {k: round(v[0], 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
+    zk.zk_timing_enable(ctx, False)
     root_batched = [r.clone() for r in root]
     restore()
     plain_tree()  # warm-up
@@ -454,7 +468,8 @@ def run_extras(zk, ctx, dev, torch):
                         "batched_folds_per_s": (count - 1) / (tt * 1e-3),
                         "plain_folds_per_s": (count - 1) / (tp * 1e-3),
                         "batched_ms": tt, "plain_ms": tp, "speedup": tp / tt,
-                        "leaf_commit_ms": t_leaf, "identical": bool(same)}
+                        "leaf_commit_ms": t_leaf, "identical": bool(same),
+                        "batched_phase_ms": ph_tree}
     return res
 
 

@@ -191,8 +191,9 @@ int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas,
  * length).  op = ZK_TUNE_MSM_WINDOW: value = window width c in [9, 20] for
  * MSMs of length in (2^(log2n-1), 2^log2n]; op = ZK_TUNE_NTT_RADIX: value =
  * log2 of the largest pass radix in [1, 11] for transforms of length 2^log2n.
- * value 0 restores the built-in choice (a cost model for the window; radix
- * 2^10).  zk_tune_measure times one candidate on synthetic device data (median
+ * value 0 restores the built-in choice (the winners of a tuning sweep on
+ * B300); zk_tune_get returns the value in effect (tuned or built-in).
+ * zk_tune_measure times one candidate on synthetic device data (median
  * of `reps` runs, ms) without changing the setting; the first use of a new
  * window width builds its window table (about W x 64 bytes per SRS point).
  * paper_2507_07031_b300/autotune.py sweeps the candidates and stores the

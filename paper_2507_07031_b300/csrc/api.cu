@@ -204,9 +204,8 @@ int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value) {
 
 int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value) {
     if (!ctx || !value || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
-    const Shared &sh = *ctx->sh;
-    if (op == ZK_TUNE_MSM_WINDOW) *value = sh.tuned_window[log2n];
-    else if (op == ZK_TUNE_NTT_RADIX) *value = sh.tuned_radix[log2n];
+    if (op == ZK_TUNE_MSM_WINDOW) *value = msm_pick_window(const_cast<zk_ctx *>(ctx), (size_t)1 << log2n, 1);
+    else if (op == ZK_TUNE_NTT_RADIX) *value = ntt_pass_radix(*ctx->sh, log2n);
     else return ZK_EINVAL;
     return ZK_OK;
 }

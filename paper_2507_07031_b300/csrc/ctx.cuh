@@ -46,8 +46,8 @@ struct Shared {
     DevBuf srs;  // affine Montgomery, srs_n points
     std::deque<WindowTable> tables;  // deque: references stay valid as tables are added
     DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg
-    int tuned_window[29] = {};   // MSM window width per log2 length (0 = cost model)
-    int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = default)
+    int tuned_window[29] = {};   // MSM window width per log2 length (0 = built-in)
+    int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = built-in)
     ~Shared();
 };
 
@@ -148,6 +148,7 @@ int ntt_impl(zk_ctx *ctx, uint32_t *data, size_t n, bool inverse, cudaStream_t s
 int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_t count,
                    bool inverse, cudaStream_t s);
 int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s);
+int ntt_pass_radix(const Shared &sh, int L);  // tuned or built-in largest pass radix (log2)
 
 // MSM (msm.cu).  Each job: scalars (device, canonical, 32 B each), length n,
 // output 64-byte canonical affine point (device).  c > 0 fixes the window

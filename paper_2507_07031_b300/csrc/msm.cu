@@ -277,34 +277,71 @@ __global__ void __launch_bounds__(kRedThreads)
     }
 }
 
-// Phase 4b + 5: one warp per MSM: total = sum_k val_k + kRedSpan sum_k k sum_k.
-__global__ void k_reduce_final(const Xyzz *__restrict__ blk_val, const Xyzz *__restrict__ blk_sum,
-                               DevJobs dj) {
+// Phase 4b + 5: one block of kFinThreads per MSM combines the block results:
+// total = sum_k val_k + kRedSpan sum_k k sum_k, with sum_k k sum_k equal to
+// sum_{j >= 1} suffix_j (suffix sums of sum_k).  Every thread holds at most
+// kFinPer blocks, so the serial depth is a few additions plus two block-wide
+// scans (each point addition is a chain of dependent products: depth, not
+// work, bounds this phase).
+constexpr int kFinThreads = 256;
+
+__device__ __forceinline__ Xyzz block_sum(Xyzz x, Xyzz *sh) {
+    const uint32_t warp = threadIdx.x >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane_id() == 0) sh[warp] = x;
+    __syncthreads();
+    Xyzz r = xyzz_inf();
+    if (warp == 0) {
+        r = lane_id() < kFinThreads / 32 ? sh[lane_id()] : xyzz_inf();
+#pragma unroll
+        for (int d = 4; d >= 1; d >>= 1) r = xyzz_add(r, shfl_down_pt(r, d));
+    }
+    return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+    k_reduce_final(const Xyzz *__restrict__ blk_val, const Xyzz *__restrict__ blk_sum, DevJobs dj) {
+    __shared__ Xyzz sh[kFinThreads / 32];
     const uint32_t job = blockIdx.x;
-    const uint32_t l = lane_id();
+    const uint32_t t = threadIdx.x;
     const uint32_t nblk = dj.kbase[job + 1] - dj.kbase[job];
-    const uint32_t q = nblk >= 32 ? nblk / 32 : 1;  // blocks per lane (power of two)
+    const uint32_t q = (nblk + kFinThreads - 1) / kFinThreads;  // blocks per thread
     const Xyzz *V = blk_val + dj.kbase[job];
     const Xyzz *Sm = blk_sum + dj.kbase[job];
+    // Thread t owns blocks [t q, t q + q): lv = sum val, ls = sum sum,
+    // lw = sum_k (k - t q) sum_k.
     Xyzz lv = xyzz_inf(), lw = xyzz_inf(), ls = xyzz_inf();
-    uint32_t lo = l * q, hi = min(lo + q, nblk);
-    // lw = sum_k (k - lo) sum_k over the lane's blocks, by a running sum from the top
+    const uint32_t lo = t * q, hi = min(lo + q, nblk);
     for (uint32_t k = hi; k-- > lo;) {
         lv = xyzz_add(lv, V[k]);
         ls = xyzz_add(ls, Sm[k]);
         if (k > lo) lw = xyzz_add(lw, ls);
     }
-    // sum_k k sum_k = sum_l lw_l + q sum_l l ls_l, and sum_l l ls_l = sum_{l >= 1} suffix_l
-    Xyzz suf = warp_suffix(ls);
+    // Block suffix sums of ls: sum_k k sum_k = sum_t lw_t + q sum_{t >= 1} suffix_t.
+    Xyzz x = warp_suffix(ls);
+    const uint32_t warp = t >> 5;
+    if (lane_id() == 0) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {  // exclusive suffix over the warp totals
+        Xyzz w = lane_id() < kFinThreads / 32 ? sh[lane_id()] : xyzz_inf();
+        Xyzz inc = warp_suffix(w);
+        Xyzz exc = shfl_down_pt(inc, 1);
+        if (lane_id() + 1 >= kFinThreads / 32) exc = xyzz_inf();
+        __syncwarp();
+        if (lane_id() < kFinThreads / 32) sh[lane_id()] = exc;
+    }
+    __syncthreads();
+    x = xyzz_add(x, sh[warp]);
     Xyzz term = lw;
-    if (l >= 1) {
-        Xyzz qs = suf;
-        for (uint32_t m = q; m > 1; m >>= 1) qs = xyzz_dbl(qs);
+    if (t >= 1) {
+        Xyzz qs = x;
+        for (uint32_t m = q; m > 1; m >>= 1) qs = xyzz_dbl(qs);  // q is a power of two
         term = xyzz_add(term, qs);
     }
-    Xyzz wsum = warp_sum(term);
-    Xyzz vsum = warp_sum(lv);
-    if (l == 0) {
+    Xyzz wsum = block_sum(term, sh);
+    Xyzz vsum = block_sum(lv, sh);
+    if (t == 0) {
         Xyzz tot = wsum;
         for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl(tot);  // x kRedSpan
         tot = xyzz_add(tot, vsum);
@@ -339,19 +376,19 @@ int recode(int c, const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscalars
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Cost model used when no tuned window is recorded: mixed additions n W(c)
-// plus about 2.8 addition-equivalents per bucket for the reduction.
-int model_window(size_t n) {
-    int best = 16;
-    double best_cost = 1e300;
-    for (int c = kMinWindow; c <= kMaxWindow; c++) {
-        double cost = (double)n * windows_for(c) + 2.8 * (double)(1u << (c - 1));
-        if (cost < best_cost) {
-            best_cost = cost;
-            best = c;
-        }
-    }
-    return best;
+// Built-in window width per log2 length when no tuned value is recorded:
+// the fastest widths of an autotuner sweep on B300 (single MSMs of uniform
+// scalars, 2^10 .. 2^22).  Wider windows cut mixed additions (n ceil(254/c))
+// but the bucket reduction's serial depth grows with the bucket count.
+int default_window(size_t n) {
+    int lg = 0;
+    while (((size_t)1 << lg) < n) lg++;
+    if (lg <= 10) return 10;
+    if (lg <= 11) return 12;
+    if (lg <= 13) return 13;
+    if (lg <= 18) return 15;
+    if (lg <= 19) return 16;
+    return 17;
 }
 
 }  // namespace
@@ -362,7 +399,7 @@ int msm_pick_window(zk_ctx *ctx, size_t n, size_t count) {
     while (((size_t)1 << lg) < n) lg++;
     const Shared &sh = *ctx->sh;
     if (lg <= kMaxLogN && sh.tuned_window[lg]) return sh.tuned_window[lg];
-    return model_window(n);
+    return default_window(n);
 }
 
 int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed, cudaStream_t s) {
@@ -520,7 +557,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     dim3 g(maxblk, (unsigned)count);
     k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, dj, bval, bsum);
     ZK_LAUNCHED();
-    k_reduce_final<<<(unsigned)count, 32, 0, s>>>(bval, bsum, dj);
+    k_reduce_final<<<(unsigned)count, kFinThreads, 0, s>>>(bval, bsum, dj);
     ZK_LAUNCHED();
     return ZK_OK;
 }
@@ -709,7 +746,7 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     dim3 g((unsigned)kNoAllocBlk, 1);
     k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, dj, bval, bsum);
     ZK_LAUNCHED();
-    k_reduce_final<<<1, 32, 0, s>>>(bval, bsum, dj);
+    k_reduce_final<<<1, kFinThreads, 0, s>>>(bval, bsum, dj);
     ZK_LAUNCHED();
     return ZK_OK;
 }

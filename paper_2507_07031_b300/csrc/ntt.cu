@@ -3,7 +3,7 @@
 // Sec. 3 and Sec. 4.4), n = 2^L <= 2^28.
 //
 // Stockham autosort formulation in P = ceil(L / m) passes of radix R_p = 2^s_p
-// (s_p <= m, m = 10 unless tuned, at most 11): pass p computes, for each of the n / R sub-transforms j,
+// (s_p <= m; m is tuned per length, at most 11): pass p computes, for each of the n / R sub-transforms j,
 //   v_r = x[j + r n/R] * omega_{Ns R}^{r (j mod Ns)},  r < R,
 //   V   = R-point DFT of v,
 //   y[(j / Ns) Ns R + (j mod Ns) + r Ns] = V_r,
@@ -31,7 +31,6 @@ namespace zk {
 
 namespace {
 
-constexpr int kDefaultRadixLog = 10;  // largest pass radix unless tuned
 constexpr int kMaxRadixLog = 11;
 constexpr int kMaxJ = 4;
 constexpr size_t kMaxSmem = (size_t)128 << 10;  // J R 32 bytes per CTA
@@ -212,10 +211,22 @@ int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
     return ZK_OK;
 }
 
+// Built-in largest pass radix (log2) when none is tuned: the fastest choices
+// of an autotuner sweep on B300.  Smaller radices mean more passes but smaller
+// CTAs (more resident per SM, fewer block-wide barriers per element).
+static int default_radix(int L) {
+    if (L <= 9) return L ? L : 1;
+    if (L <= 16) return 6;
+    if (L <= 21) return 8;
+    return 6;
+}
+
 static int radix_for(const Shared &sh, int L) {
     int r = sh.tuned_radix[L];
-    return (r >= 1 && r <= kMaxRadixLog) ? r : kDefaultRadixLog;
+    return (r >= 1 && r <= kMaxRadixLog) ? r : default_radix(L);
 }
+
+int ntt_pass_radix(const Shared &sh, int L) { return radix_for(sh, L); }
 
 // Workspace of one group: ping-pong buffers and per-pass pointer tables.
 static size_t group_buf_bytes(const Shared &sh, size_t count, size_t n) {
