@@ -204,6 +204,70 @@ int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value);
 int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value);
 int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double *ms);
 
+/* Plans: a batched commitment or a fold tree captured once as a CUDA graph
+ * and replayed with a single launch.  Every buffer must be a DEVICE pointer
+ * (ZK_EINVAL otherwise) and stay valid, with the same shape, for the plan's
+ * life; the inputs' contents may change between launches.  Creating a plan
+ * synchronises the device, then runs the operation once (a warm-up that sizes
+ * the plan's private workspace and builds the tables it needs), so it also
+ * produces the result once.  A
+ * plan holds a lane of `ctx` (its own workspace, shared SRS tables): it must
+ * be destroyed before `ctx`, and reloading the SRS invalidates it.
+ * zk_plan_launch enqueues the graph on `stream`; zk_plan_nodes reports the
+ * graph's node count (kernels and copies). */
+typedef struct zk_plan zk_plan;
+int zk_plan_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, size_t count,
+                         unsigned flags, zk_g1 *out, zk_plan **plan);
+int zk_plan_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas,
+                      zk_acc *root, zk_plan **plan);
+int zk_plan_launch(zk_plan *plan, zk_stream stream);
+int zk_plan_nodes(const zk_plan *plan, size_t *nodes);
+int zk_plan_destroy(zk_plan *plan);
+
+/* Serving loop with continuous batching.  A job commits to one basic-block
+ * witness as a NARK leaf accumulator (INTT + MSM of each vector; Sec. 4.2:
+ * a NARK proof is the accumulator with mu = 1, e = 0) and, if acc_in is set,
+ * folds it into that resident accumulator: *acc_out = fold(*acc_in, *leaf,
+ * gamma).  Jobs are admitted in arrival order as soon as one of the server's
+ * lanes (private workspace + CUDA stream) is free and the job's workspace
+ * estimate fits in the unreserved HBM budget; admitted jobs run concurrently.
+ * All pointers in zk_job are DEVICE pointers (gamma may be host) owned by
+ * the caller and untouched by it until the job is done; acc_in is read only,
+ * so many jobs may share it.  zk_submit returns ZK_EBUSY when 65536 jobs
+ * wait, ZK_ENOMEM when one job's estimate exceeds the budget.  zk_wait
+ * returns ZK_ETIMEOUT after timeout_ms.  Times are ms since server creation. */
+typedef struct zk_server zk_server;
+typedef struct {
+    size_t n;               /* witness length, power of two <= SRS size */
+    const zk_fr *w[3];      /* m1, m2, m4 evaluations (device) */
+    zk_acc *leaf;           /* receives the leaf accumulator (device buffers) */
+    const zk_acc *acc_in;   /* resident accumulator to fold into, or NULL */
+    zk_acc *acc_out;        /* receives fold(acc_in, leaf, gamma) */
+    const zk_fr *gamma;     /* fold challenge */
+} zk_job;
+#define ZK_JOB_QUEUED 0
+#define ZK_JOB_RUNNING 1
+#define ZK_JOB_DONE 2
+#define ZK_JOB_FAILED 3
+typedef struct {
+    int status;       /* ZK_JOB_* */
+    int error;        /* ZK_OK or the failing call's code */
+    int lane;
+    double submit_ms, start_ms, end_ms;
+} zk_ticket_info;
+typedef struct {
+    unsigned long long completed;
+    size_t queued;
+    size_t reserved_bytes, peak_reserved_bytes;
+    int busy_lanes;
+} zk_server_info;
+int zk_server_create(zk_ctx *ctx, int lanes, size_t hbm_budget_bytes, zk_server **out);
+int zk_submit(zk_server *srv, const zk_job *job, uint64_t *ticket);
+int zk_poll(zk_server *srv, uint64_t ticket, zk_ticket_info *info);
+int zk_wait(zk_server *srv, uint64_t ticket, int timeout_ms, zk_ticket_info *info);
+int zk_server_stats(zk_server *srv, zk_server_info *info);
+int zk_server_destroy(zk_server *srv);
+
 /* Static description of an error code. */
 const char *zk_strerror(int code);
 

@@ -33,6 +33,26 @@ class ZkAcc(ctypes.Structure):
                 ("x", ctypes.c_void_p)]
 
 
+class ZkJob(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_size_t), ("w", ctypes.c_void_p * 3), ("leaf", ctypes.c_void_p),
+                ("acc_in", ctypes.c_void_p), ("acc_out", ctypes.c_void_p), ("gamma", ctypes.c_void_p)]
+
+
+class ZkTicketInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("lane", ctypes.c_int),
+                ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double)]
+
+
+class ZkServerInfo(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_ulonglong), ("queued", ctypes.c_size_t),
+                ("reserved_bytes", ctypes.c_size_t), ("peak_reserved_bytes", ctypes.c_size_t),
+                ("busy_lanes", ctypes.c_int)]
+
+
+ZK_JOB_QUEUED, ZK_JOB_RUNNING, ZK_JOB_DONE, ZK_JOB_FAILED = range(4)
+
+
 _VP = ctypes.c_void_p
 _SZ = ctypes.c_size_t
 _SZP = ctypes.POINTER(ctypes.c_size_t)
@@ -62,6 +82,17 @@ def _load():
         "zk_fold_tree": [_VP, _VP, _SZ, _VP, _VP, _VP],
         "zk_timing_enable": [_VP, ctypes.c_int],
         "zk_tune_set": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "zk_plan_commit_batch": [_VP, _VP, _VP, _SZ, ctypes.c_uint, _VP, ctypes.POINTER(_VP)],
+        "zk_plan_fold_tree": [_VP, _VP, _SZ, _VP, _VP, ctypes.POINTER(_VP)],
+        "zk_plan_launch": [_VP, _VP],
+        "zk_plan_nodes": [_VP, _SZP],
+        "zk_plan_destroy": [_VP],
+        "zk_server_create": [_VP, ctypes.c_int, _SZ, ctypes.POINTER(_VP)],
+        "zk_submit": [_VP, _VP, ctypes.POINTER(ctypes.c_uint64)],
+        "zk_poll": [_VP, ctypes.c_uint64, _VP],
+        "zk_wait": [_VP, ctypes.c_uint64, ctypes.c_int, _VP],
+        "zk_server_stats": [_VP, _VP],
+        "zk_server_destroy": [_VP],
         "zk_tune_get": [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "zk_tune_measure": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_double)],
@@ -87,7 +118,10 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_noalloc", "zk_commit_batch", "zk_ntt", "zk_intt",
             "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_strerror",
             "zk_kernel_launches", "zk_probe_rates", "zk_timing_enable", "zk_timing_read",
-            "zk_tune_set", "zk_tune_get", "zk_tune_measure"]
+            "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
+            "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
+            "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
+            "zk_server_destroy"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 
@@ -253,6 +287,87 @@ def zk_ntt_batch(ctx: int, vecs, inverse: bool, stream=None) -> None:
     ptrs = (ctypes.c_void_p * max(count, 1))(*[_ptr(v) for v in vecs])
     ls = (ctypes.c_size_t * max(count, 1))(*[_nelem(v, 4) for v in vecs])
     _check(lib.zk_ntt_batch(ctx, ptrs, ls, count, int(bool(inverse)), _stream(stream)), "zk_ntt_batch")
+
+
+def zk_plan_commit_batch(ctx: int, vecs, out, flags: int = 0, lens=None) -> int:
+    count = len(vecs)
+    ptrs = (ctypes.c_void_p * max(count, 1))(*[_ptr(v) for v in vecs])
+    lens = [(_nelem(v, 4)) for v in vecs] if lens is None else list(lens)
+    ls = (ctypes.c_size_t * max(count, 1))(*lens)
+    h = _VP()
+    _check(lib.zk_plan_commit_batch(ctx, ptrs, ls, count, int(flags), _ptr(out), ctypes.byref(h)),
+           "zk_plan_commit_batch")
+    return h.value
+
+
+def zk_plan_fold_tree(ctx: int, leaves, gammas, root) -> int:
+    arr = (ZkAcc * len(leaves))(*leaves)
+    h = _VP()
+    _check(lib.zk_plan_fold_tree(ctx, arr, len(leaves), _ptr(gammas), ctypes.byref(root), ctypes.byref(h)),
+           "zk_plan_fold_tree")
+    return h.value
+
+
+def zk_plan_launch(plan: int, stream=None) -> None:
+    _check(lib.zk_plan_launch(plan, _stream(stream)), "zk_plan_launch")
+
+
+def zk_plan_nodes(plan: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.zk_plan_nodes(plan, ctypes.byref(n)), "zk_plan_nodes")
+    return n.value
+
+
+def zk_plan_destroy(plan: int) -> None:
+    _check(lib.zk_plan_destroy(plan), "zk_plan_destroy")
+
+
+def zk_server_create(ctx: int, lanes: int = 4, hbm_budget_bytes: int = 0) -> int:
+    h = _VP()
+    _check(lib.zk_server_create(ctx, int(lanes), int(hbm_budget_bytes), ctypes.byref(h)),
+           "zk_server_create")
+    return h.value
+
+
+def make_job(n: int, w, leaf: ZkAcc, acc_in: ZkAcc | None = None, acc_out: ZkAcc | None = None,
+             gamma=None) -> ZkJob:
+    j = ZkJob()
+    j.n = n
+    for i in range(3):
+        j.w[i] = _ptr(w[i])
+    j.leaf = ctypes.addressof(leaf)
+    j.acc_in = ctypes.addressof(acc_in) if acc_in is not None else 0
+    j.acc_out = ctypes.addressof(acc_out) if acc_out is not None else 0
+    j.gamma = _ptr(gamma)
+    return j
+
+
+def zk_submit(srv: int, job: ZkJob) -> int:
+    t = ctypes.c_uint64()
+    _check(lib.zk_submit(srv, ctypes.byref(job), ctypes.byref(t)), "zk_submit")
+    return t.value
+
+
+def zk_poll(srv: int, ticket: int) -> ZkTicketInfo:
+    info = ZkTicketInfo()
+    _check(lib.zk_poll(srv, ticket, ctypes.byref(info)), "zk_poll")
+    return info
+
+
+def zk_wait(srv: int, ticket: int, timeout_ms: int = 60000) -> ZkTicketInfo:
+    info = ZkTicketInfo()
+    _check(lib.zk_wait(srv, ticket, int(timeout_ms), ctypes.byref(info)), "zk_wait")
+    return info
+
+
+def zk_server_stats(srv: int) -> ZkServerInfo:
+    info = ZkServerInfo()
+    _check(lib.zk_server_stats(srv, ctypes.byref(info)), "zk_server_stats")
+    return info
+
+
+def zk_server_destroy(srv: int) -> None:
+    _check(lib.zk_server_destroy(srv), "zk_server_destroy")
 
 
 def make_acc(m, e, x) -> ZkAcc:

@@ -58,6 +58,10 @@ void dev_free(Shared &sh, DevBuf &b) {
 void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err) {
     DevBuf &b = ctx->scratch[name];
     if (b.p && b.bytes >= bytes) return b.p;
+    if (ctx->capturing) {  // a plan's warm-up run sized every buffer already
+        *err = ZK_EINVAL;
+        return nullptr;
+    }
     // Grow by at least 25% so that slowly growing requests do not reallocate
     // (cudaFree waits for the device) on every call.
     size_t want = std::max(bytes, b.bytes + b.bytes / 4);
@@ -71,6 +75,56 @@ void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err) {
         }
     }
     return b.p;
+}
+
+int upload(zk_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    Uploader &u = ctx->up;
+    const size_t b = (bytes + 255) & ~(size_t)255;
+    u.recorded += b;
+    if (ctx->capturing) {
+        if (!u.arena || u.arena_used + b > u.arena_cap) return ZK_EINVAL;
+        char *slot = u.arena + u.arena_used;
+        u.arena_used += b;
+        memcpy(slot, src, bytes);
+        ZK_CUDA_TRY(cudaMemcpyAsync(dst, slot, bytes, cudaMemcpyHostToDevice, s));
+        return ZK_OK;
+    }
+    const size_t kRing = (size_t)8 << 20;
+    if (!u.ring) {
+        if (cudaHostAlloc((void **)&u.ring, kRing, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            u.ring = nullptr;
+        } else {
+            u.cap = kRing;
+        }
+    }
+    if (!u.ring || b > u.cap) {  // no ring or oversized: plain (synchronising) copy
+        ZK_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return ZK_OK;
+    }
+    // Retire finished copies; on wrap-around wait for every older copy (the
+    // new region may overlap any of them).
+    while (!u.inflight.empty() && cudaEventQuery(u.inflight.front().ev) == cudaSuccess) {
+        cudaEventDestroy(u.inflight.front().ev);
+        u.inflight.pop_front();
+    }
+    if (u.head + b > u.cap) {
+        for (auto &r : u.inflight) {
+            cudaEventSynchronize(r.ev);
+            cudaEventDestroy(r.ev);
+        }
+        u.inflight.clear();
+        u.head = 0;
+    }
+    const size_t lo = u.head, hi = u.head + b;
+    memcpy(u.ring + lo, src, bytes);
+    ZK_CUDA_TRY(cudaMemcpyAsync(dst, u.ring + lo, bytes, cudaMemcpyHostToDevice, s));
+    cudaEvent_t ev;
+    ZK_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ZK_CUDA_TRY(cudaEventRecord(ev, s));
+    u.inflight.push_back({lo, hi, ev});
+    u.head = hi;
+    return ZK_OK;
 }
 
 bool is_device_ptr(const void *p) {
@@ -311,6 +365,10 @@ int zk_destroy(zk_ctx *ctx) {
             cudaEventDestroy(m.b);
         }
         ctx->marks.clear();
+        for (auto &r : ctx->up.inflight) cudaEventDestroy(r.ev);
+        ctx->up.inflight.clear();
+        if (ctx->up.ring) cudaFreeHost(ctx->up.ring);
+        ctx->up.ring = nullptr;
         for (auto &kv : ctx->scratch) dev_free(*ctx->sh, kv.second);
         ctx->scratch.clear();
         ctx->sh.reset();  // frees SRS and tables with the last owner

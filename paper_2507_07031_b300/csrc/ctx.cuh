@@ -59,6 +59,26 @@ struct PhaseMark {
     int phase;
     cudaEvent_t a, b;
 };
+
+// Small host-to-device uploads (job tables, pointer tables, descriptors) go
+// through pinned host memory so that they stay asynchronous: a copy from
+// pageable memory would first wait for everything queued on the stream.
+// Normally a ring of pinned memory, reused once the copies that read a region
+// have executed (tracked by events); while a graph is being captured, a
+// bump arena owned by the plan, whose contents the graph's copy nodes read at
+// every replay.
+struct Uploader {
+    char *ring = nullptr;
+    size_t cap = 0, head = 0;
+    struct Region {  // a ring region read by a queued copy
+        size_t lo, hi;
+        cudaEvent_t ev;
+    };
+    std::deque<Region> inflight;
+    char *arena = nullptr;  // set while capturing
+    size_t arena_cap = 0, arena_used = 0;
+    size_t recorded = 0;  // bytes uploaded (sizes a plan's arena)
+};
 }  // namespace zk
 
 struct zk_ctx {
@@ -67,7 +87,8 @@ struct zk_ctx {
     bool timing = false;                  // record phase intervals (zk_timing_enable)
     std::vector<zk::PhaseMark> marks;
     std::map<std::string, zk::DevBuf> scratch;  // per context (per lane)
-    zk::DevBuf host_stage;                       // device staging for host buffers
+    zk::Uploader up;
+    bool capturing = false;  // inside a plan's graph capture: no allocation allowed
     int last_error = 0;
 };
 
@@ -89,6 +110,8 @@ void dev_free(Shared &sh, DevBuf &b);
 void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err);
 
 bool is_device_ptr(const void *p);
+// Asynchronous upload of `bytes` host bytes to `dst` on stream s (see Uploader).
+int upload(zk_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s);
 
 #define ZK_CUDA_TRY(expr)                                   \
     do {                                                    \

@@ -165,7 +165,7 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, cudaStream
         jobs[f].n = n;
         jobs[f].out = descs[f].E1;
     }
-    ZK_CUDA_TRY(cudaMemcpyAsync(dd, descs.data(), F * sizeof(FoldDesc), cudaMemcpyHostToDevice, s));
+    ZK_TRY(upload(ctx, dd, descs.data(), F * sizeof(FoldDesc), s));
     dim3 g(elem_blocks(n), (unsigned)F);
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_WITNESS, s);
@@ -216,7 +216,7 @@ int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma,
     if (!is_device_ptr(gamma)) {
         uint32_t *gd = (uint32_t *)scratch(ctx, "fold.gamma", 32, &err);
         if (!gd) return err;
-        ZK_CUDA_TRY(cudaMemcpyAsync(gd, gamma, 32, cudaMemcpyHostToDevice, s));
+        ZK_TRY(upload(ctx, gd, gamma, 32, s));
         g = gd;
     }
     std::vector<FoldDesc> d(1, make_desc(L, R, out, g));
@@ -246,7 +246,7 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
     if (!is_device_ptr(gammas)) {
         uint32_t *gd = (uint32_t *)scratch(ctx, "fold.gammas", (count - 1) * 32, &err);
         if (!gd) return err;
-        ZK_CUDA_TRY(cudaMemcpyAsync(gd, gammas, (count - 1) * 32, cudaMemcpyHostToDevice, s));
+        ZK_TRY(upload(ctx, gd, gammas, (count - 1) * 32, s));
         g = gd;
     }
     // Level l accumulator j lives in leaf slot j 2^l + 2^l - 1 (the fold

@@ -496,7 +496,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hk[k + 1] = hk[k] + kb;
         maxblk = std::max(maxblk, kb);
     }
-    ZK_CUDA_TRY(cudaMemcpyAsync(jt, h.data(), h.size(), cudaMemcpyHostToDevice, s));
+    ZK_TRY(upload(ctx, jt, h.data(), h.size(), s));
     DevJobs dj;
     dj.jobs = (const JobDesc *)jt;
     dj.sbase = (const uint32_t *)(jt + jd_bytes);

@@ -259,7 +259,7 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
             h[p * tab_words + count + v] = dst;
         }
     }
-    ZK_CUDA_TRY(cudaMemcpyAsync(tabs, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s));
+    ZK_TRY(upload(ctx, tabs, h.data(), h.size() * 8, s));
     const uint32_t *tw_n;
     ZK_TRY(twiddles(ctx, L, &tw_n, s));
     int logNs = 0;
