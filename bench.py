@@ -403,9 +403,15 @@ def run_extras(zk, ctx, dev, torch):
     tp = _time(torch, plain, 3)
     ph_p = {k: round(v[0] / 3, 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
     zk.zk_timing_enable(ctx, False)
+    outg = torch.zeros_like(outb)
+    plan = zk.zk_plan_commit_batch(ctx, vecs, outg, flags=zk.ZK_EVALS)
+    tg = _time(torch, lambda: zk.zk_plan_launch(plan), 3)
+    nodes = zk.zk_plan_nodes(plan)
+    zk.zk_plan_destroy(plan)
     res["cnn_batch_commit"] = {"polys": len(vecs), "coeffs": int(sizes.sum()),
-                               "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb,
-                               "identical": bool(torch.equal(outb, outp)),
+                               "batched_ms": tb, "plain_ms": tp, "graph_ms": tg, "graph_nodes": nodes,
+                               "speedup": tp / tb,
+                               "identical": bool(torch.equal(outb, outp) and torch.equal(outg, outb)),
                                "batched_phase_ms": ph_b, "plain_phase_ms": ph_p}
     del vecs
     # Fold tree: 1024 leaves of 2^16 (config: matmul block, 4 witness vectors).
@@ -464,13 +470,85 @@ def run_extras(zk, ctx, dev, torch):
     torch.cuda.synchronize()
     tp = _time(torch, plain_tree, 1)
     same = all(torch.equal(a, b) for a, b in zip(accs[count - 1], root_batched))
+    restore()
+    torch.cuda.synchronize()
+    plan = zk.zk_plan_fold_tree(ctx, descs, gam, rdesc)  # its warm-up consumes the leaves
+    restore()
+    torch.cuda.synchronize()
+    tg = _time(torch, lambda: zk.zk_plan_launch(plan), 1)
+    same = same and all(torch.equal(a, b) for a, b in zip(root, root_batched))
+    zk.zk_plan_destroy(plan)
     res["fold_tree"] = {"leaves": count, "n": n, "folds": count - 1,
                         "batched_folds_per_s": (count - 1) / (tt * 1e-3),
                         "plain_folds_per_s": (count - 1) / (tp * 1e-3),
-                        "batched_ms": tt, "plain_ms": tp, "speedup": tp / tt,
+                        "graph_folds_per_s": (count - 1) / (tg * 1e-3),
+                        "batched_ms": tt, "plain_ms": tp, "graph_ms": tg, "speedup": tp / tt,
                         "leaf_commit_ms": t_leaf, "identical": bool(same),
                         "batched_phase_ms": ph_tree}
+    del accs, leaf_state, descs
+    torch.cuda.empty_cache()
+    res["serving"] = run_serving(zk, ctx, dev, torch)
     return res
+
+
+def run_serving(zk, ctx, dev, torch, lanes=4, layers=12, rate_hz=20.0):
+    """Poisson stream of the basic-block jobs of a 12-layer, width-768
+    transformer (sequence 128): each job commits to its witness (three int8 *
+    2^16 vectors, as a leaf accumulator) and folds it into the resident
+    accumulator of its size.  Jobs reuse a pool of output buffers per size."""
+    import time as _t
+    sizes = [1 << lg for lg in Z.transformer_job_sizes()] * layers
+    arrivals = Z.poisson_arrivals(10, len(sizes), rate_hz)
+    pool = {}
+
+    def new_acc(n):
+        m = torch.zeros((4, n, 4), dtype=torch.int64, device="cuda")
+        e = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+        x = torch.zeros(44, dtype=torch.int64, device="cuda")
+        return (m, e, x), zk.make_acc(m, e, x)
+
+    for n in sorted(set(sizes)):
+        w = [dev(Z.zkml_scalars((11 << 24) + 4 * n.bit_length() + i, n)) for i in range(3)]
+        (rm, re_, rx), rd = new_acc(n)
+        for i, k in ((0, 0), (1, 1), (3, 2)):
+            rm[i].copy_(w[k])
+        zk.zk_leaf_init(ctx, [rd])
+        slots = [(new_acc(n), new_acc(n)) for _ in range(lanes + 1)]
+        pool[n] = {"w": w, "res": ((rm, re_, rx), rd), "slots": slots, "last": [None] * len(slots), "k": 0}
+    gam = dev(Z.gammas(12, 1))
+    torch.cuda.synchronize()
+    srv = zk.zk_server_create(ctx, lanes=lanes, hbm_budget_bytes=150 << 30)
+    tickets, delays = [], []
+    keep = []
+    t0 = _t.perf_counter()
+    for n, at in zip(sizes, arrivals):
+        now = _t.perf_counter() - t0
+        if at > now:
+            _t.sleep(at - now)
+        p = pool[n]
+        k = p["k"] % len(p["slots"])
+        p["k"] += 1
+        if p["last"][k] is not None:
+            zk.zk_wait(srv, p["last"][k], 600000)
+        (_, leaf), (_, out) = p["slots"][k]
+        job = zk.make_job(n, p["w"], leaf, p["res"][1], out, gam)
+        keep.append(job)
+        delay = max(0.0, _t.perf_counter() - t0 - at)
+        tk = zk.zk_submit(srv, job)
+        p["last"][k] = tk
+        tickets.append(tk)
+        delays.append(delay * 1e3)
+    infos = [zk.zk_wait(srv, t, 600000) for t in tickets]
+    st = zk.zk_server_stats(srv)
+    zk.zk_server_destroy(srv)
+    ok = all(i.status == zk.ZK_JOB_DONE for i in infos)
+    lat = np.array([i.end_ms - i.submit_ms + d for i, d in zip(infos, delays)])
+    span_s = (max(i.end_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
+    return {"jobs": len(sizes), "rate_hz": rate_hz, "lanes": lanes, "all_done": ok,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "jobs_per_s": len(sizes) / span_s,
+            "peak_reserved_gb": st.peak_reserved_bytes / 2 ** 30,
+            "sizes_log2": sorted(set(Z.transformer_job_sizes()))}
 
 
 def _time(torch, fn, reps):

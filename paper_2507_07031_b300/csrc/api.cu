@@ -365,6 +365,9 @@ int zk_destroy(zk_ctx *ctx) {
             cudaEventDestroy(m.b);
         }
         ctx->marks.clear();
+        if (ctx->side) cudaStreamDestroy(ctx->side);
+        for (auto &e : ctx->side_ev)
+            if (e) cudaEventDestroy(e);
         for (auto &r : ctx->up.inflight) cudaEventDestroy(r.ev);
         ctx->up.inflight.clear();
         if (ctx->up.ring) cudaFreeHost(ctx->up.ring);

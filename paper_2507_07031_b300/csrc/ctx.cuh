@@ -89,6 +89,8 @@ struct zk_ctx {
     std::map<std::string, zk::DevBuf> scratch;  // per context (per lane)
     zk::Uploader up;
     bool capturing = false;  // inside a plan's graph capture: no allocation allowed
+    cudaStream_t side = nullptr;         // fold tree: instance passes overlap the next level
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     int last_error = 0;
 };
 

@@ -75,7 +75,20 @@ __device__ __forceinline__ void load_bits(const uint32_t *p, uint32_t (&k)[8]) {
     for (int i = 0; i < 8; i++) k[i] = p[i];
 }
 
-// K5: instance RLC; 5 threads per fold (C_1..C_4, and E'' with mu'').
+// mu'' = gamma mu + mu' (one thread per fold).  Runs after the witness pass,
+// which reads both mu (the output may alias R).
+__global__ void k_fold_mu(const FoldDesc *__restrict__ descs, uint32_t folds) {
+    uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= folds) return;
+    const FoldDesc &d = descs[f];
+    Fr gm = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
+    Fr mu = fe_add<FrP>(fe_mul<FrP>(fe_load<FrP>(d.Lx + kInstMu), gm), fe_load<FrP>(d.Rx + kInstMu));
+    fe_store<FrP>(d.Ox + kInstMu, mu);
+}
+
+// K5: instance RLC; 5 threads per fold (C_1..C_4, and E'').  Touches only the
+// points of the instances, so it may run on a side stream while the next
+// tree level's witness work (which reads only vectors and mu) proceeds.
 __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t folds) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 5 * folds) return;
@@ -90,14 +103,12 @@ __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t fol
         xyzz_store_canonical(d.Ox + 16 * task, r);
         return;
     }
-    // E'' = E' + gamma E1 + gamma^2 E (joint double-and-add), mu'' = gamma mu + mu'.
+    // E'' = E' + gamma E1 + gamma^2 E (joint double-and-add).
     Fr gm = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
     Fr g2 = fe_from_mont<FrP>(fe_mul<FrP>(gm, gm));
     Xyzz e1 = xyzz_load_canonical(d.E1);
     Xyzz eL = xyzz_load_canonical(d.Lx + 64);
     Xyzz eR = xyzz_load_canonical(d.Rx + 64);
-    Fr muL = fe_load<FrP>(d.Lx + kInstMu);
-    Fr muR = fe_load<FrP>(d.Rx + kInstMu);
     Xyzz acc = xyzz_inf();
     for (int i = 253; i >= 0; i--) {
         acc = xyzz_dbl(acc);
@@ -105,9 +116,7 @@ __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t fol
         if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, eL);
     }
     acc = xyzz_add(acc, eR);
-    Fr mu = fe_add<FrP>(fe_mul<FrP>(muL, gm), muR);
     xyzz_store_canonical(d.Ox + 64, acc);
-    fe_store<FrP>(d.Ox + kInstMu, mu);
 }
 
 // Leaf: m3 = m1 o m2, e = 0, mu = 1, E = infinity (C_i are written by the MSM).
@@ -144,16 +153,16 @@ bool acc_ok(const zk_acc *a, size_t n) {
 
 unsigned elem_blocks(uint32_t n) { return std::min<unsigned>((n + 255) / 256, 1024u); }
 
-// Runs a batch of folds that share the length n.  `gam_dev` holds one
-// canonical gamma per fold (device).
-int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, cudaStream_t s) {
+// Runs a batch of folds that share the length n.  dd: device descriptor
+// slots (F), E1: device points (F); the instance pass runs on s_inst after the
+// batch's E1 commitments exist (s_inst may equal s).
+int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *dd, uint32_t *E1,
+               cudaStream_t s, cudaStream_t s_inst, cudaEvent_t ev) {
     const size_t F = descs.size();
     if (F == 0) return ZK_OK;
     int err = ZK_OK;
     uint32_t *e1 = (uint32_t *)scratch(ctx, "fold.e1", F * (size_t)n * 32, &err);
-    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.E1", F * 64, &err);
-    FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.descs", F * sizeof(FoldDesc), &err);
-    if (!e1 || !E1 || !dd) return err;
+    if (!e1) return err;
     std::vector<uint32_t *> vecs(F);
     std::vector<size_t> lens(F, n);
     std::vector<MsmJob> jobs(F);
@@ -171,12 +180,18 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, cudaStream
         PhaseScope ph(ctx, ZK_PHASE_FOLD_WITNESS, s);
         k_fold_witness<<<g, 256, 0, s>>>(dd, n);
         ZK_LAUNCHED();
+        k_fold_mu<<<(unsigned)((F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
+        ZK_LAUNCHED();
     }
     ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), F, true, s));
     ZK_TRY(msm_batch_impl(ctx, jobs.data(), F, 0, s));
+    if (s_inst != s) {
+        ZK_CUDA_TRY(cudaEventRecord(ev, s));
+        ZK_CUDA_TRY(cudaStreamWaitEvent(s_inst, ev, 0));
+    }
     {
-        PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s);
-        k_fold_instance<<<(unsigned)((5 * F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
+        PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s_inst);
+        k_fold_instance<<<(unsigned)((5 * F + 63) / 64), 64, 0, s_inst>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();
     }
     return ZK_OK;
@@ -220,7 +235,10 @@ int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma,
         g = gd;
     }
     std::vector<FoldDesc> d(1, make_desc(L, R, out, g));
-    ZK_TRY(fold_batch(ctx, d, (uint32_t)n, s));
+    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.E1", 64, &err);
+    FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.descs", sizeof(FoldDesc), &err);
+    if (!E1 || !dd) return err;
+    ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd, E1, s, s, nullptr));
     if (E1_out) {
         if (is_device_ptr(E1_out)) {
             ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, 64, cudaMemcpyDeviceToDevice, s));
@@ -249,6 +267,20 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
         ZK_TRY(upload(ctx, gd, gammas, (count - 1) * 32, s));
         g = gd;
     }
+    // Per-fold descriptor slots and E1 points for the whole tree, so that a
+    // level's instance pass (side stream) can still read its own while the
+    // next level's witness work (main stream) runs.
+    FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.treedescs", (count - 1) * sizeof(FoldDesc), &err);
+    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.treeE1", (count - 1) * 64, &err);
+    if (!dd || !E1) return err;
+    if (!ctx->side) {
+        ZK_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        ZK_CUDA_TRY(cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming));
+        ZK_CUDA_TRY(cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming));
+    }
+    // The side stream starts after everything queued on s so far.
+    ZK_CUDA_TRY(cudaEventRecord(ctx->side_ev[1], s));
+    ZK_CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->side_ev[1], 0));
     // Level l accumulator j lives in leaf slot j 2^l + 2^l - 1 (the fold
     // output overwrites its R operand).
     size_t width = count, goff = 0;
@@ -260,10 +292,13 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
             zk_acc *Rp = &leaves[j * span + span - 1];
             d.push_back(make_desc(Lp, Rp, Rp, g + 8 * (goff + j)));
         }
-        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, s));
+        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd + goff, E1 + 16 * goff, s, ctx->side, ctx->side_ev[0]));
         goff += width / 2;
         width /= 2;
     }
+    // Join the side stream before the root's instance is copied.
+    ZK_CUDA_TRY(cudaEventRecord(ctx->side_ev[1], ctx->side));
+    ZK_CUDA_TRY(cudaStreamWaitEvent(s, ctx->side_ev[1], 0));
     const zk_acc &top = leaves[count - 1];
     for (int i = 0; i < 4; i++)
         ZK_CUDA_TRY(cudaMemcpyAsync(root->m[i], top.m[i], n * 32, cudaMemcpyDeviceToDevice, s));
