@@ -100,6 +100,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Largest value of x over the ranks (the slowest replica sets the job's
+    time).  Uses a CUDA tensor under NCCL and a CPU tensor under gloo."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_per_rank: float, world: int, dist=None) -> float:
+    """Weak-scaling throughput: the units all ranks processed divided by the
+    slowest rank's time."""
+    return units_per_rank * world / max_over_ranks(seconds_per_rank, dist)
+
+
 # ---------------------------------------------------------------------------
 # Clock sampling during the timed region
 # ---------------------------------------------------------------------------
@@ -293,11 +311,7 @@ def main():
     sampler.stop()
     phases = zk.zk_timing_read(ctx)
     zk.zk_timing_enable(ctx, False)
-    total_ms = t0.elapsed_time(t1)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t0.elapsed_time(t1), dist)
 
     per_op = {}
     for name, n, _ in ops:
@@ -306,8 +320,7 @@ def main():
         unit = "Mpts/s" if name.startswith("msm") else "Melem/s"
         per_op[name] = {"ms": med, unit: n / (med * 1e-3) / 1e6}
     msm_ms = statistics.median([a.elapsed_time(b) for a, b in ev["msm_2^20_uniform"]])
-    value_per_gpu = n20 / (msm_ms * 1e-3) / 1e6
-    value = value_per_gpu * world
+    value = whole_job_rate(n20, msm_ms * 1e-3, world, dist) / 1e6
 
     # Roofline of the dominant kernel class: MSM bucket accumulation.
     imad_peak, fq_mul_peak = zk.zk_probe_rates(local)
@@ -342,7 +355,7 @@ def main():
         s0 = time.perf_counter()
         zk.zk_commit(ctx, h_sc, h_out)
         e2e_t.append(time.perf_counter() - s0)
-    e2e = {"value": n20 / statistics.median(e2e_t) / 1e6 * world, "unit": UNIT,
+    e2e = {"value": whole_job_rate(n20, statistics.median(e2e_t), world, dist) / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": n20 * 32, "d2h_bytes_per_step": 64,
            "call": "zk_commit(host scalars, host out)"}
 

@@ -366,6 +366,7 @@ int zk_destroy(zk_ctx *ctx) {
         }
         ctx->marks.clear();
         if (ctx->side) cudaStreamDestroy(ctx->side);
+        if (ctx->stat_host) cudaFreeHost(ctx->stat_host);
         for (auto &e : ctx->side_ev)
             if (e) cudaEventDestroy(e);
         for (auto &r : ctx->up.inflight) cudaEventDestroy(r.ev);

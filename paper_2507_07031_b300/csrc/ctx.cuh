@@ -90,6 +90,8 @@ struct zk_ctx {
     zk::Uploader up;
     bool capturing = false;  // inside a plan's graph capture: no allocation allowed
     cudaStream_t side = nullptr;         // fold tree: instance passes overlap the next level
+    uint32_t *stat_host = nullptr;       // pinned: per-job scalar widths read back by the MSM
+    size_t stat_cap = 0;
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
     int last_error = 0;
 };

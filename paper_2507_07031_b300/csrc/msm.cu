@@ -40,6 +40,7 @@ constexpr int kRedThreads = 64;  // bucket-reduction block
 constexpr int kRedPer = 4;       // buckets per thread
 constexpr int kRedSpan = kRedThreads * kRedPer;
 constexpr int kRedSpanLog = 8;
+constexpr size_t kStatsMin = 4096;  // scalars below which the width scan is skipped
 static_assert(kRedSpan == 1 << kRedSpanLog, "reduction span");
 
 // One MSM of a batch.  Jobs are ordered by window width so that each width's
@@ -50,7 +51,8 @@ struct JobDesc {
     const Affine *table;      // window table of this job's width
     uint32_t n;
     uint32_t logB;            // buckets: B = 2^logB = 2^(c - 1)
-    uint32_t pad[2];
+    uint32_t shift;           // every scalar of the job is a multiple of 2^shift
+    uint32_t wins;            // windows that can hold nonzero digits (after the shift)
 };
 
 struct DevJobs {
@@ -82,6 +84,23 @@ __device__ __forceinline__ uint32_t window_bits(const uint32_t (&s)[8], int w) {
     uint32_t lo = word < 8 ? (s[word] >> off) : 0u;
     uint32_t hi = (off + C > 32 && word + 1 < 8) ? (s[word + 1] << (32 - off)) : 0u;
     return (lo | hi) & ((1u << C) - 1u);
+}
+
+// s >> k for a 256-bit s held in registers (k < 256), by static word moves
+// selected on the bits of k, so that s never needs dynamic indexing.
+__device__ __forceinline__ void shr256(uint32_t (&s)[8], uint32_t k) {
+#pragma unroll
+    for (int step = 4; step >= 1; step >>= 1) {
+        if ((k >> 5) & step) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) s[j] = j + step < 8 ? s[j + step] : 0u;
+        }
+    }
+    const uint32_t b = k & 31;
+    if (b) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) s[j] = __funnelshift_r(s[j], j + 1 < 8 ? s[j + 1] : 0u, b);
+    }
 }
 
 // Loads a scalar, recentres it, and returns the negation flag.
@@ -116,12 +135,14 @@ __global__ void k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n,
         i = gid - dj.sbase[job];
         bb = dj.bbase[job];
         neg = load_recentred(dj.jobs[job].scalars + 8 * (size_t)i, s);
+        shr256(s, dj.jobs[job].shift);
     }
+    const uint32_t wins = live ? dj.jobs[job].wins : 0;
     const uint32_t lt_mask = (1u << lane_id()) - 1u;
     uint32_t carry = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) {
-        uint32_t d = window_bits<C>(s, w) + carry;
+        uint32_t d = ((uint32_t)w < wins ? window_bits<C>(s, w) : 0u) + carry;
         carry = d > (1u << (C - 1)) ? 1u : 0u;
         int sd = carry ? (int)d - (1 << C) : (int)d;
         uint32_t key = (live && sd != 0) ? bb + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
@@ -139,6 +160,34 @@ __global__ void k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n,
                 sorted[base + __popc(group & lt_mask)] = (((uint32_t)w * table_n + i) << 1) | sign;
             }
         }
+    }
+}
+
+// Per job: the largest bit length and the fewest trailing zeros of the
+// recentred nonzero scalars (stats[2 j] = max length, stats[2 j + 1] = min
+// trailing zeros; initialised to 0 and 0xffffffff).
+__global__ void k_scalar_stats(DevJobs dj, uint32_t total, uint32_t *__restrict__ stats) {
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t len = 0, tz = 0xffffffffu, job = 0;
+    if (gid < total) {
+        job = search(dj.sbase, 0, dj.count, gid);
+        uint32_t s[8];
+        load_recentred(dj.jobs[job].scalars + 8 * (size_t)(gid - dj.sbase[job]), s);
+#pragma unroll
+        for (int j = 7; j >= 0; j--)
+            if (!len && s[j]) len = 32 * j + 32 - __clz(s[j]);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (tz == 0xffffffffu && s[j]) tz = 32 * j + __ffs(s[j]) - 1;
+    }
+    // one atomic per warp and job
+    const uint32_t key = gid < total ? job : 0xffffffffu;
+    const uint32_t group = __match_any_sync(0xffffffffu, key);
+    const uint32_t gl = __reduce_max_sync(group, len);
+    const uint32_t gt = __reduce_min_sync(group, tz);
+    if (key != 0xffffffffu && lane_id() == (uint32_t)(__ffs(group) - 1)) {
+        atomicMax(&stats[2 * key], gl);
+        atomicMin(&stats[2 * key + 1], gt);
     }
 }
 
@@ -345,6 +394,7 @@ __global__ void __launch_bounds__(kFinThreads)
         Xyzz tot = wsum;
         for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl(tot);  // x kRedSpan
         tot = xyzz_add(tot, vsum);
+        for (uint32_t k = 0; k < dj.jobs[job].shift; k++) tot = xyzz_dbl(tot);  // x 2^shift
         xyzz_store_canonical(dj.jobs[job].out, tot);
     }
 }
@@ -402,42 +452,122 @@ int msm_pick_window(zk_ctx *ctx, size_t n, size_t count) {
     return default_window(n);
 }
 
+// Reads, per job, the largest bit length and the fewest trailing zeros of
+// the recentred scalars (one pass over the scalars and a stream sync).
+static int scalar_stats(zk_ctx *ctx, const MsmJob *jobs, size_t count, std::vector<uint32_t> &len,
+                        std::vector<uint32_t> &tz, cudaStream_t s) {
+    int err = ZK_OK;
+    const size_t jd_bytes = align_up(count * sizeof(JobDesc), 256);
+    const size_t pre_bytes = align_up((count + 1) * 4, 256);
+    char *jt = (char *)scratch(ctx, "msm.statjobs", jd_bytes + pre_bytes, &err);
+    uint32_t *st = (uint32_t *)scratch(ctx, "msm.stats", 2 * align_up(count * 4, 256), &err);
+    if (!jt || !st) return err;
+    uint32_t *st_len = st, *st_tz = st + align_up(count * 4, 256) / 4;
+    std::vector<char> h(jd_bytes + pre_bytes, 0);
+    JobDesc *hd = (JobDesc *)h.data();
+    uint32_t *hs = (uint32_t *)(h.data() + jd_bytes);
+    for (size_t k = 0; k < count; k++) {
+        hd[k].scalars = jobs[k].scalars;
+        hd[k].n = jobs[k].n;
+        hs[k + 1] = hs[k] + jobs[k].n;
+    }
+    ZK_TRY(upload(ctx, jt, h.data(), h.size(), s));
+    ZK_CUDA_TRY(cudaMemsetAsync(st_len, 0, count * 4, s));
+    ZK_CUDA_TRY(cudaMemsetAsync(st_tz, 0xff, count * 4, s));
+    DevJobs dj;
+    dj.jobs = (const JobDesc *)jt;
+    dj.sbase = (const uint32_t *)(jt + jd_bytes);
+    dj.count = (uint32_t)count;
+    const uint32_t total = hs[count];
+    k_scalar_stats<<<(total + 255) / 256, 256, 0, s>>>(dj, total, st_len);
+    ZK_LAUNCHED();
+    if (ctx->stat_cap < 2 * count) {
+        if (ctx->stat_host) cudaFreeHost(ctx->stat_host);
+        ctx->stat_host = nullptr;
+        ctx->stat_cap = 0;
+        ZK_CUDA_TRY(cudaHostAlloc((void **)&ctx->stat_host, 2 * count * 4, cudaHostAllocDefault));
+        ctx->stat_cap = 2 * count;
+    }
+    ZK_CUDA_TRY(cudaMemcpyAsync(ctx->stat_host, st_len, count * 4, cudaMemcpyDeviceToHost, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(ctx->stat_host + count, st_tz, count * 4, cudaMemcpyDeviceToHost, s));
+    ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    len.assign(ctx->stat_host, ctx->stat_host + count);
+    tz.assign(ctx->stat_host + count, ctx->stat_host + 2 * count);
+    return ZK_OK;
+}
+
 int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed, cudaStream_t s) {
     if (count == 0) return ZK_OK;
     Shared &sh = *ctx->sh;
-    // Window width per job (fixed by the caller, or tuned / modelled per size).
+    size_t total_in = 0;
+    for (size_t k = 0; k < count; k++) {
+        const MsmJob &m = jobs_in[k];
+        if (!m.out || (m.n && !m.scalars)) return ZK_EINVAL;
+        if (m.n > sh.srs_n) return ZK_ESRS;
+        total_in += m.n;
+    }
+    if (total_in >= (1ull << 32)) return ZK_EINVAL;
+    // Small-scalar path: when the recentred scalars of a job are short (e.g.
+    // quantised int8 values times 2^16), shift out their common trailing
+    // zeros (the result is doubled back at the end) and use only the windows
+    // that can hold nonzero digits -- one window when the remaining width
+    // fits, read straight from the SRS.  Skipped while capturing a graph
+    // (it reads the statistics back to the host) and for tuning runs.
+    std::vector<uint32_t> len(count, kScalarBits - 1), tz(count, 0);
+    if (c_fixed == 0 && !ctx->capturing && total_in >= kStatsMin)
+        ZK_TRY(scalar_stats(ctx, jobs_in, count, len, tz, s));
     struct J {
         MsmJob job;
         int c;
+        uint32_t shift, wins;
     };
     std::vector<J> jv(count);
     size_t total64 = 0, entries64 = 0, nb64 = 0, nblk64 = 0;
     for (size_t k = 0; k < count; k++) {
         const MsmJob &m = jobs_in[k];
-        if (!m.out || (m.n && !m.scalars)) return ZK_EINVAL;
-        if (m.n > sh.srs_n) return ZK_ESRS;
         int c = c_fixed > 0 ? c_fixed : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
         if (c < kMinWindow || c > kMaxWindow) return ZK_EINVAL;
-        jv[k] = {m, c};
+        uint32_t shift = 0, wins = (uint32_t)windows_for(c);
+        if (len[k] == 0) {  // all scalars zero
+            c = kMinWindow;
+            wins = 0;
+        } else if (len[k] < (uint32_t)kScalarBits - 1 || tz[k] > 0) {
+            shift = tz[k];
+            const uint32_t eff = len[k] - tz[k];  // bits left after the shift
+            if ((int)eff + 1 <= c) {
+                c = std::max<int>(kMinWindow, (int)eff + 1);
+                wins = 1;
+            } else {
+                wins = (eff + 1 + c - 1) / c;
+            }
+        }
+        jv[k] = {m, c, shift, wins};
         total64 += m.n;
-        entries64 += (size_t)m.n * windows_for(c);
+        entries64 += (size_t)m.n * wins;
         nb64 += (size_t)1 << (c - 1);
         nblk64 += ((size_t)1 << (c - 1)) / kRedSpan;
     }
-    if (total64 >= (1ull << 32) || nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
-    std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) { return a.c < b.c; });
-    // Window tables (built on first use of a width, outside any timed loop).
-    std::vector<const WindowTable *> tabs(count);
-    size_t max_n = 1;
-    for (size_t k = 0; k < count; k++) max_n = std::max(max_n, (size_t)jv[k].job.n);
+    if (nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
+    std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) {
+        return a.c != b.c ? a.c < b.c : (a.wins > 1) < (b.wins > 1);
+    });
+    // Point tables: the SRS itself for one-window jobs, else the width's
+    // window table (built on first use of a width, outside any timed loop).
+    std::vector<const Affine *> tabs(count);
+    std::vector<uint32_t> tabn(count);
     for (size_t k = 0; k < count; k++) {
-        if (k == 0 || jv[k].c != jv[k - 1].c) {
-            size_t need = 1;
-            for (size_t j = k; j < count && jv[j].c == jv[k].c; j++) need = std::max(need, (size_t)jv[j].job.n);
-            ZK_TRY(table_get(ctx, jv[k].c, need, &tabs[k], s));
-        } else {
-            tabs[k] = tabs[k - 1];
+        if (jv[k].wins <= 1) {
+            tabs[k] = (const Affine *)sh.srs.p;
+            tabn[k] = (uint32_t)sh.srs_n;
+            continue;
         }
+        size_t need = 1;
+        for (size_t j = 0; j < count; j++)
+            if (jv[j].c == jv[k].c && jv[j].wins > 1) need = std::max(need, (size_t)jv[j].job.n);
+        const WindowTable *t;
+        ZK_TRY(table_get(ctx, jv[k].c, need, &t, s));
+        tabs[k] = (const Affine *)t->buf.p;
+        tabn[k] = (uint32_t)t->n;
     }
     const uint32_t total = (uint32_t)total64;
     const uint32_t nb = (uint32_t)nb64;
@@ -448,7 +578,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     int rounds = 0;
     {
         size_t m = 1;
-        for (size_t k = 0; k < count; k++) m = std::max(m, (size_t)jv[k].job.n * windows_for(jv[k].c));
+        for (size_t k = 0; k < count; k++) m = std::max(m, (size_t)jv[k].job.n * std::max<uint32_t>(jv[k].wins, 1));
         while (m > (size_t)kPiece) {
             m = (m + kPiece - 1) / kPiece;
             rounds++;
@@ -487,9 +617,11 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     for (size_t k = 0; k < count; k++) {
         hd[k].scalars = jv[k].job.scalars;
         hd[k].out = jv[k].job.out;
-        hd[k].table = (const Affine *)tabs[k]->buf.p;
+        hd[k].table = tabs[k];
         hd[k].n = jv[k].job.n;
         hd[k].logB = (uint32_t)(jv[k].c - 1);
+        hd[k].shift = jv[k].shift;
+        hd[k].wins = jv[k].wins;
         hs[k + 1] = hs[k] + jv[k].job.n;
         hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
         uint32_t kb = (1u << (jv[k].c - 1)) / kRedSpan;
@@ -514,9 +646,9 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         }
         for (size_t g0 = 0; g0 < count;) {
             size_t g1 = g0;
-            while (g1 < count && jv[g1].c == jv[g0].c) g1++;
+            while (g1 < count && jv[g1].c == jv[g0].c && tabs[g1] == tabs[g0]) g1++;
             const uint32_t ns = hs[g1] - hs[g0];
-            const uint32_t tn = (uint32_t)tabs[g0]->n;
+            const uint32_t tn = tabn[g0];
             if (pass == 0)
                 ZK_TRY(recode<false>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, counts, nullptr,
                                      nullptr, s));

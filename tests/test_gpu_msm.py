@@ -184,3 +184,29 @@ def test_autotune_table(zk, ctx_small, tmp_path):
     for lg in (10, 12):
         zk.zk_tune_set(ctx_small, zk.ZK_TUNE_MSM_WINDOW, lg, 0)
         zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, lg, 0)
+
+
+def test_msm_small_scalar_path(zk, orc, ctx_small, tau):
+    """Short recentred scalars: common trailing zeros are shifted out and only
+    the windows that can hold digits are used (one window, read from the SRS,
+    when the rest fits).  Mixed in one batch with full-width and zero jobs."""
+    import torch
+    n = 4096
+    rng = np.random.default_rng(11)
+    small = rng.integers(-300, 300, n)
+    cases = {
+        "int8x2^16": Z.zkml_scalars(21, n),
+        "pm1": Z.encode_signed(rng.integers(-1, 2, n), 0),
+        "shift200": np.stack([Z.int_to_fr((int(v) << 200) % R) for v in small]),
+        "shift37_wide": np.stack([Z.int_to_fr((int(v) << 37) % R) for v in rng.integers(0, 1 << 60, n)]),
+        "uniform": Z.fr_uniform(22, n),
+        "zero": np.zeros((n, 4), np.uint64),
+    }
+    names = list(cases)
+    out = torch.zeros((len(names), 8), dtype=torch.int64, device="cuda")
+    zk.zk_commit_batch(ctx_small, [to_dev(cases[k]) for k in names], out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    for i, k in enumerate(names):
+        assert pts_equal(got[i], orc.commit_coeffs_tau(cases[k], tau)), k
+        assert pts_equal(_commit(zk, ctx_small, cases[k]), got[i]), k

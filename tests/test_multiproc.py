@@ -1,0 +1,58 @@
+"""The replica (weak-scaling) path of bench.py with two gloo ranks on CPU:
+the whole-job rate divides all ranks' units by the slowest rank's time, and
+the reference arm under a 2-rank launch prints one line from rank 0."""
+import os
+import socket
+import subprocess
+import sys
+
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r processed 1000 units in (1 + r) seconds
+    rate = bench.whole_job_rate(1000.0, 1.0 + rank, world, dist)
+    mx = bench.max_over_ranks(10.0 * (rank + 1), dist)
+    q.put((rank, rate, mx))
+    dist.destroy_process_group()
+
+
+def test_whole_job_rate_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, rate, mx in res:
+        assert abs(rate - 2000.0 / 2.0) < 1e-9   # 2 x 1000 units / slowest 2 s
+        assert mx == 20.0
+
+
+def test_reference_arm_under_two_rank_launch():
+    port = _free_port()
+    env = dict(os.environ, ZK_ORACLE_THREADS="2")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr=127.0.0.1", "--master-port=%d" % port, os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1 and '"impl": "reference"' in lines[0]
