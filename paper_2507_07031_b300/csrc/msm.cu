@@ -163,10 +163,11 @@ __global__ void k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n,
     }
 }
 
-// Per job: the largest bit length and the fewest trailing zeros of the
-// recentred nonzero scalars (stats[2 j] = max length, stats[2 j + 1] = min
-// trailing zeros; initialised to 0 and 0xffffffff).
-__global__ void k_scalar_stats(DevJobs dj, uint32_t total, uint32_t *__restrict__ stats) {
+// Per job: the largest bit length (st_len[j], initialised to 0) and the
+// fewest trailing zeros (st_tz[j], initialised to 0xffffffff) of the
+// recentred nonzero scalars.
+__global__ void k_scalar_stats(DevJobs dj, uint32_t total, uint32_t *__restrict__ st_len,
+                               uint32_t *__restrict__ st_tz) {
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t len = 0, tz = 0xffffffffu, job = 0;
     if (gid < total) {
@@ -186,8 +187,8 @@ __global__ void k_scalar_stats(DevJobs dj, uint32_t total, uint32_t *__restrict_
     const uint32_t gl = __reduce_max_sync(group, len);
     const uint32_t gt = __reduce_min_sync(group, tz);
     if (key != 0xffffffffu && lane_id() == (uint32_t)(__ffs(group) - 1)) {
-        atomicMax(&stats[2 * key], gl);
-        atomicMin(&stats[2 * key + 1], gt);
+        atomicMax(&st_len[key], gl);
+        atomicMin(&st_tz[key], gt);
     }
 }
 
@@ -394,7 +395,8 @@ __global__ void __launch_bounds__(kFinThreads)
         Xyzz tot = wsum;
         for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl(tot);  // x kRedSpan
         tot = xyzz_add(tot, vsum);
-        for (uint32_t k = 0; k < dj.jobs[job].shift; k++) tot = xyzz_dbl(tot);  // x 2^shift
+        const uint32_t sh = min(dj.jobs[job].shift, (uint32_t)kScalarBits);
+        for (uint32_t k = 0; k < sh; k++) tot = xyzz_dbl(tot);  // x 2^shift
         xyzz_store_canonical(dj.jobs[job].out, tot);
     }
 }
@@ -479,7 +481,7 @@ static int scalar_stats(zk_ctx *ctx, const MsmJob *jobs, size_t count, std::vect
     dj.sbase = (const uint32_t *)(jt + jd_bytes);
     dj.count = (uint32_t)count;
     const uint32_t total = hs[count];
-    k_scalar_stats<<<(total + 255) / 256, 256, 0, s>>>(dj, total, st_len);
+    k_scalar_stats<<<(total + 255) / 256, 256, 0, s>>>(dj, total, st_len, st_tz);
     ZK_LAUNCHED();
     if (ctx->stat_cap < 2 * count) {
         if (ctx->stat_host) cudaFreeHost(ctx->stat_host);
@@ -528,6 +530,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         int c = c_fixed > 0 ? c_fixed : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
         if (c < kMinWindow || c > kMaxWindow) return ZK_EINVAL;
         uint32_t shift = 0, wins = (uint32_t)windows_for(c);
+        if (len[k] > (uint32_t)kScalarBits - 1 || (len[k] && tz[k] >= len[k])) return ZK_ECUDA;
         if (len[k] == 0) {  // all scalars zero
             c = kMinWindow;
             wins = 0;
@@ -775,6 +778,8 @@ __global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint3
     d->table = table;
     d->n = n;
     d->logB = kNoAllocC - 1;
+    d->shift = 0;
+    d->wins = kNoAllocW;
     uint32_t *sb = reinterpret_cast<uint32_t *>(ws + kNaJobs + 256);
     uint32_t *bb = sb + kNoAllocPre / 4;
     uint32_t *kb = bb + kNoAllocPre / 4;
