@@ -135,67 +135,6 @@ ZK_DEV Xyzz xyzz_add(const Xyzz &p, const Xyzz &q) {
     return r;
 }
 
-// ---------------------------------------------------------------------------
-// Latency-oriented forms of the same formulas: the independent products of
-// each level of the formula's dependency graph go through one interleaved
-// call (fe_mul2/3/4), so a chain of point operations in a single thread waits
-// on four or five product latencies per operation instead of ten to fourteen.
-// Used where few warps run: bucket reduction and single-point scalar
-// multiplications.
-// ---------------------------------------------------------------------------
-
-ZK_DEV Xyzz xyzz_dbl_lat(const Xyzz &p) {
-    const Fq U = fe_dbl<FqP>(p.Y);
-    Fe2<FqP> l1 = fe_mul_x2<FqP>(U, U, p.X, p.X);                     // V, X^2
-    const Fq V = l1.a;
-    const Fq M = fe_mul3<FqP>(l1.b);
-    Fe4<FqP> l2 = fe_mul_x4<FqP>(U, V, p.X, V, V, p.ZZ, M, M);        // W, S, ZZ3, M^2
-    const Fq W = l2.a, S = l2.b;
-    Xyzz r;
-    r.X = fe_sub<FqP>(l2.d, fe_dbl<FqP>(S));
-    Fe3<FqP> l3 = fe_mul_x3<FqP>(M, fe_sub<FqP>(S, r.X), W, p.Y, W, p.ZZZ);
-    r.Y = fe_sub<FqP>(l3.a, l3.b);
-    r.ZZ = l2.c;
-    r.ZZZ = l3.c;
-    return r;
-}
-
-ZK_DEV Xyzz xyzz_add_lat(const Xyzz &p, const Xyzz &q) {
-    if (xyzz_is_inf(p)) return q;
-    if (xyzz_is_inf(q)) return p;
-    Fe4<FqP> l1 = fe_mul_x4<FqP>(p.X, q.ZZ, q.X, p.ZZ, p.Y, q.ZZZ, q.Y, p.ZZZ);  // U1 U2 S1 S2
-    const Fq U1 = l1.a, S1 = l1.c;
-    const Fq P = fe_sub<FqP>(l1.b, U1);
-    const Fq R = fe_sub<FqP>(l1.d, S1);
-    if (fe_is_zero<FqP>(P)) {
-        if (fe_is_zero<FqP>(R)) return xyzz_dbl_lat(p);
-        return xyzz_inf();
-    }
-    Fe4<FqP> l2 = fe_mul_x4<FqP>(P, P, R, R, p.ZZ, q.ZZ, p.ZZZ, q.ZZZ);      // PP RR ZZ12 ZZZ12
-    const Fq PP = l2.a;
-    Fe3<FqP> l3 = fe_mul_x3<FqP>(P, PP, U1, PP, l2.c, PP);                  // PPP Q ZZ3
-    const Fq PPP = l3.a, Q = l3.b;
-    Xyzz r;
-    r.X = fe_sub<FqP>(fe_sub<FqP>(l2.b, PPP), fe_dbl<FqP>(Q));
-    Fe3<FqP> l4 = fe_mul_x3<FqP>(R, fe_sub<FqP>(Q, r.X), S1, PPP, l2.d, PPP);
-    r.Y = fe_sub<FqP>(l4.a, l4.b);
-    r.ZZ = l3.c;
-    r.ZZZ = l4.c;
-    return r;
-}
-
-// k * P for a canonical 256-bit k (MSB-first double-and-add), latency form.
-ZK_DEV Xyzz xyzz_mul_lat(const Xyzz &p, const uint32_t (&k)[8]) {
-    Xyzz acc = xyzz_inf();
-    int top = 255;
-    while (top >= 0 && !((k[top >> 5] >> (top & 31)) & 1)) top--;
-    for (int i = top; i >= 0; i--) {
-        acc = xyzz_dbl_lat(acc);
-        if ((k[i >> 5] >> (i & 31)) & 1) acc = xyzz_add_lat(acc, p);
-    }
-    return acc;
-}
-
 // XYZZ -> affine (Montgomery form).  Infinity maps to (0, 0).
 ZK_DEV Affine xyzz_to_affine(const Xyzz &p) {
     Affine a;

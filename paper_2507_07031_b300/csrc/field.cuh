@@ -337,89 +337,6 @@ template <> ZK_DEV Fe<FrP> fe_mul<FrP>(const Fe<FrP> &a, const Fe<FrP> &b) {
 
 template <class P> ZK_DEV Fe<P> fe_sqr(const Fe<P> &a) { return fe_mul<P>(a, a); }
 
-// ---------------------------------------------------------------------------
-// Latency-oriented products.  The carry-chain product above serialises on the
-// single carry flag, so one thread cannot overlap two of them.  This
-// formulation (the same CIOS order with 64-bit intermediates and no carry
-// flag) lets the compiler interleave several independent products, which cuts
-// the latency of point operations in the phases where few warps run (bucket
-// reduction, scalar multiplications of single points).  Its throughput is
-// slightly lower, so the bulk phases keep fe_mul.
-// ---------------------------------------------------------------------------
-
-template <class P> ZK_DEV Fe<P> fe_mul_c64(const Fe<P> &a, const Fe<P> &b) {
-    uint32_t t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        uint64_t C = 0;
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            uint64_t x = (uint64_t)a.v[j] * b.v[i] + t[j] + C;
-            t[j] = (uint32_t)x;
-            C = x >> 32;
-        }
-        t[8] += (uint32_t)C;  // the sum stays below 2^288 (p < 2^254)
-        const uint32_t m = t[0] * P::n0;
-        uint64_t x = (uint64_t)m * P::p(0) + t[0];
-        C = x >> 32;
-#pragma unroll
-        for (int j = 1; j < 8; j++) {
-            x = (uint64_t)m * P::p(j) + t[j] + C;
-            t[j - 1] = (uint32_t)x;
-            C = x >> 32;
-        }
-        x = (uint64_t)t[8] + C;
-        t[7] = (uint32_t)x;
-        t[8] = (uint32_t)(x >> 32);
-    }
-    // t < 2p: one conditional subtraction.
-    Fe<P> r, d;
-    int64_t br = 0;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-        int64_t y = (int64_t)t[j] - (int64_t)P::p(j) - br;
-        d.v[j] = (uint32_t)y;
-        br = y < 0;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; j++) r.v[j] = br ? t[j] : d.v[j];
-    return r;
-}
-
-template <class P> struct Fe2 { Fe<P> a, b; };
-template <class P> struct Fe3 { Fe<P> a, b, c; };
-template <class P> struct Fe4 { Fe<P> a, b, c, d; };
-
-// Two, three or four independent products in one out-of-line call.
-template <class P>
-__device__ __noinline__ Fe2<P> fe_mul_x2(const Fe<P> x0, const Fe<P> y0, const Fe<P> x1, const Fe<P> y1) {
-    Fe2<P> r;
-    r.a = fe_mul_c64<P>(x0, y0);
-    r.b = fe_mul_c64<P>(x1, y1);
-    return r;
-}
-
-template <class P>
-__device__ __noinline__ Fe3<P> fe_mul_x3(const Fe<P> x0, const Fe<P> y0, const Fe<P> x1, const Fe<P> y1,
-                                       const Fe<P> x2, const Fe<P> y2) {
-    Fe3<P> r;
-    r.a = fe_mul_c64<P>(x0, y0);
-    r.b = fe_mul_c64<P>(x1, y1);
-    r.c = fe_mul_c64<P>(x2, y2);
-    return r;
-}
-
-template <class P>
-__device__ __noinline__ Fe4<P> fe_mul_x4(const Fe<P> x0, const Fe<P> y0, const Fe<P> x1, const Fe<P> y1,
-                                       const Fe<P> x2, const Fe<P> y2, const Fe<P> x3, const Fe<P> y3) {
-    Fe4<P> r;
-    r.a = fe_mul_c64<P>(x0, y0);
-    r.b = fe_mul_c64<P>(x1, y1);
-    r.c = fe_mul_c64<P>(x2, y2);
-    r.d = fe_mul_c64<P>(x3, y3);
-    return r;
-}
-
 // Montgomery form conversions: x -> x R and x R -> x.
 template <class P> ZK_DEV Fe<P> fe_to_mont(const Fe<P> &a) { return fe_mul<P>(a, fe_r2<P>()); }
 

@@ -88,8 +88,7 @@ __global__ void k_fold_mu(const FoldDesc *__restrict__ descs, uint32_t folds) {
 
 // K5: instance RLC; 5 threads per fold (C_1..C_4, and E'').  Touches only the
 // points of the instances, so it may run on a side stream while the next
-// tree level's witness work (which reads only vectors and mu) proceeds.  Few
-// threads run, each a chain of 254 doublings: latency forms of the formulas.
+// tree level's witness work (which reads only vectors and mu) proceeds.
 __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t folds) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 5 * folds) return;
@@ -100,7 +99,7 @@ __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t fol
     if (task < 4) {
         Xyzz cl = xyzz_load_canonical(d.Lx + 16 * task);
         Xyzz cr = xyzz_load_canonical(d.Rx + 16 * task);
-        Xyzz r = xyzz_add_lat(xyzz_mul_lat(cl, g), cr);
+        Xyzz r = xyzz_add(xyzz_mul(cl, g), cr);
         xyzz_store_canonical(d.Ox + 16 * task, r);
         return;
     }
@@ -112,11 +111,11 @@ __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t fol
     Xyzz eR = xyzz_load_canonical(d.Rx + 64);
     Xyzz acc = xyzz_inf();
     for (int i = 253; i >= 0; i--) {
-        acc = xyzz_dbl_lat(acc);
-        if ((g[i >> 5] >> (i & 31)) & 1) acc = xyzz_add_lat(acc, e1);
-        if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add_lat(acc, eL);
+        acc = xyzz_dbl(acc);
+        if ((g[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, e1);
+        if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, eL);
     }
-    acc = xyzz_add_lat(acc, eR);
+    acc = xyzz_add(acc, eR);
     xyzz_store_canonical(d.Ox + 64, acc);
 }
 

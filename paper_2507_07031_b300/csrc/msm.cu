@@ -264,15 +264,12 @@ __device__ __forceinline__ Xyzz shfl_down_pt(const Xyzz &p, int d) {
     return r;
 }
 
-// The reduction phases run few warps, so they use the latency forms of the
-// point formulas (interleaved products, xyzz_add_lat / xyzz_dbl_lat).
-
 // Inclusive suffix sum over the lanes of a warp: lane l gets sum_{l' >= l} x_l'.
 __device__ __forceinline__ Xyzz warp_suffix(Xyzz x) {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         Xyzz y = shfl_down_pt(x, d);
-        if (lane_id() + d < 32) x = xyzz_add_lat(x, y);
+        if (lane_id() + d < 32) x = xyzz_add(x, y);
     }
     return x;
 }
@@ -282,7 +279,7 @@ __device__ __forceinline__ Xyzz warp_sum(Xyzz x) {
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
         Xyzz y = shfl_down_pt(x, d);
-        x = xyzz_add_lat(x, y);
+        x = xyzz_add(x, y);
     }
     return x;
 }
@@ -303,8 +300,8 @@ __global__ void __launch_bounds__(kRedThreads)
     Xyzz l = r;
 #pragma unroll
     for (int i = kRedPer - 2; i >= 0; i--) {
-        r = xyzz_add_lat(r, S[i]);
-        l = xyzz_add_lat(l, r);
+        r = xyzz_add(r, S[i]);
+        l = xyzz_add(l, r);
     }
     // block suffix sums of r
     Xyzz x = warp_suffix(r);
@@ -312,11 +309,11 @@ __global__ void __launch_bounds__(kRedThreads)
     if (lane_id() == 0) sh[warp] = x;
     __syncthreads();
     Xyzz later = xyzz_inf();
-    for (uint32_t w = warp + 1; w < kRedThreads / 32; w++) later = xyzz_add_lat(later, sh[w]);
-    x = xyzz_add_lat(x, later);  // x = sum_{t' >= t} r_t'
+    for (uint32_t w = warp + 1; w < kRedThreads / 32; w++) later = xyzz_add(later, sh[w]);
+    x = xyzz_add(x, later);  // x = sum_{t' >= t} r_t'
     // contrib_t = l_t + 4 t r_t summed over t == sum_t l_t + 4 sum_{t >= 1} suffix_t
     Xyzz c = l;
-    if (t >= 1) c = xyzz_add_lat(c, xyzz_dbl_lat(xyzz_dbl_lat(x)));
+    if (t >= 1) c = xyzz_add(c, xyzz_dbl(xyzz_dbl(x)));
     Xyzz tot_sum = x;  // suffix at t = 0 is the block sum
     __syncthreads();
     c = warp_sum(c);
@@ -324,7 +321,7 @@ __global__ void __launch_bounds__(kRedThreads)
     __syncthreads();
     if (t == 0) {
         Xyzz v = sh[0];
-        for (uint32_t w = 1; w < kRedThreads / 32; w++) v = xyzz_add_lat(v, sh[w]);
+        for (uint32_t w = 1; w < kRedThreads / 32; w++) v = xyzz_add(v, sh[w]);
         blk_val[dj.kbase[job] + blockIdx.x] = v;
         blk_sum[dj.kbase[job] + blockIdx.x] = tot_sum;
     }
@@ -348,7 +345,7 @@ __device__ __forceinline__ Xyzz block_sum(Xyzz x, Xyzz *sh) {
     if (warp == 0) {
         r = lane_id() < kFinThreads / 32 ? sh[lane_id()] : xyzz_inf();
 #pragma unroll
-        for (int d = 4; d >= 1; d >>= 1) r = xyzz_add_lat(r, shfl_down_pt(r, d));
+        for (int d = 4; d >= 1; d >>= 1) r = xyzz_add(r, shfl_down_pt(r, d));
     }
     return r;  // valid in thread 0
 }
@@ -367,9 +364,9 @@ __global__ void __launch_bounds__(kFinThreads)
     Xyzz lv = xyzz_inf(), lw = xyzz_inf(), ls = xyzz_inf();
     const uint32_t lo = t * q, hi = min(lo + q, nblk);
     for (uint32_t k = hi; k-- > lo;) {
-        lv = xyzz_add_lat(lv, V[k]);
-        ls = xyzz_add_lat(ls, Sm[k]);
-        if (k > lo) lw = xyzz_add_lat(lw, ls);
+        lv = xyzz_add(lv, V[k]);
+        ls = xyzz_add(ls, Sm[k]);
+        if (k > lo) lw = xyzz_add(lw, ls);
     }
     // Block suffix sums of ls: sum_k k sum_k = sum_t lw_t + q sum_{t >= 1} suffix_t.
     Xyzz x = warp_suffix(ls);
@@ -385,21 +382,21 @@ __global__ void __launch_bounds__(kFinThreads)
         if (lane_id() < kFinThreads / 32) sh[lane_id()] = exc;
     }
     __syncthreads();
-    x = xyzz_add_lat(x, sh[warp]);
+    x = xyzz_add(x, sh[warp]);
     Xyzz term = lw;
     if (t >= 1) {
         Xyzz qs = x;
-        for (uint32_t m = q; m > 1; m >>= 1) qs = xyzz_dbl_lat(qs);  // q is a power of two
-        term = xyzz_add_lat(term, qs);
+        for (uint32_t m = q; m > 1; m >>= 1) qs = xyzz_dbl(qs);  // q is a power of two
+        term = xyzz_add(term, qs);
     }
     Xyzz wsum = block_sum(term, sh);
     Xyzz vsum = block_sum(lv, sh);
     if (t == 0) {
         Xyzz tot = wsum;
-        for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl_lat(tot);  // x kRedSpan
-        tot = xyzz_add_lat(tot, vsum);
+        for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl(tot);  // x kRedSpan
+        tot = xyzz_add(tot, vsum);
         const uint32_t sh = min(dj.jobs[job].shift, (uint32_t)kScalarBits);
-        for (uint32_t k = 0; k < sh; k++) tot = xyzz_dbl_lat(tot);  // x 2^shift
+        for (uint32_t k = 0; k < sh; k++) tot = xyzz_dbl(tot);  // x 2^shift
         xyzz_store_canonical(dj.jobs[job].out, tot);
     }
 }
