@@ -137,8 +137,23 @@ int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream 
 int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream);
 
 /* Flags of zk_commit_batch. */
-#define ZK_EVALS 1u /* vectors are evaluations over H: INTT each one first (in place, on
-                       a workspace copy -- the caller's vectors are not modified) */
+#define ZK_EVALS 1u    /* vectors are evaluations over H: commit to their interpolants, by
+                          the context's route (zk_set_commit_route; default: INTT each one
+                          on a workspace copy -- the caller's vectors are not modified --
+                          then MSM over the SRS) */
+#define ZK_LAGRANGE 2u /* vectors are evaluations over H: commit through the Lagrange basis
+                          [L_k(tau)]_1 of H, with no INTT (same result as ZK_EVALS) */
+
+/* Route of evaluation-form commitments (ZK_EVALS, leaf accumulators, fold
+ * cross terms).  ZK_ROUTE_INTT interpolates (INTT) and commits over the SRS,
+ * as the paper's encoding describes (Sec. 3).  ZK_ROUTE_LAGRANGE commits the
+ * evaluations directly over [L_k(tau)]_1 = n^{-1} sum_j omega^{-jk} [tau^j]_1,
+ * a basis the library derives from the SRS once per size (an inverse DFT over
+ * G1); the commitment is the same point, and quantised witness values stay
+ * short scalars.  The route is shared by a context and its lanes. */
+#define ZK_ROUTE_INTT 0
+#define ZK_ROUTE_LAGRANGE 1
+int zk_set_commit_route(zk_ctx *ctx, int route);
 
 /* Commit `count` vectors in one batched pass: out[k] = commitment of vecs[k]
  * (lens[k] elements).  `vecs` is a host array of pointers (each device or

@@ -20,6 +20,8 @@ LIB_PATH = os.environ.get("ZK_B300_LIB", os.path.join(_HERE, "libzkb300.so"))
 
 ZK_OK, ZK_EINVAL, ZK_ESRS, ZK_ENOMEM, ZK_ECUDA, ZK_ETIMEOUT, ZK_EBUSY = range(7)
 ZK_EVALS = 1
+ZK_LAGRANGE = 2
+ZK_ROUTE_INTT, ZK_ROUTE_LAGRANGE = 0, 1
 
 
 class ZkError(RuntimeError):
@@ -81,6 +83,7 @@ def _load():
         "zk_fold": [_VP, _VP, _VP, _VP, _VP, _VP, _VP],
         "zk_fold_tree": [_VP, _VP, _SZ, _VP, _VP, _VP],
         "zk_timing_enable": [_VP, ctypes.c_int],
+        "zk_set_commit_route": [_VP, ctypes.c_int],
         "zk_tune_set": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "zk_plan_commit_batch": [_VP, _VP, _VP, _SZ, ctypes.c_uint, _VP, ctypes.POINTER(_VP)],
         "zk_plan_fold_tree": [_VP, _VP, _SZ, _VP, _VP, ctypes.POINTER(_VP)],
@@ -121,7 +124,7 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
-            "zk_server_destroy"]
+            "zk_server_destroy", "zk_set_commit_route"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 
@@ -141,6 +144,10 @@ def zk_probe_rates(device: int = 0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib.zk_probe_rates(int(device), ctypes.byref(a), ctypes.byref(b)), "zk_probe_rates")
     return a.value, b.value
+
+
+def zk_set_commit_route(ctx: int, route: int) -> None:
+    _check(lib.zk_set_commit_route(ctx, int(route)), "zk_set_commit_route")
 
 
 def zk_timing_enable(ctx: int, on: bool = True) -> None:

@@ -22,6 +22,8 @@ Shared::~Shared() {
     if (srs.p) cudaFree(srs.p);
     for (auto &b : tw)
         if (b.p) cudaFree(b.p);
+    for (auto &b : lag)
+        if (b.p) cudaFree(b.p);
 }
 
 int dev_alloc(Shared &sh, DevBuf &b, size_t bytes) {
@@ -314,6 +316,12 @@ int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double 
     return ZK_OK;
 }
 
+int zk_set_commit_route(zk_ctx *ctx, int route) {
+    if (!ctx || (route != ZK_ROUTE_INTT && route != ZK_ROUTE_LAGRANGE)) return ZK_EINVAL;
+    ctx->sh->commit_route = route;
+    return ZK_OK;
+}
+
 int zk_timing_enable(zk_ctx *ctx, int on) {
     if (!ctx) return ZK_EINVAL;
     ctx->timing = on != 0;
@@ -416,11 +424,14 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
                     unsigned flags, zk_g1 *out, zk_stream stream) {
     if (!ctx || !vecs || !lens || !out) return ZK_EINVAL;
     if (count == 0) return ZK_OK;
-    if (flags & ~ZK_EVALS) return ZK_EINVAL;
+    if (flags & ~(ZK_EVALS | ZK_LAGRANGE)) return ZK_EINVAL;
     DeviceGuard g(ctx);
     cudaStream_t s = (cudaStream_t)stream;
-    const bool evals = flags & ZK_EVALS;
     Shared &sh = *ctx->sh;
+    // Evaluation-form vectors go through the INTT and the SRS, or directly
+    // through the Lagrange basis of H (ZK_LAGRANGE, or the context's route).
+    const bool lagrange = (flags & ZK_LAGRANGE) || ((flags & ZK_EVALS) && sh.commit_route == ZK_ROUTE_LAGRANGE);
+    const bool evals = (flags & (ZK_EVALS | ZK_LAGRANGE)) != 0;
     if (sh.srs_n == 0) return ZK_ESRS;
     std::vector<size_t> padded(count);
     size_t total = 0;
@@ -440,8 +451,11 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
         dev_in[k] = !lens[k] || is_device_ptr(vecs[k]);
         any_host |= !dev_in[k];
     }
+    bool need_ws = any_host;
+    for (size_t k = 0; k < count; k++)
+        need_ws |= evals && (!lagrange || padded[k] != lens[k]);
     uint32_t *ws = nullptr;
-    if (evals || any_host) {
+    if (need_ws) {
         ws = (uint32_t *)scratch(ctx, "commit.ws", std::max<size_t>(total, 1) * 32, &err);
         if (!ws) return err;
     }
@@ -451,7 +465,7 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
     size_t off = 0;
     for (size_t k = 0; k < count; k++) {
         const uint32_t *src = (const uint32_t *)vecs[k];
-        if (evals || !dev_in[k]) {
+        if ((evals && (!lagrange || padded[k] != lens[k])) || !dev_in[k]) {
             uint32_t *dst = ws + off * 8;
             if (lens[k]) {
                 cudaMemcpyKind kind = dev_in[k] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -461,7 +475,7 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
                 k_zero_pad<<<64, 256, 0, s>>>((uint4 *)dst, lens[k] * 2, padded[k] * 2);
                 ZK_LAUNCHED();
             }
-            if (evals && padded[k]) {
+            if (evals && !lagrange && padded[k]) {
                 ntt_vecs.push_back(dst);
                 ntt_lens.push_back(padded[k]);
             }
@@ -469,6 +483,13 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
         }
         jobs[k].scalars = src;
         jobs[k].n = (uint32_t)padded[k];
+        if (lagrange && padded[k] > 1) {
+            int lg = 0;
+            while (((size_t)1 << lg) < padded[k]) lg++;
+            const Affine *lb;
+            ZK_TRY(lagrange_get(ctx, lg, &lb, s));
+            jobs[k].basis = lg;
+        }
         off += padded[k];
     }
     if (!ntt_vecs.empty())

@@ -16,6 +16,9 @@
 
 namespace zk {
 
+struct Affine;
+struct Xyzz;
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -30,6 +33,7 @@ struct DevBuf {
 struct WindowTable {
     int c = 0;
     int W = 0;
+    int basis = 0;  // 0: the SRS (monomial basis); lg > 0: the Lagrange basis of H, |H| = 2^lg
     size_t n = 0;
     DevBuf buf;
 };
@@ -46,6 +50,8 @@ struct Shared {
     DevBuf srs;  // affine Montgomery, srs_n points
     std::deque<WindowTable> tables;  // deque: references stay valid as tables are added
     DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg
+    DevBuf lag[29];              // lag[lg][k] = [L_k(tau)]_1 over H of size 2^lg (affine Montgomery)
+    int commit_route = 0;        // ZK_ROUTE_INTT or ZK_ROUTE_LAGRANGE for evaluation-form commitments
     int tuned_window[29] = {};   // MSM window width per log2 length (0 = built-in)
     int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = built-in)
     ~Shared();
@@ -168,7 +174,11 @@ struct PhaseScope {
 int srs_load_impl(zk_ctx *ctx, const zk_g1 *pts, size_t n, cudaStream_t s);
 int srs_generate_impl(zk_ctx *ctx, const zk_fr *tau, size_t n, cudaStream_t s);
 int srs_export_impl(zk_ctx *ctx, zk_g1 *out, size_t first, size_t count, cudaStream_t s);
-int table_get(zk_ctx *ctx, int c, size_t n, const WindowTable **out, cudaStream_t s);
+int table_get(zk_ctx *ctx, int c, size_t n, int basis, const WindowTable **out, cudaStream_t s);
+// Lagrange basis [L_k(tau)]_1 of H (|H| = 2^lg), derived from the SRS by an
+// inverse DFT over G1 on first use (lagrange.cu).
+int lagrange_get(zk_ctx *ctx, int lg, const Affine **out, cudaStream_t s);
+int normalize_points(zk_ctx *ctx, const Xyzz *in, Affine *out, size_t n, cudaStream_t s);
 
 // NTT (ntt.cu)
 int ntt_impl(zk_ctx *ctx, uint32_t *data, size_t n, bool inverse, cudaStream_t s);
@@ -185,6 +195,7 @@ struct MsmJob {
     const uint32_t *scalars;
     uint32_t n;
     void *out;
+    int basis = 0;  // 0: scalars are coefficients (SRS); lg: evaluations over H, n = 2^lg (Lagrange basis)
 };
 int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStream_t s);
 int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count);

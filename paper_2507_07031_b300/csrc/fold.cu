@@ -144,6 +144,12 @@ __global__ void k_copy(const uint4 *__restrict__ src, uint4 *__restrict__ dst, s
 
 bool pow2(size_t n) { return n && !(n & (n - 1)); }
 
+int ilog2_size(size_t n) {
+    int l = 0;
+    while (((size_t)1 << l) < n) l++;
+    return l;
+}
+
 bool acc_ok(const zk_acc *a, size_t n) {
     if (!a || a->n != n || !a->e || !a->x) return false;
     for (int i = 0; i < 4; i++)
@@ -163,6 +169,13 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     int err = ZK_OK;
     uint32_t *e1 = (uint32_t *)scratch(ctx, "fold.e1", F * (size_t)n * 32, &err);
     if (!e1) return err;
+    // E1 = Commit(e1): INTT then the SRS, or the Lagrange basis directly.
+    const int lg = ilog2_size(n);
+    const bool lagrange = ctx->sh->commit_route == ZK_ROUTE_LAGRANGE;
+    if (lagrange) {
+        const Affine *lb;
+        ZK_TRY(lagrange_get(ctx, lg, &lb, s));
+    }
     std::vector<uint32_t *> vecs(F);
     std::vector<size_t> lens(F, n);
     std::vector<MsmJob> jobs(F);
@@ -173,6 +186,7 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
         jobs[f].scalars = descs[f].e1;
         jobs[f].n = n;
         jobs[f].out = descs[f].E1;
+        jobs[f].basis = lagrange ? lg : 0;
     }
     ZK_TRY(upload(ctx, dd, descs.data(), F * sizeof(FoldDesc), s));
     dim3 g(elem_blocks(n), (unsigned)F);
@@ -183,7 +197,7 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
         k_fold_mu<<<(unsigned)((F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();
     }
-    ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), F, true, s));
+    if (!lagrange) ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), F, true, s));
     ZK_TRY(msm_batch_impl(ctx, jobs.data(), F, 0, s));
     if (s_inst != s) {
         ZK_CUDA_TRY(cudaEventRecord(ev, s));
@@ -317,11 +331,20 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
     // Commit in groups so the INTT and MSM workspace stays near 2^24 elements.
     const size_t group = std::max<size_t>(1, ((size_t)1 << 24) / (4 * n));
     int err = ZK_OK;
+    const int lg = ilog2_size(n);
+    const bool lagrange = ctx->sh->commit_route == ZK_ROUTE_LAGRANGE;
+    if (lagrange) {
+        const Affine *lb;
+        ZK_TRY(lagrange_get(ctx, lg, &lb, s));
+    }
     for (size_t a0 = 0; a0 < count; a0 += group) {
         const size_t a1 = std::min(count, a0 + group);
         const size_t G = a1 - a0;
-        uint32_t *ws = (uint32_t *)scratch(ctx, "leaf.ws", 4 * G * n * 32, &err);
-        if (!ws) return err;
+        uint32_t *ws = nullptr;
+        if (!lagrange) {
+            ws = (uint32_t *)scratch(ctx, "leaf.ws", 4 * G * n * 32, &err);
+            if (!ws) return err;
+        }
         std::vector<uint32_t *> vecs;
         std::vector<size_t> lens;
         std::vector<MsmJob> jobs;
@@ -333,20 +356,25 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
                                                             (uint32_t *)A.x, (uint32_t)n);
             ZK_LAUNCHED();
             for (int i = 0; i < 4; i++) {
-                uint32_t *dst = ws + ((a - a0) * 4 + i) * n * 8;
-                k_copy<<<elem_blocks((uint32_t)n), 256, 0, s>>>((const uint4 *)A.m[i], (uint4 *)dst,
-                                                                n * 2);
-                ZK_LAUNCHED();
-                vecs.push_back(dst);
-                lens.push_back(n);
                 MsmJob j;
-                j.scalars = dst;
                 j.n = (uint32_t)n;
                 j.out = (char *)A.x + 64 * i;
+                if (lagrange) {  // commit the evaluations in place
+                    j.scalars = (const uint32_t *)A.m[i];
+                    j.basis = lg;
+                } else {         // interpolate a copy, then commit over the SRS
+                    uint32_t *dst = ws + ((a - a0) * 4 + i) * n * 8;
+                    k_copy<<<elem_blocks((uint32_t)n), 256, 0, s>>>((const uint4 *)A.m[i],
+                                                                    (uint4 *)dst, n * 2);
+                    ZK_LAUNCHED();
+                    vecs.push_back(dst);
+                    lens.push_back(n);
+                    j.scalars = dst;
+                }
                 jobs.push_back(j);
             }
         }
-        ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), vecs.size(), true, s));
+        if (!lagrange) ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), vecs.size(), true, s));
         ZK_TRY(msm_batch_impl(ctx, jobs.data(), jobs.size(), 0, s));
     }
     return ZK_OK;

@@ -552,23 +552,29 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     }
     if (nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
     std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) {
-        return a.c != b.c ? a.c < b.c : (a.wins > 1) < (b.wins > 1);
+        if (a.c != b.c) return a.c < b.c;
+        if (a.job.basis != b.job.basis) return a.job.basis < b.job.basis;
+        return (a.wins > 1) < (b.wins > 1);
     });
-    // Point tables: the SRS itself for one-window jobs, else the width's
-    // window table (built on first use of a width, outside any timed loop).
+    // Point tables: the base points themselves (SRS, or the Lagrange basis
+    // of H for evaluation-form jobs) for one-window jobs, else the width's
+    // window table of that basis (built on first use, outside timed loops).
     std::vector<const Affine *> tabs(count);
     std::vector<uint32_t> tabn(count);
     for (size_t k = 0; k < count; k++) {
+        const int basis = jv[k].job.basis;
+        if (basis && (!sh.lag[basis].p || jv[k].job.n != (1u << basis))) return ZK_EINVAL;
         if (jv[k].wins <= 1) {
-            tabs[k] = (const Affine *)sh.srs.p;
-            tabn[k] = (uint32_t)sh.srs_n;
+            tabs[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
+            tabn[k] = basis ? (1u << basis) : (uint32_t)sh.srs_n;
             continue;
         }
         size_t need = 1;
         for (size_t j = 0; j < count; j++)
-            if (jv[j].c == jv[k].c && jv[j].wins > 1) need = std::max(need, (size_t)jv[j].job.n);
+            if (jv[j].c == jv[k].c && jv[j].job.basis == basis && jv[j].wins > 1)
+                need = std::max(need, (size_t)jv[j].job.n);
         const WindowTable *t;
-        ZK_TRY(table_get(ctx, jv[k].c, need, &t, s));
+        ZK_TRY(table_get(ctx, jv[k].c, need, basis, &t, s));
         tabs[k] = (const Affine *)t->buf.p;
         tabn[k] = (uint32_t)t->n;
     }
@@ -820,7 +826,7 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     {
         std::lock_guard<std::mutex> g(sh.mu);
         for (auto &t : sh.tables)
-            if (t.c == kNoAllocC && t.n >= n) tab = &t;
+            if (t.c == kNoAllocC && t.basis == 0 && t.n >= n) tab = &t;
     }
     if (!tab) return ZK_ESRS;  // the c = 16 table is built when the SRS is loaded
     unsigned char *ws = nullptr;

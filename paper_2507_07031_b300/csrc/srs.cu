@@ -152,15 +152,18 @@ __global__ void k_shift_window(const Affine *__restrict__ src, Xyzz *__restrict_
     dst[i] = p;
 }
 
-int build_table(zk_ctx *ctx, WindowTable &t, int c, size_t n, cudaStream_t s) {
+int build_table(zk_ctx *ctx, WindowTable &t, int c, size_t n, int basis, cudaStream_t s) {
     Shared &sh = *ctx->sh;
+    const Affine *base = (const Affine *)sh.srs.p;
+    if (basis) base = (const Affine *)sh.lag[basis].p;
     const int W = windows_for(c);
     ZK_TRY(dev_alloc(sh, t.buf, (size_t)W * n * sizeof(Affine)));
     t.c = c;
     t.W = W;
     t.n = n;
+    t.basis = basis;
     Affine *tab = (Affine *)t.buf.p;
-    ZK_CUDA_TRY(cudaMemcpyAsync(tab, sh.srs.p, n * sizeof(Affine), cudaMemcpyDeviceToDevice, s));
+    ZK_CUDA_TRY(cudaMemcpyAsync(tab, base, n * sizeof(Affine), cudaMemcpyDeviceToDevice, s));
     int err = ZK_OK;
     Xyzz *tmp = (Xyzz *)scratch(ctx, "srs.xyzz", n * sizeof(Xyzz), &err);
     if (!tmp) return err;
@@ -178,18 +181,24 @@ int build_table(zk_ctx *ctx, WindowTable &t, int c, size_t n, cudaStream_t s) {
 void drop_srs(Shared &sh) {
     for (auto &t : sh.tables) dev_free(sh, t.buf);
     sh.tables.clear();
+    for (auto &l : sh.lag) dev_free(sh, l);
     dev_free(sh, sh.srs);
     sh.srs_n = 0;
 }
 
 }  // namespace
 
-int table_get(zk_ctx *ctx, int c, size_t n, const WindowTable **out, cudaStream_t s) {
+int normalize_points(zk_ctx *ctx, const Xyzz *in, Affine *out, size_t n, cudaStream_t s) {
+    return normalize(ctx, in, out, n, s);
+}
+
+int table_get(zk_ctx *ctx, int c, size_t n, int basis, const WindowTable **out, cudaStream_t s) {
     Shared &sh = *ctx->sh;
     if (sh.srs_n == 0 || n > sh.srs_n) return ZK_ESRS;
+    if (basis && (n > ((size_t)1 << basis) || !sh.lag[basis].p)) return ZK_EINVAL;
     std::lock_guard<std::mutex> g(sh.mu);
     for (auto &t : sh.tables) {
-        if (t.c == c && t.n >= n) {
+        if (t.c == c && t.basis == basis && t.n >= n) {
             *out = &t;
             return ZK_OK;
         }
@@ -198,10 +207,10 @@ int table_get(zk_ctx *ctx, int c, size_t n, const WindowTable **out, cudaStream_
     // a smaller table of the same width stays alive for work still queued.
     size_t tn = 1;
     while (tn < n) tn <<= 1;
-    tn = std::min(tn, sh.srs_n);
+    tn = std::min(tn, basis ? ((size_t)1 << basis) : sh.srs_n);
     if ((size_t)windows_for(c) * tn >= ((size_t)1 << 31)) return ZK_EINVAL;
     sh.tables.emplace_back();
-    int r = build_table(ctx, sh.tables.back(), c, tn, s);
+    int r = build_table(ctx, sh.tables.back(), c, tn, basis, s);
     if (r != ZK_OK) {
         dev_free(sh, sh.tables.back().buf);
         sh.tables.pop_back();
@@ -243,7 +252,7 @@ int srs_load_impl(zk_ctx *ctx, const zk_g1 *pts, size_t n, cudaStream_t s) {
     }
     sh.srs_n = n;
     const WindowTable *t;
-    ZK_TRY(table_get(ctx, 16, n, &t, s));
+    ZK_TRY(table_get(ctx, 16, n, 0, &t, s));
     ZK_CUDA_TRY(cudaStreamSynchronize(s));
     return ZK_OK;
 }
@@ -279,7 +288,7 @@ int srs_generate_impl(zk_ctx *ctx, const zk_fr *tau, size_t n, cudaStream_t s) {
     ZK_CUDA_TRY(cudaStreamSynchronize(s));
     sh.srs_n = n;
     const WindowTable *t;
-    ZK_TRY(table_get(ctx, 16, n, &t, s));
+    ZK_TRY(table_get(ctx, 16, n, 0, &t, s));
     ZK_CUDA_TRY(cudaStreamSynchronize(s));
     return ZK_OK;
 }
