@@ -416,6 +416,9 @@ def run_extras(zk, ctx, dev, torch):
     tp = _time(torch, plain, 3)
     ph_p = {k: round(v[0] / 3, 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
     zk.zk_timing_enable(ctx, False)
+    outl = torch.zeros_like(outb)
+    zk.zk_commit_batch(ctx, vecs, outl, flags=zk.ZK_LAGRANGE)  # builds the bases
+    tl = _time(torch, lambda: zk.zk_commit_batch(ctx, vecs, outl, flags=zk.ZK_LAGRANGE), 3)
     outg = torch.zeros_like(outb)
     plan = zk.zk_plan_commit_batch(ctx, vecs, outg, flags=zk.ZK_EVALS)
     tg = _time(torch, lambda: zk.zk_plan_launch(plan), 3)
@@ -423,8 +426,9 @@ def run_extras(zk, ctx, dev, torch):
     zk.zk_plan_destroy(plan)
     res["cnn_batch_commit"] = {"polys": len(vecs), "coeffs": int(sizes.sum()),
                                "batched_ms": tb, "plain_ms": tp, "graph_ms": tg, "graph_nodes": nodes,
-                               "speedup": tp / tb,
-                               "identical": bool(torch.equal(outb, outp) and torch.equal(outg, outb)),
+                               "lagrange_batched_ms": tl, "speedup": tp / tb,
+                               "identical": bool(torch.equal(outb, outp) and torch.equal(outg, outb)
+                                                 and torch.equal(outl, outb)),
                                "batched_phase_ms": ph_b, "plain_phase_ms": ph_p}
     del vecs
     # Fold tree: 1024 leaves of 2^16 (config: matmul block, 4 witness vectors).
@@ -491,16 +495,35 @@ def run_extras(zk, ctx, dev, torch):
     tg = _time(torch, lambda: zk.zk_plan_launch(plan), 1)
     same = same and all(torch.equal(a, b) for a, b in zip(root, root_batched))
     zk.zk_plan_destroy(plan)
+    # Lagrange route: leaf commitments and cross terms without INTTs.
+    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
+    restore()
+    zk.zk_leaf_init(ctx, descs)  # builds the 2^16 basis
+    torch.cuda.synchronize()
+    t_leaf_l = _time(torch, lambda: zk.zk_leaf_init(ctx, descs), 1)
+    leaf_same = all(torch.equal(a[2], s_[2]) for a, s_ in zip(accs, leaf_state))
+    restore()
+    tree()
+    restore()
+    torch.cuda.synchronize()
+    tl = _time(torch, tree, 1)
+    same = same and leaf_same and all(torch.equal(a, b) for a, b in zip(root, root_batched))
+    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
     res["fold_tree"] = {"leaves": count, "n": n, "folds": count - 1,
                         "batched_folds_per_s": (count - 1) / (tt * 1e-3),
                         "plain_folds_per_s": (count - 1) / (tp * 1e-3),
                         "graph_folds_per_s": (count - 1) / (tg * 1e-3),
+                        "lagrange_folds_per_s": (count - 1) / (tl * 1e-3), "lagrange_ms": tl,
+                        "lagrange_leaf_commit_ms": t_leaf_l,
                         "batched_ms": tt, "plain_ms": tp, "graph_ms": tg, "speedup": tp / tt,
                         "leaf_commit_ms": t_leaf, "identical": bool(same),
                         "batched_phase_ms": ph_tree}
     del accs, leaf_state, descs
     torch.cuda.empty_cache()
     res["serving"] = run_serving(zk, ctx, dev, torch)
+    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
+    res["serving_lagrange"] = run_serving(zk, ctx, dev, torch)
+    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
     return res
 
 
