@@ -15,9 +15,9 @@
 //      piece sums are combined again in rounds of kPiece until every bucket
 //      is a single point, so skewed buckets (quantised ML values put 2^20
 //      points into 128 buckets) keep the whole GPU busy;
-//   4. reduce: sum_b (b + 1) S_b per MSM by block-level suffix scans
-//      (256 threads x 4 buckets per block), then one warp per MSM combines the
-//      block results;
+//   4. reduce: sum_b (b + 1) S_b per MSM by segment-level suffix scans in up
+//      to three levels, each point addition spread over the four warps of a
+//      block (team.cuh) because this phase is latency bound;
 //   5. normalise the result to canonical affine coordinates.
 // Every MSM of a batch (uneven lengths) goes through the same launches.
 #include <cuda_runtime.h>
@@ -29,6 +29,7 @@
 #include "ctx.cuh"
 #include "curve.cuh"
 #include "scan.cuh"
+#include "team.cuh"
 
 namespace zk {
 
@@ -36,12 +37,7 @@ namespace {
 
 constexpr uint32_t kInvalid = 0xffffffffu;
 constexpr int kPiece = 32;       // entries (or partial sums) per thread per round
-constexpr int kRedThreads = 64;  // bucket-reduction block
-constexpr int kRedPer = 4;       // buckets per thread
-constexpr int kRedSpan = kRedThreads * kRedPer;
-constexpr int kRedSpanLog = 8;
 constexpr size_t kStatsMin = 4096;  // scalars below which the width scan is skipped
-static_assert(kRedSpan == 1 << kRedSpanLog, "reduction span");
 
 // One MSM of a batch.  Jobs are ordered by window width so that each width's
 // scalars form one contiguous range for its recode launch.
@@ -251,154 +247,130 @@ __global__ void k_buckets_final(const uint32_t *__restrict__ sorted, DevJobs dj,
     buckets[b] = acc;
 }
 
-// Warp shuffle of a whole point.
-__device__ __forceinline__ Xyzz shfl_down_pt(const Xyzz &p, int d) {
-    Xyzz r;
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        r.X.v[i] = __shfl_down_sync(0xffffffffu, p.X.v[i], d);
-        r.Y.v[i] = __shfl_down_sync(0xffffffffu, p.Y.v[i], d);
-        r.ZZ.v[i] = __shfl_down_sync(0xffffffffu, p.ZZ.v[i], d);
-        r.ZZZ.v[i] = __shfl_down_sync(0xffffffffu, p.ZZZ.v[i], d);
-    }
-    return r;
-}
+// Phase 4: bucket reduction, sum_b (b + 1) S_b per MSM, on teams (team.cuh):
+// its scans and trees have few additions in flight, so the latency of one
+// addition, not the SM's throughput, sets their time.
+//
+// Level 0 reads the buckets.  Every level cuts its items into segments of at
+// most kSeg, and one team reduces one segment: with items k < m carrying
+// points X_k and Y_k (Y = X at level 0),
+//     V = sum_k Y_k + 2^f sum_k k X_k,   S = sum_k X_k,   f = kSegLog * level.
+// Segment g of a level becomes item g of the next one (X = S, Y = V); for
+// k = kSeg g + j,
+//     sum_k Y_k + 2^f sum_k k X_k = sum_g (V_g + 2^(f + kSegLog) g S_g),
+// so the sum is invariant across levels, and at level 0 it is
+// sum_b S_b + sum_b b S_b = sum_b (b + 1) S_b.  The level whose items fit one
+// segment is final: its V, doubled `shift` times, is the MSM.
+//
+// Within a segment, lane l owns the q = seg / 32 consecutive items
+// k = l q + t and runs the suffix form  w_l = sum_t t X_{lq+t}  (adding the
+// running sum r of the later items before each new item), r_l = sum_t X;
+// then sum_k k X_k = sum_l (w_l + q l r_l) and sum_l l r_l = sum_{l >= 1}
+// R_l with R the suffix scan of r over the lanes.
+constexpr int kSegLog = 8;
+constexpr uint32_t kSeg = 1u << kSegLog;
+constexpr int kMaxLevels = 3;
+// Level-1 outputs per MSM that level 2 reads: 2^(logB - 2 kSegLog) <= kL2Per.
+constexpr uint32_t kL2Per = 8;
+static_assert(kMaxWindow - 1 <= 3 * kSegLog && (1u << (kMaxWindow - 1 - 2 * kSegLog)) <= kL2Per,
+              "reduction levels");
 
-// Inclusive suffix sum over the lanes of a warp: lane l gets sum_{l' >= l} x_l'.
-__device__ __forceinline__ Xyzz warp_suffix(Xyzz x) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        Xyzz y = shfl_down_pt(x, d);
-        if (lane_id() + d < 32) x = xyzz_add(x, y);
-    }
-    return x;
-}
+// Shared-memory slots of the reduction team (points take four slots).
+constexpr int kSlR = 0, kSlW = 4, kSlYA = 8, kSlIn = 12, kSlYIn = 16, kSlTmp = 20, kSlT = 24;
+constexpr int kSlots = kSlT + kTeamTemps;
 
-// Sum over the lanes of a warp (valid in lane 0).
-__device__ __forceinline__ Xyzz warp_sum(Xyzz x) {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        Xyzz y = shfl_down_pt(x, d);
-        x = xyzz_add(x, y);
-    }
-    return x;
-}
-
-// Phase 4a: for block k of kRedSpan buckets of MSM j (b0 = its first bucket),
-// val = sum_b (b - b0 + 1) S_b and sum = sum_b S_b.  Grid (max blocks, jobs).
-__global__ void __launch_bounds__(kRedThreads)
-    k_reduce_blocks(const Xyzz *__restrict__ buckets, DevJobs dj, Xyzz *__restrict__ blk_val,
-                    Xyzz *__restrict__ blk_sum) {
-    __shared__ Xyzz sh[kRedThreads / 32];
+__global__ void __launch_bounds__(kTeamThreads)
+    k_reduce_team(const Xyzz *__restrict__ buckets, Xyzz *__restrict__ v1, Xyzz *__restrict__ s1,
+                  Xyzz *__restrict__ v2, Xyzz *__restrict__ s2, DevJobs dj, uint32_t level) {
+    __shared__ uint32_t f[kSlots * 8 * 32];
     const uint32_t job = blockIdx.y;
-    const uint32_t nblk = dj.kbase[job + 1] - dj.kbase[job];
-    if (blockIdx.x >= nblk) return;
-    const uint32_t t = threadIdx.x;
-    const Xyzz *S = buckets + dj.bbase[job] + (size_t)blockIdx.x * kRedSpan + kRedPer * t;
-    // thread-local: l = sum_i (i + 1) S_i, r = sum_i S_i
-    Xyzz r = S[kRedPer - 1];
-    Xyzz l = r;
-#pragma unroll
-    for (int i = kRedPer - 2; i >= 0; i--) {
-        r = xyzz_add(r, S[i]);
-        l = xyzz_add(l, r);
+    const uint32_t logB = dj.jobs[job].logB;
+    if (level > 0 && logB <= kSegLog * level) return;  // final at an earlier level
+    const uint32_t m = 1u << (logB - kSegLog * level);
+    const uint32_t seg = min(m, kSeg);
+    if (blockIdx.x >= m / seg) return;
+    const bool final_level = m <= kSeg;
+    const Xyzz *X, *Y;
+    if (level == 0) {
+        X = buckets + dj.bbase[job];
+        Y = nullptr;
+    } else if (level == 1) {
+        X = s1 + dj.kbase[job];
+        Y = v1 + dj.kbase[job];
+    } else {
+        X = s2 + (size_t)kL2Per * job;
+        Y = v2 + (size_t)kL2Per * job;
     }
-    // block suffix sums of r
-    Xyzz x = warp_suffix(r);
-    const uint32_t warp = t >> 5;
-    if (lane_id() == 0) sh[warp] = x;
-    __syncthreads();
-    Xyzz later = xyzz_inf();
-    for (uint32_t w = warp + 1; w < kRedThreads / 32; w++) later = xyzz_add(later, sh[w]);
-    x = xyzz_add(x, later);  // x = sum_{t' >= t} r_t'
-    // contrib_t = l_t + 4 t r_t summed over t == sum_t l_t + 4 sum_{t >= 1} suffix_t
-    Xyzz c = l;
-    if (t >= 1) c = xyzz_add(c, xyzz_dbl(xyzz_dbl(x)));
-    Xyzz tot_sum = x;  // suffix at t = 0 is the block sum
-    __syncthreads();
-    c = warp_sum(c);
-    if (lane_id() == 0) sh[warp] = c;
-    __syncthreads();
-    if (t == 0) {
-        Xyzz v = sh[0];
-        for (uint32_t w = 1; w < kRedThreads / 32; w++) v = xyzz_add(v, sh[w]);
-        blk_val[dj.kbase[job] + blockIdx.x] = v;
-        blk_sum[dj.kbase[job] + blockIdx.x] = tot_sum;
-    }
-}
+    X += (size_t)blockIdx.x * seg;
+    if (Y) Y += (size_t)blockIdx.x * seg;
+    const uint32_t l = team_lane(), w = team_warp();
+    const uint32_t q = seg >= 32 ? seg / 32 : 1;
 
-// Phase 4b + 5: one block of kFinThreads per MSM combines the block results:
-// total = sum_k val_k + kRedSpan sum_k k sum_k, with sum_k k sum_k equal to
-// sum_{j >= 1} suffix_j (suffix sums of sum_k).  Every thread holds at most
-// kFinPer blocks, so the serial depth is a few additions plus two block-wide
-// scans (each point addition is a chain of dependent products: depth, not
-// work, bounds this phase).
-constexpr int kFinThreads = 256;
-
-__device__ __forceinline__ Xyzz block_sum(Xyzz x, Xyzz *sh) {
-    const uint32_t warp = threadIdx.x >> 5;
-    x = warp_sum(x);
-    __syncthreads();
-    if (lane_id() == 0) sh[warp] = x;
-    __syncthreads();
-    Xyzz r = xyzz_inf();
-    if (warp == 0) {
-        r = lane_id() < kFinThreads / 32 ? sh[lane_id()] : xyzz_inf();
-#pragma unroll
-        for (int d = 4; d >= 1; d >>= 1) r = xyzz_add(r, shfl_down_pt(r, d));
+    team_set_inf_nosync(f, kSlR);
+    team_set_inf_nosync(f, kSlW);
+    team_set_inf_nosync(f, kSlYA);
+    // Serial part, items t = q - 1 .. 0 of this lane; the next item's
+    // coordinate is fetched while the current one is added.
+    uint32_t k = l * q + (q - 1);
+    Fq nx = team_fetch(X + k, k < seg);
+    Fq ny = Y ? team_fetch(Y + k, k < seg) : fe_zero<FqP>();
+    for (uint32_t t = q; t-- > 0;) {
+        tf_store(f, kSlIn + w, nx);
+        if (Y) tf_store(f, kSlYIn + w, ny);
+        if (t > 0) {
+            k = l * q + (t - 1);
+            nx = team_fetch(X + k, k < seg);
+            if (Y) ny = team_fetch(Y + k, k < seg);
+        }
+        __syncthreads();
+        team_add(f, kSlW, kSlR, kSlW, kSlT);  // w += (sum of the later items)
+        team_add(f, kSlR, kSlIn, kSlR, kSlT);
+        if (Y) team_add(f, kSlYA, kSlYIn, kSlYA, kSlT);
     }
-    return r;  // valid in thread 0
-}
-
-__global__ void __launch_bounds__(kFinThreads)
-    k_reduce_final(const Xyzz *__restrict__ blk_val, const Xyzz *__restrict__ blk_sum, DevJobs dj) {
-    __shared__ Xyzz sh[kFinThreads / 32];
-    const uint32_t job = blockIdx.x;
-    const uint32_t t = threadIdx.x;
-    const uint32_t nblk = dj.kbase[job + 1] - dj.kbase[job];
-    const uint32_t q = (nblk + kFinThreads - 1) / kFinThreads;  // blocks per thread
-    const Xyzz *V = blk_val + dj.kbase[job];
-    const Xyzz *Sm = blk_sum + dj.kbase[job];
-    // Thread t owns blocks [t q, t q + q): lv = sum val, ls = sum sum,
-    // lw = sum_k (k - t q) sum_k.
-    Xyzz lv = xyzz_inf(), lw = xyzz_inf(), ls = xyzz_inf();
-    const uint32_t lo = t * q, hi = min(lo + q, nblk);
-    for (uint32_t k = hi; k-- > lo;) {
-        lv = xyzz_add(lv, V[k]);
-        ls = xyzz_add(ls, Sm[k]);
-        if (k > lo) lw = xyzz_add(lw, ls);
+    // Inclusive suffix scan of r over the lanes: R_l = sum_{l' >= l} r_l'.
+    for (int d = 1; d < 32; d <<= 1) {
+        team_shift(f, kSlR, kSlTmp, d);
+        team_add(f, kSlR, kSlTmp, kSlR, kSlT);
     }
-    // Block suffix sums of ls: sum_k k sum_k = sum_t lw_t + q sum_{t >= 1} suffix_t.
-    Xyzz x = warp_suffix(ls);
-    const uint32_t warp = t >> 5;
-    if (lane_id() == 0) sh[warp] = x;
-    __syncthreads();
-    if (warp == 0) {  // exclusive suffix over the warp totals
-        Xyzz w = lane_id() < kFinThreads / 32 ? sh[lane_id()] : xyzz_inf();
-        Xyzz inc = warp_suffix(w);
-        Xyzz exc = shfl_down_pt(inc, 1);
-        if (lane_id() + 1 >= kFinThreads / 32) exc = xyzz_inf();
-        __syncwarp();
-        if (lane_id() < kFinThreads / 32) sh[lane_id()] = exc;
+    // term_l = w_l + q R_l (l >= 1), then u_l = y_l + 2^f term_l.
+    team_copy(f, kSlR, kSlTmp, l >= 1);
+    for (uint32_t e = q; e > 1; e >>= 1) team_dbl(f, kSlTmp, kSlTmp, kSlT);
+    team_add(f, kSlW, kSlTmp, kSlW, kSlT);
+    for (uint32_t e = 0; e < kSegLog * level; e++) team_dbl(f, kSlW, kSlW, kSlT);
+    if (Y) team_add(f, kSlW, kSlYA, kSlW, kSlT);
+    // Sum over the lanes (lane 0), then sum_k Y_k = R_0 at level 0.
+    for (int d = 16; d >= 1; d >>= 1) {
+        team_shift(f, kSlW, kSlTmp, d);
+        team_add(f, kSlW, kSlTmp, kSlW, kSlT);
     }
-    __syncthreads();
-    x = xyzz_add(x, sh[warp]);
-    Xyzz term = lw;
-    if (t >= 1) {
-        Xyzz qs = x;
-        for (uint32_t m = q; m > 1; m >>= 1) qs = xyzz_dbl(qs);  // q is a power of two
-        term = xyzz_add(term, qs);
-    }
-    Xyzz wsum = block_sum(term, sh);
-    Xyzz vsum = block_sum(lv, sh);
-    if (t == 0) {
-        Xyzz tot = wsum;
-        for (int k = 0; k < kRedSpanLog; k++) tot = xyzz_dbl(tot);  // x kRedSpan
-        tot = xyzz_add(tot, vsum);
+    if (!Y) team_add(f, kSlW, kSlR, kSlW, kSlT);
+    if (final_level) {
         const uint32_t sh = min(dj.jobs[job].shift, (uint32_t)kScalarBits);
-        for (uint32_t k = 0; k < sh; k++) tot = xyzz_dbl(tot);  // x 2^shift
-        xyzz_store_canonical(dj.jobs[job].out, tot);
+        for (uint32_t e = 0; e < sh; e++) team_dbl(f, kSlW, kSlW, kSlT);  // x 2^shift
+        if (threadIdx.x == 0) xyzz_store_canonical(dj.jobs[job].out, team_point(f, kSlW));
+    } else if (l == 0) {
+        const size_t o = (level == 0 ? dj.kbase[job] : (size_t)kL2Per * job) + blockIdx.x;
+        team_put(f, kSlW, (level == 0 ? v1 : v2) + o);
+        team_put(f, kSlR, (level == 0 ? s1 : s2) + o);
     }
+}
+
+// Launches the reduction levels for jobs whose bucket counts are 2^logB[k].
+int launch_reduce(const Xyzz *buckets, Xyzz *v1, Xyzz *s1, Xyzz *v2, Xyzz *s2, const DevJobs &dj,
+                  const uint32_t *logB, size_t count, cudaStream_t s) {
+    for (uint32_t level = 0; level < (uint32_t)kMaxLevels; level++) {
+        uint32_t gx = 0;
+        for (size_t k = 0; k < count; k++) {
+            if (level > 0 && logB[k] <= kSegLog * level) continue;
+            const uint32_t lm = logB[k] - kSegLog * level;
+            gx = std::max(gx, lm > (uint32_t)kSegLog ? 1u << (lm - kSegLog) : 1u);
+        }
+        if (!gx) break;
+        k_reduce_team<<<dim3(gx, (unsigned)count), kTeamThreads, 0, s>>>(buckets, v1, s1, v2, s2, dj,
+                                                                          level);
+        ZK_LAUNCHED();
+    }
+    return ZK_OK;
 }
 
 template <int C, bool SCATTER>
@@ -548,7 +520,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         total64 += m.n;
         entries64 += (size_t)m.n * wins;
         nb64 += (size_t)1 << (c - 1);
-        nblk64 += ((size_t)1 << (c - 1)) / kRedSpan;
+        nblk64 += ((size_t)1 << (c - 1)) / kSeg;
     }
     if (nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
     std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) {
@@ -611,9 +583,11 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     Xyzz *buckets = (Xyzz *)scratch(ctx, "msm.buckets", nb64 * sizeof(Xyzz), &err);
     Xyzz *bval = (Xyzz *)scratch(ctx, "msm.bval", std::max<size_t>(nblk64, 1) * sizeof(Xyzz), &err);
     Xyzz *bsum = (Xyzz *)scratch(ctx, "msm.bsum", std::max<size_t>(nblk64, 1) * sizeof(Xyzz), &err);
+    Xyzz *bv2 = (Xyzz *)scratch(ctx, "msm.bv2", count * kL2Per * sizeof(Xyzz), &err);
+    Xyzz *bs2 = (Xyzz *)scratch(ctx, "msm.bs2", count * kL2Per * sizeof(Xyzz), &err);
     void *scan_tmp = scratch(ctx, "msm.scantmp", scan_temp_bytes(nb), &err);
     if (!jt || !counts || !off0 || !offa || !offb || !cursor || !sorted || !pa || !pb || !buckets ||
-        !bval || !bsum || !scan_tmp)
+        !bval || !bsum || !bv2 || !bs2 || !scan_tmp)
         return err;
 
     // Job table: descriptors and the three prefix arrays.
@@ -622,7 +596,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     uint32_t *hs = (uint32_t *)(h.data() + jd_bytes);
     uint32_t *hb = (uint32_t *)(h.data() + jd_bytes + pre_bytes);
     uint32_t *hk = (uint32_t *)(h.data() + jd_bytes + 2 * pre_bytes);
-    uint32_t maxblk = 1;
+    std::vector<uint32_t> logBs(count);
     for (size_t k = 0; k < count; k++) {
         hd[k].scalars = jv[k].job.scalars;
         hd[k].out = jv[k].job.out;
@@ -633,9 +607,8 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hd[k].wins = jv[k].wins;
         hs[k + 1] = hs[k] + jv[k].job.n;
         hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
-        uint32_t kb = (1u << (jv[k].c - 1)) / kRedSpan;
-        hk[k + 1] = hk[k] + kb;
-        maxblk = std::max(maxblk, kb);
+        hk[k + 1] = hk[k] + (1u << (jv[k].c - 1)) / kSeg;
+        logBs[k] = (uint32_t)(jv[k].c - 1);
     }
     ZK_TRY(upload(ctx, jt, h.data(), h.size(), s));
     DevJobs dj;
@@ -695,12 +668,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
 
     // 4-5: bucket reduction and output.
     PhaseScope ph_reduce(ctx, ZK_PHASE_MSM_REDUCE, s);
-    dim3 g(maxblk, (unsigned)count);
-    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, dj, bval, bsum);
-    ZK_LAUNCHED();
-    k_reduce_final<<<(unsigned)count, kFinThreads, 0, s>>>(bval, bsum, dj);
-    ZK_LAUNCHED();
-    return ZK_OK;
+    return launch_reduce(buckets, bval, bsum, bv2, bs2, dj, logBs.data(), count, s);
 }
 
 }  // namespace zk
@@ -728,7 +696,7 @@ constexpr uint32_t kNoAllocB = 1u << (kNoAllocC - 1);
 constexpr uint32_t kNoAllocW = (kScalarBits + kNoAllocC - 1) / kNoAllocC;
 constexpr size_t kNoAllocEntries = (size_t)kNoAllocMaxN * kNoAllocW;
 constexpr size_t kNoAllocPieces = kNoAllocEntries / kPiece + kNoAllocB + 1;
-constexpr size_t kNoAllocBlk = kNoAllocB / kRedSpan;
+constexpr size_t kNoAllocBlk = kNoAllocB / kSeg;
 constexpr size_t kNoAllocPre = 256;  // one prefix array of the job table
 
 constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
@@ -886,10 +854,9 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, dj, nxt, off_prev, nb,
                                                       rounds == 0 ? 1 : 0, buckets);
     ZK_LAUNCHED();
-    dim3 g((unsigned)kNoAllocBlk, 1);
-    k_reduce_blocks<<<g, kRedThreads, 0, s>>>(buckets, dj, bval, bsum);
-    ZK_LAUNCHED();
-    k_reduce_final<<<1, kFinThreads, 0, s>>>(bval, bsum, dj);
-    ZK_LAUNCHED();
-    return ZK_OK;
+    // Two reduction levels (2^15 buckets); level 2 never runs, so its
+    // outputs can point anywhere.
+    const uint32_t logB = kNoAllocC - 1;
+    static_assert(kNoAllocC - 1 <= 2 * kSegLog, "no-alloc reduction levels");
+    return launch_reduce(buckets, bval, bsum, bval, bsum, dj, &logB, 1, s);
 }
