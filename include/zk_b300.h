@@ -123,7 +123,7 @@ int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream 
  * deployment variant of the same commitment.
  *   coeffs, out : DEVICE pointers (ZK_EINVAL for host pointers); 1 <= n <= 4096
  *                 (ZK_EINVAL above that), n <= SRS size (ZK_ESRS otherwise).
- *   Workspace   : one fixed 14 MiB device array inside the library, shared by
+ *   Workspace   : one fixed 15 MiB device array inside the library, shared by
  *                 every call; each GPU that loads the library holds it until
  *                 the process exits.  The call allocates nothing (no
  *                 cudaMalloc, cudaFree or allocating library routine) and

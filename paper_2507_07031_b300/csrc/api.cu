@@ -238,6 +238,10 @@ int zk_init(zk_ctx **out, int device, size_t hbm_budget_bytes) {
         delete c;
         return ZK_ECUDA;
     }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+        c->sh->sms = sms;
+    cudaGetLastError();
     *out = c;
     return ZK_OK;
 }

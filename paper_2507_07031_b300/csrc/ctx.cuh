@@ -42,6 +42,7 @@ struct WindowTable {
 // from it never change after loading, so lanes read them concurrently.
 struct Shared {
     int device = 0;
+    int sms = 148;  // streaming multiprocessors of the device
     size_t budget = 0;
     size_t used = 0;
     std::mutex mu;        // SRS / tables / twiddles

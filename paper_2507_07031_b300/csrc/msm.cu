@@ -10,11 +10,13 @@
 //      builds the bucket histogram;
 //   2. sort: an exclusive scan gives bucket offsets and a warp-aggregated
 //      scatter writes the (table index, sign) words bucket by bucket;
-//   3. accumulate: each bucket's list is cut into pieces of kPiece entries,
-//      one thread per piece adds them in XYZZ coordinates (mixed additions);
-//      piece sums are combined again in rounds of kPiece until every bucket
-//      is a single point, so skewed buckets (quantised ML values put 2^20
-//      points into 128 buckets) keep the whole GPU busy;
+//   3. accumulate: the sorted entries are cut into equal chunks, one thread
+//      per chunk adds its entries in XYZZ coordinates (mixed additions) and
+//      emits a partial sum per bucket it meets; the partial sums are combined
+//      in further rounds, which a plan made on the device from the largest
+//      bucket skips when the buckets do not need them, so skewed buckets
+//      (quantised ML values put 2^20 points into 128 buckets) keep the whole
+//      GPU busy and uniform ones pay for no extra round;
 //   4. reduce: sum_b (b + 1) S_b per MSM by segment-level suffix scans in up
 //      to three levels, each point addition spread over the four warps of a
 //      block (team.cuh) because this phase is latency bound;
@@ -36,7 +38,6 @@ namespace zk {
 namespace {
 
 constexpr uint32_t kInvalid = 0xffffffffu;
-constexpr int kPiece = 32;       // entries (or partial sums) per thread per round
 constexpr size_t kStatsMin = 4096;  // scalars below which the width scan is skipped
 
 // One MSM of a batch.  Jobs are ordered by window width so that each width's
@@ -195,32 +196,99 @@ __device__ __forceinline__ Affine table_point(const DevJobs &dj, uint32_t b, uin
     return a;
 }
 
-// Phase 3a: first round of piece sums over the sorted table indices.
-// off0: entry offsets per bucket (nb + 1); off1: piece offsets (nb + 1).
+// Phase 3: bucket sums.  Round 0 cuts the sorted entries into fixed chunks
+// of p0 consecutive entries (whatever the bucket boundaries, so every thread
+// does the same work) and emits one partial sum per bucket a chunk meets.
+// Rounds 1, 2, ... add each bucket's items kPiece at a time.  The rounds are
+// launched for the worst case (every entry of a job in one bucket), but a
+// round plan computed on the device from the largest bucket skips, at
+// execution time, the rounds (and their scans) that the actual buckets do not
+// need.  The last stage sums what is left per bucket: one thread per bucket,
+// or, for small bucket sets whose buckets still hold more than a few items
+// (quantised scalars put many entries in few buckets), one team per bucket.
+constexpr uint32_t kPiece = 32;             // items per thread in rounds >= 1
+constexpr uint32_t kP0Min = 8;              // smallest round-0 chunk
+constexpr int kMaxRounds = 8;
+constexpr uint32_t kTailBuckets = 4096;     // bucket sets that may end on teams
+constexpr uint32_t kTailItems = 1024;       // items a team sums per bucket (32 per lane)
+constexpr uint32_t kTailMin = 4;            // fewer items per bucket: one thread
+
+struct RoundPlan {
+    uint32_t run[kMaxRounds];  // round rd executes
+    uint32_t last;             // rounds that execute (a prefix of 0 .. rounds-1)
+    uint32_t team;             // the last stage runs on teams
+};
+
+// Largest bucket (entries) into *dmax (zeroed by the caller).
+__global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, uint32_t *dmax) {
+    uint32_t m = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+        m = max(m, counts[i]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane_id() == 0 && m) atomicMax(dmax, m);
+}
+
+// Round rd runs while the largest bucket still holds more than `thr` items
+// (kPiece, or kTailItems for a small bucket set that may end on teams).
+__global__ void k_round_plan(const uint32_t *dmax, uint32_t p0, uint32_t rounds, uint32_t tail,
+                             RoundPlan *plan) {
+    if (threadIdx.x || blockIdx.x) return;
+    uint32_t x = *dmax, last = 0;
+    const uint32_t thr = tail ? kTailItems : kPiece;
+    for (uint32_t rd = 0; rd < (uint32_t)kMaxRounds; rd++) {
+        const bool run = rd < rounds && x > thr;
+        plan->run[rd] = run;
+        if (run) {
+            const uint32_t k = rd ? kPiece : p0;
+            x = (x + k - 1) / k;
+            last = rd + 1;
+        }
+    }
+    plan->last = last;
+    plan->team = tail && x > kTailMin;
+}
+
+// Round 0.  Thread c adds entries [c p0, (c + 1) p0); bucket b's items are
+// off1[b] .. off1[b + 1] - 1, one per chunk its entries meet, in chunk order.
 __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32_t *__restrict__ off0,
-                               const uint32_t *__restrict__ off1, uint32_t nb, DevJobs dj,
-                               Xyzz *__restrict__ pieces) {
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= off1[nb]) return;
-    uint32_t b = upper_index(off1, nb, p);
-    uint32_t k = p - off1[b];
-    uint32_t lo = off0[b] + k * kPiece;
-    uint32_t hi = min(lo + kPiece, off0[b + 1]);
-    const Affine *table = dj.jobs[search(dj.bbase, 0, dj.count, b)].table;
+                               const uint32_t *__restrict__ off1, uint32_t nb, uint32_t p0, DevJobs dj,
+                               const RoundPlan *__restrict__ plan, Xyzz *__restrict__ pieces) {
+    if (!plan->run[0]) return;
+    const uint32_t total = off0[nb];  // entries (zero digits have none)
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((uint64_t)c * p0 >= total) return;
+    const uint32_t lo = c * p0, hi = min(lo + p0, total);
+    uint32_t b = upper_index(off0, nb, lo);  // bucket holding entry lo
+    uint32_t end = off0[b + 1];
+    uint32_t job = search(dj.bbase, 0, dj.count, b);
+    const Affine *table = dj.jobs[job].table;
+    uint32_t jend = dj.bbase[job + 1];
     Xyzz acc = xyzz_inf();
     for (uint32_t j = lo; j < hi; j++) {
-        uint32_t v = sorted[j];
+        if (j >= end) {  // bucket b ends inside the chunk
+            pieces[off1[b] + c - off0[b] / p0] = acc;
+            acc = xyzz_inf();
+            do b++; while (off0[b + 1] <= j);  // skip empty buckets
+            end = off0[b + 1];
+            if (b >= jend) {
+                job = search(dj.bbase, 0, dj.count, b);
+                table = dj.jobs[job].table;
+                jend = dj.bbase[job + 1];
+            }
+        }
+        const uint32_t v = sorted[j];
         Affine a = affine_ldg(table + (v >> 1));
         if (v & 1) a = affine_neg(a);
         acc = xyzz_add_affine(acc, a);
     }
-    pieces[p] = acc;
+    pieces[off1[b] + c - off0[b] / p0] = acc;
 }
 
-// Phase 3b: further rounds over partial sums.
+// Round rd >= 1 over partial sums.
 __global__ void k_pieces_next(const Xyzz *__restrict__ in, const uint32_t *__restrict__ off_in,
                               const uint32_t *__restrict__ off_out, uint32_t nb,
-                              Xyzz *__restrict__ out) {
+                              const RoundPlan *__restrict__ plan, uint32_t rd, Xyzz *__restrict__ out) {
+    if (!plan->run[rd]) return;
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= off_out[nb]) return;
     uint32_t b = upper_index(off_out, nb, p);
@@ -232,19 +300,149 @@ __global__ void k_pieces_next(const Xyzz *__restrict__ in, const uint32_t *__res
     out[p] = acc;
 }
 
-// Phase 3c: one thread per bucket sums its (at most kPiece) remaining items;
-// `first` selects table entries (no piece round ran) or partial sums.
-__global__ void k_buckets_final(const uint32_t *__restrict__ sorted, DevJobs dj,
-                                const Xyzz *__restrict__ in, const uint32_t *__restrict__ off,
-                                uint32_t nb, int first, Xyzz *__restrict__ buckets) {
+// Where the last executed round left its items (round rd writes buffer
+// rd % 2); no round: the sorted entries themselves.
+struct FinalItems {
+    const uint32_t *sorted, *off0;
+    const Xyzz *in0, *in1;
+    const uint32_t *off_a, *off_b;
+};
+
+// Last stage, one thread per bucket.
+__global__ void k_buckets_final(FinalItems fi, DevJobs dj, uint32_t nb,
+                                const RoundPlan *__restrict__ plan, Xyzz *__restrict__ buckets) {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+    if (b >= nb || plan->team) return;
+    const uint32_t last = plan->last;
     Xyzz acc = xyzz_inf();
-    for (uint32_t j = off[b]; j < off[b + 1]; j++) {
-        if (first) acc = xyzz_add_affine(acc, table_point(dj, b, sorted[j]));
-        else acc = xyzz_add(acc, in[j]);
+    if (last == 0) {
+        for (uint32_t j = fi.off0[b]; j < fi.off0[b + 1]; j++)
+            acc = xyzz_add_affine(acc, table_point(dj, b, fi.sorted[j]));
+    } else {
+        const Xyzz *in = ((last - 1) & 1) ? fi.in1 : fi.in0;
+        const uint32_t *off = ((last - 1) & 1) ? fi.off_b : fi.off_a;
+        for (uint32_t j = off[b]; j < off[b + 1]; j++) acc = xyzz_add(acc, in[j]);
     }
     buckets[b] = acc;
+}
+
+// Last stage on teams, block b for bucket b: lane l adds items l, l + 32,
+// ..., then the lanes' sums are added in a tree.
+constexpr int kBtAcc = 0, kBtIn = 4, kBtTmp = 8, kBtT = 12;
+__global__ void __launch_bounds__(kTeamThreads)
+    k_buckets_team(FinalItems fi, DevJobs dj, const RoundPlan *__restrict__ plan,
+                   Xyzz *__restrict__ buckets) {
+    __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
+    if (!plan->team) return;
+    const uint32_t b = blockIdx.x, l = team_lane(), w = team_warp();
+    const uint32_t last = plan->last;
+    const bool entries = last == 0;
+    const uint32_t *off = entries ? fi.off0 : (((last - 1) & 1) ? fi.off_b : fi.off_a);
+    const Xyzz *in = entries ? nullptr : (((last - 1) & 1) ? fi.in1 : fi.in0);
+    const Affine *table = dj.jobs[search(dj.bbase, 0, dj.count, b)].table;
+    const uint32_t lo = off[b], hi = off[b + 1];
+    // Coordinate w of item j (a table point with sign, or a partial sum).
+    auto fetch = [&](uint32_t j) -> Fq {
+        if (j >= hi) return fe_zero<FqP>();
+        if (!entries) return team_fetch(in + j, true);
+        const uint32_t v = fi.sorted[j];
+        if (w >= 2) return fe_mont_one<FqP>();
+        const Fq c = fe_ldg<FqP>(reinterpret_cast<const char *>(table + (v >> 1)) + 32 * w);
+        return (w == 1 && (v & 1)) ? fe_neg<FqP>(c) : c;
+    };
+    team_set_inf_nosync(f, kBtAcc);
+    for (uint32_t j0 = lo; j0 < hi; j0 += 32) {
+        tf_store(f, kBtIn + w, fetch(j0 + l));
+        __syncthreads();
+        team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
+    }
+    for (int d = 16; d >= 1; d >>= 1) {
+        team_shift(f, kBtAcc, kBtTmp, d);
+        team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
+    }
+    if (l == 0) team_put(f, kBtAcc, buckets + b);
+}
+
+// Shape of phase 3 for `total` entries in `nb` buckets with at most `worst`
+// entries in one bucket.
+struct AccumShape {
+    uint32_t p0;
+    int rounds;
+    size_t cap0;  // items after round 0 (bound)
+    bool tail;
+};
+
+// Round 0 runs as one wave: every resident thread of the GPU takes one chunk
+// of p0 = ceil(total / threads) entries (at least kP0Min), so no thread waits
+// for a partial last wave.
+AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms) {
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pieces_first, 128, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        return b;
+    }();
+    AccumShape a;
+    const size_t threads = (size_t)std::max(sms, 1) * per_sm * 128;
+    a.p0 = (uint32_t)std::max<size_t>(kP0Min, (total + threads - 1) / threads);
+    a.rounds = 0;
+    for (size_t x = worst; x > kPiece && a.rounds < kMaxRounds; a.rounds++)
+        x = (x + (a.rounds ? kPiece : a.p0) - 1) / (a.rounds ? kPiece : a.p0);
+    a.cap0 = (total + a.p0 - 1) / a.p0 + nb + 1;
+    a.tail = nb <= kTailBuckets;
+    return a;
+}
+
+struct AccumBufs {
+    uint32_t *offa, *offb;
+    Xyzz *pa, *pb;
+    uint32_t *dmax;
+    RoundPlan *plan;
+    void *scan_tmp;
+};
+
+// Phase 3 launches: sorted entries (offsets off0, histogram counts; at most
+// `total` entries) -> one point per bucket.
+int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint32_t *off0, uint32_t nb,
+                      size_t total, const AccumShape &a, const DevJobs &dj, const AccumBufs &w,
+                      Xyzz *buckets, int sms, cudaStream_t s) {
+    ZK_CUDA_TRY(cudaMemsetAsync(w.dmax, 0, sizeof(uint32_t), s));
+    const unsigned mb = (unsigned)std::min<size_t>((nb + 255) / 256, (size_t)sms * 4);
+    k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, w.dmax);
+    ZK_LAUNCHED();
+    k_round_plan<<<1, 32, 0, s>>>(w.dmax, a.p0, (uint32_t)a.rounds, a.tail ? 1u : 0u, w.plan);
+    ZK_LAUNCHED();
+    const uint32_t *off_prev = off0;
+    size_t cap = a.cap0;
+    for (int rd = 0; rd < a.rounds; rd++) {
+        uint32_t *off_new = (rd % 2 == 0) ? w.offa : w.offb;
+        Xyzz *out = (rd % 2 == 0) ? w.pa : w.pb;
+        const uint32_t *gate = &w.plan->run[rd];
+        if (rd == 0) {
+            ZK_TRY(scan_exclusive(off_prev, off_new, nb, -(int)a.p0, w.scan_tmp, s, gate));
+            const size_t chunks = std::max<size_t>((total + a.p0 - 1) / a.p0, 1);  // 0 entries: all zero
+            k_pieces_first<<<(unsigned)((chunks + 127) / 128), 128, 0, s>>>(sorted, off_prev, off_new, nb,
+                                                                           a.p0, dj, w.plan, out);
+        } else {
+            ZK_TRY(scan_exclusive(off_prev, off_new, nb, (int)kPiece, w.scan_tmp, s, gate));
+            const Xyzz *in = (rd % 2 == 1) ? w.pa : w.pb;
+            cap = cap / kPiece + nb + 1;  // bound on this round's items
+            k_pieces_next<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(in, off_prev, off_new, nb, w.plan,
+                                                                       (uint32_t)rd, out);
+        }
+        ZK_LAUNCHED();
+        off_prev = off_new;
+    }
+    const FinalItems fi{sorted, off0, w.pa, w.pb, w.offa, w.offb};
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(fi, dj, nb, w.plan, buckets);
+    ZK_LAUNCHED();
+    if (a.tail) {
+        k_buckets_team<<<nb, kTeamThreads, 0, s>>>(fi, dj, w.plan, buckets);
+        ZK_LAUNCHED();
+    }
+    return ZK_OK;
 }
 
 // Phase 4: bucket reduction, sum_b (b + 1) S_b per MSM, on teams (team.cuh):
@@ -554,18 +752,13 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     const uint32_t nb = (uint32_t)nb64;
     const size_t entries_max = entries64;
 
-    // Piece rounds: after R rounds a bucket with at most max_n W entries holds
-    // ceil(max_n W / kPiece^R) items; stop once that is <= kPiece.
-    int rounds = 0;
-    {
-        size_t m = 1;
-        for (size_t k = 0; k < count; k++) m = std::max(m, (size_t)jv[k].job.n * std::max<uint32_t>(jv[k].wins, 1));
-        while (m > (size_t)kPiece) {
-            m = (m + kPiece - 1) / kPiece;
-            rounds++;
-        }
-    }
-    const size_t piece_cap = entries_max / kPiece + nb + 1;
+    // Phase 3 shape: a bucket holds at most max_n W entries (all of a job's
+    // digits in one bucket).
+    size_t worst = 1;
+    for (size_t k = 0; k < count; k++)
+        worst = std::max(worst, (size_t)jv[k].job.n * std::max<uint32_t>(jv[k].wins, 1));
+    const AccumShape shape = accum_shape(entries_max, worst, nb, sh.sms);
+    const size_t piece_cap = shape.cap0;
 
     // Workspace.
     int err = ZK_OK;
@@ -586,8 +779,9 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     Xyzz *bv2 = (Xyzz *)scratch(ctx, "msm.bv2", count * kL2Per * sizeof(Xyzz), &err);
     Xyzz *bs2 = (Xyzz *)scratch(ctx, "msm.bs2", count * kL2Per * sizeof(Xyzz), &err);
     void *scan_tmp = scratch(ctx, "msm.scantmp", scan_temp_bytes(nb), &err);
+    char *plan = (char *)scratch(ctx, "msm.plan", 256 + sizeof(RoundPlan), &err);
     if (!jt || !counts || !off0 || !offa || !offb || !cursor || !sorted || !pa || !pb || !buckets ||
-        !bval || !bsum || !bv2 || !bs2 || !scan_tmp)
+        !bval || !bsum || !bv2 || !bs2 || !scan_tmp || !plan)
         return err;
 
     // Job table: descriptors and the three prefix arrays.
@@ -643,27 +837,10 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     (void)total;
     ph_sort.end();
 
-    // 3: piece rounds, then one point per bucket.
+    // 3: bucket sums.
     PhaseScope ph_accum(ctx, ZK_PHASE_MSM_ACCUM, s);
-    const uint32_t *off_prev = off0;
-    Xyzz *cur = pa, *nxt = pb;
-    size_t cap = piece_cap;
-    for (int rd = 0; rd < rounds; rd++) {
-        uint32_t *off_new = (rd % 2 == 0) ? offa : offb;
-        ZK_TRY(scan_exclusive(off_prev, off_new, nb, kPiece, scan_tmp, s));
-        unsigned blocks = (unsigned)((cap + 127) / 128);
-        if (rd == 0)
-            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb, dj, cur);
-        else
-            k_pieces_next<<<blocks, 128, 0, s>>>(nxt, off_prev, off_new, nb, cur);
-        ZK_LAUNCHED();
-        std::swap(cur, nxt);  // nxt now holds this round's output
-        off_prev = off_new;
-        cap = cap / kPiece + nb + 1;
-    }
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, dj, nxt, off_prev, nb, rounds == 0 ? 1 : 0,
-                                                      buckets);
-    ZK_LAUNCHED();
+    const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)plan, (RoundPlan *)(plan + 256), scan_tmp};
+    ZK_TRY(launch_accumulate(sorted, counts, off0, nb, entries_max, shape, dj, ab, buckets, sh.sms, s));
     ph_accum.end();
 
     // 4-5: bucket reduction and output.
@@ -695,7 +872,7 @@ constexpr int kNoAllocC = 16;
 constexpr uint32_t kNoAllocB = 1u << (kNoAllocC - 1);
 constexpr uint32_t kNoAllocW = (kScalarBits + kNoAllocC - 1) / kNoAllocC;
 constexpr size_t kNoAllocEntries = (size_t)kNoAllocMaxN * kNoAllocW;
-constexpr size_t kNoAllocPieces = kNoAllocEntries / kPiece + kNoAllocB + 1;
+constexpr size_t kNoAllocPieces = kNoAllocEntries / kP0Min + kNoAllocB + 1;
 constexpr size_t kNoAllocBlk = kNoAllocB / kSeg;
 constexpr size_t kNoAllocPre = 256;  // one prefix array of the job table
 
@@ -714,7 +891,8 @@ constexpr size_t kNaBuckets = kNaPieceB + na_align(kNoAllocPieces * sizeof(Xyzz)
 constexpr size_t kNaBval = kNaBuckets + na_align(kNoAllocB * sizeof(Xyzz));
 constexpr size_t kNaBsum = kNaBval + na_align(kNoAllocBlk * sizeof(Xyzz));
 constexpr size_t kNaScan = kNaBsum + na_align(kNoAllocBlk * sizeof(Xyzz));
-constexpr size_t kNoAllocBytes = kNaScan + na_align(((size_t)kNoAllocB / 2048 + 2) * 4);
+constexpr size_t kNaPlan = kNaScan + na_align(((size_t)kNoAllocB / 2048 + 2) * 4);
+constexpr size_t kNoAllocBytes = kNaPlan + 256 + na_align(sizeof(RoundPlan));
 
 // The workspace.  Host code must not use this name as an address: it is a
 // host-side stand-in.  The device address comes from cudaGetSymbolAddress.
@@ -833,27 +1011,12 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
     ZK_TRY((launch_recode_c<kNoAllocC, true>(dj, 0, 1, total, (uint32_t)tab->n, nullptr, cursor,
                                               sorted, s)));
-    int rounds = 0;
-    for (size_t m = (size_t)n * kNoAllocW; m > (size_t)kPiece; m = (m + kPiece - 1) / kPiece) rounds++;
-    const uint32_t *off_prev = off0;
-    Xyzz *cur = pa, *nxt = pb;
-    size_t cap = kNoAllocPieces;
-    for (int rd = 0; rd < rounds; rd++) {
-        uint32_t *off_new = (rd % 2 == 0) ? offa : offb;
-        ZK_TRY(scan_exclusive(off_prev, off_new, nb, kPiece, scan_tmp, s));
-        unsigned blocks = (unsigned)((cap + 127) / 128);
-        if (rd == 0)
-            k_pieces_first<<<blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb, dj, cur);
-        else
-            k_pieces_next<<<blocks, 128, 0, s>>>(nxt, off_prev, off_new, nb, cur);
-        ZK_LAUNCHED();
-        std::swap(cur, nxt);
-        off_prev = off_new;
-        cap = cap / kPiece + nb + 1;
-    }
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(sorted, dj, nxt, off_prev, nb,
-                                                      rounds == 0 ? 1 : 0, buckets);
-    ZK_LAUNCHED();
+    const AccumShape shape = accum_shape((size_t)n * kNoAllocW, (size_t)n * kNoAllocW, nb, sh.sms);
+    if (shape.cap0 > kNoAllocPieces) return ZK_EINVAL;  // cannot happen: p0 >= kP0Min
+    const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)(ws + kNaPlan), (RoundPlan *)(ws + kNaPlan + 256),
+                       scan_tmp};
+    ZK_TRY(launch_accumulate(sorted, counts, off0, nb, (size_t)n * kNoAllocW, shape, dj, ab, buckets, sh.sms,
+                             s));
     // Two reduction levels (2^15 buckets); level 2 never runs, so its
     // outputs can point anywhere.
     const uint32_t logB = kNoAllocC - 1;

@@ -16,13 +16,17 @@ constexpr int kThreads = 256;
 constexpr int kPer = 8;
 constexpr int kTile = kThreads * kPer;
 
-// Element b of the scanned sequence: in[b], or ceil((in[b+1] - in[b]) / K)
-// when K > 0 (the item count of bucket b after one round of K-way pieces).
+// Element b of the scanned sequence: in[b] when K = 0; for bucket offsets
+// `in`, the item count of bucket b after one round of K-way pieces,
+// ceil((in[b+1] - in[b]) / K), when K > 0; and the number of fixed chunks of
+// -K consecutive entries that bucket b's entries meet, when K < 0.
 __device__ __forceinline__ uint32_t elem(const uint32_t *in, uint32_t b, uint32_t n, int K) {
     if (b >= n) return 0;
     if (K == 0) return in[b];
-    uint32_t d = in[b + 1] - in[b];
-    return (d + (uint32_t)K - 1) / (uint32_t)K;
+    const uint32_t lo = in[b], hi = in[b + 1];
+    if (K > 0) return (hi - lo + (uint32_t)K - 1) / (uint32_t)K;
+    const uint32_t c = (uint32_t)(-K);
+    return hi > lo ? (hi - 1) / c - lo / c + 1 : 0u;
 }
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
@@ -53,7 +57,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 }
 
 __global__ void k_tile_sums(const uint32_t *__restrict__ in, uint32_t n, int K,
-                            uint32_t *__restrict__ sums) {
+                            uint32_t *__restrict__ sums, const uint32_t *gate) {
+    if (gate && !*gate) return;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t s = 0;
 #pragma unroll
@@ -63,7 +68,8 @@ __global__ void k_tile_sums(const uint32_t *__restrict__ in, uint32_t n, int K,
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_sums(uint32_t *__restrict__ sums, uint32_t tiles) {
+__global__ void k_scan_sums(uint32_t *__restrict__ sums, uint32_t tiles, const uint32_t *gate) {
+    if (gate && !*gate) return;
     const uint32_t per = (tiles + kThreads - 1) / kThreads;
     const uint32_t lo = threadIdx.x * per;
     uint32_t s = 0;
@@ -80,7 +86,8 @@ __global__ void k_scan_sums(uint32_t *__restrict__ sums, uint32_t tiles) {
 
 __global__ void k_tile_scan(const uint32_t *__restrict__ in, uint32_t n, int K,
                             const uint32_t *__restrict__ sums, uint32_t tiles,
-                            uint32_t *__restrict__ out) {
+                            uint32_t *__restrict__ out, const uint32_t *gate) {
+    if (gate && !*gate) return;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t v[kPer];
     uint32_t s = 0;
@@ -106,16 +113,17 @@ inline size_t scan_temp_bytes(uint32_t n) {
 }
 
 // out[b] = sum_{b' < b} elem(b'), out[n] = total.  `in` may equal neither
-// `out` nor `tmp`.
+// `out` nor `tmp`.  With a `gate` (device word), the scan does nothing when
+// the word is zero at execution time.
 inline int scan_exclusive(const uint32_t *in, uint32_t *out, uint32_t n, int K, void *tmp,
-                          cudaStream_t s) {
+                          cudaStream_t s, const uint32_t *gate = nullptr) {
     using namespace scan_detail;
     uint32_t tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) tiles = 1;
     uint32_t *sums = (uint32_t *)tmp;
-    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums);
-    k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles);
-    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out);
+    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate);
+    k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, gate);
+    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate);
     count_launches(3);
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
