@@ -204,9 +204,11 @@ static void fhalf(u256 *x, const u256 *m) {
 }
 
 /* Inverse of a != 0 modulo the odd prime m by the binary extended Euclidean
- * algorithm.  Invariants: x1 * a = u and x2 * a = v (mod m). */
+ * algorithm.  Invariants: x1 * a = u and x2 * a = v (mod m).  a = 0 has no
+ * inverse and returns 0 (the loop would never end on it). */
 static void finv(u256 *r, const u256 *a, const u256 *m) {
     u256 u = *a, v = *m, x1, x2, one;
+    if (is_zero(&u)) { *r = u; return; }  /* 0 has no inverse: 0 by convention */
     set_small(&x1, 1);
     set_small(&x2, 0);
     set_small(&one, 1);

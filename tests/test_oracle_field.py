@@ -59,6 +59,7 @@ def test_inverse_and_power(orc, f, m):
         inv = orc.finv(f, A)
         assert orc.to_int(orc.fmul(f, A, inv)) == 1
         assert orc.to_int(inv) == pow(a, -1, m)
+    assert orc.to_int(orc.finv(f, orc.from_int(0))) == 0  # no inverse: 0 by convention
     for a in [rng.randrange(1, m) for _ in range(10)]:
         # Fermat: a^(m-1) = 1 for the prime m.
         assert orc.to_int(orc.fpow(f, orc.from_int(a), orc.from_int(m - 1))) == 1
