@@ -296,6 +296,27 @@ const char *zk_strerror(int code);
 unsigned long long zk_kernel_launches(void);
 int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s);
 
+/* Elementwise field arithmetic on canonical vectors (tests of the device
+ * field code; the prover does not call it).  The paper has no counterpart:
+ * it checks the F_q / F_r arithmetic every step of the hot path is built on
+ * (BN254 fields, Sec. 6.1).
+ *   field : ZK_FIELD_Q (base field q) or ZK_FIELD_R (scalar field r).
+ *   op    : ZK_FOP_MUL out = a b, ZK_FOP_SQR out = a^2, ZK_FOP_INV out = a^-1
+ *           (0 for 0), ZK_FOP_ADD out = a + b, ZK_FOP_SUB out = a - b.
+ *   a, b, out : DEVICE pointers to n canonical 32-byte little-endian elements
+ *           (< modulus; not checked); b is ignored by SQR and INV; out may
+ *           alias a or b.  Stream-ordered on `stream`.
+ * Errors: ZK_EINVAL (bad field/op, null or host pointer, n > 2^31),
+ * ZK_ECUDA. */
+#define ZK_FIELD_Q 0
+#define ZK_FIELD_R 1
+#define ZK_FOP_MUL 0
+#define ZK_FOP_SQR 1
+#define ZK_FOP_INV 2
+#define ZK_FOP_ADD 3
+#define ZK_FOP_SUB 4
+int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk_fr *out, size_t n, zk_stream stream);
+
 /* Phase timing: with timing on, each call brackets its phases with CUDA events
  * on its stream; zk_timing_read waits for them, adds up the device time (ms)
  * and interval count per phase since the last read, and clears the record. */

@@ -100,6 +100,7 @@ def _load():
         "zk_tune_measure": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_double)],
         "zk_timing_read": [_VP, _VP, _VP],
+        "zk_field_op": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _SZ, _VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -124,9 +125,11 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
-            "zk_server_destroy", "zk_set_commit_route"]
+            "zk_server_destroy", "zk_set_commit_route", "zk_field_op"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
+ZK_FIELD_Q, ZK_FIELD_R = 0, 1
+ZK_FOP_MUL, ZK_FOP_SQR, ZK_FOP_INV, ZK_FOP_ADD, ZK_FOP_SUB = range(5)
 
 PHASES = ["msm_sort", "msm_accum", "msm_reduce", "ntt", "fold_witness", "fold_instance"]
 
@@ -144,6 +147,15 @@ def zk_probe_rates(device: int = 0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib.zk_probe_rates(int(device), ctypes.byref(a), ctypes.byref(b)), "zk_probe_rates")
     return a.value, b.value
+
+
+def zk_field_op(field: int, op: int, a, b, out, n: int = None, stream=None) -> None:
+    """Elementwise field arithmetic on device vectors of canonical elements
+    (int64 tensors of shape (n, 4)); b is ignored by SQR and INV."""
+    if n is None:
+        n = a.numel() // 4
+    _check(lib.zk_field_op(int(field), int(op), _ptr(a), _ptr(b), _ptr(out), int(n), _stream(stream)),
+           "zk_field_op")
 
 
 def zk_set_commit_route(ctx: int, route: int) -> None:

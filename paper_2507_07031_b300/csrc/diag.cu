@@ -111,3 +111,54 @@ extern "C" int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per
     cudaSetDevice(prev);
     return e == cudaSuccess ? ZK_OK : ZK_ECUDA;
 }
+
+// ---------------------------------------------------------------------------
+// zk_field_op: elementwise F_q / F_r arithmetic on canonical vectors, through
+// the same device code the prover uses (Montgomery conversions, product,
+// squaring, inversion, addition, subtraction), for tests of that code.
+// ---------------------------------------------------------------------------
+
+namespace zk {
+
+namespace {
+
+template <class P>
+__global__ void k_field_op(int op, const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
+                           uint32_t *__restrict__ out, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Fe<P> x = fe_to_mont<P>(fe_load<P>(a + 8 * i));
+    Fe<P> y = fe_zero<P>();
+    if (op == ZK_FOP_MUL || op == ZK_FOP_ADD || op == ZK_FOP_SUB) y = fe_to_mont<P>(fe_load<P>(b + 8 * i));
+    Fe<P> r;
+    switch (op) {
+        case ZK_FOP_MUL: r = fe_mul<P>(x, y); break;
+        case ZK_FOP_SQR: r = fe_sqr<P>(x); break;
+        case ZK_FOP_INV: r = fe_inv<P>(x); break;
+        case ZK_FOP_ADD: r = fe_add<P>(x, y); break;
+        default: r = fe_sub<P>(x, y); break;
+    }
+    fe_store<P>(out + 8 * i, fe_from_mont<P>(r));
+}
+
+}  // namespace
+
+}  // namespace zk
+
+extern "C" int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk_fr *out, size_t n,
+                           zk_stream stream) {
+    using namespace zk;
+    if (field != ZK_FIELD_Q && field != ZK_FIELD_R) return ZK_EINVAL;
+    if (op < ZK_FOP_MUL || op > ZK_FOP_SUB) return ZK_EINVAL;
+    if (n == 0) return ZK_OK;
+    const bool binary = op == ZK_FOP_MUL || op == ZK_FOP_ADD || op == ZK_FOP_SUB;
+    if (!a || !out || (binary && !b) || n > ((size_t)1 << 31)) return ZK_EINVAL;
+    if (!is_device_ptr(a) || !is_device_ptr(out) || (binary && !is_device_ptr(b))) return ZK_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    const uint32_t *pa = (const uint32_t *)a, *pb = (const uint32_t *)b;
+    if (field == ZK_FIELD_Q) k_field_op<FqP><<<blocks, 128, 0, s>>>(op, pa, pb, (uint32_t *)out, n);
+    else k_field_op<FrP><<<blocks, 128, 0, s>>>(op, pa, pb, (uint32_t *)out, n);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? ZK_OK : ZK_ECUDA;
+}

@@ -309,6 +309,217 @@ template <class P> ZK_DEV Fe<P> fe_mul_inline(const Fe<P> &a, const Fe<P> &b) {
     return r;
 }
 
+// Montgomery squaring in separated form: the 28 cross products a_i a_j
+// (i < j) once, doubled, plus the 8 squares a_i^2 (72 IMADs instead of 128),
+// then the 8 reduction rows t += m p 2^(32 i).  Cross-product row i adds
+// a_i (a_{i+1} .. a_7) at word 2i + 1; after it the partial sum is below
+// 2^(32 (i + 9)), so its chain ends at word i + 8 without a carry out.  A
+// reduction row's carry out of word i + 8 is carried into the next row.
+namespace detail {
+
+template <int K>
+ZK_DEV void sqr_row1(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %2, %3, %0;\n\t"
+        "addc.u32       %1, %1, 0;\n\t"
+        "mad.hi.u32     %1, %2, %3, %1;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1])
+        : "r"(x[0]), "r"(y));
+}
+
+template <int K>
+ZK_DEV void sqr_row2(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %3, %5, %0;\n\t"
+        "madc.lo.cc.u32 %1, %4, %5, %1;\n\t"
+        "addc.u32       %2, %2, 0;\n\t"
+        "mad.hi.cc.u32  %1, %3, %5, %1;\n\t"
+        "madc.hi.u32    %2, %4, %5, %2;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1]), "+r"(t[K + 2])
+        : "r"(x[0]), "r"(x[1]), "r"(y));
+}
+
+template <int K>
+ZK_DEV void sqr_row3(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %4, %7, %0;\n\t"
+        "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
+        "addc.u32       %3, %3, 0;\n\t"
+        "mad.hi.cc.u32  %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32    %3, %6, %7, %3;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1]), "+r"(t[K + 2]), "+r"(t[K + 3])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(y));
+}
+
+template <int K>
+ZK_DEV void sqr_row4(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %5, %9, %0;\n\t"
+        "madc.lo.cc.u32 %1, %6, %9, %1;\n\t"
+        "madc.lo.cc.u32 %2, %7, %9, %2;\n\t"
+        "madc.lo.cc.u32 %3, %8, %9, %3;\n\t"
+        "addc.u32       %4, %4, 0;\n\t"
+        "mad.hi.cc.u32  %1, %5, %9, %1;\n\t"
+        "madc.hi.cc.u32 %2, %6, %9, %2;\n\t"
+        "madc.hi.cc.u32 %3, %7, %9, %3;\n\t"
+        "madc.hi.u32    %4, %8, %9, %4;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1]), "+r"(t[K + 2]), "+r"(t[K + 3]), "+r"(t[K + 4])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(y));
+}
+
+template <int K>
+ZK_DEV void sqr_row5(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %6, %11, %0;\n\t"
+        "madc.lo.cc.u32 %1, %7, %11, %1;\n\t"
+        "madc.lo.cc.u32 %2, %8, %11, %2;\n\t"
+        "madc.lo.cc.u32 %3, %9, %11, %3;\n\t"
+        "madc.lo.cc.u32 %4, %10, %11, %4;\n\t"
+        "addc.u32       %5, %5, 0;\n\t"
+        "mad.hi.cc.u32  %1, %6, %11, %1;\n\t"
+        "madc.hi.cc.u32 %2, %7, %11, %2;\n\t"
+        "madc.hi.cc.u32 %3, %8, %11, %3;\n\t"
+        "madc.hi.cc.u32 %4, %9, %11, %4;\n\t"
+        "madc.hi.u32    %5, %10, %11, %5;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1]), "+r"(t[K + 2]), "+r"(t[K + 3]), "+r"(t[K + 4]), "+r"(t[K + 5])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(y));
+}
+
+template <int K>
+ZK_DEV void sqr_row6(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %7, %13, %0;\n\t"
+        "madc.lo.cc.u32 %1, %8, %13, %1;\n\t"
+        "madc.lo.cc.u32 %2, %9, %13, %2;\n\t"
+        "madc.lo.cc.u32 %3, %10, %13, %3;\n\t"
+        "madc.lo.cc.u32 %4, %11, %13, %4;\n\t"
+        "madc.lo.cc.u32 %5, %12, %13, %5;\n\t"
+        "addc.u32       %6, %6, 0;\n\t"
+        "mad.hi.cc.u32  %1, %7, %13, %1;\n\t"
+        "madc.hi.cc.u32 %2, %8, %13, %2;\n\t"
+        "madc.hi.cc.u32 %3, %9, %13, %3;\n\t"
+        "madc.hi.cc.u32 %4, %10, %13, %4;\n\t"
+        "madc.hi.cc.u32 %5, %11, %13, %5;\n\t"
+        "madc.hi.u32    %6, %12, %13, %6;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1]), "+r"(t[K + 2]), "+r"(t[K + 3]), "+r"(t[K + 4]), "+r"(t[K + 5]), "+r"(t[K + 6])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(y));
+}
+
+template <int K>
+ZK_DEV void sqr_row7(uint32_t (&t)[17], const uint32_t *x, uint32_t y) {
+    asm("mad.lo.cc.u32  %0, %8, %15, %0;\n\t"
+        "madc.lo.cc.u32 %1, %9, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %10, %15, %2;\n\t"
+        "madc.lo.cc.u32 %3, %11, %15, %3;\n\t"
+        "madc.lo.cc.u32 %4, %12, %15, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, %15, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %15, %6;\n\t"
+        "addc.u32       %7, %7, 0;\n\t"
+        "mad.hi.cc.u32  %1, %8, %15, %1;\n\t"
+        "madc.hi.cc.u32 %2, %9, %15, %2;\n\t"
+        "madc.hi.cc.u32 %3, %10, %15, %3;\n\t"
+        "madc.hi.cc.u32 %4, %11, %15, %4;\n\t"
+        "madc.hi.cc.u32 %5, %12, %15, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, %15, %6;\n\t"
+        "madc.hi.u32    %7, %14, %15, %7;"
+        : "+r"(t[K + 0]), "+r"(t[K + 1]), "+r"(t[K + 2]), "+r"(t[K + 3]), "+r"(t[K + 4]), "+r"(t[K + 5]), "+r"(t[K + 6]), "+r"(t[K + 7])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(y));
+}
+
+ZK_DEV void sqr_diag(uint32_t (&t)[17], const uint32_t (&a)[8]) {
+    asm("mad.lo.cc.u32  %0, %16, %16, %0;\n\t"
+        "madc.hi.cc.u32 %1, %16, %16, %1;\n\t"
+        "madc.lo.cc.u32 %2, %17, %17, %2;\n\t"
+        "madc.hi.cc.u32 %3, %17, %17, %3;\n\t"
+        "madc.lo.cc.u32 %4, %18, %18, %4;\n\t"
+        "madc.hi.cc.u32 %5, %18, %18, %5;\n\t"
+        "madc.lo.cc.u32 %6, %19, %19, %6;\n\t"
+        "madc.hi.cc.u32 %7, %19, %19, %7;\n\t"
+        "madc.lo.cc.u32 %8, %20, %20, %8;\n\t"
+        "madc.hi.cc.u32 %9, %20, %20, %9;\n\t"
+        "madc.lo.cc.u32 %10, %21, %21, %10;\n\t"
+        "madc.hi.cc.u32 %11, %21, %21, %11;\n\t"
+        "madc.lo.cc.u32 %12, %22, %22, %12;\n\t"
+        "madc.hi.cc.u32 %13, %22, %22, %13;\n\t"
+        "madc.lo.cc.u32 %14, %23, %23, %14;\n\t"
+        "madc.hi.u32    %15, %23, %23, %15;"
+        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]));
+}
+
+template <int I>
+ZK_DEV void sqr_red_row(uint32_t (&t)[17], uint32_t &c, const uint32_t (&pm)[8], uint32_t m) {
+    asm("mad.lo.cc.u32  %0, %10, %18, %0;\n\t"
+        "madc.lo.cc.u32 %1, %11, %18, %1;\n\t"
+        "madc.lo.cc.u32 %2, %12, %18, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, %18, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %18, %4;\n\t"
+        "madc.lo.cc.u32 %5, %15, %18, %5;\n\t"
+        "madc.lo.cc.u32 %6, %16, %18, %6;\n\t"
+        "madc.lo.cc.u32 %7, %17, %18, %7;\n\t"
+        "addc.cc.u32    %8, %8, %9;\n\t"
+        "addc.u32       %9, 0, 0;\n\t"
+        "mad.hi.cc.u32  %1, %10, %18, %1;\n\t"
+        "madc.hi.cc.u32 %2, %11, %18, %2;\n\t"
+        "madc.hi.cc.u32 %3, %12, %18, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, %18, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %18, %5;\n\t"
+        "madc.hi.cc.u32 %6, %15, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %16, %18, %7;\n\t"
+        "madc.hi.cc.u32 %8, %17, %18, %8;\n\t"
+        "addc.u32       %9, %9, 0;"
+        : "+r"(t[I + 0]), "+r"(t[I + 1]), "+r"(t[I + 2]), "+r"(t[I + 3]), "+r"(t[I + 4]), "+r"(t[I + 5]), "+r"(t[I + 6]), "+r"(t[I + 7]), "+r"(t[I + 8]), "+r"(c)
+        : "r"(pm[0]), "r"(pm[1]), "r"(pm[2]), "r"(pm[3]), "r"(pm[4]), "r"(pm[5]), "r"(pm[6]), "r"(pm[7]), "r"(m));
+}
+
+
+}  // namespace detail
+
+template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) {
+    using namespace detail;
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = 0;
+    sqr_row7<1>(t, &a.v[1], a.v[0]);
+    sqr_row6<3>(t, &a.v[2], a.v[1]);
+    sqr_row5<5>(t, &a.v[3], a.v[2]);
+    sqr_row4<7>(t, &a.v[4], a.v[3]);
+    sqr_row3<9>(t, &a.v[5], a.v[4]);
+    sqr_row2<11>(t, &a.v[6], a.v[5]);
+    sqr_row1<13>(t, &a.v[7], a.v[6]);
+#pragma unroll
+    for (int k = 15; k >= 1; k--) t[k] = __funnelshift_l(t[k - 1], t[k], 1);
+    sqr_diag(t, a.v);
+    const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
+    uint32_t c = 0;
+    sqr_red_row<0>(t, c, pm, t[0] * P::n0);
+    sqr_red_row<1>(t, c, pm, t[1] * P::n0);
+    sqr_red_row<2>(t, c, pm, t[2] * P::n0);
+    sqr_red_row<3>(t, c, pm, t[3] * P::n0);
+    sqr_red_row<4>(t, c, pm, t[4] * P::n0);
+    sqr_red_row<5>(t, c, pm, t[5] * P::n0);
+    sqr_red_row<6>(t, c, pm, t[6] * P::n0);
+    sqr_red_row<7>(t, c, pm, t[7] * P::n0);
+    // (a^2 + M p) / 2^256 < 2p (a < p < 2^254): the final carry is 0.
+    Fe<P> s, r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s.v[i] = t[8 + i];
+    uint32_t borrow;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;"
+        : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]),
+          "=r"(r.v[6]), "=r"(r.v[7]), "=r"(borrow)
+        : "r"(s.v[0]), "r"(s.v[1]), "r"(s.v[2]), "r"(s.v[3]), "r"(s.v[4]), "r"(s.v[5]),
+          "r"(s.v[6]), "r"(s.v[7]), "r"(P::p(0)), "r"(P::p(1)), "r"(P::p(2)), "r"(P::p(3)),
+          "r"(P::p(4)), "r"(P::p(5)), "r"(P::p(6)), "r"(P::p(7)));
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = (s.v[i] & borrow) | (r.v[i] & ~borrow);
+    return r;
+}
+
 // One out-of-line copy of the product per field: the curve formulas call it
 // ten to fourteen times per point operation, and inlining every call makes
 // the kernels' hot code larger than the instruction cache.
@@ -335,7 +546,15 @@ template <> ZK_DEV Fe<FrP> fe_mul<FrP>(const Fe<FrP> &a, const Fe<FrP> &b) {
 #endif
 }
 
+template <class P>
+__device__ __noinline__ Fe<P> fe_sqr_call(const Fe<P> a) {
+    return fe_sqr_inline<P>(a);
+}
+
+// F_q squarings (two of the ten products of a mixed addition) take the
+// separated form out of line; F_r keeps the product (the NTT never squares).
 template <class P> ZK_DEV Fe<P> fe_sqr(const Fe<P> &a) { return fe_mul<P>(a, a); }
+template <> ZK_DEV Fe<FqP> fe_sqr<FqP>(const Fe<FqP> &a) { return fe_sqr_call<FqP>(a); }
 
 // Montgomery form conversions: x -> x R and x R -> x.
 template <class P> ZK_DEV Fe<P> fe_to_mont(const Fe<P> &a) { return fe_mul<P>(a, fe_r2<P>()); }
@@ -350,95 +569,197 @@ template <class P> ZK_DEV Fe<P> fe_from_mont(const Fe<P> &a) {
 template <class P> ZK_DEV Fe<P> fe_mul3(const Fe<P> &a) { return fe_add<P>(fe_add<P>(a, a), a); }
 
 // ---------------------------------------------------------------------------
-// Inversion of a canonical (non-Montgomery) value by the binary extended
-// Euclidean algorithm (Menezes et al., Handbook of Applied Cryptography,
-// Alg. 14.61, with halving modulo p).  Variable time; the values inverted in
-// this library are public (commitments, twiddle set-up).  Returns 0 for 0.
+// Inversion of a canonical (non-Montgomery) value by Bernstein-Yang divsteps
+// (D. J. Bernstein, B.-Y. Yang, "Fast constant-time gcd computation and
+// modular inversion", TCHES 2019), run in variable time: the values inverted
+// in this library are public (commitments, twiddle set-up).  Returns 0 for 0.
+//
+// With f = p, g = x, a divstep maps (delta, f, g), f odd, to
+//     (1 - delta, g, (g - f) / 2)   if delta > 0 and g is odd,
+//     (1 + delta, f, (g + f) / 2)   if delta <= 0 and g is odd,
+//     (1 + delta, f, g / 2)         if g is even,
+// and g reaches 0 with f = +-gcd = +-1 after ~526 steps for 254-bit p
+// (at most 742 by the paper's bound).  The choices of 30 consecutive steps
+// depend only on the low 30 bits of f and g, so they are made on one word
+// and gathered into a matrix T with 2^30 [f', g'] = T [f, g] (entries of
+// absolute row sum <= 2^30), which is then applied once to the full values
+// and to d, e with f = d x, g = e x (mod p): [d', e'] = T [d, e] / 2^30 mod p.
+// At the end x^-1 = +-d.  A batch costs ~30 word operations plus four short
+// multi-word products, so one inversion is ~18 batches instead of ~750
+// multi-word shift/subtract steps of the binary extended Euclid.
 // ---------------------------------------------------------------------------
 
 namespace detail {
 
-ZK_DEV bool u256_is_one(const uint32_t (&a)[8]) {
-    uint32_t x = a[0] ^ 1u;
-#pragma unroll
-    for (int i = 1; i < 8; i++) x |= a[i];
-    return x == 0;
-}
+constexpr int kDivBatch = 30;
+constexpr int kDivMaxBatches = 26;  // 780 > 742 divsteps
 
-ZK_DEV void u256_shr1(uint32_t (&a)[8], uint32_t top) {
-#pragma unroll
-    for (int i = 0; i < 7; i++) a[i] = __funnelshift_r(a[i], a[i + 1], 1);
-    a[7] = (a[7] >> 1) | (top << 31);
-}
+// 288-bit two's complement integer, little-endian words.
+struct S288 {
+    uint32_t w[9];
+};
 
-ZK_DEV bool u256_ge(const uint32_t (&a)[8], const uint32_t (&b)[8]) {
-#pragma unroll
-    for (int i = 7; i >= 0; i--) {
-        if (a[i] != b[i]) return a[i] > b[i];
+// Thirty divsteps on the low words of f and g; returns the new delta and T.
+ZK_HD int divsteps30(int delta, uint32_t f, uint32_t g, int32_t &u, int32_t &v, int32_t &q, int32_t &r) {
+    u = 1;
+    v = 0;
+    q = 0;
+    r = 1;
+    for (int i = 0; i < kDivBatch; i++) {
+        if (g & 1) {
+            if (delta > 0) {
+                delta = 1 - delta;
+                const uint32_t t = f;
+                f = g;
+                g = (g - t) >> 1;
+                const int32_t nu = 2 * q, nv = 2 * r;
+                q -= u;
+                r -= v;
+                u = nu;
+                v = nv;
+            } else {
+                delta = 1 + delta;
+                g = (g + f) >> 1;
+                q += u;
+                r += v;
+                u *= 2;
+                v *= 2;
+            }
+        } else {
+            delta = 1 + delta;
+            g >>= 1;
+            u *= 2;
+            v *= 2;
+        }
     }
-    return true;
+    return delta;
 }
 
-ZK_DEV uint32_t u256_add(uint32_t (&r)[8], const uint32_t (&a)[8], const uint32_t (&b)[8]) {
-    uint64_t c = 0;
-#pragma unroll
+// (ca a + cb b) / 2^30 for |ca| + |cb| <= 2^30 (exact division).
+ZK_HD S288 lin_shr30(const S288 &a, const S288 &b, int32_t ca, int32_t cb) {
+    uint32_t t[9];
+    int64_t acc = 0;
+    for (int i = 0; i < 9; i++) {
+        const int64_t ai = i == 8 ? (int64_t)(int32_t)a.w[i] : (int64_t)a.w[i];
+        const int64_t bi = i == 8 ? (int64_t)(int32_t)b.w[i] : (int64_t)b.w[i];
+        acc += ai * ca + bi * cb;  // |.| < 2^62 + 2^32
+        t[i] = (uint32_t)acc;
+        acc >>= 32;  // arithmetic
+    }
+    S288 r;
+    for (int i = 0; i < 8; i++) r.w[i] = (t[i] >> kDivBatch) | (t[i + 1] << (32 - kDivBatch));
+    r.w[8] = (uint32_t)((int32_t)t[8] >> kDivBatch);
+    return r;
+}
+
+// (ca d + cb e) / 2^30 mod p for d, e in [0, p), result in [0, p).
+// n0 = -p^-1 mod 2^32 makes the numerator divisible by 2^30.
+ZK_HD void lin_mod_shr30(const uint32_t *d, const uint32_t *e, int32_t ca, int32_t cb, const uint32_t *pm,
+                         uint32_t n0, uint32_t *out) {
+    uint32_t t[9];
+    int64_t acc = 0;
     for (int i = 0; i < 8; i++) {
-        c += (uint64_t)a[i] + b[i];
-        r[i] = (uint32_t)c;
-        c >>= 32;
+        acc += (int64_t)d[i] * ca + (int64_t)e[i] * cb;
+        t[i] = (uint32_t)acc;
+        acc >>= 32;
     }
-    return (uint32_t)c;
+    t[8] = (uint32_t)acc;  // sign word: |ca d + cb e| < 2^30 p < 2^284
+    const uint32_t m = (t[0] * n0) & ((1u << kDivBatch) - 1u);
+    acc = 0;
+    for (int i = 0; i < 9; i++) {
+        acc += (int64_t)(i == 8 ? (int64_t)(int32_t)t[i] : (int64_t)t[i]) + (i < 8 ? (int64_t)m * pm[i] : 0);
+        t[i] = (uint32_t)acc;
+        acc >>= 32;
+    }
+    // t = (ca d + cb e + m p), divisible by 2^30, in (-2^30 p, 2^31 p): the
+    // quotient lies in (-p, 2p).
+    uint32_t x[9];
+    for (int i = 0; i < 8; i++) x[i] = (t[i] >> kDivBatch) | (t[i + 1] << (32 - kDivBatch));
+    x[8] = (uint32_t)((int32_t)t[8] >> kDivBatch);
+    if ((int32_t)x[8] < 0) {  // add p
+        uint64_t c = 0;
+        for (int i = 0; i < 8; i++) {
+            c += (uint64_t)x[i] + pm[i];
+            x[i] = (uint32_t)c;
+            c >>= 32;
+        }
+        x[8] += (uint32_t)c;
+    }
+    // subtract p while x >= p (at most once)
+    bool ge = x[8] != 0;
+    if (!ge) {
+        ge = true;
+        for (int i = 7; i >= 0; i--)
+            if (x[i] != pm[i]) {
+                ge = x[i] > pm[i];
+                break;
+            }
+    }
+    if (ge) {
+        int64_t br = 0;
+        for (int i = 0; i < 8; i++) {
+            const int64_t dd = (int64_t)x[i] - pm[i] - br;
+            x[i] = (uint32_t)dd;
+            br = dd < 0;
+        }
+    }
+    for (int i = 0; i < 8; i++) out[i] = x[i];
 }
 
-ZK_DEV void u256_sub(uint32_t (&r)[8], const uint32_t (&a)[8], const uint32_t (&b)[8]) {
-    int64_t br = 0;
-#pragma unroll
+// x^-1 mod p for canonical x (0 for 0); pm = p (odd), n0 = -p^-1 mod 2^32.
+ZK_HD void inv_divsteps(const uint32_t *x, const uint32_t *pm, uint32_t n0, uint32_t *out) {
+    S288 f, g;
+    uint32_t d[8], e[8];
+    bool zero = true;
     for (int i = 0; i < 8; i++) {
-        int64_t d = (int64_t)a[i] - b[i] - br;
-        r[i] = (uint32_t)d;
-        br = d < 0;
+        f.w[i] = pm[i];
+        g.w[i] = x[i];
+        zero = zero && x[i] == 0;
+        d[i] = 0;
+        e[i] = 0;
     }
-}
-
-template <class P> ZK_DEV void half_mod(uint32_t (&x)[8]) {
-    const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
-    uint32_t c = 0;
-    if (x[0] & 1) c = u256_add(x, x, pm);
-    u256_shr1(x, c);
+    f.w[8] = g.w[8] = 0;
+    e[0] = 1;
+    int delta = 1;
+    for (int it = 0; it < kDivMaxBatches && !zero; it++) {
+        bool gz = true;
+        for (int i = 0; i < 9; i++) gz = gz && g.w[i] == 0;
+        if (gz) break;
+        int32_t u, v, q, r;
+        delta = divsteps30(delta, f.w[0], g.w[0], u, v, q, r);
+        const S288 nf = lin_shr30(f, g, u, v);
+        const S288 ng = lin_shr30(f, g, q, r);
+        f = nf;
+        g = ng;
+        uint32_t nd[8], ne[8];
+        lin_mod_shr30(d, e, u, v, pm, n0, nd);
+        lin_mod_shr30(d, e, q, r, pm, n0, ne);
+        for (int i = 0; i < 8; i++) {
+            d[i] = nd[i];
+            e[i] = ne[i];
+        }
+    }
+    // f = -1: x^-1 = p - d
+    const bool neg = (int32_t)f.w[8] < 0;
+    bool dz = true;
+    for (int i = 0; i < 8; i++) dz = dz && d[i] == 0;
+    if (neg && !dz) {
+        int64_t br = 0;
+        for (int i = 0; i < 8; i++) {
+            const int64_t dd = (int64_t)pm[i] - d[i] - br;
+            d[i] = (uint32_t)dd;
+            br = dd < 0;
+        }
+    }
+    for (int i = 0; i < 8; i++) out[i] = zero ? 0u : d[i];
 }
 
 }  // namespace detail
 
 template <class P> ZK_DEV Fe<P> fe_inv_canonical(const Fe<P> &a) {
-    using namespace detail;
-    if (fe_is_zero<P>(a)) return a;
-    uint32_t u[8], v[8], x1[8], x2[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        u[i] = a.v[i];
-        v[i] = P::p(i);
-        x1[i] = 0;
-        x2[i] = 0;
-    }
-    x1[0] = 1;
     const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
-    while (!u256_is_one(u) && !u256_is_one(v)) {
-        while (!(u[0] & 1)) { u256_shr1(u, 0); half_mod<P>(x1); }
-        while (!(v[0] & 1)) { u256_shr1(v, 0); half_mod<P>(x2); }
-        if (u256_ge(u, v)) {
-            u256_sub(u, u, v);
-            if (!u256_ge(x1, x2)) u256_add(x1, x1, pm);
-            u256_sub(x1, x1, x2);
-        } else {
-            u256_sub(v, v, u);
-            if (!u256_ge(x2, x1)) u256_add(x2, x2, pm);
-            u256_sub(x2, x2, x1);
-        }
-    }
     Fe<P> r;
-    const bool uo = u256_is_one(u);
-#pragma unroll
-    for (int i = 0; i < 8; i++) r.v[i] = uo ? x1[i] : x2[i];
+    detail::inv_divsteps(a.v, pm, P::n0, r.v);
     return r;
 }
 
