@@ -38,6 +38,12 @@ SRS_LOG = 22
 # per Montgomery product 264 32-bit IMADs (8 x (16 product + 16 reduction + 1)).
 FQ_MUL_PER_MADD = 10
 IMAD_PER_MUL = 264
+IMAD_LO, IMAD_HI = 136, 128  # mad.lo (incl. the 8 m = t n0 products) and mad.hi per product
+# DRAM bytes (read + write) of one k_pieces_first launch, uniform 2^20, c = 17,
+# from ncu (profiles/msm_accum_k_pieces_first_msm2^20.md); None when the
+# kernel has changed since.
+ACCUM_TRAFFIC = 2.060e9
+CPU_SAMPLE_LOG = 15  # oracle MSM sample: 2^15 points, ~10-15 s on 16 cores
 
 
 def parse():
@@ -50,6 +56,9 @@ def parse():
     ap.add_argument("--case", default=None, choices=["msm", "ntt", "fold"],
                     help="profiling case: two calls of one op at --log2n (for ncu captures)")
     ap.add_argument("--log2n", type=int, default=18)
+    ap.add_argument("--cpu-sample-log", type=int, default=CPU_SAMPLE_LOG,
+                    help="log2 points of the oracle MSM sample (cpu_baseline; the reference arm "
+                         "times 2^(this - 1) per step)")
     return ap.parse_args()
 
 
@@ -181,12 +190,17 @@ class ClockSampler:
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
 
+_ORACLE_SRS = {}
+
+
 def oracle_msm_rate(sample_n: int):
-    """The oracle's affine double-and-add MSM timed on sample_n points."""
+    """The oracle's affine double-and-add MSM timed on sample_n points (its
+    SRS is generated once per process, untimed)."""
     import oracle as orc
     orc.lib()
-    tau = Z.tau(0)
-    srs = orc.srs_gen(tau, sample_n)
+    if sample_n not in _ORACLE_SRS:
+        _ORACLE_SRS[sample_n] = orc.srs_gen(Z.tau(0), sample_n)
+    srs = _ORACLE_SRS[sample_n]
     c = Z.fr_uniform(3, sample_n)
     t0 = time.perf_counter()
     orc.msm(srs, c)
@@ -204,7 +218,7 @@ def run_reference(args):
             return
     import oracle as orc
     orc.lib()
-    sample = 1 << 9
+    sample = 1 << max(args.cpu_sample_log - 1, 1)  # default: each step ~5-7 s on 16 cores
     rates, times = [], []
     for _ in range(args.warmup):
         oracle_msm_rate(sample)
@@ -216,7 +230,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact F_q/F_r)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "MSM of %d points" % sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "affine double-and-add MSM, %d points, SRS from seeded tau" % sample},
@@ -280,6 +294,8 @@ def main():
             if record:
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
+                # phase intervals of the headline MSM only (the roofline's)
+                zk.zk_timing_enable(ctx, name == "msm_2^20_uniform")
                 a.record(stream)
                 fn()
                 b.record(stream)
@@ -291,7 +307,6 @@ def main():
         step(False)
     torch.cuda.synchronize()
     zk.zk_timing_read(ctx)  # discard
-    zk.zk_timing_enable(ctx, True)
     sampler = ClockSampler(local)
     sampler.start()
     if dist is not None:
@@ -322,25 +337,31 @@ def main():
     msm_ms = statistics.median([a.elapsed_time(b) for a, b in ev["msm_2^20_uniform"]])
     value = whole_job_rate(n20, msm_ms * 1e-3, world, dist) / 1e6
 
-    # Roofline of the dominant kernel class: MSM bucket accumulation.
+    # Roofline of the dominant kernel class: bucket accumulation of the
+    # uniform 2^20 MSM (k_pieces_first and the short rounds after it).
     imad_peak, fq_mul_peak = zk.zk_probe_rates(local)
     acc_ms, acc_cnt = phases["msm_accum"]
     c = zk.zk_tune_get(ctx, zk.ZK_TUNE_MSM_WINDOW, 20)
     W = -(-254 // c)
-    # Mixed additions per step: W nonzero digits per uniform scalar; a
-    # recentred int8 * 2^16 scalar has |q| 2^16 < 2^23, i.e. its nonzero bits
-    # fall into 1 window (c >= 16, window-aligned) or 2 (c = 17 splits bit 16).
-    q_digits = 1 if (c == 16 or 16 % c == 0) else 2
-    madds = (n20 * W + n20 * q_digits) * args.steps
+    madds = n20 * W * args.steps  # one mixed addition per nonzero signed digit
     achieved = madds * FQ_MUL_PER_MADD * IMAD_PER_MUL / (acc_ms * 1e-3) / 1e12 if acc_ms else None
+    # The IMAD pipe's ceiling for the product's instruction mix: mad.hi issues
+    # at half the mad.lo rate, so the 136 lo + 128 hi IMADs of a product take
+    # 136 + 2 * 128 mad.lo issue slots.
+    mix_peak = imad_peak * IMAD_PER_MUL / (IMAD_LO + 2 * IMAD_HI) / 1e12
     roofline = {
-        "bound": "alu", "kernel": "k_pieces_first/k_pieces_next/k_buckets_final (MSM accumulation)",
-        "window_c": c,
-        "achieved": achieved, "peak": imad_peak / 1e12, "unit": "TIMAD/s",
-        "frac": (achieved / (imad_peak / 1e12)) if achieved else None,
-        "peak_source": "measured live: independent 32-bit mad.lo issue rate (zk_probe_rates)",
-        "fq_mul_peak_per_s": fq_mul_peak, "traffic": None,
-        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "bound": "alu", "kernel": "MSM bucket accumulation (k_pieces_first + rounds + k_buckets_final), "
+                                  "uniform 2^20, c=%d" % c,
+        "achieved": achieved, "peak": mix_peak, "unit": "TIMAD/s",
+        "frac": (achieved / mix_peak) if achieved else None,
+        "peak_source": "of measured: live mad.lo issue rate (zk_probe_rates) x 264 / (136 + 2 x 128), "
+                       "mad.hi at half rate",
+        "mad_lo_peak": imad_peak / 1e12, "frac_of_mad_lo_peak": (achieved / (imad_peak / 1e12)) if achieved else None,
+        "product_loop_peak": fq_mul_peak * IMAD_PER_MUL / 1e12,
+        "algorithmic": "%d mixed additions x 10 F_q products x 264 IMADs per MSM" % (n20 * W),
+        "traffic": ACCUM_TRAFFIC, "traffic_kernel": "k_pieces_first (ncu, bytes per launch)",
+        "ms_per_launch": acc_ms / max(acc_cnt, 1),
+        "phase_ms_per_msm": {k: v[0] / args.steps for k, v in phases.items()},
     }
 
     # End to end through the C ABI with host buffers (pinned): H2D of the
@@ -365,9 +386,10 @@ def main():
 
     cpu = None
     if rank == 0:
-        r, dt, cores = oracle_msm_rate(1 << 9)
+        r, dt, cores = oracle_msm_rate(1 << args.cpu_sample_log)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "affine double-and-add MSM of 512 points (SRS from seeded tau), %.1f s" % dt}
+               "sample": "affine double-and-add MSM of %d uniform scalars (SRS from seeded tau), %.1f s"
+                         % (1 << args.cpu_sample_log, dt)}
 
     zk.zk_destroy(ctx)
     if rank != 0:
@@ -377,7 +399,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact F_q/F_r)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded SplitMix64; SRS from seeded tau)",
         "config": {"workload": WORKLOAD, "srs": "2^22 points, window tables c=16",
                    "l2": "flushed (512 MiB write) before every op", "parallelism": "replicas" if world > 1 else "single"},
