@@ -600,39 +600,35 @@ struct S288 {
 };
 
 // Thirty divsteps on the low words of f and g; returns the new delta and T.
+// Branch-free (masks and selects), so the lanes of a warp never diverge:
+// with odd = g mod 2 and swap = odd and delta > 0,
+//   f' = swap ? g : f,   g' = (g + (odd ? (swap ? -f : f) : 0)) / 2,
+//   delta' = 1 + (swap ? -delta : delta),
+//   (u, v) <- 2 (swap ? (q, r) : (u, v)),
+//   (q, r) <- (q, r) + (odd ? (swap ? -(u, v) : (u, v)) : 0).
 ZK_HD int divsteps30(int delta, uint32_t f, uint32_t g, int32_t &u, int32_t &v, int32_t &q, int32_t &r) {
-    u = 1;
-    v = 0;
-    q = 0;
-    r = 1;
+    uint32_t uu = 1, vv = 0, qq = 0, rr = 1;  // two's complement
+    uint32_t d = (uint32_t)delta;
     for (int i = 0; i < kDivBatch; i++) {
-        if (g & 1) {
-            if (delta > 0) {
-                delta = 1 - delta;
-                const uint32_t t = f;
-                f = g;
-                g = (g - t) >> 1;
-                const int32_t nu = 2 * q, nv = 2 * r;
-                q -= u;
-                r -= v;
-                u = nu;
-                v = nv;
-            } else {
-                delta = 1 + delta;
-                g = (g + f) >> 1;
-                q += u;
-                r += v;
-                u *= 2;
-                v *= 2;
-            }
-        } else {
-            delta = 1 + delta;
-            g >>= 1;
-            u *= 2;
-            v *= 2;
-        }
+        const uint32_t odd = g & 1u;
+        const uint32_t m_odd = 0u - odd;
+        const uint32_t m_sw = 0u - (odd & (uint32_t)((int32_t)d > 0));
+        const uint32_t nf = f ^ ((f ^ g) & m_sw);
+        g = (g + (((f ^ m_sw) - m_sw) & m_odd)) >> 1;
+        f = nf;
+        d = 1u + ((d ^ m_sw) - m_sw);
+        const uint32_t nu = uu ^ ((uu ^ qq) & m_sw);
+        const uint32_t nv = vv ^ ((vv ^ rr) & m_sw);
+        qq += ((uu ^ m_sw) - m_sw) & m_odd;
+        rr += ((vv ^ m_sw) - m_sw) & m_odd;
+        uu = nu << 1;
+        vv = nv << 1;
     }
-    return delta;
+    u = (int32_t)uu;
+    v = (int32_t)vv;
+    q = (int32_t)qq;
+    r = (int32_t)rr;
+    return (int)d;
 }
 
 // (ca a + cb b) / 2^30 for |ca| + |cb| <= 2^30 (exact division).

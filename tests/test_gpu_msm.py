@@ -210,3 +210,29 @@ def test_msm_small_scalar_path(zk, orc, ctx_small, tau):
     for i, k in enumerate(names):
         assert pts_equal(got[i], orc.commit_coeffs_tau(cases[k], tau)), k
         assert pts_equal(_commit(zk, ctx_small, cases[k]), got[i]), k
+
+
+def test_msm_repeated_and_opposite_points(zk, orc):
+    """An SRS of 2048 copies of G puts equal and opposite points into the same
+    buckets, so the bucket sums meet a = b (doubling) and a = -b (infinity)
+    throughout; the commitment must be (sum_i s_i) G."""
+    n = 2048
+    G = orc.g1_generator()
+    ctx = zk.zk_init(0)
+    try:
+        zk.zk_srs_load(ctx, np.ascontiguousarray(np.tile(G, (n, 1))))
+        rng = np.random.default_rng(5)
+        cases = {
+            "small": Z.encode_signed(rng.integers(-300, 300, n), 0),
+            "pm1": Z.encode_signed(rng.integers(-1, 2, n), 0),
+            "uniform": Z.fr_uniform(9, n),
+            "equal": np.tile(Z.int_to_fr(7), (n, 1)),
+            "cancel": np.concatenate([np.tile(Z.int_to_fr(5), (n // 2, 1)),
+                                      np.tile(Z.int_to_fr(R - 5), (n // 2, 1))]),
+        }
+        for name, c in cases.items():
+            total = sum(Z.fr_to_int(v) for v in c) % R
+            want = orc.g1_mul(G, Z.int_to_fr(total)) if total else np.zeros(8, np.uint64)
+            assert pts_equal(_commit(zk, ctx, c), want), name
+    finally:
+        zk.zk_destroy(ctx)
