@@ -67,6 +67,8 @@ def lib():
             "orc_srs_gen": (None, [_P, _SZ, _P]),
             "orc_msm": (None, [_P, _P, _SZ, _P]),
             "orc_commit_coeffs_tau": (None, [_P, _SZ, _P, _P]),
+            "orc_open": (None, [_P, _SZ, _P, _P, _P]),
+            "orc_open_batch": (None, [_P, ctypes.c_void_p, _SZ, _P, _P, _P, _P]),
             "orc_root_of_unity": (None, [_SZ, _P]),
             "orc_lagrange_at": (None, [_SZ, _P, _P]),
             "orc_commit_evals_tau": (None, [_P, _SZ, _P, _P]),
@@ -222,6 +224,28 @@ def commit_coeffs_tau(coeffs, tau) -> np.ndarray:
     out = np.zeros(8, dtype=np.uint64)
     lib().orc_commit_coeffs_tau(_p(c), c.shape[0], _p(_u(tau)), _p(out))
     return out
+
+
+def open_poly(coeffs, x):
+    """KZG opening by synthetic division: (y = f(x), quotient (f - y)/(X - x))."""
+    c = _u(coeffs).reshape(-1, 4)
+    n = c.shape[0]
+    y = np.zeros(4, dtype=np.uint64)
+    q = np.zeros((max(n - 1, 1), 4), dtype=np.uint64)
+    lib().orc_open(_p(c), n, _p(_u(x)), _p(y), _p(q))
+    return y, q[: max(n - 1, 0)]
+
+
+def open_batch(polys, x, gamma):
+    """Batch opening at x: ([f_i(x)], quotient of sum_i gamma^i f_i)."""
+    polys = [_u(f).reshape(-1, 4) for f in polys]
+    lens = (ctypes.c_size_t * len(polys))(*[f.shape[0] for f in polys])
+    flat = np.ascontiguousarray(np.concatenate(polys)) if polys else np.zeros((1, 4), np.uint64)
+    nmax = max(f.shape[0] for f in polys)
+    ys = np.zeros((len(polys), 4), dtype=np.uint64)
+    h = np.zeros((max(nmax - 1, 1), 4), dtype=np.uint64)
+    lib().orc_open_batch(_p(flat), lens, len(polys), _p(_u(x)), _p(_u(gamma)), _p(ys), _p(h))
+    return ys, h[: max(nmax - 1, 0)]
 
 
 def commit_evals_tau(v, tau) -> np.ndarray:

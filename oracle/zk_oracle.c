@@ -23,6 +23,9 @@
  *     f(tau) = sum_k v_k L_k(tau), L_k(tau) = omega^k (tau^n - 1) / (n (tau - omega^k)).
  *   - The NTT over F_r as the O(n^2) DFT  NTT(c)_k = sum_j c_j omega^{jk},
  *     INTT(v)_j = n^{-1} sum_k v_k omega^{-jk},  omega_n = 5^{(r-1)/n}.
+ *   - KZG opening (Sec. 2.1): y = f(x) and the quotient (f - y) / (X - x) by
+ *     synthetic division; batch opening at one point with the gamma-weighted
+ *     combination sum_i gamma^i f_i.
  *   - One generalised-Mira fold (Sec. 4.2, prover steps 2-7, degree d = 2) for
  *     the relation m1 o m2 - mu m3 = e over H, and the binary fold tree
  *     ("Merkle tree reduction", Sec. 4.2) as sequential loops.
@@ -450,6 +453,59 @@ void orc_commit_coeffs_tau(const uint64_t *coeffs, size_t n, const uint64_t *tau
         fadd(&acc, &acc, &c, &MODR);
     }
     pt g, r; pt_generator(&g); pt_mul(&r, &g, &acc); pt_store(out, &r);
+}
+
+/* KZG opening (Sec. 2.1): for f = sum_i c_i X^i (n >= 1 coefficients) and a
+ * point x, y = f(x) and the quotient q(X) = (f(X) - y) / (X - x), whose n - 1
+ * coefficients come from synthetic division by (X - x), highest first:
+ * q_{n-2} = c_{n-1},  q_{k-1} = c_k + x q_k,  and y = c_0 + x q_0.
+ * The proof is the commitment [q(tau)]_1. */
+void orc_open(const uint64_t *coeffs, size_t n, const uint64_t *x64, uint64_t *y_out, uint64_t *q_out) {
+    u256 x, carry, c;
+    load(&x, x64);
+    set_small(&carry, 0); /* the running value: q_k, then y */
+    for (size_t k = n; k-- > 0;) {
+        load(&c, coeffs + 4 * k);
+        u256 t;
+        fmul(&t, &carry, &x, &MODR);
+        fadd(&carry, &t, &c, &MODR);
+        if (k >= 1) store(q_out + 4 * (k - 1), &carry); /* q_{k-1} */
+    }
+    store(y_out, &carry);
+}
+
+/* Batch opening at one point (Sec. 2.1): y_i = f_i(x) for each polynomial and
+ * h(X) = sum_i gamma^i (f_i(X) - f_i(x)) / (X - x), the quotient of the
+ * combination F = sum_i gamma^i f_i (whose value at x is sum_i gamma^i y_i).
+ * polys holds the coefficient vectors back to back, lens their lengths; h has
+ * max(lens) - 1 coefficients. */
+void orc_open_batch(const uint64_t *polys, const size_t *lens, size_t count, const uint64_t *x64,
+                    const uint64_t *gamma64, uint64_t *ys_out, uint64_t *h_out) {
+    size_t nmax = 0, off = 0;
+    for (size_t i = 0; i < count; i++) if (lens[i] > nmax) nmax = lens[i];
+    uint64_t *F = (uint64_t *)calloc(4 * (nmax ? nmax : 1), sizeof(uint64_t));
+    uint64_t *qtmp = (uint64_t *)calloc(4 * (nmax ? nmax : 1), sizeof(uint64_t));
+    u256 gamma, gpow;
+    load(&gamma, gamma64);
+    set_small(&gpow, 1); /* gamma^i */
+    for (size_t i = 0; i < count; i++) {
+        const uint64_t *f = polys + 4 * off;
+        orc_open(f, lens[i], x64, ys_out + 4 * i, qtmp); /* y_i */
+        for (size_t j = 0; j < lens[i]; j++) {            /* F += gamma^i f_i */
+            u256 a, b, t;
+            load(&a, F + 4 * j);
+            load(&b, f + 4 * j);
+            fmul(&t, &b, &gpow, &MODR);
+            fadd(&a, &a, &t, &MODR);
+            store(F + 4 * j, &a);
+        }
+        fmul(&gpow, &gpow, &gamma, &MODR);
+        off += lens[i];
+    }
+    uint64_t yF[4];
+    if (nmax) orc_open(F, nmax, x64, yF, h_out);
+    free(F);
+    free(qtmp);
 }
 
 /* omega_n = 5^{(r-1)/n} for n a power of two dividing 2^28. */
