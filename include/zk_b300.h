@@ -144,6 +144,31 @@ int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk
 #define ZK_LAGRANGE 2u /* vectors are evaluations over H: commit through the Lagrange basis
                           [L_k(tau)]_1 of H, with no INTT (same result as ZK_EVALS) */
 
+/* KZG opening (Sec. 2.1): for f = sum_k coeffs[k] X^k (n >= 1 coefficients,
+ * canonical; the quotient's n - 1 coefficients need an SRS of at least n - 1
+ * points) and a point x:
+ *   y = f(x),  quotient = (f(X) - y) / (X - x)  (n - 1 coefficients),
+ *   proof = [quotient(tau)]_1  (the commitment of the quotient),
+ * so that the verifier's pairing check e(proof, [tau - x]_2) =
+ * e(com - [y]_1, [1]_2) holds.  coeffs and x may be device or host pointers;
+ * y (32 bytes), proof (64 bytes, affine canonical) and quotient (optional,
+ * NULL to skip) may be device or host pointers (host outputs are written
+ * before the call returns; device outputs are stream-ordered).
+ * Errors: ZK_EINVAL (null pointer, n = 0 or n > 2^31), ZK_ESRS (no SRS, or
+ * n - 1 > SRS size), ZK_ENOMEM, ZK_ECUDA. */
+int zk_open(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *x, zk_fr *y, zk_g1 *proof,
+            zk_fr *quotient, zk_stream stream);
+
+/* Batch opening at one point (Sec. 2.1): ys[i] = f_i(x) for the count
+ * polynomials polys[i] (lens[i] >= 1 coefficients each, device or host
+ * pointers; `polys` and `lens` are host arrays), and one proof
+ * [h(tau)]_1 with h(X) = sum_i gamma^i (f_i(X) - f_i(x)) / (X - x), the
+ * quotient of sum_i gamma^i f_i.  x and gamma: one scalar each (device or
+ * host); ys: count scalars; proof: 64 bytes (device or host).  Errors as for
+ * zk_open, with max(lens) in place of n. */
+int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, size_t count, const zk_fr *x,
+                  const zk_fr *gamma, zk_fr *ys, zk_g1 *proof, zk_stream stream);
+
 /* Route of evaluation-form commitments (ZK_EVALS, leaf accumulators, fold
  * cross terms).  ZK_ROUTE_INTT interpolates (INTT) and commits over the SRS,
  * as the paper's encoding describes (Sec. 3).  ZK_ROUTE_LAGRANGE commits the

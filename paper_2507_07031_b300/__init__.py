@@ -101,6 +101,8 @@ def _load():
                             ctypes.POINTER(ctypes.c_double)],
         "zk_timing_read": [_VP, _VP, _VP],
         "zk_field_op": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _SZ, _VP],
+        "zk_open": [_VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
+        "zk_open_batch": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -125,7 +127,7 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
-            "zk_server_destroy", "zk_set_commit_route", "zk_field_op"]
+            "zk_server_destroy", "zk_set_commit_route", "zk_field_op", "zk_open", "zk_open_batch"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 ZK_FIELD_Q, ZK_FIELD_R = 0, 1
@@ -156,6 +158,24 @@ def zk_field_op(field: int, op: int, a, b, out, n: int = None, stream=None) -> N
         n = a.numel() // 4
     _check(lib.zk_field_op(int(field), int(op), _ptr(a), _ptr(b), _ptr(out), int(n), _stream(stream)),
            "zk_field_op")
+
+
+def zk_open(ctx: int, coeffs, x, y, proof, quotient=None, n: int = None, stream=None) -> None:
+    """KZG opening at x: y = f(x), proof = [q(tau)]_1, q = (f - y)/(X - x)
+    (optionally written to `quotient`, n - 1 scalars).  Buffers: torch tensors
+    (device or host) or numpy arrays of canonical limbs."""
+    if n is None:
+        n = _nelem(coeffs, 4)
+    _check(lib.zk_open(ctx, _ptr(coeffs), int(n), _ptr(x), _ptr(y), _ptr(proof), _ptr(quotient),
+                       _stream(stream)), "zk_open")
+
+
+def zk_open_batch(ctx: int, polys, x, gamma, ys, proof, stream=None) -> None:
+    """Batch opening at x: ys[i] = f_i(x), one proof for sum_i gamma^i f_i."""
+    ptrs = (ctypes.c_void_p * len(polys))(*[_ptr(p) for p in polys])
+    lens = (ctypes.c_size_t * len(polys))(*[_nelem(p, 4) for p in polys])
+    _check(lib.zk_open_batch(ctx, ptrs, lens, len(polys), _ptr(x), _ptr(gamma), _ptr(ys), _ptr(proof),
+                             _stream(stream)), "zk_open_batch")
 
 
 def zk_set_commit_route(ctx: int, route: int) -> None:

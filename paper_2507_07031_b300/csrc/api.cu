@@ -417,6 +417,97 @@ int zk_srs_export(zk_ctx *ctx, zk_g1 *out, size_t first, size_t count, zk_stream
     return srs_export_impl(ctx, out, first, count, (cudaStream_t)stream);
 }
 
+// Output buffer of an opening: the caller's device pointer, or workspace
+// copied back to the host pointer after the call.
+struct OutBuf {
+    void *user = nullptr, *dev = nullptr;
+    size_t bytes = 0;
+    int init(zk_ctx *ctx, void *p, size_t n, const char *name) {
+        user = p;
+        bytes = n;
+        if (!p || is_device_ptr(p)) {
+            dev = p;
+            return ZK_OK;
+        }
+        int err = ZK_OK;
+        dev = scratch(ctx, name, std::max<size_t>(n, 32), &err);
+        return dev ? ZK_OK : err;
+    }
+    int finish(cudaStream_t s) {
+        if (user && dev != user) ZK_CUDA_TRY(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, s));
+        return ZK_OK;
+    }
+    bool host() const { return user && dev != user; }
+};
+
+int zk_open(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *x, zk_fr *y, zk_g1 *proof, zk_fr *quotient,
+            zk_stream stream) {
+    if (!ctx || !coeffs || !x || !y || !proof || n == 0) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->sh->srs_n == 0) return ZK_ESRS;
+    const void *dc, *dx;
+    ZK_TRY(stage_in(ctx, coeffs, n * 32, "open.in0", &dc, s));
+    ZK_TRY(stage_in(ctx, x, 32, "open.x", &dx, s));
+    OutBuf oy, op, oq;
+    ZK_TRY(oy.init(ctx, y, 32, "open.y"));
+    ZK_TRY(op.init(ctx, proof, 64, "open.proof"));
+    ZK_TRY(oq.init(ctx, quotient, (n - 1) * 32, "open.quot"));
+    const uint32_t *pv[1] = {(const uint32_t *)dc};
+    const size_t lv[1] = {n};
+    ZK_TRY(open_impl(ctx, pv, lv, 1, (const uint32_t *)dx, nullptr, (uint32_t *)oy.dev, (uint32_t *)oq.dev,
+                     (uint32_t *)op.dev, s));
+    ZK_TRY(oy.finish(s));
+    ZK_TRY(op.finish(s));
+    ZK_TRY(oq.finish(s));
+    if (oy.host() || op.host() || oq.host()) ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    return ZK_OK;
+}
+
+int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, size_t count, const zk_fr *x,
+                  const zk_fr *gamma, zk_fr *ys, zk_g1 *proof, zk_stream stream) {
+    if (!ctx || !polys || !lens || !x || !gamma || !ys || !proof || count == 0) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->sh->srs_n == 0) return ZK_ESRS;
+    std::vector<const uint32_t *> pv(count);
+    std::vector<size_t> lv(count);
+    size_t host_bytes = 0;
+    for (size_t i = 0; i < count; i++) {
+        if (!polys[i] || lens[i] == 0) return ZK_EINVAL;
+        lv[i] = lens[i];
+        if (!is_device_ptr(polys[i])) host_bytes += lens[i] * 32;
+    }
+    int err = ZK_OK;
+    char *stage = nullptr;
+    if (host_bytes) {
+        stage = (char *)scratch(ctx, "open.inb", host_bytes, &err);
+        if (!stage) return err;
+    }
+    size_t off = 0;
+    for (size_t i = 0; i < count; i++) {
+        if (is_device_ptr(polys[i])) {
+            pv[i] = (const uint32_t *)polys[i];
+        } else {
+            ZK_CUDA_TRY(cudaMemcpyAsync(stage + off, polys[i], lens[i] * 32, cudaMemcpyHostToDevice, s));
+            pv[i] = (const uint32_t *)(stage + off);
+            off += lens[i] * 32;
+        }
+    }
+    const void *dx, *dg;
+    ZK_TRY(stage_in(ctx, x, 32, "open.x", &dx, s));
+    ZK_TRY(stage_in(ctx, gamma, 32, "open.gamma", &dg, s));
+    OutBuf oy, op;
+    ZK_TRY(oy.init(ctx, ys, count * 32, "open.ys"));
+    ZK_TRY(op.init(ctx, proof, 64, "open.proof"));
+    ZK_TRY(open_impl(ctx, pv.data(), lv.data(), count, (const uint32_t *)dx, (const uint32_t *)dg,
+                     (uint32_t *)oy.dev, nullptr, (uint32_t *)op.dev, s));
+    ZK_TRY(oy.finish(s));
+    ZK_TRY(op.finish(s));
+    if (oy.host() || op.host()) ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    return ZK_OK;
+}
+
 int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream) {
     if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
     const size_t lens[1] = {n};

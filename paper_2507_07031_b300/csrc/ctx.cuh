@@ -199,6 +199,13 @@ struct MsmJob {
     int basis = 0;  // 0: scalars are coefficients (SRS); lg: evaluations over H, n = 2^lg (Lagrange basis)
 };
 int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStream_t s);
+
+// KZG opening (open.cu), device pointers only: without gamma, one polynomial
+// (count = 1): ys[0] = f(x), quotient = (f - f(x)) / (X - x), proof = its
+// commitment; with gamma, ys[i] = f_i(x) and the quotient and proof of
+// sum_i gamma^i f_i.  quotient may be null (workspace).
+int open_impl(zk_ctx *ctx, const uint32_t *const *polys, const size_t *lens, size_t count, const uint32_t *x,
+              const uint32_t *gamma, uint32_t *ys, uint32_t *quotient, uint32_t *proof, cudaStream_t s);
 int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count);
 
 // Fold (fold.cu)
