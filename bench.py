@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip batch / fold-tree comparisons")
-    ap.add_argument("--case", default=None, choices=["msm", "ntt", "fold"],
+    ap.add_argument("--case", default=None, choices=["msm", "ntt", "fold", "open"],
                     help="profiling case: two calls of one op at --log2n (for ncu captures)")
     ap.add_argument("--log2n", type=int, default=18)
     ap.add_argument("--cpu-sample-log", type=int, default=CPU_SAMPLE_LOG,
@@ -83,6 +83,13 @@ def run_case(args):
         x = dev(Z.fr_uniform(5, n))
         for _ in range(2):
             zk.zk_ntt(ctx, x)
+    elif args.case == "open":
+        c = dev(Z.fr_uniform(11, n + 1))
+        pt = dev(Z.fr_uniform(12, 1)[0])
+        y = torch.zeros(4, dtype=torch.int64, device="cuda")
+        proof = torch.zeros(8, dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            zk.zk_open(ctx, c, pt, y, proof)
     else:
         L, R = [], []
         for j in range(2):
@@ -542,11 +549,55 @@ def run_extras(zk, ctx, dev, torch):
                         "batched_phase_ms": ph_tree}
     del accs, leaf_state, descs
     torch.cuda.empty_cache()
+    res["kzg_open"] = run_openings(zk, ctx, dev, torch)
     res["serving"] = run_serving(zk, ctx, dev, torch)
     zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
     res["serving_lagrange"] = run_serving(zk, ctx, dev, torch)
     zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
     return res
+
+
+def run_openings(zk, ctx, dev, torch, reps=5):
+    """KZG opening (Sec. 2.1) at 2^20: one polynomial (division + MSM of the
+    quotient), and a gamma-batched opening of 16 polynomials of 2^16 at one
+    point.  Device time with CUDA events, inputs resident, L2 flushed."""
+    n = 1 << 20
+    c = dev(Z.fr_uniform(13, n + 1))
+    pt = dev(Z.fr_uniform(14, 1)[0])
+    y = torch.zeros(4, dtype=torch.int64, device="cuda")
+    proof = torch.zeros(8, dtype=torch.int64, device="cuda")
+    polys = [dev(Z.fr_uniform(15 + i, 1 << 16)) for i in range(16)]
+    gamma = dev(Z.fr_uniform(40, 1)[0])
+    ys = torch.zeros((16, 4), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    zk.zk_timing_read(ctx)
+    one = timed(lambda: zk.zk_open(ctx, c, pt, y, proof))
+    zk.zk_timing_enable(ctx, True)
+    zk.zk_open(ctx, c, pt, y, proof)
+    torch.cuda.synchronize()
+    ph = zk.zk_timing_read(ctx)
+    zk.zk_timing_enable(ctx, False)
+    msm_ms = sum(ph[k][0] for k in ("msm_sort", "msm_accum", "msm_reduce"))
+    batch = timed(lambda: zk.zk_open_batch(ctx, polys, pt, gamma, ys, proof))
+    return {"open_2^20_ms": one, "open_2^20_msm_ms": msm_ms, "open_2^20_division_ms": one - msm_ms,
+            "open_batch_16x2^16_ms": batch}
 
 
 def run_serving(zk, ctx, dev, torch, lanes=4, layers=12, rate_hz=20.0):
