@@ -68,6 +68,7 @@ def lib():
             "orc_msm": (None, [_P, _P, _SZ, _P]),
             "orc_commit_coeffs_tau": (None, [_P, _SZ, _P, _P]),
             "orc_open": (None, [_P, _SZ, _P, _P, _P]),
+            "orc_mul_quotient": (ctypes.c_int, [_P, _P, _SZ, _P]),
             "orc_open_batch": (None, [_P, ctypes.c_void_p, _SZ, _P, _P, _P, _P]),
             "orc_root_of_unity": (None, [_SZ, _P]),
             "orc_lagrange_at": (None, [_SZ, _P, _P]),
@@ -246,6 +247,17 @@ def open_batch(polys, x, gamma):
     h = np.zeros((max(nmax - 1, 1), 4), dtype=np.uint64)
     lib().orc_open_batch(_p(flat), lens, len(polys), _p(_u(x)), _p(_u(gamma)), _p(ys), _p(h))
     return ys, h[: max(nmax - 1, 0)]
+
+
+def mul_quotient(a, b):
+    """t = (A B - L) / (X^n - 1) for evaluation vectors a, b over H (L
+    interpolates a o b): (t with n - 1 coefficients, exact division flag)."""
+    a = _u(a).reshape(-1, 4)
+    b = _u(b).reshape(-1, 4)
+    n = a.shape[0]
+    t = np.zeros((max(n - 1, 1), 4), dtype=np.uint64)
+    bad = lib().orc_mul_quotient(_p(a), _p(b), n, _p(t))
+    return t[: max(n - 1, 0)], bad == 0
 
 
 def commit_evals_tau(v, tau) -> np.ndarray:

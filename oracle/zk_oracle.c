@@ -26,6 +26,8 @@
  *   - KZG opening (Sec. 2.1): y = f(x) and the quotient (f - y) / (X - x) by
  *     synthetic division; batch opening at one point with the gamma-weighted
  *     combination sum_i gamma^i f_i.
+ *   - The Mul / MatMul quotient (Sec. 4.4.1) t = (A B - L) / (X^n - 1) by
+ *     schoolbook multiplication and long division.
  *   - One generalised-Mira fold (Sec. 4.2, prover steps 2-7, degree d = 2) for
  *     the relation m1 o m2 - mu m3 = e over H, and the binary fold tree
  *     ("Merkle tree reduction", Sec. 4.2) as sequential loops.
@@ -455,6 +457,8 @@ void orc_commit_coeffs_tau(const uint64_t *coeffs, size_t n, const uint64_t *tau
     pt g, r; pt_generator(&g); pt_mul(&r, &g, &acc); pt_store(out, &r);
 }
 
+void orc_dft(const uint64_t *in, size_t n, int inverse, uint64_t *out);
+
 /* KZG opening (Sec. 2.1): for f = sum_i c_i X^i (n >= 1 coefficients) and a
  * point x, y = f(x) and the quotient q(X) = (f(X) - y) / (X - x), whose n - 1
  * coefficients come from synthetic division by (X - x), highest first:
@@ -506,6 +510,58 @@ void orc_open_batch(const uint64_t *polys, const size_t *lens, size_t count, con
     if (nmax) orc_open(F, nmax, x64, yF, h_out);
     free(F);
     free(qtmp);
+}
+
+/* Quotient of the Mul relation (Sec. 4.4.1; also MatMul's Q_l with l = a o b):
+ * for evaluation vectors a, b over H (n = 2^k) with interpolants A, B, and L
+ * the interpolant of l_i = a_i b_i, the product A B - L vanishes on H, and
+ * t(X) = (A(X) B(X) - L(X)) / (X^n - 1)
+ * has n - 1 coefficients.  Steps as defined: A, B, L by the inverse DFT,
+ * A B by schoolbook multiplication, then long division by X^n - 1 from the
+ * top coefficient down.  Returns 0, or 1 if the remainder is not zero. */
+int orc_mul_quotient(const uint64_t *a, const uint64_t *b, size_t n, uint64_t *t_out) {
+    uint64_t *A = (uint64_t *)malloc(32 * n), *B = (uint64_t *)malloc(32 * n), *L = (uint64_t *)malloc(32 * n);
+    uint64_t *l = (uint64_t *)malloc(32 * n);
+    for (size_t i = 0; i < n; i++) {
+        u256 x, y, z;
+        load(&x, a + 4 * i);
+        load(&y, b + 4 * i);
+        fmul(&z, &x, &y, &MODR);
+        store(l + 4 * i, &z);
+    }
+    orc_dft(a, n, 1, A);
+    orc_dft(b, n, 1, B);
+    orc_dft(l, n, 1, L);
+    /* D = A B - L, degree <= 2n - 2 */
+    u256 *D = (u256 *)calloc(2 * n, sizeof(u256));
+    for (size_t i = 0; i < n; i++) {
+        u256 ai;
+        load(&ai, A + 4 * i);
+        for (size_t j = 0; j < n; j++) {
+            u256 bj, p;
+            load(&bj, B + 4 * j);
+            fmul(&p, &ai, &bj, &MODR);
+            fadd(&D[i + j], &D[i + j], &p, &MODR);
+        }
+    }
+    for (size_t i = 0; i < n; i++) {
+        u256 li;
+        load(&li, L + 4 * i);
+        fsub(&D[i], &D[i], &li, &MODR);
+    }
+    /* divide by X^n - 1: for k from the top, q_{k-n} = D_k, D_{k-n} += D_k */
+    u256 *q = (u256 *)calloc(n, sizeof(u256));
+    for (size_t k = 2 * n; k-- > n;) {
+        q[k - n] = D[k];
+        fadd(&D[k - n], &D[k - n], &D[k], &MODR);
+        memset(&D[k], 0, sizeof(u256));
+    }
+    int bad = 0;
+    for (size_t i = 0; i < n; i++) bad |= !is_zero(&D[i]);
+    bad |= n >= 1 && !is_zero(&q[n - 1]);  /* degree <= n - 2 */
+    for (size_t i = 0; i + 1 < n; i++) store(t_out + 4 * i, &q[i]);
+    free(A); free(B); free(L); free(l); free(D); free(q);
+    return bad;
 }
 
 /* omega_n = 5^{(r-1)/n} for n a power of two dividing 2^28. */
