@@ -549,7 +549,7 @@ def run_extras(zk, ctx, dev, torch):
                         "batched_phase_ms": ph_tree}
     del accs, leaf_state, descs
     torch.cuda.empty_cache()
-    res["kzg_open"] = run_openings(zk, ctx, dev, torch)
+    res["kzg_open_and_quotient"] = run_openings(zk, ctx, dev, torch)
     res["serving"] = run_serving(zk, ctx, dev, torch)
     zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
     res["serving_lagrange"] = run_serving(zk, ctx, dev, torch)
@@ -596,8 +596,14 @@ def run_openings(zk, ctx, dev, torch, reps=5):
     zk.zk_timing_enable(ctx, False)
     msm_ms = sum(ph[k][0] for k in ("msm_sort", "msm_accum", "msm_reduce"))
     batch = timed(lambda: zk.zk_open_batch(ctx, polys, pt, gamma, ys, proof))
+    # Mul / MatMul quotient (Sec. 4.4.1) of two 2^20 evaluation vectors:
+    # six transforms of length 2^20, three pointwise passes, one MSM.
+    a = dev(Z.zkml_scalars(41, n))
+    b = dev(Z.fr_uniform(42, n))
+    com = torch.zeros(8, dtype=torch.int64, device="cuda")
+    mq = timed(lambda: zk.zk_mul_quotient(ctx, a, b, com))
     return {"open_2^20_ms": one, "open_2^20_msm_ms": msm_ms, "open_2^20_division_ms": one - msm_ms,
-            "open_batch_16x2^16_ms": batch}
+            "open_batch_16x2^16_ms": batch, "mul_quotient_2^20_ms": mq}
 
 
 def run_serving(zk, ctx, dev, torch, lanes=4, layers=12, rate_hz=20.0):

@@ -169,6 +169,19 @@ int zk_open(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *x, zk_fr *y
 int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, size_t count, const zk_fr *x,
                   const zk_fr *gamma, zk_fr *ys, zk_g1 *proof, zk_stream stream);
 
+/* Quotient of the Mul basic block, also MatMul's Q_l (Sec. 4.4.1): for
+ * evaluation vectors a, b over H = <omega_n> (n a power of two, 1 <= n <= 2^27,
+ * canonical scalars) with interpolants A, B, and L the interpolant of the
+ * elementwise product a o b,
+ *   t(X) = (A(X) B(X) - L(X)) / (X^n - 1)   (an exact division; n - 1
+ *   coefficients, degree <= n - 2),
+ * and com = [t(tau)]_1 (needs an SRS of at least n - 1 points).  a, b: device
+ * or host; t (optional, NULL to skip; n - 1 scalars) and com (64 bytes): device
+ * or host.  Errors: ZK_EINVAL (null pointer, n not a power of two or too
+ * large), ZK_ESRS, ZK_ENOMEM, ZK_ECUDA. */
+int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr *t, zk_g1 *com,
+                    zk_stream stream);
+
 /* Route of evaluation-form commitments (ZK_EVALS, leaf accumulators, fold
  * cross terms).  ZK_ROUTE_INTT interpolates (INTT) and commits over the SRS,
  * as the paper's encoding describes (Sec. 3).  ZK_ROUTE_LAGRANGE commits the

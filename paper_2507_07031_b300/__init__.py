@@ -103,6 +103,7 @@ def _load():
         "zk_field_op": [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _SZ, _VP],
         "zk_open": [_VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
         "zk_open_batch": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
+        "zk_mul_quotient": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -127,7 +128,8 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
-            "zk_server_destroy", "zk_set_commit_route", "zk_field_op", "zk_open", "zk_open_batch"]
+            "zk_server_destroy", "zk_set_commit_route", "zk_field_op", "zk_open", "zk_open_batch",
+            "zk_mul_quotient"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 ZK_FIELD_Q, ZK_FIELD_R = 0, 1
@@ -176,6 +178,15 @@ def zk_open_batch(ctx: int, polys, x, gamma, ys, proof, stream=None) -> None:
     lens = (ctypes.c_size_t * len(polys))(*[_nelem(p, 4) for p in polys])
     _check(lib.zk_open_batch(ctx, ptrs, lens, len(polys), _ptr(x), _ptr(gamma), _ptr(ys), _ptr(proof),
                              _stream(stream)), "zk_open_batch")
+
+
+def zk_mul_quotient(ctx: int, a, b, com, t=None, n: int = None, stream=None) -> None:
+    """Mul / MatMul quotient t = (A B - L)/(X^n - 1) of evaluation vectors a, b
+    over H (L interpolates a o b); com = [t(tau)]_1, t optional."""
+    if n is None:
+        n = _nelem(a, 4)
+    _check(lib.zk_mul_quotient(ctx, _ptr(a), _ptr(b), int(n), _ptr(t), _ptr(com), _stream(stream)),
+           "zk_mul_quotient")
 
 
 def zk_set_commit_route(ctx: int, route: int) -> None:

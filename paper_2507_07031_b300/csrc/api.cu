@@ -508,6 +508,26 @@ int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, si
     return ZK_OK;
 }
 
+int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr *t, zk_g1 *com,
+                    zk_stream stream) {
+    if (!ctx || !a || !b || !com || n == 0) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->sh->srs_n == 0) return ZK_ESRS;
+    const void *da, *db;
+    ZK_TRY(stage_in(ctx, a, n * 32, "mq.in_a", &da, s));
+    ZK_TRY(stage_in(ctx, b, n * 32, "mq.in_b", &db, s));
+    OutBuf ot, oc;
+    ZK_TRY(ot.init(ctx, t, (n - 1) * 32, "mq.out_t"));
+    ZK_TRY(oc.init(ctx, com, 64, "mq.out_com"));
+    ZK_TRY(mul_quotient_impl(ctx, (const uint32_t *)da, (const uint32_t *)db, n, (uint32_t *)ot.dev,
+                             (uint32_t *)oc.dev, s));
+    ZK_TRY(ot.finish(s));
+    ZK_TRY(oc.finish(s));
+    if (ot.host() || oc.host()) ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    return ZK_OK;
+}
+
 int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream) {
     if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
     const size_t lens[1] = {n};

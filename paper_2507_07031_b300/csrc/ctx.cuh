@@ -206,6 +206,11 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStr
 // sum_i gamma^i f_i.  quotient may be null (workspace).
 int open_impl(zk_ctx *ctx, const uint32_t *const *polys, const size_t *lens, size_t count, const uint32_t *x,
               const uint32_t *gamma, uint32_t *ys, uint32_t *quotient, uint32_t *proof, cudaStream_t s);
+
+// Mul / MatMul quotient (quotient.cu), device pointers only: t (n - 1
+// coefficients, may be null) and its commitment com.
+int mul_quotient_impl(zk_ctx *ctx, const uint32_t *a, const uint32_t *b, size_t n, uint32_t *t, uint32_t *com,
+                      cudaStream_t s);
 int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count);
 
 // Fold (fold.cu)
