@@ -69,6 +69,7 @@ def lib():
             "orc_commit_coeffs_tau": (None, [_P, _SZ, _P, _P]),
             "orc_open": (None, [_P, _SZ, _P, _P, _P]),
             "orc_mul_quotient": (ctypes.c_int, [_P, _P, _SZ, _P]),
+            "orc_commit_hiding": (None, [_P, _P, _SZ, _P, _P, _P]),
             "orc_open_batch": (None, [_P, ctypes.c_void_p, _SZ, _P, _P, _P, _P]),
             "orc_root_of_unity": (None, [_SZ, _P]),
             "orc_lagrange_at": (None, [_SZ, _P, _P]),
@@ -258,6 +259,15 @@ def mul_quotient(a, b):
     t = np.zeros((max(n - 1, 1), 4), dtype=np.uint64)
     bad = lib().orc_mul_quotient(_p(a), _p(b), n, _p(t))
     return t[: max(n - 1, 0)], bad == 0
+
+
+def commit_hiding(points, coeffs, H, s):
+    """[f(tau)]_1 + s H: MSM over `points` plus s H."""
+    points = _u(points).reshape(-1, 8)
+    c = _u(coeffs).reshape(-1, 4)
+    out = np.zeros(8, dtype=np.uint64)
+    lib().orc_commit_hiding(_p(points), _p(c), c.shape[0], _p(_u(H)), _p(_u(s)), _p(out))
+    return out
 
 
 def commit_evals_tau(v, tau) -> np.ndarray:

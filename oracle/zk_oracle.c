@@ -26,6 +26,7 @@
  *   - KZG opening (Sec. 2.1): y = f(x) and the quotient (f - y) / (X - x) by
  *     synthetic division; batch opening at one point with the gamma-weighted
  *     combination sum_i gamma^i f_i.
+ *   - The hiding commitment [f(tau)]_1 + s H (Sec. 4.2).
  *   - The Mul / MatMul quotient (Sec. 4.4.1) t = (A B - L) / (X^n - 1) by
  *     schoolbook multiplication and long division.
  *   - One generalised-Mira fold (Sec. 4.2, prover steps 2-7, degree d = 2) for
@@ -458,6 +459,7 @@ void orc_commit_coeffs_tau(const uint64_t *coeffs, size_t n, const uint64_t *tau
 }
 
 void orc_dft(const uint64_t *in, size_t n, int inverse, uint64_t *out);
+void orc_msm(const uint64_t *pts, const uint64_t *scalars, size_t n, uint64_t *out);
 
 /* KZG opening (Sec. 2.1): for f = sum_i c_i X^i (n >= 1 coefficients) and a
  * point x, y = f(x) and the quotient q(X) = (f(X) - y) / (X - x), whose n - 1
@@ -562,6 +564,23 @@ int orc_mul_quotient(const uint64_t *a, const uint64_t *b, size_t n, uint64_t *t
     for (size_t i = 0; i + 1 < n; i++) store(t_out + 4 * i, &q[i]);
     free(A); free(B); free(L); free(l); free(D); free(q);
     return bad;
+}
+
+/* Hiding commitment (the blinding of the accumulation's zero-knowledge
+ * argument, Sec. 4.2): com = [f(tau)]_1 + s H for a random s and a group
+ * element H, computed as the MSM over the SRS plus s H by double-and-add. */
+void orc_commit_hiding(const uint64_t *srs, const uint64_t *coeffs, size_t n, const uint64_t *H64,
+                       const uint64_t *s64, uint64_t *out) {
+    uint64_t m[8];
+    orc_msm(srs, coeffs, n, m);
+    pt a, h, sh, r;
+    u256 s;
+    pt_load(&a, m);
+    pt_load(&h, H64);
+    load(&s, s64);
+    pt_mul(&sh, &h, &s);
+    pt_add(&r, &a, &sh);
+    pt_store(out, &r);
 }
 
 /* omega_n = 5^{(r-1)/n} for n a power of two dividing 2^28. */
