@@ -182,6 +182,21 @@ int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, si
 int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr *t, zk_g1 *com,
                     zk_stream stream);
 
+/* Hiding commitments (the blinding in the zero-knowledge argument of the
+ * accumulation scheme, Sec. 4.2: every KZG commitment gets an extra s H).
+ * zk_set_hiding_base: sets the context's hiding base H (64 bytes, canonical
+ * affine, device or host; must be on the curve and not infinity) and builds
+ * its fixed-base table (256 KB of device memory); synchronous.  The base is
+ * shared with the context's lanes; a failed call leaves no base set.
+ * zk_commit_hiding: out = [f(tau)]_1 + s H for n >= 1 canonical coefficients
+ * and one scalar s (the caller's random draw), all device or host pointers.
+ * The paper draws H and s at random; the caller supplies both.
+ * Errors: ZK_EINVAL (null pointer, n = 0, H off the curve, no base set),
+ * ZK_ESRS, ZK_ENOMEM, ZK_ECUDA. */
+int zk_set_hiding_base(zk_ctx *ctx, const zk_g1 *H);
+int zk_commit_hiding(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *s, zk_g1 *out,
+                     zk_stream stream);
+
 /* Route of evaluation-form commitments (ZK_EVALS, leaf accumulators, fold
  * cross terms).  ZK_ROUTE_INTT interpolates (INTT) and commits over the SRS,
  * as the paper's encoding describes (Sec. 3).  ZK_ROUTE_LAGRANGE commits the

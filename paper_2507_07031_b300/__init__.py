@@ -104,6 +104,8 @@ def _load():
         "zk_open": [_VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
         "zk_open_batch": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
         "zk_mul_quotient": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP],
+        "zk_set_hiding_base": [_VP, _VP],
+        "zk_commit_hiding": [_VP, _VP, _SZ, _VP, _VP, _VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -129,7 +131,7 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
             "zk_server_destroy", "zk_set_commit_route", "zk_field_op", "zk_open", "zk_open_batch",
-            "zk_mul_quotient"]
+            "zk_mul_quotient", "zk_set_hiding_base", "zk_commit_hiding"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 ZK_FIELD_Q, ZK_FIELD_R = 0, 1
@@ -187,6 +189,19 @@ def zk_mul_quotient(ctx: int, a, b, com, t=None, n: int = None, stream=None) -> 
         n = _nelem(a, 4)
     _check(lib.zk_mul_quotient(ctx, _ptr(a), _ptr(b), int(n), _ptr(t), _ptr(com), _stream(stream)),
            "zk_mul_quotient")
+
+
+def zk_set_hiding_base(ctx: int, H) -> None:
+    """Hiding base H (64-byte canonical affine point) for zk_commit_hiding."""
+    _check(lib.zk_set_hiding_base(ctx, _ptr(H)), "zk_set_hiding_base")
+
+
+def zk_commit_hiding(ctx: int, coeffs, s, out, n: int = None, stream=None) -> None:
+    """out = [f(tau)]_1 + s H."""
+    if n is None:
+        n = _nelem(coeffs, 4)
+    _check(lib.zk_commit_hiding(ctx, _ptr(coeffs), int(n), _ptr(s), _ptr(out), _stream(stream)),
+           "zk_commit_hiding")
 
 
 def zk_set_commit_route(ctx: int, route: int) -> None:

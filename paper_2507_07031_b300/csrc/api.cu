@@ -24,6 +24,7 @@ Shared::~Shared() {
         if (b.p) cudaFree(b.p);
     for (auto &b : lag)
         if (b.p) cudaFree(b.p);
+    if (hide_tab.p) cudaFree(hide_tab.p);
 }
 
 int dev_alloc(Shared &sh, DevBuf &b, size_t bytes) {
@@ -525,6 +526,32 @@ int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr
     ZK_TRY(ot.finish(s));
     ZK_TRY(oc.finish(s));
     if (ot.host() || oc.host()) ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    return ZK_OK;
+}
+
+int zk_set_hiding_base(zk_ctx *ctx, const zk_g1 *H) {
+    if (!ctx || !H) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    const void *dh;
+    ZK_TRY(stage_in(ctx, H, 64, "hide.in", &dh, 0));
+    return hiding_base_impl(ctx, (const uint32_t *)dh, 0);
+}
+
+int zk_commit_hiding(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *s, zk_g1 *out,
+                     zk_stream stream) {
+    if (!ctx || !coeffs || !s || !out || n == 0) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->sh->srs_n == 0) return ZK_ESRS;
+    if (n > ctx->sh->srs_n) return ZK_ESRS;
+    const void *dc, *ds;
+    ZK_TRY(stage_in(ctx, coeffs, n * 32, "hide.coeffs", &dc, st));
+    ZK_TRY(stage_in(ctx, s, 32, "hide.s", &ds, st));
+    OutBuf oo;
+    ZK_TRY(oo.init(ctx, out, 64, "hide.out"));
+    ZK_TRY(commit_hiding_impl(ctx, (const uint32_t *)dc, n, (const uint32_t *)ds, (uint32_t *)oo.dev, st));
+    ZK_TRY(oo.finish(st));
+    if (oo.host()) ZK_CUDA_TRY(cudaStreamSynchronize(st));
     return ZK_OK;
 }
 

@@ -53,6 +53,7 @@ struct Shared {
     DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg
     DevBuf lag[29];              // lag[lg][k] = [L_k(tau)]_1 over H of size 2^lg (affine Montgomery)
     int commit_route = 0;        // ZK_ROUTE_INTT or ZK_ROUTE_LAGRANGE for evaluation-form commitments
+    DevBuf hide_tab;             // hiding base H: d 2^(8w) H, w < 32, d = 1 .. 128 (affine Montgomery)
     int tuned_window[29] = {};   // MSM window width per log2 length (0 = built-in)
     int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = built-in)
     ~Shared();
@@ -211,6 +212,11 @@ int open_impl(zk_ctx *ctx, const uint32_t *const *polys, const size_t *lens, siz
 // coefficients, may be null) and its commitment com.
 int mul_quotient_impl(zk_ctx *ctx, const uint32_t *a, const uint32_t *b, size_t n, uint32_t *t, uint32_t *com,
                       cudaStream_t s);
+
+// Hiding commitments (hiding.cu), device pointers only.
+int hiding_base_impl(zk_ctx *ctx, const uint32_t *H, cudaStream_t s);
+int commit_hiding_impl(zk_ctx *ctx, const uint32_t *coeffs, size_t n, const uint32_t *sc, uint32_t *out,
+                       cudaStream_t s);
 int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count);
 
 // Fold (fold.cu)
