@@ -49,6 +49,8 @@ def lib():
         L = ctypes.CDLL(_LIB)
         sig = {
             "orc_set_threads": (None, [ctypes.c_int]),
+            "orc_set_degree": (None, [ctypes.c_int]),
+            "orc_get_degree": (ctypes.c_int, []),
             "orc_get_threads": (ctypes.c_int, []),
             "orc_has_openmp": (ctypes.c_int, []),
             "orc_fadd": (None, [ctypes.c_int, _P, _P, _P]),
@@ -355,9 +357,12 @@ def _commit_args(mode, srs, tau):
 
 
 def leaf_init(m1, m2, m4, mode=COMMIT_TAU, srs=None, tau=None) -> Acc:
+    """Degree 2: inputs m1, m2, m4 (m3 = m1 o m2); degree 3: inputs m1, m2, m3
+    in the three positional slots (m4 = m1 o m2 o m3)."""
     n = np.asarray(m1).reshape(-1, 4).shape[0]
     m = np.zeros((4, n, 4), dtype=np.uint64)
-    m[0], m[1], m[3] = (np.asarray(x, dtype=np.uint64).reshape(n, 4) for x in (m1, m2, m4))
+    third = 2 if get_degree() == 3 else 3
+    m[0], m[1], m[third] = (np.asarray(x, dtype=np.uint64).reshape(n, 4) for x in (m1, m2, m4))
     e = np.zeros((n, 4), dtype=np.uint64)
     inst = np.zeros(INST_LIMBS, dtype=np.uint64)
     md, s, t = _commit_args(mode, srs, tau)
@@ -365,13 +370,23 @@ def leaf_init(m1, m2, m4, mode=COMMIT_TAU, srs=None, tau=None) -> Acc:
     return Acc(m, e, inst)
 
 
+def set_degree(d: int) -> None:
+    """Degree of the folded relation: 2 (m1 o m2 - mu m3 = e) or 3
+    (m1 o m2 o m3 - mu^2 m4 = e)."""
+    lib().orc_set_degree(int(d))
+
+
+def get_degree() -> int:
+    return int(lib().orc_get_degree())
+
+
 def fold(L: Acc, R: Acc, gamma, mode=COMMIT_TAU, srs=None, tau=None):
-    """Returns (acc'', E1)."""
+    """Returns (acc'', E) with E = E_1 (degree 2) or (E_1, E_2) (degree 3)."""
     n = L.n
     Om = np.zeros_like(L.m)
     Oe = np.zeros_like(L.e)
     Oi = np.zeros(INST_LIMBS, dtype=np.uint64)
-    E1 = np.zeros(8, dtype=np.uint64)
+    E1 = np.zeros(8 * (get_degree() - 1), dtype=np.uint64)
     md, s, t = _commit_args(mode, srs, tau)
     lib().orc_fold(n, _p(L.m), _p(L.e), _p(L.inst), _p(R.m), _p(R.e), _p(R.inst), _p(_u(gamma)),
                    md, s, t, _p(Om), _p(Oe), _p(Oi), _p(E1))

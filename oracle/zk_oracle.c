@@ -341,6 +341,13 @@ static void pt_mul(pt *r, const pt *p, const u256 *k) {
 static int g_threads = 1;
 
 void orc_set_threads(int t) { g_threads = t > 0 ? t : 1; }
+
+/* Degree d of the folded relation: 2 (m1 o m2 - mu m3 = e) or 3
+ * (m1 o m2 o m3 - mu^2 m4 = e, the homogeneous degree-3 analogue, whose fold
+ * has the two cross terms E_1, E_2 of Sec. 4.2's general-d expansion). */
+static int g_degree = 2;
+void orc_set_degree(int d) { g_degree = d == 3 ? 3 : 2; }
+int orc_get_degree(void) { return g_degree; }
 int orc_get_threads(void) { return g_threads; }
 int orc_has_openmp(void) {
 #ifdef _OPENMP
@@ -765,24 +772,55 @@ static void fold_one(const committer *cm, size_t n,
     load(&g, gamma64);
     fmul(&g2, &g, &g, &MODR);
 
-    /* step 2: cross term */
+    /* step 2: cross terms.  Degree 2: the X^1 coefficient of
+     * (X a1 + b1)(X a2 + b2) - (X mu + mu')(X a3 + b3).  Degree 3: the X^1
+     * and X^2 coefficients of
+     * (X a1 + b1)(X a2 + b2)(X a3 + b3) - (X mu + mu')^2 (X a4 + b4). */
     uint64_t *e1 = (uint64_t *)malloc(32 * n);
+    uint64_t *e2 = g_degree == 3 ? (uint64_t *)malloc(32 * n) : NULL;
+    u256 muLL, muLR2, muRR;
+    fmul(&muLL, &muL, &muL, &MODR);
+    fmul(&muLR2, &muL, &muR, &MODR);
+    fadd(&muLR2, &muLR2, &muLR2, &MODR);
+    fmul(&muRR, &muR, &muR, &MODR);
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (size_t k = 0; k < n; k++) {
-        u256 a1, a2, a3, b1, b2, b3, t, acc;
+        u256 a1, a2, a3, a4, b1, b2, b3, b4, t, acc;
         load(&a1, Lm + 4 * (0 * n + k)); load(&a2, Lm + 4 * (1 * n + k)); load(&a3, Lm + 4 * (2 * n + k));
         load(&b1, Rm + 4 * (0 * n + k)); load(&b2, Rm + 4 * (1 * n + k)); load(&b3, Rm + 4 * (2 * n + k));
-        fmul(&acc, &a1, &b2, &MODR);
-        fmul(&t, &b1, &a2, &MODR);  fadd(&acc, &acc, &t, &MODR);
-        fmul(&t, &muL, &b3, &MODR); fsub(&acc, &acc, &t, &MODR);
-        fmul(&t, &muR, &a3, &MODR); fsub(&acc, &acc, &t, &MODR);
-        store(e1 + 4 * k, &acc);
+        load(&a4, Lm + 4 * (3 * n + k)); load(&b4, Rm + 4 * (3 * n + k));
+        if (g_degree == 2) {
+            fmul(&acc, &a1, &b2, &MODR);
+            fmul(&t, &b1, &a2, &MODR);  fadd(&acc, &acc, &t, &MODR);
+            fmul(&t, &muL, &b3, &MODR); fsub(&acc, &acc, &t, &MODR);
+            fmul(&t, &muR, &a3, &MODR); fsub(&acc, &acc, &t, &MODR);
+            store(e1 + 4 * k, &acc);
+        } else {
+            u256 u;
+            /* X^2: a1 a2 b3 + a1 b2 a3 + b1 a2 a3 - mu^2 b4 - 2 mu mu' a4 */
+            fmul(&t, &a1, &a2, &MODR); fmul(&acc, &t, &b3, &MODR);
+            fmul(&t, &a1, &b2, &MODR); fmul(&u, &t, &a3, &MODR); fadd(&acc, &acc, &u, &MODR);
+            fmul(&t, &b1, &a2, &MODR); fmul(&u, &t, &a3, &MODR); fadd(&acc, &acc, &u, &MODR);
+            fmul(&u, &muLL, &b4, &MODR); fsub(&acc, &acc, &u, &MODR);
+            fmul(&u, &muLR2, &a4, &MODR); fsub(&acc, &acc, &u, &MODR);
+            store(e2 + 4 * k, &acc);
+            /* X^1: a1 b2 b3 + b1 a2 b3 + b1 b2 a3 - 2 mu mu' b4 - mu'^2 a4 */
+            fmul(&t, &a1, &b2, &MODR); fmul(&acc, &t, &b3, &MODR);
+            fmul(&t, &b1, &a2, &MODR); fmul(&u, &t, &b3, &MODR); fadd(&acc, &acc, &u, &MODR);
+            fmul(&t, &b1, &b2, &MODR); fmul(&u, &t, &a3, &MODR); fadd(&acc, &acc, &u, &MODR);
+            fmul(&u, &muLR2, &b4, &MODR); fsub(&acc, &acc, &u, &MODR);
+            fmul(&u, &muRR, &a4, &MODR); fsub(&acc, &acc, &u, &MODR);
+            store(e1 + 4 * k, &acc);
+        }
     }
-    /* step 3: E1 = Commit(e1) */
-    pt E1;
+    /* step 3: E_j = Commit(e_j) */
+    pt E1, E2;
     commit_evals(cm, e1, n, &E1);
+    if (e2) commit_evals(cm, e2, n, &E2);
+    u256 g3;
+    fmul(&g3, &g2, &g, &MODR);
 
-    /* step 5: witness RLC */
+    /* step 5: witness RLC; e'' = e' + sum_j gamma^j e_j + gamma^d e */
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (size_t k = 0; k < n; k++) {
         u256 a, b, t, c;
@@ -798,11 +836,19 @@ static void fold_one(const committer *cm, size_t n,
         load(&c, e1 + 4 * k);   /* e1 */
         fmul(&t, &g, &c, &MODR);
         fadd(&t, &t, &b, &MODR);
-        fmul(&c, &g2, &a, &MODR);
+        if (e2) {
+            load(&c, e2 + 4 * k);
+            fmul(&c, &g2, &c, &MODR);
+            fadd(&t, &t, &c, &MODR);
+            fmul(&c, &g3, &a, &MODR);
+        } else {
+            fmul(&c, &g2, &a, &MODR);
+        }
         fadd(&t, &t, &c, &MODR);
         store(Oe + 4 * k, &t);
     }
     free(e1);
+    free(e2);
 
     /* step 5: instance RLC */
     pt CO[4], EO, t1, t2;
@@ -812,13 +858,22 @@ static void fold_one(const committer *cm, size_t n,
         pt_add(&CO[i], &t1, &CR[i]);
     }
     pt_mul(&t1, &E1, &g);
-    pt_mul(&t2, &EL, &g2);
     pt_add(&EO, &ER, &t1);
+    if (g_degree == 3) {
+        pt_mul(&t2, &E2, &g2);
+        pt_add(&EO, &EO, &t2);
+        pt_mul(&t2, &EL, &g3);
+    } else {
+        pt_mul(&t2, &EL, &g2);
+    }
     pt_add(&EO, &EO, &t2);
     fmul(&muO, &g, &muL, &MODR);
     fadd(&muO, &muO, &muR, &MODR);
     inst_put(Oinst, CO, &EO, &muO);
-    if (E1_out) pt_store(E1_out, &E1);
+    if (E1_out) {
+        pt_store(E1_out, &E1);
+        if (g_degree == 3) pt_store(E1_out + 8, &E2);
+    }
 }
 
 static void committer_init(committer *cm, int mode, const uint64_t *srs, const uint64_t *tau64, size_t n) {
@@ -847,8 +902,10 @@ void orc_fold(size_t n,
 }
 
 /* Leaf accumulator from a NARK witness (Sec. 4.2: a NARK proof is the special
- * accumulator with mu = 1 and e = 0): m3 = m1 o m2, e = 0, E = infinity,
- * mu = 1, C_i = Commit(m_i).  m holds m1, m2, m4 on input (m3 is written). */
+ * accumulator with mu = 1 and e = 0): e = 0, E = infinity,
+ * mu = 1, C_i = Commit(m_i).  Degree 2: m holds m1, m2, m4 on input and
+ * m3 = m1 o m2 is written; degree 3: m holds m1, m2, m3 and m4 = m1 o m2 o m3
+ * is written. */
 void orc_leaf_init(size_t n, uint64_t *m, uint64_t *e, uint64_t *inst,
                    int commit_mode, const uint64_t *srs, const uint64_t *tau) {
     for (size_t k = 0; k < n; k++) {
@@ -856,7 +913,13 @@ void orc_leaf_init(size_t n, uint64_t *m, uint64_t *e, uint64_t *inst,
         load(&a, m + 4 * (0 * n + k));
         load(&b, m + 4 * (1 * n + k));
         fmul(&c, &a, &b, &MODR);
-        store(m + 4 * (2 * n + k), &c);
+        if (g_degree == 3) { /* m4 = m1 o m2 o m3 */
+            load(&a, m + 4 * (2 * n + k));
+            fmul(&c, &c, &a, &MODR);
+            store(m + 4 * (3 * n + k), &c);
+        } else {
+            store(m + 4 * (2 * n + k), &c);
+        }
     }
     memset(e, 0, 32 * n);
     committer cm;
@@ -902,8 +965,9 @@ void orc_fold_tree(size_t count, size_t n, uint64_t *m, uint64_t *e, uint64_t *i
     committer_free(&cm);
 }
 
-/* Decider D (Sec. 4.2): the relaxed test m1 o m2 - mu m3 = e holds at every
- * point of H.  Returns the number of failing positions. */
+/* Decider D (Sec. 4.2): the relaxed test m1 o m2 - mu m3 = e (degree 2) or
+ * m1 o m2 o m3 - mu^2 m4 = e (degree 3) holds at every point of H.  Returns
+ * the number of failing positions. */
 size_t orc_decide_relation(size_t n, const uint64_t *m, const uint64_t *e, const uint64_t *mu64) {
     size_t bad = 0;
     u256 mu; load(&mu, mu64);
@@ -915,7 +979,15 @@ size_t orc_decide_relation(size_t n, const uint64_t *m, const uint64_t *e, const
         load(&c, m + 4 * (2 * n + k));
         load(&x, e + 4 * k);
         fmul(&lhs, &a, &b, &MODR);
-        fmul(&t, &mu, &c, &MODR);
+        if (g_degree == 3) { /* m1 m2 m3 - mu^2 m4 */
+            u256 d4;
+            load(&d4, m + 4 * (3 * n + k));
+            fmul(&lhs, &lhs, &c, &MODR);
+            fmul(&t, &mu, &mu, &MODR);
+            fmul(&t, &t, &d4, &MODR);
+        } else {
+            fmul(&t, &mu, &c, &MODR);
+        }
         fsub(&lhs, &lhs, &t, &MODR);
         if (cmp(&lhs, &x) != 0) bad++;
     }
@@ -942,8 +1014,18 @@ int orc_verify_fold(const uint64_t *Linst, const uint64_t *Rinst, const uint64_t
         ok &= want.inf == CO[i].inf && (want.inf || (cmp(&want.x, &CO[i].x) == 0 && cmp(&want.y, &CO[i].y) == 0));
     }
     pt_mul(&t1, &E1, &g);
-    pt_mul(&t2, &EL, &g2);
     pt_add(&want, &ER, &t1);
+    if (g_degree == 3) { /* E'' = E' + gamma E1 + gamma^2 E2 + gamma^3 E */
+        pt E2;
+        u256 g3;
+        pt_load(&E2, E1_64 + 8);
+        pt_mul(&t2, &E2, &g2);
+        pt_add(&want, &want, &t2);
+        fmul(&g3, &g2, &g, &MODR);
+        pt_mul(&t2, &EL, &g3);
+    } else {
+        pt_mul(&t2, &EL, &g2);
+    }
     pt_add(&want, &want, &t2);
     ok &= want.inf == EO.inf && (want.inf || (cmp(&want.x, &EO.x) == 0 && cmp(&want.y, &EO.y) == 0));
     fmul(&m, &g, &muL, &MODR);
