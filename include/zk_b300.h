@@ -182,6 +182,20 @@ int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, si
 int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr *t, zk_g1 *com,
                     zk_stream stream);
 
+/* Degree of the relation that zk_leaf_init, zk_fold, zk_fold_tree and the
+ * fold plans use (Sec. 4.2 folds relations of any degree d with d - 1 cross
+ * terms):
+ *   2 (default): m1 o m2 - mu m3 = e; leaves get m3 = m1 o m2 (m4 is folded
+ *      linearly); one cross term E1.
+ *   3: m1 o m2 o m3 - mu^2 m4 = e; leaves get m4 = m1 o m2 o m3 (m1, m2, m3
+ *      given); two cross terms E1, E2, and
+ *      e'' = e' + gamma e1 + gamma^2 e2 + gamma^3 e,
+ *      E'' = E' + gamma E1 + gamma^2 E2 + gamma^3 E.
+ * With degree 3, zk_fold's E1_out (when not NULL) receives E1 then E2
+ * (128 bytes).  Shared by a context and its lanes; set it before building
+ * plans or servers.  Errors: ZK_EINVAL (degree other than 2 or 3). */
+int zk_set_fold_degree(zk_ctx *ctx, int degree);
+
 /* Hiding commitments (the blinding in the zero-knowledge argument of the
  * accumulation scheme, Sec. 4.2: every KZG commitment gets an extra s H).
  * zk_set_hiding_base: sets the context's hiding base H (64 bytes, canonical
@@ -242,7 +256,8 @@ int zk_leaf_init(zk_ctx *ctx, const zk_acc *accs, size_t count, zk_stream stream
  *   m_i'' = gamma m_i + m_i',  e'' = e' + gamma e1 + gamma^2 e   (step 5)
  *   C_i'' = gamma C_i + C_i',  E'' = E' + gamma E1 + gamma^2 E,  mu'' = gamma mu + mu'.
  * `gamma` may be a host or device pointer; `out` may alias R (not L).  If
- * E1_out is not NULL it receives E1 (the correction term pf, step 7). */
+ * E1_out is not NULL it receives E1 (the correction term pf, step 7; with
+ * zk_set_fold_degree 3, E1 then E2). */
 int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
             zk_g1 *E1_out, zk_stream stream);
 

@@ -105,6 +105,7 @@ def _load():
         "zk_open_batch": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _VP, _VP],
         "zk_mul_quotient": [_VP, _VP, _VP, _SZ, _VP, _VP, _VP],
         "zk_set_hiding_base": [_VP, _VP],
+        "zk_set_fold_degree": [_VP, ctypes.c_int],
         "zk_commit_hiding": [_VP, _VP, _SZ, _VP, _VP, _VP],
     }
     for name, args in sig.items():
@@ -131,7 +132,7 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
             "zk_server_destroy", "zk_set_commit_route", "zk_field_op", "zk_open", "zk_open_batch",
-            "zk_mul_quotient", "zk_set_hiding_base", "zk_commit_hiding"]
+            "zk_mul_quotient", "zk_set_hiding_base", "zk_commit_hiding", "zk_set_fold_degree"]
 
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 ZK_FIELD_Q, ZK_FIELD_R = 0, 1
@@ -189,6 +190,11 @@ def zk_mul_quotient(ctx: int, a, b, com, t=None, n: int = None, stream=None) -> 
         n = _nelem(a, 4)
     _check(lib.zk_mul_quotient(ctx, _ptr(a), _ptr(b), int(n), _ptr(t), _ptr(com), _stream(stream)),
            "zk_mul_quotient")
+
+
+def zk_set_fold_degree(ctx: int, degree: int) -> None:
+    """Folded relation: 2 (m1 o m2 - mu m3 = e) or 3 (m1 o m2 o m3 - mu^2 m4 = e)."""
+    _check(lib.zk_set_fold_degree(ctx, int(degree)), "zk_set_fold_degree")
 
 
 def zk_set_hiding_base(ctx: int, H) -> None:

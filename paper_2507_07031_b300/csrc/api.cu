@@ -529,6 +529,12 @@ int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr
     return ZK_OK;
 }
 
+int zk_set_fold_degree(zk_ctx *ctx, int degree) {
+    if (!ctx || (degree != 2 && degree != 3)) return ZK_EINVAL;
+    ctx->sh->fold_degree = degree;
+    return ZK_OK;
+}
+
 int zk_set_hiding_base(zk_ctx *ctx, const zk_g1 *H) {
     if (!ctx || !H) return ZK_EINVAL;
     DeviceGuard g(ctx);

@@ -54,6 +54,7 @@ struct Shared {
     DevBuf lag[29];              // lag[lg][k] = [L_k(tau)]_1 over H of size 2^lg (affine Montgomery)
     int commit_route = 0;        // ZK_ROUTE_INTT or ZK_ROUTE_LAGRANGE for evaluation-form commitments
     DevBuf hide_tab;             // hiding base H: d 2^(8w) H, w < 32, d = 1 .. 128 (affine Montgomery)
+    int fold_degree = 2;         // folded relation: 2 (m1 o m2 - mu m3 = e) or 3 (m1 o m2 o m3 - mu^2 m4 = e)
     int tuned_window[29] = {};   // MSM window width per log2 length (0 = built-in)
     int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = built-in)
     ~Shared();

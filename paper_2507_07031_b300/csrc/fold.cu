@@ -1,6 +1,7 @@
 // fold.cu -- generalised Mira accumulation (paper Sec. 4.2, prover steps 2-7)
-// for the degree-2 relation m1 o m2 - mu m3 = e over H, batched over all folds
-// of a tree level.
+// for the degree-2 relation m1 o m2 - mu m3 = e over H (or, selected per
+// context, the degree-3 relation m1 o m2 o m3 - mu^2 m4 = e), batched over all
+// folds of a tree level.
 //
 // For fold(L, R, gamma) (L plays acc, scaled by gamma; R plays acc'):
 //   K4  per element k (one pass over both accumulators, in place on R allowed):
@@ -9,6 +10,9 @@
 //   INTT of every e1, then one batched MSM: E1 = Commit(e1)  (step 3)
 //   K5  per fold: C_i'' = gamma C_i + C_i', E'' = E' + gamma E1 + gamma^2 E,
 //       mu'' = gamma mu + mu'                                (step 5)
+// Degree 3 has two cross terms (the gamma^1 and gamma^2 coefficients of
+// R(gamma L + R)), e1 and e2, committed as E1, E2, and
+//   e'' = e' + gamma e1 + gamma^2 e2 + gamma^3 e,  E'' = E' + gamma E1 + gamma^2 E2 + gamma^3 E.
 // Field vectors are canonical; gamma and mu are moved into Montgomery form
 // once per thread so that mont(x, gamma R) = gamma x stays canonical.
 #include <cuda_runtime.h>
@@ -36,6 +40,9 @@ struct FoldDesc {
     const uint32_t *gamma;  // canonical F_r, device
     uint32_t *e1;           // n elements (workspace)
     uint32_t *E1;           // one canonical affine point (workspace or caller)
+    uint32_t *e2;           // degree 3: second cross term (workspace)
+    uint32_t *E2;           // degree 3: its commitment
+    uint32_t deg;           // 2 or 3
 };
 
 constexpr int kInstMu = 40 * 2;  // word offset of mu in zk_acc_inst (5 points x 16 words)
@@ -48,6 +55,39 @@ __global__ void __launch_bounds__(256) k_fold_witness(const FoldDesc *__restrict
     const Fr g2 = fe_mul<FrP>(g, g);
     const Fr muL = fe_to_mont<FrP>(fe_load<FrP>(d.Lx + kInstMu));
     const Fr muR = fe_to_mont<FrP>(fe_load<FrP>(d.Rx + kInstMu));
+    if (d.deg == 3) {
+        // mu_L^2 R, 2 mu_L mu_R R, mu_R^2 R, gamma^3 R
+        const Fr mLL = fe_mul<FrP>(muL, muL), mRR = fe_mul<FrP>(muR, muR);
+        const Fr mLR = fe_dbl<FrP>(fe_mul<FrP>(muL, muR));
+        const Fr g3 = fe_mul<FrP>(g2, g);
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+            const size_t o = 8 * (size_t)k;
+            const Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
+            const Fr a3 = fe_load<FrP>(d.Lm[2] + o), a4 = fe_load<FrP>(d.Lm[3] + o);
+            const Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
+            const Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
+            const Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
+            const Fr A1 = fe_to_mont<FrP>(a1), B1 = fe_to_mont<FrP>(b1);
+            const Fr A3 = fe_to_mont<FrP>(a3), B3 = fe_to_mont<FrP>(b3);
+            const Fr paa = fe_mul<FrP>(A1, a2), pbb = fe_mul<FrP>(B1, b2);  // a1 a2, b1 b2
+            const Fr sx = fe_add<FrP>(fe_mul<FrP>(A1, b2), fe_mul<FrP>(B1, a2));  // a1 b2 + b1 a2
+            // gamma^2: a1 a2 b3 + (a1 b2 + b1 a2) a3 - mu_L^2 b4 - 2 mu_L mu_R a4
+            Fr e2 = fe_add<FrP>(fe_mul<FrP>(paa, B3), fe_mul<FrP>(sx, A3));
+            e2 = fe_sub<FrP>(e2, fe_add<FrP>(fe_mul<FrP>(b4, mLL), fe_mul<FrP>(a4, mLR)));
+            // gamma^1: (a1 b2 + b1 a2) b3 + b1 b2 a3 - 2 mu_L mu_R b4 - mu_R^2 a4
+            Fr e1 = fe_add<FrP>(fe_mul<FrP>(sx, B3), fe_mul<FrP>(pbb, A3));
+            e1 = fe_sub<FrP>(e1, fe_add<FrP>(fe_mul<FrP>(b4, mLR), fe_mul<FrP>(a4, mRR)));
+            fe_store<FrP>(d.e1 + o, e1);
+            fe_store<FrP>(d.e2 + o, e2);
+            fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
+            fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
+            fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
+            fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+            Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(e2, g2)));
+            fe_store<FrP>(d.Oe + o, fe_add<FrP>(eo, fe_mul<FrP>(eL, g3)));
+        }
+        return;
+    }
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const size_t o = 8 * (size_t)k;
         Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
@@ -103,31 +143,42 @@ __global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t fol
         xyzz_store_canonical(d.Ox + 16 * task, r);
         return;
     }
-    // E'' = E' + gamma E1 + gamma^2 E (joint double-and-add).
+    // E'' = E' + gamma E1 + gamma^2 E (degree 2) or
+    // E' + gamma E1 + gamma^2 E2 + gamma^3 E (degree 3), joint double-and-add.
     Fr gm = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
-    Fr g2 = fe_from_mont<FrP>(fe_mul<FrP>(gm, gm));
+    const Fr g2m = fe_mul<FrP>(gm, gm);
+    const Fr g2 = fe_from_mont<FrP>(g2m);
+    const Fr g3 = fe_from_mont<FrP>(fe_mul<FrP>(g2m, gm));
+    const bool three = d.deg == 3;
     Xyzz e1 = xyzz_load_canonical(d.E1);
+    Xyzz e2 = three ? xyzz_load_canonical(d.E2) : xyzz_inf();
     Xyzz eL = xyzz_load_canonical(d.Lx + 64);
     Xyzz eR = xyzz_load_canonical(d.Rx + 64);
     Xyzz acc = xyzz_inf();
     for (int i = 253; i >= 0; i--) {
         acc = xyzz_dbl(acc);
         if ((g[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, e1);
-        if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, eL);
+        if (three) {
+            if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, e2);
+            if ((g3.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, eL);
+        } else if ((g2.v[i >> 5] >> (i & 31)) & 1) {
+            acc = xyzz_add(acc, eL);
+        }
     }
     acc = xyzz_add(acc, eR);
     xyzz_store_canonical(d.Ox + 64, acc);
 }
 
-// Leaf: m3 = m1 o m2, e = 0, mu = 1, E = infinity (C_i are written by the MSM).
-__global__ void k_leaf(const uint32_t *m1, const uint32_t *m2, uint32_t *m3, uint32_t *e,
-                       uint32_t *x, uint32_t n) {
-    const Fr r2 = fe_r2<FrP>();
+// Leaf: out = m1 o m2 (degree 2: out = m3) or m1 o m2 o m3 (degree 3, m3 given:
+// out = m4), e = 0, mu = 1, E = infinity (C_i are written by the MSM).
+__global__ void k_leaf(const uint32_t *m1, const uint32_t *m2, const uint32_t *m3, uint32_t *out,
+                       uint32_t *e, uint32_t *x, uint32_t n) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const size_t o = 8 * (size_t)k;
         Fr a = fe_to_mont<FrP>(fe_load<FrP>(m1 + o));
-        (void)r2;
-        fe_store<FrP>(m3 + o, fe_mul<FrP>(a, fe_load<FrP>(m2 + o)));
+        Fr p = fe_mul<FrP>(a, fe_load<FrP>(m2 + o));  // canonical m1 m2
+        if (m3) p = fe_mul<FrP>(fe_to_mont<FrP>(p), fe_load<FrP>(m3 + o));
+        fe_store<FrP>(out + o, p);
         fe_store<FrP>(e + o, fe_zero<FrP>());
     }
     if (blockIdx.x == 0 && threadIdx.x < 16) {
@@ -167,7 +218,9 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     const size_t F = descs.size();
     if (F == 0) return ZK_OK;
     int err = ZK_OK;
-    uint32_t *e1 = (uint32_t *)scratch(ctx, "fold.e1", F * (size_t)n * 32, &err);
+    const bool three = descs[0].deg == 3;
+    const size_t nx = three ? 2 : 1;  // cross terms per fold
+    uint32_t *e1 = (uint32_t *)scratch(ctx, "fold.e1", nx * F * (size_t)n * 32, &err);
     if (!e1) return err;
     // E1 = Commit(e1): INTT then the SRS, or the Lagrange basis directly.
     const int lg = ilog2_size(n);
@@ -176,9 +229,10 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
         const Affine *lb;
         ZK_TRY(lagrange_get(ctx, lg, &lb, s));
     }
-    std::vector<uint32_t *> vecs(F);
-    std::vector<size_t> lens(F, n);
-    std::vector<MsmJob> jobs(F);
+    // E1 points of the batch at E1[16 f], E2 points (degree 3) at E1[16 (F + f)].
+    std::vector<uint32_t *> vecs(nx * F);
+    std::vector<size_t> lens(nx * F, n);
+    std::vector<MsmJob> jobs(nx * F);
     for (size_t f = 0; f < F; f++) {
         descs[f].e1 = e1 + f * (size_t)n * 8;
         if (!descs[f].E1) descs[f].E1 = E1 + 16 * f;
@@ -187,6 +241,15 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
         jobs[f].n = n;
         jobs[f].out = descs[f].E1;
         jobs[f].basis = lagrange ? lg : 0;
+        if (three) {
+            descs[f].e2 = e1 + (F + f) * (size_t)n * 8;
+            if (!descs[f].E2) descs[f].E2 = E1 + 16 * (F + f);
+            vecs[F + f] = descs[f].e2;
+            jobs[F + f].scalars = descs[f].e2;
+            jobs[F + f].n = n;
+            jobs[F + f].out = descs[f].E2;
+            jobs[F + f].basis = lagrange ? lg : 0;
+        }
     }
     ZK_TRY(upload(ctx, dd, descs.data(), F * sizeof(FoldDesc), s));
     dim3 g(elem_blocks(n), (unsigned)F);
@@ -197,8 +260,8 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
         k_fold_mu<<<(unsigned)((F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();
     }
-    if (!lagrange) ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), F, true, s));
-    ZK_TRY(msm_batch_impl(ctx, jobs.data(), F, 0, s));
+    if (!lagrange) ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), nx * F, true, s));
+    ZK_TRY(msm_batch_impl(ctx, jobs.data(), nx * F, 0, s));
     if (s_inst != s) {
         ZK_CUDA_TRY(cudaEventRecord(ev, s));
         ZK_CUDA_TRY(cudaStreamWaitEvent(s_inst, ev, 0));
@@ -211,7 +274,7 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     return ZK_OK;
 }
 
-FoldDesc make_desc(const zk_acc *L, const zk_acc *R, const zk_acc *O, const uint32_t *gamma) {
+FoldDesc make_desc(const zk_acc *L, const zk_acc *R, const zk_acc *O, const uint32_t *gamma, uint32_t deg) {
     FoldDesc d;
     for (int i = 0; i < 4; i++) {
         d.Lm[i] = (const uint32_t *)L->m[i];
@@ -227,6 +290,9 @@ FoldDesc make_desc(const zk_acc *L, const zk_acc *R, const zk_acc *O, const uint
     d.gamma = gamma;
     d.e1 = nullptr;
     d.E1 = nullptr;
+    d.e2 = nullptr;
+    d.E2 = nullptr;
+    d.deg = deg;
     return d;
 }
 
@@ -248,16 +314,18 @@ int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma,
         ZK_TRY(upload(ctx, gd, gamma, 32, s));
         g = gd;
     }
-    std::vector<FoldDesc> d(1, make_desc(L, R, out, g));
-    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.E1", 64, &err);
+    const uint32_t deg = (uint32_t)ctx->sh->fold_degree;
+    std::vector<FoldDesc> d(1, make_desc(L, R, out, g, deg));
+    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.E1", 128, &err);
     FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.descs", sizeof(FoldDesc), &err);
     if (!E1 || !dd) return err;
     ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd, E1, s, s, nullptr));
-    if (E1_out) {
+    if (E1_out) {  // E1, then E2 for degree 3 (contiguous in the workspace)
+        const size_t bytes = 64 * (deg - 1);
         if (is_device_ptr(E1_out)) {
-            ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, 64, cudaMemcpyDeviceToDevice, s));
+            ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, bytes, cudaMemcpyDeviceToDevice, s));
         } else {
-            ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, 64, cudaMemcpyDeviceToHost, s));
+            ZK_CUDA_TRY(cudaMemcpyAsync(E1_out, d[0].E1, bytes, cudaMemcpyDeviceToHost, s));
             ZK_CUDA_TRY(cudaStreamSynchronize(s));
         }
     }
@@ -285,7 +353,7 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
     // level's instance pass (side stream) can still read its own while the
     // next level's witness work (main stream) runs.
     FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.treedescs", (count - 1) * sizeof(FoldDesc), &err);
-    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.treeE1", (count - 1) * 64, &err);
+    uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.treeE1", (count - 1) * 128, &err);
     if (!dd || !E1) return err;
     if (!ctx->side) {
         ZK_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
@@ -304,9 +372,10 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
         for (size_t j = 0; j < width / 2; j++) {
             const zk_acc *Lp = &leaves[j * span + span / 2 - 1];
             zk_acc *Rp = &leaves[j * span + span - 1];
-            d.push_back(make_desc(Lp, Rp, Rp, g + 8 * (goff + j)));
+            d.push_back(make_desc(Lp, Rp, Rp, g + 8 * (goff + j), (uint32_t)ctx->sh->fold_degree));
         }
-        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd + goff, E1 + 16 * goff, s, ctx->side, ctx->side_ev[0]));
+        // the level's E1 points at 2 goff (E1 then E2 for degree 3): disjoint per level
+        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd + goff, E1 + 32 * goff, s, ctx->side, ctx->side_ev[0]));
         goff += width / 2;
         width /= 2;
     }
@@ -350,10 +419,11 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
         std::vector<MsmJob> jobs;
         for (size_t a = a0; a < a1; a++) {
             const zk_acc &A = accs[a];
-            k_leaf<<<elem_blocks((uint32_t)n), 256, 0, s>>>((const uint32_t *)A.m[0],
-                                                            (const uint32_t *)A.m[1],
-                                                            (uint32_t *)A.m[2], (uint32_t *)A.e,
-                                                            (uint32_t *)A.x, (uint32_t)n);
+            const bool three = ctx->sh->fold_degree == 3;
+            k_leaf<<<elem_blocks((uint32_t)n), 256, 0, s>>>(
+                (const uint32_t *)A.m[0], (const uint32_t *)A.m[1],
+                three ? (const uint32_t *)A.m[2] : nullptr, (uint32_t *)(three ? A.m[3] : A.m[2]),
+                (uint32_t *)A.e, (uint32_t *)A.x, (uint32_t)n);
             ZK_LAUNCHED();
             for (int i = 0; i < 4; i++) {
                 MsmJob j;
