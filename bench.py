@@ -537,8 +537,26 @@ def run_extras(zk, ctx, dev, torch):
     torch.cuda.synchronize()
     tl = _time(torch, tree, 1)
     same = same and leaf_same and all(torch.equal(a, b) for a, b in zip(root, root_batched))
+    # Degree 3 (m1 o m2 o m3 - mu^2 m4 = e, two cross terms), Lagrange route,
+    # over the same 1024 leaves: m1, m2 as before and m3 := the degree-2
+    # leaves' fourth int8 vector; leaf init computes m4 = m1 o m2 o m3.
+    zk.zk_set_fold_degree(ctx, 3)
+    for (m, e, x), (m0, e0, x0) in zip(accs, leaf_state):
+        m.copy_(m0)
+        m[2].copy_(m0[3])
+    zk.zk_leaf_init(ctx, descs)
+    state3 = [(a[0].clone(), a[1].clone(), a[2].clone()) for a in accs]
+    tree()  # warm-up
+    for a, s_ in zip(accs, state3):
+        for t, u in zip(a, s_):
+            t.copy_(u)
+    torch.cuda.synchronize()
+    t3 = _time(torch, tree, 1)
+    zk.zk_set_fold_degree(ctx, 2)
+    del state3
     zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
     res["fold_tree"] = {"leaves": count, "n": n, "folds": count - 1,
+                        "degree3_lagrange_folds_per_s": (count - 1) / (t3 * 1e-3), "degree3_lagrange_ms": t3,
                         "batched_folds_per_s": (count - 1) / (tt * 1e-3),
                         "plain_folds_per_s": (count - 1) / (tp * 1e-3),
                         "graph_folds_per_s": (count - 1) / (tg * 1e-3),
