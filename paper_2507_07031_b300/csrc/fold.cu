@@ -22,6 +22,7 @@
 
 #include "ctx.cuh"
 #include "curve.cuh"
+#include "team.cuh"
 
 namespace zk {
 
@@ -47,15 +48,20 @@ struct FoldDesc {
 
 constexpr int kInstMu = 40 * 2;  // word offset of mu in zk_acc_inst (5 points x 16 words)
 
-// K4: cross term and witness RLC, grid (elements, folds).
-__global__ void __launch_bounds__(256) k_fold_witness(const FoldDesc *__restrict__ descs, uint32_t n) {
+// K4: cross terms and witness RLC, grid (elements, folds); one instance per
+// relation degree, so that degree 2 does not carry degree 3's registers and
+// fits two blocks per SM (128 registers, no spills), which the ten input
+// streams need to keep their loads in flight.
+template <int DEG>
+__global__ void __launch_bounds__(256, DEG == 2 ? 2 : 1)
+    k_fold_witness(const FoldDesc *__restrict__ descs, uint32_t n) {
     const FoldDesc &d = descs[blockIdx.y];
     const Fr r2 = fe_r2<FrP>();
     const Fr g = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
     const Fr g2 = fe_mul<FrP>(g, g);
     const Fr muL = fe_to_mont<FrP>(fe_load<FrP>(d.Lx + kInstMu));
     const Fr muR = fe_to_mont<FrP>(fe_load<FrP>(d.Rx + kInstMu));
-    if (d.deg == 3) {
+    if (DEG == 3) {
         // mu_L^2 R, 2 mu_L mu_R R, mu_R^2 R, gamma^3 R
         const Fr mLL = fe_mul<FrP>(muL, muL), mRR = fe_mul<FrP>(muR, muR);
         const Fr mLR = fe_dbl<FrP>(fe_mul<FrP>(muL, muR));
@@ -110,11 +116,6 @@ __global__ void __launch_bounds__(256) k_fold_witness(const FoldDesc *__restrict
     }
 }
 
-__device__ __forceinline__ void load_bits(const uint32_t *p, uint32_t (&k)[8]) {
-#pragma unroll
-    for (int i = 0; i < 8; i++) k[i] = p[i];
-}
-
 // mu'' = gamma mu + mu' (one thread per fold).  Runs after the witness pass,
 // which reads both mu (the output may alias R).
 __global__ void k_fold_mu(const FoldDesc *__restrict__ descs, uint32_t folds) {
@@ -126,47 +127,58 @@ __global__ void k_fold_mu(const FoldDesc *__restrict__ descs, uint32_t folds) {
     fe_store<FrP>(d.Ox + kInstMu, mu);
 }
 
-// K5: instance RLC; 5 threads per fold (C_1..C_4, and E'').  Touches only the
-// points of the instances, so it may run on a side stream while the next
-// tree level's witness work (which reads only vectors and mu) proceeds.
-__global__ void k_fold_instance(const FoldDesc *__restrict__ descs, uint32_t folds) {
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 5 * folds) return;
-    const FoldDesc &d = descs[t / 5];
-    const uint32_t task = t % 5;
-    uint32_t g[8];
-    load_bits(d.gamma, g);
-    if (task < 4) {
-        Xyzz cl = xyzz_load_canonical(d.Lx + 16 * task);
-        Xyzz cr = xyzz_load_canonical(d.Rx + 16 * task);
-        Xyzz r = xyzz_add(xyzz_mul(cl, g), cr);
-        xyzz_store_canonical(d.Ox + 16 * task, r);
-        return;
+// K5: instance RLC, C_i'' = gamma C_i + C_i' and E'' = E' + gamma E1 +
+// gamma^2 E (degree 3: E' + gamma E1 + gamma^2 E2 + gamma^3 E).  It touches
+// only the points of the instances, so it may run on a side stream while the
+// next tree level's witness work (which reads only vectors and mu) proceeds.
+//
+// Every product of a scalar and a point is its own lane of a team (four warps
+// sharing each point operation): per fold, lanes C_1..C_4 (gamma), gamma E1,
+// then gamma^2 E (degree 2) or gamma^2 E2, gamma^3 E (degree 3).  A lane runs
+// double-and-add over its 254 scalar bits; the lanes of one fold then meet in
+// one thread per output point, which adds the primed point and normalises.
+template <int DEG>
+__global__ void __launch_bounds__(kTeamThreads) k_fold_instance(const FoldDesc *__restrict__ descs,
+                                                                uint32_t folds) {
+    constexpr int kOps = DEG == 3 ? 7 : 6;  // scalar-point products per fold
+    constexpr int kFolds = 32 / kOps;       // folds per team
+    constexpr int kAcc = 0, kBase = 4, kTmp = 8, kT = 12;
+    __shared__ uint32_t f[(kT + kTeamTemps) * 8 * 32];
+    const uint32_t l = team_lane(), w = team_warp();
+    const uint32_t fl = blockIdx.x * kFolds + l / kOps, op = l % kOps;
+    const bool valid = l < kFolds * kOps && fl < folds;
+    uint32_t k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Xyzz base = xyzz_inf();
+    if (valid) {
+        const FoldDesc &d = descs[fl];
+        const Fr gm = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
+        const int pw = op < 5 ? 1 : (int)op - 3;  // power of gamma
+        Fr sm = gm;
+        for (int j = 1; j < pw; j++) sm = fe_mul<FrP>(sm, gm);
+        const Fr sc = fe_from_mont<FrP>(sm);
+#pragma unroll
+        for (int i = 0; i < 8; i++) k[i] = sc.v[i];
+        const uint32_t *src = op < 4 ? d.Lx + 16 * op : op == 4 ? d.E1 : (DEG == 3 && op == 5) ? d.E2 : d.Lx + 64;
+        base = xyzz_load_canonical(src);
     }
-    // E'' = E' + gamma E1 + gamma^2 E (degree 2) or
-    // E' + gamma E1 + gamma^2 E2 + gamma^3 E (degree 3), joint double-and-add.
-    Fr gm = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
-    const Fr g2m = fe_mul<FrP>(gm, gm);
-    const Fr g2 = fe_from_mont<FrP>(g2m);
-    const Fr g3 = fe_from_mont<FrP>(fe_mul<FrP>(g2m, gm));
-    const bool three = d.deg == 3;
-    Xyzz e1 = xyzz_load_canonical(d.E1);
-    Xyzz e2 = three ? xyzz_load_canonical(d.E2) : xyzz_inf();
-    Xyzz eL = xyzz_load_canonical(d.Lx + 64);
-    Xyzz eR = xyzz_load_canonical(d.Rx + 64);
-    Xyzz acc = xyzz_inf();
+    tf_store(f, kBase + w, w == 0 ? base.X : w == 1 ? base.Y : w == 2 ? base.ZZ : base.ZZZ);
+    team_set_inf_nosync(f, kAcc);
+    __syncthreads();
     for (int i = 253; i >= 0; i--) {
-        acc = xyzz_dbl(acc);
-        if ((g[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, e1);
-        if (three) {
-            if ((g2.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, e2);
-            if ((g3.v[i >> 5] >> (i & 31)) & 1) acc = xyzz_add(acc, eL);
-        } else if ((g2.v[i >> 5] >> (i & 31)) & 1) {
-            acc = xyzz_add(acc, eL);
-        }
+        team_dbl(f, kAcc, kAcc, kT);
+        team_copy(f, kBase, kTmp, (k[i >> 5] >> (i & 31)) & 1);
+        team_add(f, kAcc, kTmp, kAcc, kT);
     }
-    acc = xyzz_add(acc, eR);
-    xyzz_store_canonical(d.Ox + 64, acc);
+    // One thread per output point: C_1..C_4 and E of each fold.
+    const uint32_t t = threadIdx.x;
+    const uint32_t fo = blockIdx.x * kFolds + t / 5, out = t % 5;
+    if (t >= 5 * kFolds || fo >= folds) return;
+    const FoldDesc &d = descs[fo];
+    const uint32_t lane0 = (t / 5) * kOps;
+    Xyzz r = xyzz_load_canonical(d.Rx + 16 * out);
+    const uint32_t first = out < 4 ? out : 4, last = out < 4 ? out : kOps - 1;
+    for (uint32_t j = first; j <= last; j++) r = xyzz_add(r, team_point_of(f, kAcc, lane0 + j));
+    xyzz_store_canonical(d.Ox + 16 * out, r);
 }
 
 // Leaf: out = m1 o m2 (degree 2: out = m3) or m1 o m2 o m3 (degree 3, m3 given:
@@ -255,7 +267,8 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     dim3 g(elem_blocks(n), (unsigned)F);
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_WITNESS, s);
-        k_fold_witness<<<g, 256, 0, s>>>(dd, n);
+        if (three) k_fold_witness<3><<<g, 256, 0, s>>>(dd, n);
+        else k_fold_witness<2><<<g, 256, 0, s>>>(dd, n);
         ZK_LAUNCHED();
         k_fold_mu<<<(unsigned)((F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();
@@ -268,7 +281,8 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     }
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s_inst);
-        k_fold_instance<<<(unsigned)((5 * F + 63) / 64), 64, 0, s_inst>>>(dd, (uint32_t)F);
+        if (three) k_fold_instance<3><<<(unsigned)((F + 3) / 4), kTeamThreads, 0, s_inst>>>(dd, (uint32_t)F);
+        else k_fold_instance<2><<<(unsigned)((F + 4) / 5), kTeamThreads, 0, s_inst>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();
     }
     return ZK_OK;
@@ -356,7 +370,11 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
     uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.treeE1", (count - 1) * 128, &err);
     if (!dd || !E1) return err;
     if (!ctx->side) {
-        ZK_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        // Highest priority: the instance pass's few blocks are dispatched
+        // ahead of the next level's queued MSM blocks instead of after them.
+        int least = 0, greatest = 0;
+        ZK_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ZK_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest));
         ZK_CUDA_TRY(cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming));
         ZK_CUDA_TRY(cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming));
     }

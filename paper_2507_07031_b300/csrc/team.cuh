@@ -215,6 +215,20 @@ ZK_DEV void team_put(const uint32_t *f, int p, Xyzz *dst) {
     fe_store<FqP>(reinterpret_cast<char *>(dst) + 32 * team_warp(), tf_load(f, p + team_warp()));
 }
 
+// The point in slots p of lane `lane` (any thread may call it after a
+// barrier).
+ZK_DEV Xyzz team_point_of(const uint32_t *f, int p, uint32_t lane) {
+    Xyzz r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        r.X.v[i] = f[((p + 0) * 8 + i) * 32 + lane];
+        r.Y.v[i] = f[((p + 1) * 8 + i) * 32 + lane];
+        r.ZZ.v[i] = f[((p + 2) * 8 + i) * 32 + lane];
+        r.ZZZ.v[i] = f[((p + 3) * 8 + i) * 32 + lane];
+    }
+    return r;
+}
+
 // The point in slots p for the calling thread's lane, gathered from the
 // four coordinates (any warp may call it after a barrier).
 ZK_DEV Xyzz team_point(const uint32_t *f, int p) {
