@@ -370,7 +370,10 @@ int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s);
  * (BN254 fields, Sec. 6.1).
  *   field : ZK_FIELD_Q (base field q) or ZK_FIELD_R (scalar field r).
  *   op    : ZK_FOP_MUL out = a b, ZK_FOP_SQR out = a^2, ZK_FOP_INV out = a^-1
- *           (0 for 0), ZK_FOP_ADD out = a + b, ZK_FOP_SUB out = a - b.
+ *           (0 for 0), ZK_FOP_ADD out = a + b, ZK_FOP_SUB out = a - b,
+ *           ZK_FOP_MULSUB out[i] = a[i] b[i] - a[n-1-i] b[n-1-i] (the
+ *           difference of two products that point additions and doublings
+ *           take for their Y coordinate; F_q reduces it once).
  *   a, b, out : DEVICE pointers to n canonical 32-byte little-endian elements
  *           (< modulus; not checked); b is ignored by SQR and INV; out may
  *           alias a or b.  Stream-ordered on `stream`.
@@ -383,6 +386,7 @@ int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s);
 #define ZK_FOP_INV 2
 #define ZK_FOP_ADD 3
 #define ZK_FOP_SUB 4
+#define ZK_FOP_MULSUB 5
 int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk_fr *out, size_t n, zk_stream stream);
 
 /* Phase timing: with timing on, each call brackets its phases with CUDA events

@@ -66,7 +66,7 @@ ZK_DEV Xyzz xyzz_dbl_affine(const Affine &a) {
     Fq M = fe_mul3<FqP>(fe_sqr<FqP>(a.x));
     Xyzz r;
     r.X = fe_sub<FqP>(fe_sqr<FqP>(M), fe_dbl<FqP>(S));
-    r.Y = fe_sub<FqP>(fe_mul<FqP>(M, fe_sub<FqP>(S, r.X)), fe_mul<FqP>(W, a.y));
+    r.Y = fe_mul_sub_mul<FqP>(M, fe_sub<FqP>(S, r.X), W, a.y);
     r.ZZ = V;
     r.ZZZ = W;
     return r;
@@ -82,7 +82,7 @@ ZK_DEV Xyzz xyzz_dbl(const Xyzz &p) {
     Fq M = fe_mul3<FqP>(fe_sqr<FqP>(p.X));
     Xyzz r;
     r.X = fe_sub<FqP>(fe_sqr<FqP>(M), fe_dbl<FqP>(S));
-    r.Y = fe_sub<FqP>(fe_mul<FqP>(M, fe_sub<FqP>(S, r.X)), fe_mul<FqP>(W, p.Y));
+    r.Y = fe_mul_sub_mul<FqP>(M, fe_sub<FqP>(S, r.X), W, p.Y);
     r.ZZ = fe_mul<FqP>(V, p.ZZ);
     r.ZZZ = fe_mul<FqP>(W, p.ZZZ);
     return r;
@@ -104,7 +104,7 @@ ZK_DEV Xyzz xyzz_add_affine(const Xyzz &p, const Affine &q) {
     Fq Q = fe_mul<FqP>(p.X, PP);
     Xyzz r;
     r.X = fe_sub<FqP>(fe_sub<FqP>(fe_sqr<FqP>(R), PPP), fe_dbl<FqP>(Q));
-    r.Y = fe_sub<FqP>(fe_mul<FqP>(R, fe_sub<FqP>(Q, r.X)), fe_mul<FqP>(p.Y, PPP));
+    r.Y = fe_mul_sub_mul<FqP>(R, fe_sub<FqP>(Q, r.X), p.Y, PPP);
     r.ZZ = fe_mul<FqP>(p.ZZ, PP);
     r.ZZZ = fe_mul<FqP>(p.ZZZ, PPP);
     return r;
@@ -129,7 +129,7 @@ ZK_DEV Xyzz xyzz_add(const Xyzz &p, const Xyzz &q) {
     Fq Q = fe_mul<FqP>(U1, PP);
     Xyzz r;
     r.X = fe_sub<FqP>(fe_sub<FqP>(fe_sqr<FqP>(R), PPP), fe_dbl<FqP>(Q));
-    r.Y = fe_sub<FqP>(fe_mul<FqP>(R, fe_sub<FqP>(Q, r.X)), fe_mul<FqP>(S1, PPP));
+    r.Y = fe_mul_sub_mul<FqP>(R, fe_sub<FqP>(Q, r.X), S1, PPP);
     r.ZZ = fe_mul<FqP>(fe_mul<FqP>(p.ZZ, q.ZZ), PP);
     r.ZZZ = fe_mul<FqP>(fe_mul<FqP>(p.ZZZ, q.ZZZ), PPP);
     return r;

@@ -115,7 +115,8 @@ extern "C" int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per
 // ---------------------------------------------------------------------------
 // zk_field_op: elementwise F_q / F_r arithmetic on canonical vectors, through
 // the same device code the prover uses (Montgomery conversions, product,
-// squaring, inversion, addition, subtraction), for tests of that code.
+// squaring, inversion, addition, subtraction, and the difference of two
+// products that point additions use), for tests of that code.
 // ---------------------------------------------------------------------------
 
 namespace zk {
@@ -129,10 +130,15 @@ __global__ void k_field_op(int op, const uint32_t *__restrict__ a, const uint32_
     if (i >= n) return;
     const Fe<P> x = fe_to_mont<P>(fe_load<P>(a + 8 * i));
     Fe<P> y = fe_zero<P>();
-    if (op == ZK_FOP_MUL || op == ZK_FOP_ADD || op == ZK_FOP_SUB) y = fe_to_mont<P>(fe_load<P>(b + 8 * i));
+    if (op != ZK_FOP_SQR && op != ZK_FOP_INV) y = fe_to_mont<P>(fe_load<P>(b + 8 * i));
     Fe<P> r;
     switch (op) {
         case ZK_FOP_MUL: r = fe_mul<P>(x, y); break;
+        case ZK_FOP_MULSUB: {
+            const size_t m = n - 1 - i;  // mirror element
+            r = fe_mul_sub_mul<P>(x, y, fe_to_mont<P>(fe_load<P>(a + 8 * m)), fe_to_mont<P>(fe_load<P>(b + 8 * m)));
+            break;
+        }
         case ZK_FOP_SQR: r = fe_sqr<P>(x); break;
         case ZK_FOP_INV: r = fe_inv<P>(x); break;
         case ZK_FOP_ADD: r = fe_add<P>(x, y); break;
@@ -149,9 +155,9 @@ extern "C" int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk
                            zk_stream stream) {
     using namespace zk;
     if (field != ZK_FIELD_Q && field != ZK_FIELD_R) return ZK_EINVAL;
-    if (op < ZK_FOP_MUL || op > ZK_FOP_SUB) return ZK_EINVAL;
+    if (op < ZK_FOP_MUL || op > ZK_FOP_MULSUB) return ZK_EINVAL;
     if (n == 0) return ZK_OK;
-    const bool binary = op == ZK_FOP_MUL || op == ZK_FOP_ADD || op == ZK_FOP_SUB;
+    const bool binary = op != ZK_FOP_SQR && op != ZK_FOP_INV;
     if (!a || !out || (binary && !b) || n > ((size_t)1 << 31)) return ZK_EINVAL;
     if (!is_device_ptr(a) || !is_device_ptr(out) || (binary && !is_device_ptr(b))) return ZK_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

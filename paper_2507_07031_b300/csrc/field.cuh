@@ -520,6 +520,111 @@ template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) {
     return r;
 }
 
+// (a b - c d) 2^-256 mod p with a single Montgomery reduction (lazy
+// reduction).  Both products are formed in full, 512 bits each, by the
+// product rows alone; their difference T lies in (-p^2, p^2).  A negative T
+// is lifted by p 2^256 (the borrow out of the 512-bit subtraction cancels the
+// carry out of that addition), which leaves T unchanged modulo p and puts it
+// in [0, p 2^256).  The squaring's reduction rows then give (T + M p) / 2^256
+// < 2p, and one conditional subtraction makes it canonical.  Against two
+// products and a subtraction this drops one reduction: 8 + 64 mad.lo and 64
+// mad.hi.
+template <class P>
+ZK_DEV Fe<P> fe_mul_sub_mul_inline(const Fe<P> &a, const Fe<P> &b, const Fe<P> &c, const Fe<P> &d) {
+    using namespace detail;
+    uint32_t t[17], u[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = u[i] = 0;
+    mac_row<0>(t, a.v, b.v[0]);
+    mac_row<1>(t, a.v, b.v[1]);
+    mac_row<2>(t, a.v, b.v[2]);
+    mac_row<3>(t, a.v, b.v[3]);
+    mac_row<4>(t, a.v, b.v[4]);
+    mac_row<5>(t, a.v, b.v[5]);
+    mac_row<6>(t, a.v, b.v[6]);
+    mac_row<7>(t, a.v, b.v[7]);
+    mac_row<0>(u, c.v, d.v[0]);
+    mac_row<1>(u, c.v, d.v[1]);
+    mac_row<2>(u, c.v, d.v[2]);
+    mac_row<3>(u, c.v, d.v[3]);
+    mac_row<4>(u, c.v, d.v[4]);
+    mac_row<5>(u, c.v, d.v[5]);
+    mac_row<6>(u, c.v, d.v[6]);
+    mac_row<7>(u, c.v, d.v[7]);
+    // t -= u over 16 words; `neg` = all ones when it borrowed out.
+    uint32_t bw, neg;
+    asm("sub.cc.u32  %0, %0, %9;\n\t"
+        "subc.cc.u32 %1, %1, %10;\n\t"
+        "subc.cc.u32 %2, %2, %11;\n\t"
+        "subc.cc.u32 %3, %3, %12;\n\t"
+        "subc.cc.u32 %4, %4, %13;\n\t"
+        "subc.cc.u32 %5, %5, %14;\n\t"
+        "subc.cc.u32 %6, %6, %15;\n\t"
+        "subc.cc.u32 %7, %7, %16;\n\t"
+        "subc.u32    %8, 0, 0;"
+        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+          "=r"(bw)
+        : "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7]));
+    asm("{\n\t.reg .u32 z;\n\t"
+        "sub.cc.u32  z, 0, %17;\n\t"  // borrow flag <- (bw != 0)
+        "subc.cc.u32 %0, %0, %9;\n\t"
+        "subc.cc.u32 %1, %1, %10;\n\t"
+        "subc.cc.u32 %2, %2, %11;\n\t"
+        "subc.cc.u32 %3, %3, %12;\n\t"
+        "subc.cc.u32 %4, %4, %13;\n\t"
+        "subc.cc.u32 %5, %5, %14;\n\t"
+        "subc.cc.u32 %6, %6, %15;\n\t"
+        "subc.cc.u32 %7, %7, %16;\n\t"
+        "subc.u32    %8, 0, 0;\n\t}"
+        : "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]),
+          "+r"(t[15]), "=r"(neg)
+        : "r"(u[8]), "r"(u[9]), "r"(u[10]), "r"(u[11]), "r"(u[12]), "r"(u[13]), "r"(u[14]), "r"(u[15]),
+          "r"(bw));
+    asm("add.cc.u32  %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32    %7, %7, %15;"
+        : "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15])
+        : "r"(P::p(0) & neg), "r"(P::p(1) & neg), "r"(P::p(2) & neg), "r"(P::p(3) & neg), "r"(P::p(4) & neg),
+          "r"(P::p(5) & neg), "r"(P::p(6) & neg), "r"(P::p(7) & neg));
+    const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
+    uint32_t cy = 0;
+    sqr_red_row<0>(t, cy, pm, t[0] * P::n0);
+    sqr_red_row<1>(t, cy, pm, t[1] * P::n0);
+    sqr_red_row<2>(t, cy, pm, t[2] * P::n0);
+    sqr_red_row<3>(t, cy, pm, t[3] * P::n0);
+    sqr_red_row<4>(t, cy, pm, t[4] * P::n0);
+    sqr_red_row<5>(t, cy, pm, t[5] * P::n0);
+    sqr_red_row<6>(t, cy, pm, t[6] * P::n0);
+    sqr_red_row<7>(t, cy, pm, t[7] * P::n0);
+    // T + M p < 2 p 2^256 < 2^512: no carry out of word 15, result < 2p.
+    Fe<P> sv, r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) sv.v[i] = t[8 + i];
+    uint32_t borrow;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;"
+        : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]),
+          "=r"(r.v[6]), "=r"(r.v[7]), "=r"(borrow)
+        : "r"(sv.v[0]), "r"(sv.v[1]), "r"(sv.v[2]), "r"(sv.v[3]), "r"(sv.v[4]), "r"(sv.v[5]),
+          "r"(sv.v[6]), "r"(sv.v[7]), "r"(P::p(0)), "r"(P::p(1)), "r"(P::p(2)), "r"(P::p(3)),
+          "r"(P::p(4)), "r"(P::p(5)), "r"(P::p(6)), "r"(P::p(7)));
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = (sv.v[i] & borrow) | (r.v[i] & ~borrow);
+    return r;
+}
+
 // One out-of-line copy of the product per field: the curve formulas call it
 // ten to fourteen times per point operation, and inlining every call makes
 // the kernels' hot code larger than the instruction cache.
@@ -555,6 +660,22 @@ __device__ __noinline__ Fe<P> fe_sqr_call(const Fe<P> a) {
 // separated form out of line; F_r keeps the product (the NTT never squares).
 template <class P> ZK_DEV Fe<P> fe_sqr(const Fe<P> &a) { return fe_mul<P>(a, a); }
 template <> ZK_DEV Fe<FqP> fe_sqr<FqP>(const Fe<FqP> &a) { return fe_sqr_call<FqP>(a); }
+
+template <class P>
+__device__ __noinline__ Fe<P> fe_mul_sub_mul_call(const Fe<P> a, const Fe<P> b, const Fe<P> c, const Fe<P> d) {
+    return fe_mul_sub_mul_inline<P>(a, b, c, d);
+}
+
+// a b - c d (Montgomery form in, Montgomery form out).  F_q takes the
+// out-of-line lazy form (the Y coordinate of every point addition and
+// doubling); other fields use two products.
+template <class P> ZK_DEV Fe<P> fe_mul_sub_mul(const Fe<P> &a, const Fe<P> &b, const Fe<P> &c, const Fe<P> &d) {
+    return fe_sub<P>(fe_mul<P>(a, b), fe_mul<P>(c, d));
+}
+template <>
+ZK_DEV Fe<FqP> fe_mul_sub_mul<FqP>(const Fe<FqP> &a, const Fe<FqP> &b, const Fe<FqP> &c, const Fe<FqP> &d) {
+    return fe_mul_sub_mul_call<FqP>(a, b, c, d);
+}
 
 // Montgomery form conversions: x -> x R and x R -> x.
 template <class P> ZK_DEV Fe<P> fe_to_mont(const Fe<P> &a) { return fe_mul<P>(a, fe_r2<P>()); }

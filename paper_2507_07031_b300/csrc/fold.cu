@@ -49,11 +49,11 @@ struct FoldDesc {
 constexpr int kInstMu = 40 * 2;  // word offset of mu in zk_acc_inst (5 points x 16 words)
 
 // K4: cross terms and witness RLC, grid (elements, folds); one instance per
-// relation degree, so that degree 2 does not carry degree 3's registers and
-// fits two blocks per SM (128 registers, no spills), which the ten input
-// streams need to keep their loads in flight.
+// relation degree.  Both fit two blocks per SM (128 registers; degree 3 with
+// a 32-byte spill), twice the warps that one block at ~190-240 registers
+// gave, which the pass needs to keep its product chains issuing.
 template <int DEG>
-__global__ void __launch_bounds__(256, DEG == 2 ? 2 : 1)
+__global__ void __launch_bounds__(256, 2)
     k_fold_witness(const FoldDesc *__restrict__ descs, uint32_t n) {
     const FoldDesc &d = descs[blockIdx.y];
     const Fr r2 = fe_r2<FrP>();
@@ -68,27 +68,38 @@ __global__ void __launch_bounds__(256, DEG == 2 ? 2 : 1)
         const Fr g3 = fe_mul<FrP>(g2, g);
         for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
             const size_t o = 8 * (size_t)k;
-            const Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
-            const Fr a3 = fe_load<FrP>(d.Lm[2] + o), a4 = fe_load<FrP>(d.Lm[3] + o);
-            const Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
-            const Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
-            const Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
-            const Fr A1 = fe_to_mont<FrP>(a1), B1 = fe_to_mont<FrP>(b1);
-            const Fr A3 = fe_to_mont<FrP>(a3), B3 = fe_to_mont<FrP>(b3);
-            const Fr paa = fe_mul<FrP>(A1, a2), pbb = fe_mul<FrP>(B1, b2);  // a1 a2, b1 b2
-            const Fr sx = fe_add<FrP>(fe_mul<FrP>(A1, b2), fe_mul<FrP>(B1, a2));  // a1 b2 + b1 a2
-            // gamma^2: a1 a2 b3 + (a1 b2 + b1 a2) a3 - mu_L^2 b4 - 2 mu_L mu_R a4
-            Fr e2 = fe_add<FrP>(fe_mul<FrP>(paa, B3), fe_mul<FrP>(sx, A3));
-            e2 = fe_sub<FrP>(e2, fe_add<FrP>(fe_mul<FrP>(b4, mLL), fe_mul<FrP>(a4, mLR)));
-            // gamma^1: (a1 b2 + b1 a2) b3 + b1 b2 a3 - 2 mu_L mu_R b4 - mu_R^2 a4
-            Fr e1 = fe_add<FrP>(fe_mul<FrP>(sx, B3), fe_mul<FrP>(pbb, A3));
-            e1 = fe_sub<FrP>(e1, fe_add<FrP>(fe_mul<FrP>(b4, mLR), fe_mul<FrP>(a4, mRR)));
+            // Consumed in three groups, each finished (its RLC outputs
+            // stored) before the next is loaded, to keep the live set small.
+            Fr sx, paa, pbb;  // a1 b2 + b1 a2, a1 a2, b1 b2
+            {
+                const Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
+                const Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
+                const Fr A1 = fe_to_mont<FrP>(a1), B1 = fe_to_mont<FrP>(b1);
+                paa = fe_mul<FrP>(A1, a2);
+                pbb = fe_mul<FrP>(B1, b2);
+                sx = fe_add<FrP>(fe_mul<FrP>(A1, b2), fe_mul<FrP>(B1, a2));
+                fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
+                fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
+            }
+            Fr e1, e2;
+            {
+                const Fr a3 = fe_load<FrP>(d.Lm[2] + o), b3 = fe_load<FrP>(d.Rm[2] + o);
+                const Fr A3 = fe_to_mont<FrP>(a3), B3 = fe_to_mont<FrP>(b3);
+                // gamma^2: a1 a2 b3 + (a1 b2 + b1 a2) a3;  gamma^1: (a1 b2 + b1 a2) b3 + b1 b2 a3
+                e2 = fe_add<FrP>(fe_mul<FrP>(paa, B3), fe_mul<FrP>(sx, A3));
+                e1 = fe_add<FrP>(fe_mul<FrP>(sx, B3), fe_mul<FrP>(pbb, A3));
+                fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
+            }
+            {
+                const Fr a4 = fe_load<FrP>(d.Lm[3] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
+                // - mu_L^2 b4 - 2 mu_L mu_R a4 (gamma^2), - 2 mu_L mu_R b4 - mu_R^2 a4 (gamma^1)
+                e2 = fe_sub<FrP>(e2, fe_add<FrP>(fe_mul<FrP>(b4, mLL), fe_mul<FrP>(a4, mLR)));
+                e1 = fe_sub<FrP>(e1, fe_add<FrP>(fe_mul<FrP>(b4, mLR), fe_mul<FrP>(a4, mRR)));
+                fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+            }
             fe_store<FrP>(d.e1 + o, e1);
             fe_store<FrP>(d.e2 + o, e2);
-            fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
-            fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
-            fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
-            fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+            const Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
             Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(e2, g2)));
             fe_store<FrP>(d.Oe + o, fe_add<FrP>(eo, fe_mul<FrP>(eL, g3)));
         }

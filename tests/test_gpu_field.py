@@ -62,6 +62,39 @@ def test_field_ops_match_oracle(zk, orc, field):
         assert bad.size == 0, (op, [(a[i], b[i]) for i in bad[:4]])
 
 
+@pytest.mark.parametrize("field", ["q", "r"])
+def test_field_mul_sub_mul_matches_oracle(zk, orc, field):
+    """a_i b_i - a_m b_m with m = n - 1 - i (ZK_FOP_MULSUB), the form every
+    point addition and doubling takes for Y; F_q reduces the 512-bit
+    difference once, lifting it by p 2^256 when negative.  Three layouts:
+    every pair of edge values against its mirror pair (both signs, products
+    near 0 and near p^2), swapped mirrors (a b - b a = 0 exactly) around
+    uniform pairs, and an odd length whose middle element meets itself."""
+    import torch
+    M = Z.Q_MOD if field == "q" else Z.R_MOD
+    f_orc = orc.FQ if field == "q" else orc.FR
+    f_dev = zk.ZK_FIELD_Q if field == "q" else zk.ZK_FIELD_R
+    edge = _edge(M)
+    rng = np.random.default_rng(43 if field == "q" else 47)
+    uni = [(int.from_bytes(rng.bytes(32), "little") % M, int.from_bytes(rng.bytes(32), "little") % M)
+           for _ in range(1001)]
+    grid = [(x, y) for x in edge for y in edge]
+    layouts = [grid, grid + uni + [(y, x) for (x, y) in reversed(grid)], uni]
+    for pairs in layouts:
+        a = [x for x, _ in pairs]
+        b = [y for _, y in pairs]
+        A, B = _limbs(a), _limbs(b)
+        out = torch.zeros((len(a), 4), dtype=torch.int64, device="cuda")
+        zk.zk_field_op(f_dev, zk.ZK_FOP_MULSUB, to_dev(A), to_dev(B), out)
+        torch.cuda.synchronize()
+        got = to_host(out)
+        n = len(a)
+        want = np.stack([orc.fsub(f_orc, orc.fmul(f_orc, A[i], B[i]), orc.fmul(f_orc, A[n - 1 - i], B[n - 1 - i]))
+                         for i in range(n)])
+        bad = np.nonzero(~np.all(got == want, axis=1))[0]
+        assert bad.size == 0, [(a[i], b[i], a[n - 1 - i], b[n - 1 - i]) for i in bad[:4]]
+
+
 def test_field_inverse_round_trip(zk, orc):
     """x * x^-1 = 1 for every nonzero input, in both fields (an invariant that
     holds without the oracle)."""
