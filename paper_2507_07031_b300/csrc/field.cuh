@@ -471,8 +471,35 @@ ZK_DEV void sqr_red_row(uint32_t (&t)[17], uint32_t &c, const uint32_t (&pm)[8],
 
 }  // namespace detail
 
-template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) {
-    using namespace detail;
+// Separated Montgomery arithmetic: a 512-bit product or square, then one
+// reduction.  These pieces also let the F_q routines share code (below).
+namespace detail {
+
+struct Wide {
+    uint32_t w[16];
+};
+
+// a b in full (product rows only; a, b < p < 2^254).
+template <class P> ZK_DEV Wide wide_mul(const Fe<P> &a, const Fe<P> &b) {
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = 0;
+    mac_row<0>(t, a.v, b.v[0]);
+    mac_row<1>(t, a.v, b.v[1]);
+    mac_row<2>(t, a.v, b.v[2]);
+    mac_row<3>(t, a.v, b.v[3]);
+    mac_row<4>(t, a.v, b.v[4]);
+    mac_row<5>(t, a.v, b.v[5]);
+    mac_row<6>(t, a.v, b.v[6]);
+    mac_row<7>(t, a.v, b.v[7]);
+    Wide r;
+#pragma unroll
+    for (int i = 0; i < 16; i++) r.w[i] = t[i];
+    return r;
+}
+
+// a^2 in full, separated form (cross products once, doubled, plus squares).
+template <class P> ZK_DEV Wide wide_sqr(const Fe<P> &a) {
     uint32_t t[17];
 #pragma unroll
     for (int i = 0; i < 17; i++) t[i] = 0;
@@ -486,6 +513,68 @@ template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) {
 #pragma unroll
     for (int k = 15; k >= 1; k--) t[k] = __funnelshift_l(t[k - 1], t[k], 1);
     sqr_diag(t, a.v);
+    Wide r;
+#pragma unroll
+    for (int i = 0; i < 16; i++) r.w[i] = t[i];
+    return r;
+}
+
+// x - y over 512 bits, plus p 2^256 when that borrowed out (x, y < p^2):
+// the same value modulo p, in [0, p 2^256).  The borrow out of the
+// subtraction cancels the carry out of the addition.
+template <class P> ZK_DEV Wide wide_sub_lift(const Wide &x, const Wide &y) {
+    Wide t = x;
+    uint32_t bw, neg;
+    asm("sub.cc.u32  %0, %0, %9;\n\t"
+        "subc.cc.u32 %1, %1, %10;\n\t"
+        "subc.cc.u32 %2, %2, %11;\n\t"
+        "subc.cc.u32 %3, %3, %12;\n\t"
+        "subc.cc.u32 %4, %4, %13;\n\t"
+        "subc.cc.u32 %5, %5, %14;\n\t"
+        "subc.cc.u32 %6, %6, %15;\n\t"
+        "subc.cc.u32 %7, %7, %16;\n\t"
+        "subc.u32    %8, 0, 0;"
+        : "+r"(t.w[0]), "+r"(t.w[1]), "+r"(t.w[2]), "+r"(t.w[3]), "+r"(t.w[4]), "+r"(t.w[5]), "+r"(t.w[6]),
+          "+r"(t.w[7]), "=r"(bw)
+        : "r"(y.w[0]), "r"(y.w[1]), "r"(y.w[2]), "r"(y.w[3]), "r"(y.w[4]), "r"(y.w[5]), "r"(y.w[6]), "r"(y.w[7]));
+    asm("{\n\t.reg .u32 z;\n\t"
+        "sub.cc.u32  z, 0, %17;\n\t"  // borrow flag <- (bw != 0)
+        "subc.cc.u32 %0, %0, %9;\n\t"
+        "subc.cc.u32 %1, %1, %10;\n\t"
+        "subc.cc.u32 %2, %2, %11;\n\t"
+        "subc.cc.u32 %3, %3, %12;\n\t"
+        "subc.cc.u32 %4, %4, %13;\n\t"
+        "subc.cc.u32 %5, %5, %14;\n\t"
+        "subc.cc.u32 %6, %6, %15;\n\t"
+        "subc.cc.u32 %7, %7, %16;\n\t"
+        "subc.u32    %8, 0, 0;\n\t}"
+        : "+r"(t.w[8]), "+r"(t.w[9]), "+r"(t.w[10]), "+r"(t.w[11]), "+r"(t.w[12]), "+r"(t.w[13]),
+          "+r"(t.w[14]), "+r"(t.w[15]), "=r"(neg)
+        : "r"(y.w[8]), "r"(y.w[9]), "r"(y.w[10]), "r"(y.w[11]), "r"(y.w[12]), "r"(y.w[13]), "r"(y.w[14]),
+          "r"(y.w[15]), "r"(bw));
+    asm("add.cc.u32  %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32    %7, %7, %15;"
+        : "+r"(t.w[8]), "+r"(t.w[9]), "+r"(t.w[10]), "+r"(t.w[11]), "+r"(t.w[12]), "+r"(t.w[13]),
+          "+r"(t.w[14]), "+r"(t.w[15])
+        : "r"(P::p(0) & neg), "r"(P::p(1) & neg), "r"(P::p(2) & neg), "r"(P::p(3) & neg), "r"(P::p(4) & neg),
+          "r"(P::p(5) & neg), "r"(P::p(6) & neg), "r"(P::p(7) & neg));
+    return t;
+}
+
+// Montgomery reduction of x < p 2^256: the 8 rows t += m p 2^(32 i), then
+// (x + M p) / 2^256 < 2p (p < 2^254, so no carry leaves word 15) and one
+// conditional subtraction.
+template <class P> ZK_DEV Fe<P> redc_wide(const Wide &x) {
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 16; i++) t[i] = x.w[i];
+    t[16] = 0;
     const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
     uint32_t c = 0;
     sqr_red_row<0>(t, c, pm, t[0] * P::n0);
@@ -496,7 +585,6 @@ template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) {
     sqr_red_row<5>(t, c, pm, t[5] * P::n0);
     sqr_red_row<6>(t, c, pm, t[6] * P::n0);
     sqr_red_row<7>(t, c, pm, t[7] * P::n0);
-    // (a^2 + M p) / 2^256 < 2p (a < p < 2^254): the final carry is 0.
     Fe<P> s, r;
 #pragma unroll
     for (int i = 0; i < 8; i++) s.v[i] = t[8 + i];
@@ -520,118 +608,34 @@ template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) {
     return r;
 }
 
+}  // namespace detail
+
+template <class P> ZK_DEV Fe<P> fe_sqr_inline(const Fe<P> &a) { return detail::redc_wide<P>(detail::wide_sqr<P>(a)); }
+
 // (a b - c d) 2^-256 mod p with a single Montgomery reduction (lazy
-// reduction).  Both products are formed in full, 512 bits each, by the
-// product rows alone; their difference T lies in (-p^2, p^2).  A negative T
-// is lifted by p 2^256 (the borrow out of the 512-bit subtraction cancels the
-// carry out of that addition), which leaves T unchanged modulo p and puts it
-// in [0, p 2^256).  The squaring's reduction rows then give (T + M p) / 2^256
-// < 2p, and one conditional subtraction makes it canonical.  Against two
-// products and a subtraction this drops one reduction: 8 + 64 mad.lo and 64
-// mad.hi.
+// reduction): both products in full, their difference lifted by p 2^256
+// when negative (|a b - c d| < p^2), one reduction.  Against two products
+// and a subtraction this drops 8 + 64 mad.lo and 64 mad.hi.
 template <class P>
 ZK_DEV Fe<P> fe_mul_sub_mul_inline(const Fe<P> &a, const Fe<P> &b, const Fe<P> &c, const Fe<P> &d) {
     using namespace detail;
-    uint32_t t[17], u[17];
-#pragma unroll
-    for (int i = 0; i < 17; i++) t[i] = u[i] = 0;
-    mac_row<0>(t, a.v, b.v[0]);
-    mac_row<1>(t, a.v, b.v[1]);
-    mac_row<2>(t, a.v, b.v[2]);
-    mac_row<3>(t, a.v, b.v[3]);
-    mac_row<4>(t, a.v, b.v[4]);
-    mac_row<5>(t, a.v, b.v[5]);
-    mac_row<6>(t, a.v, b.v[6]);
-    mac_row<7>(t, a.v, b.v[7]);
-    mac_row<0>(u, c.v, d.v[0]);
-    mac_row<1>(u, c.v, d.v[1]);
-    mac_row<2>(u, c.v, d.v[2]);
-    mac_row<3>(u, c.v, d.v[3]);
-    mac_row<4>(u, c.v, d.v[4]);
-    mac_row<5>(u, c.v, d.v[5]);
-    mac_row<6>(u, c.v, d.v[6]);
-    mac_row<7>(u, c.v, d.v[7]);
-    // t -= u over 16 words; `neg` = all ones when it borrowed out.
-    uint32_t bw, neg;
-    asm("sub.cc.u32  %0, %0, %9;\n\t"
-        "subc.cc.u32 %1, %1, %10;\n\t"
-        "subc.cc.u32 %2, %2, %11;\n\t"
-        "subc.cc.u32 %3, %3, %12;\n\t"
-        "subc.cc.u32 %4, %4, %13;\n\t"
-        "subc.cc.u32 %5, %5, %14;\n\t"
-        "subc.cc.u32 %6, %6, %15;\n\t"
-        "subc.cc.u32 %7, %7, %16;\n\t"
-        "subc.u32    %8, 0, 0;"
-        : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
-          "=r"(bw)
-        : "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7]));
-    asm("{\n\t.reg .u32 z;\n\t"
-        "sub.cc.u32  z, 0, %17;\n\t"  // borrow flag <- (bw != 0)
-        "subc.cc.u32 %0, %0, %9;\n\t"
-        "subc.cc.u32 %1, %1, %10;\n\t"
-        "subc.cc.u32 %2, %2, %11;\n\t"
-        "subc.cc.u32 %3, %3, %12;\n\t"
-        "subc.cc.u32 %4, %4, %13;\n\t"
-        "subc.cc.u32 %5, %5, %14;\n\t"
-        "subc.cc.u32 %6, %6, %15;\n\t"
-        "subc.cc.u32 %7, %7, %16;\n\t"
-        "subc.u32    %8, 0, 0;\n\t}"
-        : "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]),
-          "+r"(t[15]), "=r"(neg)
-        : "r"(u[8]), "r"(u[9]), "r"(u[10]), "r"(u[11]), "r"(u[12]), "r"(u[13]), "r"(u[14]), "r"(u[15]),
-          "r"(bw));
-    asm("add.cc.u32  %0, %0, %8;\n\t"
-        "addc.cc.u32 %1, %1, %9;\n\t"
-        "addc.cc.u32 %2, %2, %10;\n\t"
-        "addc.cc.u32 %3, %3, %11;\n\t"
-        "addc.cc.u32 %4, %4, %12;\n\t"
-        "addc.cc.u32 %5, %5, %13;\n\t"
-        "addc.cc.u32 %6, %6, %14;\n\t"
-        "addc.u32    %7, %7, %15;"
-        : "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15])
-        : "r"(P::p(0) & neg), "r"(P::p(1) & neg), "r"(P::p(2) & neg), "r"(P::p(3) & neg), "r"(P::p(4) & neg),
-          "r"(P::p(5) & neg), "r"(P::p(6) & neg), "r"(P::p(7) & neg));
-    const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
-    uint32_t cy = 0;
-    sqr_red_row<0>(t, cy, pm, t[0] * P::n0);
-    sqr_red_row<1>(t, cy, pm, t[1] * P::n0);
-    sqr_red_row<2>(t, cy, pm, t[2] * P::n0);
-    sqr_red_row<3>(t, cy, pm, t[3] * P::n0);
-    sqr_red_row<4>(t, cy, pm, t[4] * P::n0);
-    sqr_red_row<5>(t, cy, pm, t[5] * P::n0);
-    sqr_red_row<6>(t, cy, pm, t[6] * P::n0);
-    sqr_red_row<7>(t, cy, pm, t[7] * P::n0);
-    // T + M p < 2 p 2^256 < 2^512: no carry out of word 15, result < 2p.
-    Fe<P> sv, r;
-#pragma unroll
-    for (int i = 0; i < 8; i++) sv.v[i] = t[8 + i];
-    uint32_t borrow;
-    asm("sub.cc.u32 %0, %9, %17;\n\t"
-        "subc.cc.u32 %1, %10, %18;\n\t"
-        "subc.cc.u32 %2, %11, %19;\n\t"
-        "subc.cc.u32 %3, %12, %20;\n\t"
-        "subc.cc.u32 %4, %13, %21;\n\t"
-        "subc.cc.u32 %5, %14, %22;\n\t"
-        "subc.cc.u32 %6, %15, %23;\n\t"
-        "subc.cc.u32 %7, %16, %24;\n\t"
-        "subc.u32 %8, 0, 0;"
-        : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]),
-          "=r"(r.v[6]), "=r"(r.v[7]), "=r"(borrow)
-        : "r"(sv.v[0]), "r"(sv.v[1]), "r"(sv.v[2]), "r"(sv.v[3]), "r"(sv.v[4]), "r"(sv.v[5]),
-          "r"(sv.v[6]), "r"(sv.v[7]), "r"(P::p(0)), "r"(P::p(1)), "r"(P::p(2)), "r"(P::p(3)),
-          "r"(P::p(4)), "r"(P::p(5)), "r"(P::p(6)), "r"(P::p(7)));
-#pragma unroll
-    for (int i = 0; i < 8; i++) r.v[i] = (sv.v[i] & borrow) | (r.v[i] & ~borrow);
-    return r;
+    return redc_wide<P>(wide_sub_lift<P>(wide_mul<P>(a, b), wide_mul<P>(c, d)));
 }
 
-// One out-of-line copy of the product per field: the curve formulas call it
-// ten to fourteen times per point operation, and inlining every call makes
-// the kernels' hot code larger than the instruction cache.
+// Out-of-line F_q code.  The curve formulas make ten to fourteen products
+// per point operation; inlining them makes the kernels' hot code larger than
+// the instruction cache.  The three F_q routines (product, squaring, product
+// difference) are built from three shared out-of-line pieces: the 512-bit
+// product, the 512-bit square and the reduction.
 template <class P>
 __device__ __noinline__ Fe<P> fe_mul_call(const Fe<P> a, const Fe<P> b) {
     return fe_mul_inline<P>(a, b);
 }
+static __device__ __noinline__ detail::Wide fq_wide_mul_call(const Fe<FqP> a, const Fe<FqP> b) {
+    return detail::wide_mul<FqP>(a, b);
+}
+static __device__ __noinline__ detail::Wide fq_wide_sqr_call(const Fe<FqP> a) { return detail::wide_sqr<FqP>(a); }
+static __device__ __noinline__ Fe<FqP> fq_redc_call(const detail::Wide x) { return detail::redc_wide<FqP>(x); }
 
 template <class P> ZK_DEV Fe<P> fe_mul(const Fe<P> &a, const Fe<P> &b);
 
@@ -639,7 +643,7 @@ template <> ZK_DEV Fe<FqP> fe_mul<FqP>(const Fe<FqP> &a, const Fe<FqP> &b) {
 #ifdef ZK_INLINE_MUL_FQ
     return fe_mul_inline<FqP>(a, b);
 #else
-    return fe_mul_call<FqP>(a, b);
+    return fq_redc_call(fq_wide_mul_call(a, b));
 #endif
 }
 
@@ -651,30 +655,20 @@ template <> ZK_DEV Fe<FrP> fe_mul<FrP>(const Fe<FrP> &a, const Fe<FrP> &b) {
 #endif
 }
 
-template <class P>
-__device__ __noinline__ Fe<P> fe_sqr_call(const Fe<P> a) {
-    return fe_sqr_inline<P>(a);
-}
-
 // F_q squarings (two of the ten products of a mixed addition) take the
-// separated form out of line; F_r keeps the product (the NTT never squares).
+// separated form; F_r keeps the product (the NTT never squares).
 template <class P> ZK_DEV Fe<P> fe_sqr(const Fe<P> &a) { return fe_mul<P>(a, a); }
-template <> ZK_DEV Fe<FqP> fe_sqr<FqP>(const Fe<FqP> &a) { return fe_sqr_call<FqP>(a); }
+template <> ZK_DEV Fe<FqP> fe_sqr<FqP>(const Fe<FqP> &a) { return fq_redc_call(fq_wide_sqr_call(a)); }
 
-template <class P>
-__device__ __noinline__ Fe<P> fe_mul_sub_mul_call(const Fe<P> a, const Fe<P> b, const Fe<P> c, const Fe<P> d) {
-    return fe_mul_sub_mul_inline<P>(a, b, c, d);
-}
-
-// a b - c d (Montgomery form in, Montgomery form out).  F_q takes the
-// out-of-line lazy form (the Y coordinate of every point addition and
-// doubling); other fields use two products.
+// a b - c d (Montgomery form in, Montgomery form out).  F_q reduces once (the
+// Y coordinate of every point addition and doubling); other fields use two
+// products.
 template <class P> ZK_DEV Fe<P> fe_mul_sub_mul(const Fe<P> &a, const Fe<P> &b, const Fe<P> &c, const Fe<P> &d) {
     return fe_sub<P>(fe_mul<P>(a, b), fe_mul<P>(c, d));
 }
 template <>
 ZK_DEV Fe<FqP> fe_mul_sub_mul<FqP>(const Fe<FqP> &a, const Fe<FqP> &b, const Fe<FqP> &c, const Fe<FqP> &d) {
-    return fe_mul_sub_mul_call<FqP>(a, b, c, d);
+    return fq_redc_call(detail::wide_sub_lift<FqP>(fq_wide_mul_call(a, b), fq_wide_mul_call(c, d)));
 }
 
 // Montgomery form conversions: x -> x R and x R -> x.

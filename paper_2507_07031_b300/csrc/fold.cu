@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256, 2)
     const Fr g2 = fe_mul<FrP>(g, g);
     const Fr muL = fe_to_mont<FrP>(fe_load<FrP>(d.Lx + kInstMu));
     const Fr muR = fe_to_mont<FrP>(fe_load<FrP>(d.Rx + kInstMu));
-    if (DEG == 3) {
+    if constexpr (DEG == 3) {
         // mu_L^2 R, 2 mu_L mu_R R, mu_R^2 R, gamma^3 R
         const Fr mLL = fe_mul<FrP>(muL, muL), mRR = fe_mul<FrP>(muR, muR);
         const Fr mLR = fe_dbl<FrP>(fe_mul<FrP>(muL, muR));
@@ -103,27 +103,27 @@ __global__ void __launch_bounds__(256, 2)
             Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(e2, g2)));
             fe_store<FrP>(d.Oe + o, fe_add<FrP>(eo, fe_mul<FrP>(eL, g3)));
         }
-        return;
-    }
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t o = 8 * (size_t)k;
-        Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
-        Fr a3 = fe_load<FrP>(d.Lm[2] + o), a4 = fe_load<FrP>(d.Lm[3] + o);
-        Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
-        Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
-        Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
-        // (m1 m2' + m1' m2) R^-1, then * R^2 R^-1 -> canonical
-        Fr x = fe_add<FrP>(fe_mul<FrP>(a1, b2), fe_mul<FrP>(b1, a2));
-        x = fe_mul<FrP>(x, r2);
-        Fr y = fe_add<FrP>(fe_mul<FrP>(b3, muL), fe_mul<FrP>(a3, muR));
-        Fr e1 = fe_sub<FrP>(x, y);
-        fe_store<FrP>(d.e1 + o, e1);
-        fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
-        fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
-        fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
-        fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
-        Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(eL, g2)));
-        fe_store<FrP>(d.Oe + o, eo);
+    } else {
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+            const size_t o = 8 * (size_t)k;
+            Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
+            Fr a3 = fe_load<FrP>(d.Lm[2] + o), a4 = fe_load<FrP>(d.Lm[3] + o);
+            Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
+            Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
+            Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
+            // (m1 m2' + m1' m2) R^-1, then * R^2 R^-1 -> canonical
+            Fr x = fe_add<FrP>(fe_mul<FrP>(a1, b2), fe_mul<FrP>(b1, a2));
+            x = fe_mul<FrP>(x, r2);
+            Fr y = fe_add<FrP>(fe_mul<FrP>(b3, muL), fe_mul<FrP>(a3, muR));
+            Fr e1 = fe_sub<FrP>(x, y);
+            fe_store<FrP>(d.e1 + o, e1);
+            fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
+            fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
+            fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
+            fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+            Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(eL, g2)));
+            fe_store<FrP>(d.Oe + o, eo);
+        }
     }
 }
 
