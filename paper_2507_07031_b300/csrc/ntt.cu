@@ -77,7 +77,7 @@ __global__ void k_twiddles(const Fr *__restrict__ root, uint32_t lg, Fr *__restr
 struct PassArgs {
     const uint32_t *const *in_tab;  // per vector (blockIdx.y)
     uint32_t *const *out_tab;
-    uint32_t logn, logR, logNs, J;
+    uint32_t logn, logR, logNs, J, logJ;  // J = 2^logJ sub-transforms per CTA
     const Fr *tw_n;  // size-n table (+ n^{-1} at index n)
     const Fr *tw_R;  // size-R table
     int inverse;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
 
     // Load, apply the inter-pass twiddle omega_{Ns R}^{r (j mod Ns)}.
     for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
-        uint32_t r = e / J, jj = e % J;
+        uint32_t r = e >> a.logJ, jj = e & (J - 1);
         uint64_t j = j0 + jj;
         Fr x = fe_load<FrP>(in + 8 * (j + (uint64_t)r * stride));
         uint64_t m = j & (Ns - 1);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     for (uint32_t lh = a.logR; lh >= 1; lh--) {
         const uint32_t h = 1u << (lh - 1);
         for (uint32_t bf = threadIdx.x; bf < J * half; bf += blockDim.x) {
-            uint32_t jj = bf % J, k = bf / J;
+            uint32_t jj = bf & (J - 1), k = bf >> a.logJ;
             uint32_t pos = k & (h - 1);
             uint32_t i0 = ((((k >> (lh - 1)) << lh) + pos) * J) + jj;
             uint32_t i1 = i0 + h * J;
@@ -151,8 +151,8 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
         uint32_t r, jj;
         if (Ns >= J) {
-            r = e / J;
-            jj = e % J;
+            r = e >> a.logJ;
+            jj = e & (J - 1);
         } else {
             uint32_t q = e >> (a.logNs + a.logR);
             uint32_t rem = e & ((Ns << a.logR) - 1);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
 #pragma unroll
         for (int l = 0; l < 8; l++) x.v[l] = sm[l * JR + src * J + jj];
         if (a.scale) x = fe_mul<FrP>(x, sc);
-        uint64_t dst = (j / Ns) * ((uint64_t)Ns << a.logR) + (j & (Ns - 1)) + (uint64_t)r * Ns;
+        uint64_t dst = ((j >> a.logNs) << (a.logNs + a.logR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
         fe_store<FrP>(out + 8 * dst, x);
     }
 }
@@ -277,6 +277,8 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         const uint64_t subs = (uint64_t)n >> logR;
         a.J = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(kMaxJ, subs),
                                            kMaxSmem / ((size_t)32 << logR));
+        a.logJ = 0;
+        while ((1u << a.logJ) < a.J) a.logJ++;
         a.tw_n = (const Fr *)tw_n;
         a.tw_R = (const Fr *)tw_R;
         a.inverse = inverse ? 1 : 0;
