@@ -84,11 +84,15 @@ struct PassArgs {
     int scale;  // multiply outputs by n^{-1}
 };
 
+// One instance per staged size J R = 2^LJR (2 .. 4096): limb l of staged
+// element i is at sm[l JR + i], so with JR a compile-time constant every
+// limb's offset is an immediate of the shared-memory access.
+template <int LJR>
 __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     extern __shared__ uint32_t sm[];
     const uint32_t R = 1u << a.logR;
     const uint32_t J = a.J;
-    const uint32_t JR = J * R;
+    constexpr uint32_t JR = 1u << LJR;
     const uint64_t n = 1ull << a.logn;
     const uint32_t Ns = 1u << a.logNs;
     const uint64_t stride = n >> a.logR;  // n / R
@@ -167,6 +171,38 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
         if (a.scale) x = fe_mul<FrP>(x, sc);
         uint64_t dst = ((j >> a.logNs) << (a.logNs + a.logR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
         fe_store<FrP>(out + 8 * dst, x);
+    }
+}
+
+template <int LJR>
+int launch_pass_t(dim3 grid, uint32_t threads, size_t smem, cudaStream_t s, const PassArgs &a) {
+    static bool attr_set = false;  // per instance
+    if (!attr_set) {
+        ZK_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<LJR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMaxSmem));
+        attr_set = true;
+    }
+    k_ntt_pass<LJR><<<grid, threads, smem, s>>>(a);
+    ZK_LAUNCHED();
+    return ZK_OK;
+}
+
+// J R = 2^ljr with 1 <= ljr <= 12 (J <= 4, J R 32 bytes <= 128 KiB).
+int launch_pass(uint32_t ljr, dim3 grid, uint32_t threads, size_t smem, cudaStream_t s, const PassArgs &a) {
+    switch (ljr) {
+        case 1: return launch_pass_t<1>(grid, threads, smem, s, a);
+        case 2: return launch_pass_t<2>(grid, threads, smem, s, a);
+        case 3: return launch_pass_t<3>(grid, threads, smem, s, a);
+        case 4: return launch_pass_t<4>(grid, threads, smem, s, a);
+        case 5: return launch_pass_t<5>(grid, threads, smem, s, a);
+        case 6: return launch_pass_t<6>(grid, threads, smem, s, a);
+        case 7: return launch_pass_t<7>(grid, threads, smem, s, a);
+        case 8: return launch_pass_t<8>(grid, threads, smem, s, a);
+        case 9: return launch_pass_t<9>(grid, threads, smem, s, a);
+        case 10: return launch_pass_t<10>(grid, threads, smem, s, a);
+        case 11: return launch_pass_t<11>(grid, threads, smem, s, a);
+        case 12: return launch_pass_t<12>(grid, threads, smem, s, a);
+        default: return ZK_EINVAL;
     }
 }
 
@@ -286,15 +322,8 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         const uint32_t JR = a.J << logR;
         const uint32_t threads = std::min<uint32_t>(512, std::max<uint32_t>(32, JR / 2));
         const size_t smem = (size_t)JR * 32;
-        static bool attr_set = false;
-        if (!attr_set) {
-            ZK_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMaxSmem));
-            attr_set = true;
-        }
         dim3 grid((unsigned)(subs / a.J), (unsigned)count);
-        k_ntt_pass<<<grid, threads, smem, s>>>(a);
-        ZK_LAUNCHED();
+        ZK_TRY(launch_pass(a.logJ + (uint32_t)logR, grid, threads, smem, s, a));
         logNs += logR;
     }
     return ZK_OK;
