@@ -1,12 +1,15 @@
 // field.cuh -- 254-bit prime-field arithmetic for BN254 on sm_103a.
 //
 // Elements are eight 32-bit little-endian limbs.  Multiplication is
-// Montgomery's method (R = 2^256) in the coarsely integrated operand scanning
-// order, written as PTX carry chains (mad.lo.cc / madc.hi.cc) so that every
-// partial product is one IMAD on the integer pipe and carries never leave the
-// carry flag.  Both moduli are below 2^254, so the running sum fits in nine
-// limbs and needs no extra carry word; a final conditional subtraction returns
-// a canonical value in [0, p).
+// Montgomery's method (R = 2^256), written as PTX carry chains (mad.lo.cc /
+// madc.hi.cc) so that every partial product is one IMAD on the integer pipe
+// and carries never leave the carry flag.  F_r products (NTT, folds) use the
+// coarsely integrated operand scanning order, inline; both moduli are below
+// 2^254, so its running sum fits in nine limbs and needs no extra carry word.
+// F_q products (curve arithmetic) use the separated form -- a 512-bit product
+// or square, then the reduction rows -- from shared out-of-line pieces, which
+// also give a b - c d with one reduction.  A final conditional subtraction
+// returns a canonical value in [0, p).
 //
 // Moduli: q (base field of G1) and r (the group order, scalar field), the
 // standard BN254 parameters (the paper's Sec. 6 fixes BN254).
