@@ -40,8 +40,8 @@ FQ_MUL_PER_MADD = 10
 IMAD_PER_MUL = 264
 IMAD_LO, IMAD_HI = 136, 128  # mad.lo (incl. the 8 m = t n0 products) and mad.hi per product
 # DRAM bytes (read + write) of one k_pieces_first launch, uniform 2^20, c = 17,
-# from ncu (profiles/msm_accum_k_pieces_first_msm2^20.md); None when the
-# kernel has changed since.
+# from an ncu capture of that launch (dram__bytes_read.sum +
+# dram__bytes_write.sum); None when the kernel has changed since.
 ACCUM_TRAFFIC = 2.060e9
 CPU_SAMPLE_LOG = 15  # oracle MSM sample: 2^15 points, ~10-15 s on 16 cores
 
