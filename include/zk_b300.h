@@ -266,7 +266,11 @@ int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, z
  * L) and 2j+1 (as R) with gammas[(count - count/2^(l-1)) + j] (level-major,
  * count - 1 challenges; host or device pointer).  All folds of one level run
  * as one batch.  The leaves' buffers are overwritten (used as the tree's
- * storage); the root is copied into *root (which must not alias a leaf). */
+ * storage); the root is copied into *root (which must not alias a leaf).
+ * Each level's instance combination (the G1 part) runs on the context's
+ * internal side stream, created at the highest stream priority on first use.
+ * It is forked from `stream` by an event and joined back before the root is
+ * copied, so the call stays ordered on `stream` like any other. */
 int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
                  zk_stream stream);
 
