@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <vector>
 
@@ -176,11 +177,17 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
 
 template <int LJR>
 int launch_pass_t(dim3 grid, uint32_t threads, size_t smem, cudaStream_t s, const PassArgs &a) {
-    static bool attr_set = false;  // per instance
-    if (!attr_set) {
+    // The shared-memory limit is a per-device attribute of the kernel: set it
+    // once on each device this instance runs on (the context's device is
+    // current here).
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    ZK_CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0;
+    if (!bit || !(attr_set.load() & bit)) {
         ZK_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<LJR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem));
-        attr_set = true;
+        attr_set.fetch_or(bit);
     }
     k_ntt_pass<LJR><<<grid, threads, smem, s>>>(a);
     ZK_LAUNCHED();
