@@ -447,7 +447,7 @@ int zk_open(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *x, zk_fr *y
     DeviceGuard g(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->sh->srs_n == 0) return ZK_ESRS;
-    const void *dc, *dx;
+    const void *dc = nullptr, *dx = nullptr;
     ZK_TRY(stage_in(ctx, coeffs, n * 32, "open.in0", &dc, s));
     ZK_TRY(stage_in(ctx, x, 32, "open.x", &dx, s));
     OutBuf oy, op, oq;
@@ -495,7 +495,7 @@ int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, si
             off += lens[i] * 32;
         }
     }
-    const void *dx, *dg;
+    const void *dx = nullptr, *dg = nullptr;
     ZK_TRY(stage_in(ctx, x, 32, "open.x", &dx, s));
     ZK_TRY(stage_in(ctx, gamma, 32, "open.gamma", &dg, s));
     OutBuf oy, op;
@@ -515,7 +515,7 @@ int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr
     DeviceGuard g(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->sh->srs_n == 0) return ZK_ESRS;
-    const void *da, *db;
+    const void *da = nullptr, *db = nullptr;
     ZK_TRY(stage_in(ctx, a, n * 32, "mq.in_a", &da, s));
     ZK_TRY(stage_in(ctx, b, n * 32, "mq.in_b", &db, s));
     OutBuf ot, oc;
@@ -538,7 +538,7 @@ int zk_set_fold_degree(zk_ctx *ctx, int degree) {
 int zk_set_hiding_base(zk_ctx *ctx, const zk_g1 *H) {
     if (!ctx || !H) return ZK_EINVAL;
     DeviceGuard g(ctx);
-    const void *dh;
+    const void *dh = nullptr;
     ZK_TRY(stage_in(ctx, H, 64, "hide.in", &dh, 0));
     return hiding_base_impl(ctx, (const uint32_t *)dh, 0);
 }
@@ -550,7 +550,7 @@ int zk_commit_hiding(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *s,
     cudaStream_t st = (cudaStream_t)stream;
     if (ctx->sh->srs_n == 0) return ZK_ESRS;
     if (n > ctx->sh->srs_n) return ZK_ESRS;
-    const void *dc, *ds;
+    const void *dc = nullptr, *ds = nullptr;
     ZK_TRY(stage_in(ctx, coeffs, n * 32, "hide.coeffs", &dc, st));
     ZK_TRY(stage_in(ctx, s, 32, "hide.s", &ds, st));
     OutBuf oo;
