@@ -95,6 +95,10 @@ size_t job_bytes(zk_ctx *ctx, size_t n) {
     b += 2 * (jobs * n * W / 32 + jobs * B) * 128;  // piece sums
     b += jobs * B * (128 + 5 * 4);         // buckets, counts and offsets
     b += n * 32;                           // fold cross term
+    // The piece-sum term assumes 32 entries per piece.  Round 0 cuts chunks
+    // as short as 8 entries when a batch is small, which needs up to
+    // 2 x 128 B x (3/4 of the resident accumulation threads) more: 14.5 MB
+    // on 148 SMs at 4 blocks of 128 threads, inside the 16 MiB slack below.
     return b + ((size_t)16 << 20);
 }
 
