@@ -322,7 +322,10 @@ int zk_plan_destroy(zk_plan *plan);
  * the caller and untouched by it until the job is done; acc_in is read only,
  * so many jobs may share it.  zk_submit returns ZK_EBUSY when 65536 jobs
  * wait, ZK_ENOMEM when one job's estimate exceeds the budget.  zk_wait
- * returns ZK_ETIMEOUT after timeout_ms.  Times are ms since server creation. */
+ * returns ZK_ETIMEOUT after timeout_ms.  Times are ms since server creation.
+ * Every ticket stays queryable until zk_server_destroy, so the server keeps
+ * a small record (about 200 bytes) per job submitted.  zk_server_create
+ * leaves the calling thread's current device as it found it. */
 typedef struct zk_server zk_server;
 typedef struct {
     size_t n;               /* witness length, power of two <= SRS size */

@@ -210,23 +210,31 @@ int zk_server_create(zk_ctx *ctx, int lanes, size_t hbm_budget_bytes, zk_server 
     srv->ctx = ctx;
     srv->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)-1;
     srv->t0 = Clock::now();
-    int dev = ctx->sh->device;
-    cudaSetDevice(dev);
+    const int dev = ctx->sh->device;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(dev);  // the lanes' streams belong to the context's device
+    int rc = ZK_OK;
     srv->lanes.resize(lanes);
     for (auto &l : srv->lanes) {
         if (zk_lane_create(ctx, &l.ctx) != ZK_OK ||
             cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
-            zk_server_destroy(srv);
-            return ZK_ECUDA;
+            rc = ZK_ECUDA;
+            break;
         }
     }
-    srv->sched = std::thread([srv, dev] {
-        cudaSetDevice(dev);
-        scheduler(srv);
-    });
-    *out = srv;
-    return ZK_OK;
+    if (rc == ZK_OK) {
+        srv->sched = std::thread([srv, dev] {
+            cudaSetDevice(dev);
+            scheduler(srv);
+        });
+        *out = srv;
+    } else {
+        zk_server_destroy(srv);
+    }
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    return rc;
 }
 
 int zk_submit(zk_server *srv, const zk_job *job, uint64_t *ticket) {
