@@ -318,9 +318,15 @@ int zk_plan_destroy(zk_plan *plan);
  * gamma).  Jobs are admitted in arrival order as soon as one of the server's
  * lanes (private workspace + CUDA stream) is free and the job's workspace
  * estimate fits in the unreserved HBM budget; admitted jobs run concurrently.
- * All pointers in zk_job are DEVICE pointers (gamma may be host) owned by
- * the caller and untouched by it until the job is done; acc_in is read only,
- * so many jobs may share it.  zk_submit returns ZK_EBUSY when 65536 jobs
+ * Pointers in zk_job: w[] are DEVICE pointers; leaf, acc_in and acc_out
+ * point to HOST zk_acc structs (the scheduler thread reads them) whose m, e
+ * and x buffers are device memory; gamma may be host or device.  All are
+ * owned by the caller and left untouched by it until the job is done; acc_in
+ * is read only, so many jobs may share it.  The witnesses w[] are m1, m2, m4
+ * for the degree-2 relation and m1, m2, m3 under zk_set_fold_degree 3 (the
+ * remaining vector is derived by the leaf step); the degree in effect when
+ * the scheduler starts a job applies to it, and the job's HBM reservation
+ * covers its d - 1 cross terms.  zk_submit returns ZK_EBUSY when 65536 jobs
  * wait, ZK_ENOMEM when one job's estimate exceeds the budget.  zk_wait
  * returns ZK_ETIMEOUT after timeout_ms.  Times are ms since server creation.
  * Every ticket stays queryable until zk_server_destroy, so the server keeps
@@ -329,10 +335,10 @@ int zk_plan_destroy(zk_plan *plan);
 typedef struct zk_server zk_server;
 typedef struct {
     size_t n;               /* witness length, power of two <= SRS size */
-    const zk_fr *w[3];      /* m1, m2, m4 evaluations (device) */
-    zk_acc *leaf;           /* receives the leaf accumulator (device buffers) */
-    const zk_acc *acc_in;   /* resident accumulator to fold into, or NULL */
-    zk_acc *acc_out;        /* receives fold(acc_in, leaf, gamma) */
+    const zk_fr *w[3];      /* m1, m2, m4 evaluations (degree 3: m1, m2, m3); device */
+    zk_acc *leaf;           /* host struct; receives the leaf accumulator in its device buffers */
+    const zk_acc *acc_in;   /* host struct: resident accumulator to fold into, or NULL */
+    zk_acc *acc_out;        /* host struct; receives fold(acc_in, leaf, gamma) */
     const zk_fr *gamma;     /* fold challenge */
 } zk_job;
 #define ZK_JOB_QUEUED 0

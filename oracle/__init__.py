@@ -78,6 +78,8 @@ def lib():
             "orc_commit_evals_tau": (None, [_P, _SZ, _P, _P]),
             "orc_dft": (None, [_P, _SZ, ctypes.c_int, _P]),
             "orc_dft_rows": (None, [_P, _SZ, ctypes.c_int, _PI, _SZ, _P]),
+            "orc_poly_eval": (None, [_P, _SZ, _P, _P]),
+            "orc_ntt_fingerprint": (ctypes.c_int, [_P, _SZ, _P, _P]),
             "orc_fold": (None, [_SZ, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P,
                                 _P, _P, _P, _P]),
             "orc_leaf_init": (None, [_SZ, _P, _P, _P, ctypes.c_int, _P, _P]),
@@ -315,6 +317,25 @@ def dft_rows(x, rows, inverse: bool) -> np.ndarray:
     return out
 
 
+def poly_eval(v, z) -> np.ndarray:
+    """sum_k v_k z^k (Horner)."""
+    v = _u(v).reshape(-1, 4)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_poly_eval(_p(v), v.shape[0], _p(_u(z)), _p(out))
+    return out
+
+
+def ntt_fingerprint(c, z) -> np.ndarray:
+    """sum_k z^k NTT(c)_k, computed as sum_j c_j (z^n - 1)/(z omega^j - 1)
+    in O(n) (no transform).  Raises if z omega^j = 1 for some j."""
+    c = _u(c).reshape(-1, 4)
+    out = np.zeros(4, dtype=np.uint64)
+    ok = lib().orc_ntt_fingerprint(_p(c), c.shape[0], _p(_u(z)), _p(out))
+    if not ok:
+        raise ValueError("z omega^j = 1: the fingerprint identity does not apply")
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Fold (generalised Mira, Sec. 4.2)
 # ----------------------------------------------------------------------------
@@ -405,6 +426,30 @@ def fold_tree(leaves, gammas, mode=COMMIT_TAU, srs=None, tau=None) -> Acc:
     md, s, t = _commit_args(mode, srs, tau)
     lib().orc_fold_tree(count, n, _p(m), _p(e), _p(inst), _p(g), md, s, t)
     return Acc(m[0], e[0], inst[0])
+
+
+def fold_tree_stacked(m, e, inst, gammas, mode=COMMIT_NONE, srs=None, tau=None) -> None:
+    """The sequential fold tree of fold_tree() on accumulators already stacked
+    as m (count, 4, n, 4), e (count, n, 4), inst (count, 44), in place (the
+    root ends in slot 0).  For trees too large to hold twice in host memory."""
+    count, n = m.shape[0], m.shape[2]
+    for a in (m, e, inst):
+        assert a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]
+    assert e.shape == (count, n, 4) and inst.shape == (count, INST_LIMBS)
+    g = _u(gammas).reshape(-1, 4)
+    assert g.shape[0] == count - 1
+    md, s, t = _commit_args(mode, srs, tau)
+    lib().orc_fold_tree(count, n, _p(m), _p(e), _p(inst), _p(g), md, s, t)
+
+
+def leaf_init_into(m, e, inst, mode=COMMIT_NONE, srs=None, tau=None) -> None:
+    """leaf_init() on caller-owned arrays m (4, n, 4), e (n, 4), inst (44,)
+    (for example, one slot of the stacked arrays of fold_tree_stacked)."""
+    n = m.shape[1]
+    for a in (m, e, inst):
+        assert a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]
+    md, s, t = _commit_args(mode, srs, tau)
+    lib().orc_leaf_init(n, _p(m), _p(e), _p(inst), md, s, t)
 
 
 def decide_relation(acc: Acc) -> int:

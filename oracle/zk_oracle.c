@@ -22,7 +22,10 @@
  *     H = <omega> (Sec. 4.4, "f|_H"), the polynomial is its interpolant and
  *     f(tau) = sum_k v_k L_k(tau), L_k(tau) = omega^k (tau^n - 1) / (n (tau - omega^k)).
  *   - The NTT over F_r as the O(n^2) DFT  NTT(c)_k = sum_j c_j omega^{jk},
- *     INTT(v)_j = n^{-1} sum_k v_k omega^{-jk},  omega_n = 5^{(r-1)/n}.
+ *     INTT(v)_j = n^{-1} sum_k v_k omega^{-jk},  omega_n = 5^{(r-1)/n}; and, for
+ *     checks at sizes where the DFT is out of reach, the geometric-series
+ *     fingerprint sum_k z^k NTT(c)_k = sum_j c_j (z^n - 1)/(z omega^j - 1)
+ *     beside Horner evaluation.
  *   - KZG opening (Sec. 2.1): y = f(x) and the quotient (f - y) / (X - x) by
  *     synthetic division; batch opening at one point with the gamma-weighted
  *     combination sum_i gamma^i f_i.
@@ -704,6 +707,71 @@ void orc_dft(const uint64_t *in, size_t n, int inverse, uint64_t *out) {
 void orc_dft_rows(const uint64_t *in, size_t n, int inverse, const int64_t *rows, size_t nrows,
                   uint64_t *out) {
     dft_rows(in, n, inverse, rows, nrows, out);
+}
+
+/* p(z) = sum_k v_k z^k by Horner's rule (values of a transform's output
+ * polynomial; the left side of the fingerprint below). */
+void orc_poly_eval(const uint64_t *v, size_t n, const uint64_t *z64, uint64_t *out) {
+    u256 z, acc, c, t;
+    load(&z, z64);
+    set_small(&acc, 0);
+    for (size_t k = n; k-- > 0;) {
+        load(&c, v + 4 * k);
+        fmul(&t, &acc, &z, &MODR);
+        fadd(&acc, &t, &c, &MODR);
+    }
+    store(out, &acc);
+}
+
+/* Fingerprint of the NTT of c without computing it: for z with z^n != 1 and
+ * z omega^j != 1,
+ *   sum_k z^k NTT(c)_k = sum_k z^k sum_j c_j omega^{jk}
+ *                      = sum_j c_j sum_k (z omega^j)^k
+ *                      = sum_j c_j ((z omega^j)^n - 1) / (z omega^j - 1)
+ *                      = sum_j c_j (z^n - 1) / (z omega^j - 1)      (omega^n = 1).
+ * Every coefficient (z^n - 1)/(z omega^j - 1) is nonzero, so an error in any
+ * single output of a transform changes the left side.  O(n) products and n
+ * inversions; returns 1, or 0 when z omega^j = 1 for some j (the identity
+ * does not apply). */
+int orc_ntt_fingerprint(const uint64_t *c, size_t n, const uint64_t *z64, uint64_t *out) {
+    u256 z, w, zn, one, num;
+    load(&z, z64);
+    root_of_unity(&w, n);
+    set_small(&one, 1);
+    set_small(&zn, 1);
+    for (size_t i = 0; i < n; i++) fmul(&zn, &zn, &z, &MODR); /* z^n */
+    fsub(&num, &zn, &one, &MODR);
+    u256 *zw = (u256 *)malloc(sizeof(u256) * (n ? n : 1)); /* z omega^j */
+    zw[0] = z;
+    for (size_t j = 1; j < n; j++) fmul(&zw[j], &zw[j - 1], &w, &MODR);
+    int ok = 1;
+    u256 total;
+    set_small(&total, 0);
+#pragma omp parallel num_threads(g_threads)
+    {
+        u256 part;
+        set_small(&part, 0);
+#pragma omp for schedule(static)
+        for (size_t j = 0; j < n; j++) {
+            u256 den, x, t;
+            fsub(&den, &zw[j], &one, &MODR);
+            if (is_zero(&den)) {
+#pragma omp atomic write
+                ok = 0;
+                continue;
+            }
+            finv(&den, &den, &MODR);
+            load(&x, c + 4 * j);
+            fmul(&t, &x, &num, &MODR);
+            fmul(&t, &t, &den, &MODR);
+            fadd(&part, &part, &t, &MODR);
+        }
+#pragma omp critical
+        fadd(&total, &total, &part, &MODR);
+    }
+    free(zw);
+    store(out, &total);
+    return ok;
 }
 
 /* ------------------------------------------------------------------ */

@@ -15,8 +15,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# ZK_B300_LIB selects another build of the same library (kernel experiments).
-LIB_PATH = os.environ.get("ZK_B300_LIB", os.path.join(_HERE, "libzkb300.so"))
+LIB_PATH = os.path.join(_HERE, "libzkb300.so")
 
 ZK_OK, ZK_EINVAL, ZK_ESRS, ZK_ENOMEM, ZK_ECUDA, ZK_ETIMEOUT, ZK_EBUSY = range(7)
 ZK_EVALS = 1

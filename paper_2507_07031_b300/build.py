@@ -14,12 +14,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-# ZK_B300_LIB / ZK_B300_NVCC_FLAGS build a variant library elsewhere (kernel
-# experiments); the default is the in-tree libzkb300.so.
-LIB = os.environ.get("ZK_B300_LIB", os.path.join(HERE, "libzkb300.so"))
-OBJ = os.path.join(os.path.dirname(LIB), "_build" if "ZK_B300_LIB" not in os.environ
-                   else "_build_" + os.path.basename(LIB).replace(".so", ""))
-EXTRA = os.environ.get("ZK_B300_NVCC_FLAGS", "").split()
+LIB = os.path.join(HERE, "libzkb300.so")
+OBJ = os.path.join(HERE, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -40,7 +36,7 @@ def _compile(src: str, extra) -> str:
     obj = os.path.join(OBJ, src[:-3] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime():
         return obj
-    cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))

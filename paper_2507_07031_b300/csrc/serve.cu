@@ -80,21 +80,25 @@ namespace {
 
 constexpr size_t kMaxQueue = 1 << 16;
 
-// Device workspace a job needs on its lane (leaf commitments of three
-// vectors and one fold of length n): INTT copies and ping-pong buffers,
-// MSM entries, piece sums and buckets, the fold's cross-term vector.
+// Device workspace a job needs on its lane (leaf commitments of four
+// vectors, then one fold of length n with d - 1 cross terms, d the fold
+// degree): INTT copies and ping-pong buffers, MSM entries, piece sums and
+// buckets, the fold's cross-term vectors.  The leaf's four MSMs run as one
+// batch; a fold's d - 1 cross-term MSMs run as one batch after it, in the
+// same workspace, so the larger of the two batches sets the MSM terms.
 size_t job_bytes(zk_ctx *ctx, size_t n) {
     const int c = msm_pick_window(ctx, n, 4);
     const size_t W = (size_t)windows_for(c);
     const size_t B = (size_t)1 << (c - 1);
-    const size_t jobs = 4;
+    const size_t cross = (size_t)(ctx->sh->fold_degree - 1);
+    const size_t jobs = 4 > cross ? 4 : cross;
     size_t b = 0;
     b += jobs * n * 32;                    // INTT staging
     b += 2 * jobs * n * 32;                // NTT ping-pong
     b += jobs * n * W * 4;                 // sorted MSM entries
     b += 2 * (jobs * n * W / 32 + jobs * B) * 128;  // piece sums
     b += jobs * B * (128 + 5 * 4);         // buckets, counts and offsets
-    b += n * 32;                           // fold cross term
+    b += cross * n * 32;                   // fold cross terms
     // The piece-sum term assumes 32 entries per piece.  Round 0 cuts chunks
     // as short as 8 entries when a batch is small, which needs up to
     // 2 x 128 B x (3/4 of the resident accumulation threads) more: 14.5 MB
@@ -137,8 +141,11 @@ int run_job(zk_server *srv, Lane &lane, Ticket &t) {
     zk_stream zs = (zk_stream)s;
     const size_t n = j.n;
     int rc = ZK_OK;
+    // The third witness is m4 for the degree-2 relation (m3 = m1 o m2 is
+    // derived) and m3 for the degree-3 one (m4 = m1 o m2 o m3 is derived).
+    const int third = lane.ctx->sh->fold_degree == 3 ? 2 : 3;
     const zk_fr *src[3] = {j.w[0], j.w[1], j.w[2]};
-    zk_fr *dst[3] = {j.leaf->m[0], j.leaf->m[1], j.leaf->m[3]};
+    zk_fr *dst[3] = {j.leaf->m[0], j.leaf->m[1], j.leaf->m[third]};
     for (int i = 0; i < 3 && rc == ZK_OK; i++)
         if (src[i] != dst[i] && cudaMemcpyAsync(dst[i], src[i], n * 32, cudaMemcpyDefault, s) != cudaSuccess)
             rc = ZK_ECUDA;
@@ -213,7 +220,12 @@ int zk_server_create(zk_ctx *ctx, int lanes, size_t hbm_budget_bytes, zk_server 
     const int dev = ctx->sh->device;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    cudaSetDevice(dev);  // the lanes' streams belong to the context's device
+    // The lanes' streams belong to the context's device.
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete srv;
+        return ZK_ECUDA;
+    }
     int rc = ZK_OK;
     srv->lanes.resize(lanes);
     for (auto &l : srv->lanes) {

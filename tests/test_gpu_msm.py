@@ -148,11 +148,11 @@ def test_big_srs_samples(zk, orc, ctx_big, tau):
     zk.zk_srs_export(ctx_big, out, 0, n)
     torch.cuda.synchronize()
     pts = to_host(out)
-    assert orc.count_off_curve(pts[:: 64]) == 0
+    assert orc.count_off_curve(pts) == 0  # every point on the curve
     G = orc.g1_generator()
     t = Z.fr_to_int(tau)
     rng = np.random.default_rng(0)
-    for i in [0, 1, 2, n - 1] + rng.integers(0, n, 16).tolist():
+    for i in [0, 1, 2, n - 1] + rng.integers(0, n, 64).tolist():
         assert pts_equal(pts[i], orc.g1_mul(G, Z.int_to_fr(pow(t, int(i), R)))), i
 
 

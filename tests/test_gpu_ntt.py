@@ -1,8 +1,10 @@
 """GPU parity of the F_r NTT / INTT against the oracle's O(n^2) DFT.
 
-Full comparison up to 2^12 (every radix split of one and two passes);
-sampled rows plus exact round trips and the Aurora identity at 2^20, 2^21
-(three passes) and 2^22."""
+Full comparison up to 2^12 (every radix split of one and two passes).  At
+2^20, 2^21 (three passes) and 2^22 every output is checked by the O(n)
+geometric fingerprint sum_k z^k NTT(c)_k = sum_j c_j (z^n - 1)/(z omega^j - 1)
+at a seeded z (a wrong output at any position changes the left side), next
+to sampled DFT rows, exact round trips and the Aurora identity."""
 import numpy as np
 import pytest
 
@@ -44,6 +46,19 @@ def test_ntt_at_scale_sampled(zk, orc, ctx_small, lg):
     assert np.array_equal(_run(zk, ctx_small, b, False), x)
     total = sum(Z.fr_to_int(v) for v in x[:: 1]) % R
     assert Z.fr_to_int(b[0]) * n % R == total
+
+
+@pytest.mark.parametrize("lg", [20, 21, 22])
+def test_ntt_at_scale_fingerprint(zk, orc, ctx_small, lg):
+    n = 1 << lg
+    x = Z.fr_uniform(650 + lg, n)
+    z = Z.fr_uniform(660 + lg, 1)[0]
+    # NTT: the transform's output evaluated at z equals the closed form of x.
+    f = _run(zk, ctx_small, x, False)
+    assert np.array_equal(orc.poly_eval(f, z), orc.ntt_fingerprint(x, z))
+    # INTT: NTT(INTT(x)) = x, so the closed form of the output is x(z).
+    b = _run(zk, ctx_small, x, True)
+    assert np.array_equal(orc.ntt_fingerprint(b, z), orc.poly_eval(x, z))
 
 
 def test_ntt_batch_and_host_buffers(zk, orc, ctx_small):
@@ -95,6 +110,8 @@ def test_ntt_two_pass_radix_2_11_at_2_22(zk, orc, ctx_small):
         zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, 22, 11)
         f = _run(zk, ctx_small, x, False)
         assert np.array_equal(f[rows], orc.dft_rows(x, rows, False))
+        z = Z.fr_uniform(803, 1)[0]
+        assert np.array_equal(orc.poly_eval(f, z), orc.ntt_fingerprint(x, z))
         assert np.array_equal(_run(zk, ctx_small, f, True), x)
     finally:
         zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, 22, 0)

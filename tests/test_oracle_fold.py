@@ -101,3 +101,44 @@ def test_fold_tree_is_sequential_pairwise_folding(orc, tau):
     for i in range(4):
         assert (root.C[i] == orc.commit_evals_tau(root.m[i], tau)).all()
     assert (root.E == orc.commit_evals_tau(root.e, tau)).all()
+
+
+def _relation_holds(acc):
+    """m1 o m2 - mu m3 = e at every position, over Python integers."""
+    mu = Z.fr_to_int(acc.mu)
+    for k in range(acc.n):
+        a = [Z.fr_to_int(acc.m[i][k]) for i in range(3)]
+        if (a[0] * a[1] - mu * a[2] - Z.fr_to_int(acc.e[k])) % R:
+            return False
+    return True
+
+
+def test_decider_recheck_over_python_integers(orc, tau):
+    n = 16
+    L = _leaf(orc, 1000, n, orc.COMMIT_TAU, tau)
+    Rr = _leaf(orc, 1100, n, orc.COMMIT_TAU, tau)
+    assert _relation_holds(L) and _relation_holds(Rr)
+    O, _ = orc.fold(L, Rr, Z.gammas(1, 1)[0], orc.COMMIT_NONE)
+    O2, _ = orc.fold(O, O.copy(), Z.gammas(2, 1)[0], orc.COMMIT_NONE)
+    for a in (O, O2):
+        assert _relation_holds(a) and orc.decide_relation(a) == 0
+    # one wrong error entry fails both the decider and the recheck
+    bad = O2.copy()
+    bad.e[3] = Z.int_to_fr((Z.fr_to_int(bad.e[3]) + 1) % R)
+    assert not _relation_holds(bad) and orc.decide_relation(bad) == 1
+
+
+def test_stacked_tree_matches_list_tree(orc, tau):
+    n, count = 8, 8
+    leaves = [_leaf(orc, 1200 + 10 * i, n, orc.COMMIT_NONE, tau) for i in range(count)]
+    gam = np.concatenate([Z.gammas(l, count >> l) for l in range(1, 4)])
+    want = orc.fold_tree(leaves, gam, orc.COMMIT_NONE)
+    m = np.zeros((count, 4, n, 4), np.uint64)
+    e = np.zeros((count, n, 4), np.uint64)
+    inst = np.zeros((count, orc.INST_LIMBS), np.uint64)
+    for j in range(count):
+        base = 1200 + 10 * j
+        m[j, 0], m[j, 1], m[j, 3] = (Z.zkml_scalars(base + i, n) for i in range(3))
+        orc.leaf_init_into(m[j], e[j], inst[j])
+    orc.fold_tree_stacked(m, e, inst, gam)
+    assert (m[0] == want.m).all() and (e[0] == want.e).all() and (inst[0] == want.inst).all()

@@ -76,3 +76,47 @@ def test_sampled_rows_match_full_transform(orc):
     rows = np.array([0, 1, 5, 100, 255])
     assert (orc.dft_rows(x, rows, False) == orc.ntt(x)[rows]).all()
     assert (orc.dft_rows(x, rows, True) == orc.intt(x)[rows]).all()
+
+
+def test_poly_eval_against_python_horner(orc):
+    v = Z.fr_uniform(9, 37)
+    z = Z.fr_uniform(10, 1)[0]
+    zi = Z.fr_to_int(z)
+    acc = 0
+    for c in reversed(_ints(v)):
+        acc = (acc * zi + c) % R
+    assert Z.fr_to_int(orc.poly_eval(v, z)) == acc
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 16])
+def test_fingerprint_against_python_brute_force(orc, n):
+    # sum_k z^k sum_j c_j omega^{jk}, every term with Python integers.
+    c = Z.fr_uniform(11, n)
+    z = Z.fr_uniform(12, 1)[0]
+    zi, w = Z.fr_to_int(z), Z.fr_to_int(orc.root_of_unity(n))
+    ci = _ints(c)
+    want = sum(pow(zi, k, R) * ci[j] * pow(w, j * k, R) for k in range(n) for j in range(n)) % R
+    assert Z.fr_to_int(orc.ntt_fingerprint(c, z)) == want
+
+
+@pytest.mark.parametrize("n", [2, 64, 1024])
+def test_fingerprint_matches_evaluated_dft(orc, n):
+    c = Z.fr_uniform(13, n)
+    z = Z.fr_uniform(14, 1)[0]
+    f = orc.ntt(c)
+    assert (orc.poly_eval(f, z) == orc.ntt_fingerprint(c, z)).all()
+    # the INTT side: NTT(INTT(v)) = v, so the fingerprint of INTT(v) is v(z)
+    assert (orc.ntt_fingerprint(orc.intt(c), z) == orc.poly_eval(c, z)).all()
+    # a planted error in one output (any position) changes the left side
+    for k in (0, n // 2, n - 1):
+        bad = f.copy()
+        bad[k] = Z.int_to_fr((Z.fr_to_int(bad[k]) + 1) % R)
+        assert not (orc.poly_eval(bad, z) == orc.ntt_fingerprint(c, z)).all()
+
+
+def test_fingerprint_rejects_z_on_the_inverse_subgroup(orc):
+    n = 8
+    w = Z.fr_to_int(orc.root_of_unity(n))
+    z = Z.int_to_fr(pow(w, n - 3, R))  # z omega^3 = 1
+    with pytest.raises(ValueError):
+        orc.ntt_fingerprint(Z.fr_uniform(15, n), z)
