@@ -377,6 +377,29 @@ const char *zk_strerror(int code);
 unsigned long long zk_kernel_launches(void);
 int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s);
 
+/* zk_probe_pipes: the issue rates the roofline of the integer kernels is
+ * stated against, measured on `device` (synchronous; tens of milliseconds).
+ * rates must hold ZK_NPROBES doubles, indexed by:
+ *   ZK_PROBE_MAD_LO   mad.lo.u32 per second (independent chains; the IMAD
+ *                     pipe's peak, the denominator of the reported fraction)
+ *   ZK_PROBE_MAD_HI   mad.hi.u32 per second
+ *   ZK_PROBE_MAD_WIDE mad.wide.u32 (64-bit addend) per second
+ *   ZK_PROBE_MAD_PAIR mad.lo.cc.u32 + madc.hi.u32 pairs per second (one limb
+ *                     product of a carry chain)
+ *   ZK_PROBE_ADD_PAIR add.cc.u32 + addc.u32 pairs per second (integer ALU)
+ *   ZK_PROBE_FQ_MUL   this library's F_q Montgomery products per second
+ *   ZK_PROBE_FR_MUL   this library's F_r Montgomery products per second
+ * Errors: ZK_EINVAL (null rates or bad device), ZK_ENOMEM, ZK_ECUDA. */
+#define ZK_PROBE_MAD_LO 0
+#define ZK_PROBE_MAD_HI 1
+#define ZK_PROBE_MAD_WIDE 2
+#define ZK_PROBE_MAD_PAIR 3
+#define ZK_PROBE_ADD_PAIR 4
+#define ZK_PROBE_FQ_MUL 5
+#define ZK_PROBE_FR_MUL 6
+#define ZK_NPROBES 7
+int zk_probe_pipes(int device, double *rates);
+
 /* Elementwise field arithmetic on canonical vectors (tests of the device
  * field code; the prover does not call it).  The paper has no counterpart:
  * it checks the F_q / F_r arithmetic every step of the hot path is built on

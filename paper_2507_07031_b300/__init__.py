@@ -118,6 +118,8 @@ def _load():
     L.zk_probe_rates.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double)]
     L.zk_probe_rates.restype = ctypes.c_int
+    L.zk_probe_pipes.argtypes = [ctypes.c_int, _VP]
+    L.zk_probe_pipes.restype = ctypes.c_int
     return L
 
 
@@ -126,7 +128,7 @@ lib = _load()
 EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_generate",
             "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_noalloc", "zk_commit_batch", "zk_ntt", "zk_intt",
             "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_strerror",
-            "zk_kernel_launches", "zk_probe_rates", "zk_timing_enable", "zk_timing_read",
+            "zk_kernel_launches", "zk_probe_rates", "zk_probe_pipes", "zk_timing_enable", "zk_timing_read",
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
             "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
@@ -153,6 +155,17 @@ def zk_probe_rates(device: int = 0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib.zk_probe_rates(int(device), ctypes.byref(a), ctypes.byref(b)), "zk_probe_rates")
     return a.value, b.value
+
+
+PROBES = ["mad_lo", "mad_hi", "mad_wide", "mad_pair", "add_pair", "fq_mul", "fr_mul"]
+
+
+def zk_probe_pipes(device: int = 0) -> dict:
+    """Measured issue rates (per second) of the integer instruction forms the
+    product code is built from, and of the F_q / F_r products themselves."""
+    r = (ctypes.c_double * len(PROBES))()
+    _check(lib.zk_probe_pipes(int(device), r), "zk_probe_pipes")
+    return {k: r[i] for i, k in enumerate(PROBES)}
 
 
 def zk_field_op(field: int, op: int, a, b, out, n: int = None, stream=None) -> None:

@@ -1,6 +1,7 @@
-// diag.cu -- measurement helpers for the roofline: the integer multiply-add
-// issue rate of the device (independent 32-bit mad.lo chains) and the
-// sustained Montgomery-multiplication rate of this library's F_q multiply.
+// diag.cu -- measurement helpers for the roofline: the issue rates of the
+// integer instruction forms the field products are built from (independent
+// chains of mad.lo, mad.hi, mad.wide, lo/hi carry pairs and ALU carry adds)
+// and the sustained Montgomery-product rates of this library's F_q and F_r code.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,19 +36,65 @@ __global__ void k_probe_imad(uint32_t *sink, uint32_t iters, uint32_t seed) {
     if (x == 0x12345678u) sink[0] = x;  // keep the chains alive
 }
 
-// Each thread runs `iters` rounds of 4 independent F_q Montgomery products.
+// The other instruction forms of the product code, each as kChains
+// independent chains per thread (kChains * kUnroll instructions, or pairs,
+// per iteration):
+//   HI   mad.hi.u32                  (the high half of a limb product)
+//   WIDE mad.wide.u32 with a 64-bit addend (both halves in one instruction)
+//   PAIR mad.lo.cc.u32 + madc.hi.u32 (one limb product of a carry chain)
+//   ADD  add.cc.u32 + addc.u32        (integer ALU carry chain)
+enum ProbeForm { kHi = 0, kWide = 1, kPair = 2, kAdd = 3 };
+
+template <int F>
+__global__ void k_probe_form(uint32_t *sink, uint32_t iters, uint32_t seed) {
+    uint32_t a[kChains], h[kChains];
+    uint64_t w[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) {
+        a[j] = seed + threadIdx.x * 7u + j * 131u;
+        h[j] = a[j] ^ 0x5bd1e995u;
+        w[j] = ((uint64_t)h[j] << 32) | a[j];
+    }
+    const uint32_t b = seed ^ 0x9e3779b9u;
+    for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+#pragma unroll
+            for (int j = 0; j < kChains; j++) {
+                if (F == kHi)
+                    asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[j]) : "r"(b), "r"(a[(j + 1) % kChains]));
+                else if (F == kWide)
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[j]) : "r"(a[j]), "r"(b));
+                else if (F == kPair)
+                    asm volatile("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
+                                 : "+r"(a[j]), "+r"(h[j]) : "r"(a[(j + 1) % kChains]), "r"(b));
+                else
+                    asm volatile("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;"
+                                 : "+r"(a[j]), "+r"(h[j]) : "r"(b), "r"(a[(j + 1) % kChains]));
+            }
+        }
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) x ^= a[j] ^ h[j] ^ (uint32_t)w[j] ^ (uint32_t)(w[j] >> 32);
+    if (x == 0x12345678u) sink[0] = x;  // keep the chains alive
+}
+
+// Each thread runs `iters` rounds of 4 independent Montgomery products of
+// the field P (this library's product code).
+template <class P>
 __global__ void k_probe_mont(uint32_t *sink, uint32_t iters, uint32_t seed) {
-    Fq x[4];
+    Fe<P> x[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        x[j] = fe_mont_one<FqP>();
+        x[j] = fe_mont_one<P>();
         x[j].v[0] ^= seed + threadIdx.x + 17u * j;
         x[j].v[7] &= 0x0fffffffu;
     }
-    Fq y = x[1];
+    Fe<P> y = x[1];
     for (uint32_t i = 0; i < iters; i++) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) x[j] = fe_mul<FqP>(x[j], y);
+        for (int j = 0; j < 4; j++) x[j] = fe_mul<P>(x[j], y);
     }
     uint32_t acc = 0;
 #pragma unroll
@@ -81,8 +128,9 @@ double time_kernel(K kern, int blocks, int threads, uint32_t iters, uint32_t *si
 
 using namespace zk;
 
-extern "C" int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s) {
-    if (!imad_per_s || !fq_mul_per_s) return ZK_EINVAL;
+// Measures every rate of zk_probe_pipes into r[ZK_NPROBES] (or only the
+// mad.lo and F_q product rates when `all` is false).
+static int probe(int device, bool all, double *r) {
     int prev = 0;
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) {
@@ -99,17 +147,44 @@ extern "C" int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per
     }
     const int blocks = sms * 8, threads = 256;
     const uint32_t it1 = 2048;
-    double t1 = time_kernel(k_probe_imad, blocks, threads, it1, sink);
-    *imad_per_s = (double)blocks * threads * it1 * kChains * kUnroll / t1;
+    const double per = (double)blocks * threads * it1 * kChains * kUnroll;  // instructions (pairs)
+    r[ZK_PROBE_MAD_LO] = per / time_kernel(k_probe_imad, blocks, threads, it1, sink);
+    int launches = 4;
+    if (all) {
+        r[ZK_PROBE_MAD_HI] = per / time_kernel(k_probe_form<kHi>, blocks, threads, it1, sink);
+        r[ZK_PROBE_MAD_WIDE] = per / time_kernel(k_probe_form<kWide>, blocks, threads, it1, sink);
+        r[ZK_PROBE_MAD_PAIR] = per / time_kernel(k_probe_form<kPair>, blocks, threads, it1, sink);
+        r[ZK_PROBE_ADD_PAIR] = per / time_kernel(k_probe_form<kAdd>, blocks, threads, it1, sink);
+        launches += 16;
+    }
     const int mblocks = sms * 4, mthreads = 256;
     const uint32_t it2 = 256;
-    double t2 = time_kernel(k_probe_mont, mblocks, mthreads, it2, sink);
-    *fq_mul_per_s = (double)mblocks * mthreads * it2 * 4 / t2;
-    count_launches(8);
+    const double prods = (double)mblocks * mthreads * it2 * 4;
+    r[ZK_PROBE_FQ_MUL] = prods / time_kernel(k_probe_mont<FqP>, mblocks, mthreads, it2, sink);
+    launches += 4;
+    if (all) {
+        r[ZK_PROBE_FR_MUL] = prods / time_kernel(k_probe_mont<FrP>, mblocks, mthreads, it2, sink);
+        launches += 4;
+    }
+    count_launches(launches);
     cudaError_t e = cudaGetLastError();
     cudaFree(sink);
     cudaSetDevice(prev);
     return e == cudaSuccess ? ZK_OK : ZK_ECUDA;
+}
+
+extern "C" int zk_probe_rates(int device, double *imad_per_s, double *fq_mul_per_s) {
+    if (!imad_per_s || !fq_mul_per_s) return ZK_EINVAL;
+    double r[ZK_NPROBES] = {0};
+    ZK_TRY(probe(device, false, r));
+    *imad_per_s = r[ZK_PROBE_MAD_LO];
+    *fq_mul_per_s = r[ZK_PROBE_FQ_MUL];
+    return ZK_OK;
+}
+
+extern "C" int zk_probe_pipes(int device, double *rates) {
+    if (!rates) return ZK_EINVAL;
+    return probe(device, true, rates);
 }
 
 // ---------------------------------------------------------------------------

@@ -38,25 +38,36 @@ namespace zk {
 namespace {
 
 constexpr uint32_t kInvalid = 0xffffffffu;
+constexpr int kMaxLevels = 4;  // bucket-reduction levels (phase 4)
 constexpr size_t kStatsMin = 4096;  // scalars below which the width scan is skipped
 
 // One MSM of a batch.  Jobs are ordered by window width so that each width's
-// scalars form one contiguous range for its recode launch.
+// scalars form one contiguous range for its recode launch.  The host writes
+// the full-width shape (window width c, ceil(254 / c) windows over the
+// width's window table); when the scalars' widths are measured, a plan
+// kernel rewrites shift, wins, logB and table on the device before the
+// recode runs (small-scalar path).
 struct JobDesc {
     const uint32_t *scalars;  // n canonical scalars (device)
     void *out;                // canonical affine result (device)
-    const Affine *table;      // window table of this job's width
+    const Affine *table;      // points the sorted entries index (window table, or `base`)
+    const Affine *base;       // base points: SRS, or the Lagrange basis of H
+    const Affine *wtable;     // window table of width c over the base points
+    const Affine *t16;        // window table of width 16 over the base points, or null
+    uint32_t t16n;            // its points per window
     uint32_t n;
-    uint32_t logB;            // buckets: B = 2^logB = 2^(c - 1)
+    uint32_t logB;            // buckets in use: 2^logB (2^(c - 1), or fewer for short scalars)
     uint32_t shift;           // every scalar of the job is a multiple of 2^shift
     uint32_t wins;            // windows that can hold nonzero digits (after the shift)
+    uint32_t c;               // window width of the job's recode launch
+    uint32_t dbl;             // doublings of the reduced sum (the shifted-out factor 2^dbl)
+    uint32_t lbase[kMaxLevels - 1];  // first item of the job in reduction levels 1, 2, 3
 };
 
 struct DevJobs {
     const JobDesc *jobs;     // count entries
     const uint32_t *sbase;   // scalar prefix over jobs, count + 1
     const uint32_t *bbase;   // first global bucket of each job, count + 1
-    const uint32_t *kbase;   // first reduction block of each job, count + 1
     uint32_t count;
 };
 
@@ -114,32 +125,109 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
 // Phases 1 and 2 for the jobs [g0, g1) of window width C: with SCATTER false,
 // the bucket histogram; with SCATTER true, the (table index << 1 | sign)
-// words written bucket by bucket.  Lanes with equal keys are aggregated into
-// one atomic per warp (skewed scalar distributions hit few buckets).
+// words written bucket by bucket.  The scalars are cut into chunks of
+// kRecPer.  A chunk whose scalars all belong to one job that uses a single
+// window over at most kSmemBuckets buckets (short scalars) is counted in
+// shared memory by one block (k_recode_short), which touches each global
+// counter (or cursor) once: quantised values put 2^20 scalars into about a
+// hundred buckets, and same-address global atomics serialise.  Every other
+// chunk goes through k_recode, one scalar per thread, where lanes with equal
+// keys are aggregated into one atomic per warp.  The order of entries within
+// a bucket is unspecified (bucket sums do not depend on it).
+constexpr uint32_t kRecThreads = 256;
+constexpr uint32_t kRecPer = 2048;
+constexpr uint32_t kRecEach = kRecPer / kRecThreads;
+constexpr uint32_t kSmemBucketsLog = 12;
+constexpr uint32_t kSmemBuckets = 1u << kSmemBucketsLog;
+
+struct Chunk {
+    uint32_t first, last, job;
+    bool smem;
+};
+
+// Chunk k of the scalars of jobs [g0, g1): its range and whether it takes
+// the shared-memory path.
+__device__ __forceinline__ Chunk rec_chunk(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t k) {
+    Chunk c;
+    c.first = dj.sbase[g0] + k * kRecPer;
+    c.last = min(c.first + kRecPer, dj.sbase[g1]) - 1;
+    c.job = search(dj.sbase, g0, g1, c.first);
+    const JobDesc &J = dj.jobs[c.job];
+    c.smem = search(dj.sbase, g0, g1, c.last) == c.job && J.wins == 1 && J.logB <= kSmemBucketsLog;
+    return c;
+}
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(kRecThreads)
+    k_recode_short(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t *__restrict__ counts,
+                   uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted) {
+    __shared__ uint32_t hist[kSmemBuckets];
+    const Chunk ch = rec_chunk(dj, g0, g1, blockIdx.x);
+    if (!ch.smem) return;  // block-uniform
+    const JobDesc &J = dj.jobs[ch.job];
+    const uint32_t nbj = 1u << J.logB, bb = dj.bbase[ch.job], sb = dj.sbase[ch.job];
+    for (uint32_t b = threadIdx.x; b < nbj; b += kRecThreads) hist[b] = 0;
+    __syncthreads();
+    uint32_t key[kRecEach], word[kRecEach];
+#pragma unroll
+    for (uint32_t e = 0; e < kRecEach; e++) {
+        const uint32_t gid = ch.first + threadIdx.x + e * kRecThreads;
+        key[e] = kInvalid;
+        if (gid <= ch.last) {
+            uint32_t sc[8];
+            const bool neg = load_recentred(J.scalars + 8 * (size_t)(gid - sb), sc);
+            shr256(sc, J.shift);
+            // One window: the shifted scalar is its own digit (below 2^(c' - 1)).
+            const uint32_t d = sc[0];
+            if (d) {
+                key[e] = d - 1u;
+                word[e] = ((gid - sb) << 1) | (neg ? 1u : 0u);
+                atomicAdd(&hist[d - 1u], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if constexpr (!SCATTER) {
+        for (uint32_t b = threadIdx.x; b < nbj; b += kRecThreads)
+            if (hist[b]) atomicAdd(&counts[bb + b], hist[b]);
+    } else {
+        for (uint32_t b = threadIdx.x; b < nbj; b += kRecThreads)
+            if (hist[b]) hist[b] = atomicAdd(&cursor[bb + b], hist[b]);
+        __syncthreads();
+#pragma unroll
+        for (uint32_t e = 0; e < kRecEach; e++)
+            if (key[e] != kInvalid) sorted[atomicAdd(&hist[key[e]], 1u)] = word[e];
+    }
+}
+
 template <int C, bool SCATTER>
-__global__ void k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n,
-                         uint32_t *__restrict__ counts, uint32_t *__restrict__ cursor,
-                         uint32_t *__restrict__ sorted) {
+__global__ void __launch_bounds__(kRecThreads)
+    k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n, uint32_t *__restrict__ counts,
+             uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted) {
     constexpr int W = (kScalarBits + C - 1) / C;
-    const uint32_t s0 = dj.sbase[g0];
-    const uint32_t gid = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    static_assert(kRecPer % kRecThreads == 0, "a block lies in one chunk");
+    if (rec_chunk(dj, g0, g1, blockIdx.x / kRecEach).smem) return;  // block-uniform
+    const uint32_t gid = dj.sbase[g0] + blockIdx.x * kRecThreads + threadIdx.x;
     const bool live = gid < dj.sbase[g1];
-    uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t sc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t job = g0, i = 0, bb = 0;
     bool neg = false;
     if (live) {
         job = search(dj.sbase, g0, g1, gid);
         i = gid - dj.sbase[job];
         bb = dj.bbase[job];
-        neg = load_recentred(dj.jobs[job].scalars + 8 * (size_t)i, s);
-        shr256(s, dj.jobs[job].shift);
+        neg = load_recentred(dj.jobs[job].scalars + 8 * (size_t)i, sc);
+        shr256(sc, dj.jobs[job].shift);
     }
     const uint32_t wins = live ? dj.jobs[job].wins : 0;
+    // Windows past every lane's last one hold no digits: stop before them.
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, wins);
     const uint32_t lt_mask = (1u << lane_id()) - 1u;
     uint32_t carry = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) {
-        uint32_t d = ((uint32_t)w < wins ? window_bits<C>(s, w) : 0u) + carry;
+        if ((uint32_t)w >= wmax) break;
+        uint32_t d = ((uint32_t)w < wins ? window_bits<C>(sc, w) : 0u) + carry;
         carry = d > (1u << (C - 1)) ? 1u : 0u;
         int sd = carry ? (int)d - (1 << C) : (int)d;
         uint32_t key = (live && sd != 0) ? bb + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
@@ -162,30 +250,108 @@ __global__ void k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n,
 
 // Per job: the largest bit length (st_len[j], initialised to 0) and the
 // fewest trailing zeros (st_tz[j], initialised to 0xffffffff) of the
-// recentred nonzero scalars.
-__global__ void k_scalar_stats(DevJobs dj, uint32_t total, uint32_t *__restrict__ st_len,
-                               uint32_t *__restrict__ st_tz) {
-    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t len = 0, tz = 0xffffffffu, job = 0;
-    if (gid < total) {
-        job = search(dj.sbase, 0, dj.count, gid);
-        uint32_t s[8];
-        load_recentred(dj.jobs[job].scalars + 8 * (size_t)(gid - dj.sbase[job]), s);
+// recentred nonzero scalars.  A block takes kRecPer consecutive scalars;
+// when they all belong to one job the block reduces them and makes one
+// atomic per statistic, else one per warp and job.
+__global__ void __launch_bounds__(kRecThreads)
+    k_scalar_stats(DevJobs dj, uint32_t total, uint32_t *__restrict__ st_len, uint32_t *__restrict__ st_tz) {
+    __shared__ uint32_t red[2][kRecThreads / 32];
+    const uint32_t first = blockIdx.x * kRecPer;
+    const uint32_t last = min(first + kRecPer, total) - 1;
+    const uint32_t jf = search(dj.sbase, 0, dj.count, first);
+    const uint32_t jl = search(dj.sbase, 0, dj.count, last);
+    const bool one_job = jf == jl;  // block-uniform
+    uint32_t blen = 0, btz = 0xffffffffu;
+    for (uint32_t e = 0; e < kRecEach; e++) {
+        const uint32_t gid = first + threadIdx.x + e * kRecThreads;
+        uint32_t len = 0, tz = 0xffffffffu, job = jf;
+        if (gid <= last) {
+            if (!one_job) job = search(dj.sbase, jf, jl + 1, gid);
+            uint32_t sc[8];
+            load_recentred(dj.jobs[job].scalars + 8 * (size_t)(gid - dj.sbase[job]), sc);
 #pragma unroll
-        for (int j = 7; j >= 0; j--)
-            if (!len && s[j]) len = 32 * j + 32 - __clz(s[j]);
+            for (int j = 7; j >= 0; j--)
+                if (!len && sc[j]) len = 32 * j + 32 - __clz(sc[j]);
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-            if (tz == 0xffffffffu && s[j]) tz = 32 * j + __ffs(s[j]) - 1;
+            for (int j = 0; j < 8; j++)
+                if (tz == 0xffffffffu && sc[j]) tz = 32 * j + __ffs(sc[j]) - 1;
+        }
+        if (one_job) {
+            blen = max(blen, len);
+            btz = min(btz, tz);
+            continue;
+        }
+        // one atomic per warp and job
+        const uint32_t key = gid <= last ? job : 0xffffffffu;
+        const uint32_t group = __match_any_sync(0xffffffffu, key);
+        const uint32_t gl = __reduce_max_sync(group, len);
+        const uint32_t gt = __reduce_min_sync(group, tz);
+        if (key != 0xffffffffu && lane_id() == (uint32_t)(__ffs(group) - 1)) {
+            if (gl) atomicMax(&st_len[key], gl);
+            if (gt != 0xffffffffu) atomicMin(&st_tz[key], gt);
+        }
     }
-    // one atomic per warp and job
-    const uint32_t key = gid < total ? job : 0xffffffffu;
-    const uint32_t group = __match_any_sync(0xffffffffu, key);
-    const uint32_t gl = __reduce_max_sync(group, len);
-    const uint32_t gt = __reduce_min_sync(group, tz);
-    if (key != 0xffffffffu && lane_id() == (uint32_t)(__ffs(group) - 1)) {
-        atomicMax(&st_len[key], gl);
-        atomicMin(&st_tz[key], gt);
+    if (!one_job) return;
+    blen = __reduce_max_sync(0xffffffffu, blen);
+    btz = __reduce_min_sync(0xffffffffu, btz);
+    if (lane_id() == 0) {
+        red[0][threadIdx.x >> 5] = blen;
+        red[1][threadIdx.x >> 5] = btz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (uint32_t w = 1; w < kRecThreads / 32; w++) {
+            blen = max(blen, red[0][w]);
+            btz = min(btz, red[1][w]);
+        }
+        if (blen) atomicMax(&st_len[jf], blen);
+        if (btz != 0xffffffffu) atomicMin(&st_tz[jf], btz);
+    }
+}
+
+// Small-scalar plan, one thread per job, from the width statistics: the
+// common trailing zeros are shifted out (the result is doubled back at the
+// end) and only the windows that can hold digits are used; when the rest
+// fits one window (c' = bits + 1 <= c) the digits index the base points
+// directly, with 2^(c' - 1) buckets.  When at least 16 trailing zeros are
+// shifted out and the base's width-16 window table exists, the single window
+// indexes window k = tz / 16 of that table (points 2^(16 k) P_i) instead, so
+// the factor 2^(16 k) needs no doublings at the end (quantised values times
+// 2^16 have exactly 16).  Jobs whose scalars are all zero get no windows.
+// Scalars that are full width keep the host's shape.
+__global__ void k_msm_plan(JobDesc *__restrict__ jobs, uint32_t count, const uint32_t *__restrict__ st_len,
+                           const uint32_t *__restrict__ st_tz) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    JobDesc &d = jobs[k];
+    const uint32_t len = min(st_len[k], (uint32_t)kScalarBits - 1);
+    const uint32_t tz = st_tz[k];
+    const uint32_t c = d.c;
+    if (len == 0) {  // all scalars zero
+        d.wins = 0;
+        d.shift = 0;
+        d.dbl = 0;
+        d.logB = kMinWindow - 1;
+        d.table = d.base;
+    } else if (len < (uint32_t)kScalarBits - 1 || tz > 0) {
+        const uint32_t sh = min(tz, len - 1);
+        const uint32_t eff = len - sh;  // bits left after the shift
+        d.shift = sh;
+        d.dbl = sh;
+        if (eff + 1 <= c) {
+            d.wins = 1;
+            d.logB = max(eff + 1, (uint32_t)kMinWindow) - 1;
+            d.table = d.base;
+            const uint32_t k16 = min(sh / 16, 15u);
+            if (d.t16 && k16 && (sh & 15) <= 1 && eff + (sh & 15) + 1 <= c) {
+                d.shift = 16 * k16;
+                d.dbl = 0;
+                d.logB = max(eff + (sh & 15) + 1, (uint32_t)kMinWindow) - 1;
+                d.table = d.t16 + (size_t)k16 * d.t16n;
+            }
+        } else {
+            d.wins = (eff + 1 + c - 1) / c;
+        }
     }
 }
 
@@ -217,23 +383,40 @@ struct RoundPlan {
     uint32_t run[kMaxRounds];  // round rd executes
     uint32_t last;             // rounds that execute (a prefix of 0 .. rounds-1)
     uint32_t team;             // the last stage runs on teams
+    uint32_t p0;               // round-0 chunk (entries per thread)
+    int p0neg;                 // -p0 (the scan's chunk-count mode)
+    const uint32_t *off;       // offsets of the items the last stage sums
+    Xyzz *parts;               // a piece buffer the last round does not hold (team tail partials)
 };
 
-// Largest bucket (entries) into *dmax (zeroed by the caller).
-__global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, uint32_t *dmax) {
-    uint32_t m = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+// Largest bucket (entries) into stat[0] and the number of nonempty buckets
+// into stat[1] (both zeroed by the caller).
+__global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, uint32_t *stat) {
+    uint32_t m = 0, used = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
         m = max(m, counts[i]);
+        used += counts[i] != 0;
+    }
     m = __reduce_max_sync(0xffffffffu, m);
-    if (lane_id() == 0 && m) atomicMax(dmax, m);
+    used = __reduce_add_sync(0xffffffffu, used);
+    if (lane_id() == 0 && m) atomicMax(&stat[0], m);
+    if (lane_id() == 0 && used) atomicAdd(&stat[1], used);
 }
 
-// Round rd runs while the largest bucket still holds more than `thr` items
-// (kPiece, or kTailItems for a small bucket set that may end on teams).
-__global__ void k_round_plan(const uint32_t *dmax, uint32_t p0, uint32_t rounds, uint32_t tail,
-                             RoundPlan *plan) {
+// Shape of phase 3 from the actual entries (their count at off0[nb], the
+// largest bucket and the nonempty buckets in stat): round 0 gives every
+// resident thread one chunk of p0 = ceil(entries / resident) entries (at
+// least kP0Min), so it runs as one wave; round rd runs while the largest
+// bucket still holds more than `thr` items (kPiece, or kTailItems when few
+// buckets are in use and the last stage may run on teams).
+__global__ void k_round_plan(const uint32_t *stat, const uint32_t *total, uint32_t resident,
+                             uint32_t rounds, const uint32_t *off0, const uint32_t *offa, const uint32_t *offb,
+                             Xyzz *pa, Xyzz *pb, RoundPlan *plan) {
     if (threadIdx.x || blockIdx.x) return;
-    uint32_t x = *dmax, last = 0;
+    const uint32_t entries = *total;
+    const uint32_t p0 = max(kP0Min, (uint32_t)(((uint64_t)entries + resident - 1) / resident));
+    const bool tail = stat[1] <= kTailBuckets;
+    uint32_t x = stat[0], last = 0;
     const uint32_t thr = tail ? kTailItems : kPiece;
     for (uint32_t rd = 0; rd < (uint32_t)kMaxRounds; rd++) {
         const bool run = rd < rounds && x > thr;
@@ -246,14 +429,20 @@ __global__ void k_round_plan(const uint32_t *dmax, uint32_t p0, uint32_t rounds,
     }
     plan->last = last;
     plan->team = tail && x > kTailMin;
+    plan->p0 = p0;
+    plan->p0neg = -(int)p0;
+    // Round rd writes buffer rd % 2 (pa, pb).
+    plan->off = last == 0 ? off0 : (((last - 1) & 1) ? offb : offa);
+    plan->parts = (last == 0 || ((last - 1) & 1)) ? pa : pb;
 }
 
 // Round 0.  Thread c adds entries [c p0, (c + 1) p0); bucket b's items are
 // off1[b] .. off1[b + 1] - 1, one per chunk its entries meet, in chunk order.
 __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32_t *__restrict__ off0,
-                               const uint32_t *__restrict__ off1, uint32_t nb, uint32_t p0, DevJobs dj,
+                               const uint32_t *__restrict__ off1, uint32_t nb, DevJobs dj,
                                const RoundPlan *__restrict__ plan, Xyzz *__restrict__ pieces) {
     if (!plan->run[0]) return;
+    const uint32_t p0 = plan->p0;
     const uint32_t total = off0[nb];  // entries (zero digits have none)
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if ((uint64_t)c * p0 >= total) return;
@@ -326,55 +515,92 @@ __global__ void k_buckets_final(FinalItems fi, DevJobs dj, uint32_t nb,
     buckets[b] = acc;
 }
 
-// Last stage on teams, block b for bucket b: lane l adds items l, l + 32,
-// ..., then the lanes' sums are added in a tree.
+// Last stage on teams (few buckets in use, each with up to kTailItems
+// items), in two levels.  Level A: team g sums slice g of the items, at most
+// kSlice of them (two per lane, then a tree over the lanes); bucket b's
+// slices are off_s[b] .. off_s[b + 1] - 1 (a scan of ceil(items / kSlice)),
+// and slice k covers its items kSlice k .. kSlice (k + 1) - 1.  Level B: a
+// team per bucket adds its at most kTailItems / kSlice partial sums in a
+// tree.  Every team operation spreads one point addition over the block's
+// four warps (team.cuh), so the depth is about ten additions.
+constexpr uint32_t kSlice = 64;
 constexpr int kBtAcc = 0, kBtIn = 4, kBtTmp = 8, kBtT = 12;
+static_assert(kTailItems / kSlice <= 32, "level B sums one partial per lane");
+
 __global__ void __launch_bounds__(kTeamThreads)
-    k_buckets_team(FinalItems fi, DevJobs dj, const RoundPlan *__restrict__ plan,
+    k_tail_slices(FinalItems fi, DevJobs dj, uint32_t nb, const uint32_t *__restrict__ off_s,
+                  const RoundPlan *__restrict__ plan) {
+    __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
+    if (!plan->team) return;
+    const uint32_t l = team_lane(), w = team_warp();
+    const bool entries = plan->last == 0;
+    const uint32_t *off = plan->off;
+    const Xyzz *in = entries ? nullptr : (((plan->last - 1) & 1) ? fi.in1 : fi.in0);
+    Xyzz *parts = plan->parts;
+    const uint32_t nslices = off_s[nb];
+    for (uint32_t g = blockIdx.x; g < nslices; g += gridDim.x) {  // block-uniform
+        const uint32_t b = upper_index(off_s, nb, g);
+        const uint32_t lo = off[b] + (g - off_s[b]) * kSlice;
+        const uint32_t hi = min(lo + kSlice, off[b + 1]);
+        const Affine *table = entries ? dj.jobs[search(dj.bbase, 0, dj.count, b)].table : nullptr;
+        // Coordinate w of item j (a table point with sign, or a partial sum).
+        auto fetch = [&](uint32_t j) -> Fq {
+            if (j >= hi) return fe_zero<FqP>();
+            if (!entries) return team_fetch(in + j, true);
+            const uint32_t v = fi.sorted[j];
+            if (w >= 2) return fe_mont_one<FqP>();
+            const Fq c = fe_ldg<FqP>(reinterpret_cast<const char *>(table + (v >> 1)) + 32 * w);
+            return (w == 1 && (v & 1)) ? fe_neg<FqP>(c) : c;
+        };
+        tf_store(f, kBtAcc + w, fetch(lo + l));
+        tf_store(f, kBtIn + w, fetch(lo + 32 + l));
+        __syncthreads();
+        if (hi - lo > 32) team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
+        for (uint32_t d = 16; d >= 1; d >>= 1) {
+            if (d >= hi - lo) continue;  // lanes d.. hold infinity
+            team_shift(f, kBtAcc, kBtTmp, (int)d);
+            team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
+        }
+        if (l == 0) team_put(f, kBtAcc, parts + g);
+        __syncthreads();  // the slots are reused by the next slice
+    }
+}
+
+__global__ void __launch_bounds__(kTeamThreads)
+    k_tail_buckets(uint32_t nb, const uint32_t *__restrict__ off_s, const RoundPlan *__restrict__ plan,
                    Xyzz *__restrict__ buckets) {
     __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
     if (!plan->team) return;
-    const uint32_t b = blockIdx.x, l = team_lane(), w = team_warp();
-    const uint32_t last = plan->last;
-    const bool entries = last == 0;
-    const uint32_t *off = entries ? fi.off0 : (((last - 1) & 1) ? fi.off_b : fi.off_a);
-    const Xyzz *in = entries ? nullptr : (((last - 1) & 1) ? fi.in1 : fi.in0);
-    const Affine *table = dj.jobs[search(dj.bbase, 0, dj.count, b)].table;
-    const uint32_t lo = off[b], hi = off[b + 1];
-    // Coordinate w of item j (a table point with sign, or a partial sum).
-    auto fetch = [&](uint32_t j) -> Fq {
-        if (j >= hi) return fe_zero<FqP>();
-        if (!entries) return team_fetch(in + j, true);
-        const uint32_t v = fi.sorted[j];
-        if (w >= 2) return fe_mont_one<FqP>();
-        const Fq c = fe_ldg<FqP>(reinterpret_cast<const char *>(table + (v >> 1)) + 32 * w);
-        return (w == 1 && (v & 1)) ? fe_neg<FqP>(c) : c;
-    };
-    team_set_inf_nosync(f, kBtAcc);
-    for (uint32_t j0 = lo; j0 < hi; j0 += 32) {
-        tf_store(f, kBtIn + w, fetch(j0 + l));
+    const uint32_t l = team_lane(), w = team_warp();
+    const Xyzz *parts = plan->parts;
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {  // block-uniform
+        const uint32_t lo = off_s[b], cnt = off_s[b + 1] - lo;
+        if (cnt <= 1) {
+            if (threadIdx.x == 0) buckets[b] = cnt ? parts[lo] : xyzz_inf();
+            continue;
+        }
+        tf_store(f, kBtAcc + w, team_fetch(parts + lo + l, l < cnt));
         __syncthreads();
-        team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
+        for (uint32_t d = 16; d >= 1; d >>= 1) {
+            if (d >= cnt) continue;
+            team_shift(f, kBtAcc, kBtTmp, (int)d);
+            team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
+        }
+        if (l == 0) team_put(f, kBtAcc, buckets + b);
+        __syncthreads();
     }
-    for (int d = 16; d >= 1; d >>= 1) {
-        team_shift(f, kBtAcc, kBtTmp, d);
-        team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
-    }
-    if (l == 0) team_put(f, kBtAcc, buckets + b);
 }
 
-// Shape of phase 3 for `total` entries in `nb` buckets with at most `worst`
-// entries in one bucket.
+// Host bounds of phase 3 for at most `total` entries in `nb` buckets with
+// at most `worst` entries in one bucket; the actual chunk size and the
+// rounds that run are decided on the device (k_round_plan).
 struct AccumShape {
-    uint32_t p0;
-    int rounds;
-    size_t cap0;  // items after round 0 (bound)
-    bool tail;
+    int rounds;        // rounds launched (the worst case; gated on the device)
+    size_t cap0;       // items after round 0 (bound)
+    uint32_t resident; // threads of one wave of k_pieces_first
+    uint32_t blocks;   // its grid
 };
 
-// Round 0 runs as one wave: every resident thread of the GPU takes one chunk
-// of p0 = ceil(total / threads) entries (at least kP0Min), so no thread waits
-// for a partial last wave.
 AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms) {
     static const int per_sm = [] {
         int b = 0;
@@ -385,34 +611,40 @@ AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms) {
         return b;
     }();
     AccumShape a;
-    const size_t threads = (size_t)std::max(sms, 1) * per_sm * 128;
-    a.p0 = (uint32_t)std::max<size_t>(kP0Min, (total + threads - 1) / threads);
+    a.blocks = (uint32_t)std::max(sms, 1) * (uint32_t)per_sm;
+    a.resident = a.blocks * 128;
+    // p0 >= kP0Min bounds the rounds; p0 >= entries / resident bounds the
+    // chunks, and every chunk emits one item per bucket it meets.
     a.rounds = 0;
     for (size_t x = worst; x > kPiece && a.rounds < kMaxRounds; a.rounds++)
-        x = (x + (a.rounds ? kPiece : a.p0) - 1) / (a.rounds ? kPiece : a.p0);
-    a.cap0 = (total + a.p0 - 1) / a.p0 + nb + 1;
-    a.tail = nb <= kTailBuckets;
+        x = (x + (a.rounds ? kPiece : kP0Min) - 1) / (a.rounds ? kPiece : kP0Min);
+    const size_t chunks = std::min<size_t>(a.resident, (total + kP0Min - 1) / kP0Min);
+    // The team tail's partial sums (at most entries / kSlice + nb) reuse a
+    // piece buffer.
+    a.cap0 = std::max<size_t>(chunks, (total + kSlice - 1) / kSlice) + nb + 1;
     return a;
 }
 
 struct AccumBufs {
     uint32_t *offa, *offb;
     Xyzz *pa, *pb;
-    uint32_t *dmax;
+    uint32_t *stat;  // two words
     RoundPlan *plan;
     void *scan_tmp;
+    uint32_t *offs;  // nb + 1 words: slice offsets of the team tail
 };
 
 // Phase 3 launches: sorted entries (offsets off0, histogram counts; at most
 // `total` entries) -> one point per bucket.
 int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint32_t *off0, uint32_t nb,
-                      size_t total, const AccumShape &a, const DevJobs &dj, const AccumBufs &w,
-                      Xyzz *buckets, int sms, cudaStream_t s) {
-    ZK_CUDA_TRY(cudaMemsetAsync(w.dmax, 0, sizeof(uint32_t), s));
+                      const AccumShape &a, const DevJobs &dj, const AccumBufs &w, Xyzz *buckets, int sms,
+                      cudaStream_t s) {
+    ZK_CUDA_TRY(cudaMemsetAsync(w.stat, 0, 2 * sizeof(uint32_t), s));
     const unsigned mb = (unsigned)std::min<size_t>((nb + 255) / 256, (size_t)sms * 4);
-    k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, w.dmax);
+    k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, w.stat);
     ZK_LAUNCHED();
-    k_round_plan<<<1, 32, 0, s>>>(w.dmax, a.p0, (uint32_t)a.rounds, a.tail ? 1u : 0u, w.plan);
+    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, (uint32_t)a.rounds, off0, w.offa, w.offb, w.pa,
+                                  w.pb, w.plan);
     ZK_LAUNCHED();
     const uint32_t *off_prev = off0;
     size_t cap = a.cap0;
@@ -421,10 +653,8 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
         Xyzz *out = (rd % 2 == 0) ? w.pa : w.pb;
         const uint32_t *gate = &w.plan->run[rd];
         if (rd == 0) {
-            ZK_TRY(scan_exclusive(off_prev, off_new, nb, -(int)a.p0, w.scan_tmp, s, gate));
-            const size_t chunks = std::max<size_t>((total + a.p0 - 1) / a.p0, 1);  // 0 entries: all zero
-            k_pieces_first<<<(unsigned)((chunks + 127) / 128), 128, 0, s>>>(sorted, off_prev, off_new, nb,
-                                                                           a.p0, dj, w.plan, out);
+            ZK_TRY(scan_exclusive(off_prev, off_new, nb, -(int)kP0Min, w.scan_tmp, s, gate, &w.plan->p0neg));
+            k_pieces_first<<<a.blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb, dj, w.plan, out);
         } else {
             ZK_TRY(scan_exclusive(off_prev, off_new, nb, (int)kPiece, w.scan_tmp, s, gate));
             const Xyzz *in = (rd % 2 == 1) ? w.pa : w.pb;
@@ -438,10 +668,14 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
     const FinalItems fi{sorted, off0, w.pa, w.pb, w.offa, w.offb};
     k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(fi, dj, nb, w.plan, buckets);
     ZK_LAUNCHED();
-    if (a.tail) {
-        k_buckets_team<<<nb, kTeamThreads, 0, s>>>(fi, dj, w.plan, buckets);
-        ZK_LAUNCHED();
-    }
+    // Gated on the device: runs when few buckets are in use and they still
+    // hold many items (the round plan's `team`).
+    ZK_TRY(scan_exclusive(nullptr, w.offs, nb, (int)kSlice, w.scan_tmp, s, &w.plan->team, nullptr, &w.plan->off));
+    const unsigned tb = (unsigned)std::min<size_t>(std::max<uint32_t>(nb, 1), (size_t)sms * 8);
+    k_tail_slices<<<tb, kTeamThreads, 0, s>>>(fi, dj, nb, w.offs, w.plan);
+    ZK_LAUNCHED();
+    k_tail_buckets<<<tb, kTeamThreads, 0, s>>>(nb, w.offs, w.plan, buckets);
+    ZK_LAUNCHED();
     return ZK_OK;
 }
 
@@ -449,70 +683,104 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
 // its scans and trees have few additions in flight, so the latency of one
 // addition, not the SM's throughput, sets their time.
 //
-// Level 0 reads the buckets.  Every level cuts its items into segments of at
-// most kSeg, and one team reduces one segment: with items k < m carrying
-// points X_k and Y_k (Y = X at level 0),
-//     V = sum_k Y_k + 2^f sum_k k X_k,   S = sum_k X_k,   f = kSegLog * level.
-// Segment g of a level becomes item g of the next one (X = S, Y = V); for
-// k = kSeg g + j,
-//     sum_k Y_k + 2^f sum_k k X_k = sum_g (V_g + 2^(f + kSegLog) g S_g),
+// Level 0 reads the buckets.  Every level cuts its m items into segments of
+// 2^g, and one team reduces one segment: with items k carrying points X_k
+// and Y_k (Y = X at level 0),
+//     V = sum_k Y_k + 2^f sum_k k X_k,   S = sum_k X_k,
+// f the sum of the earlier levels' g.  Segment h of a level becomes item h
+// of the next one (X = S, Y = V); for k = 2^g h + j,
+//     sum_k Y_k + 2^f sum_k k X_k = sum_h (V_h + 2^(f + g) h S_h),
 // so the sum is invariant across levels, and at level 0 it is
 // sum_b S_b + sum_b b S_b = sum_b (b + 1) S_b.  The level whose items fit one
-// segment is final: its V, doubled `shift` times, is the MSM.
+// team (at most 32) is final: its V, doubled `dbl` times, is the MSM.
+//
+// Segments are 2^8 items while a level holds at least 2^13 (many teams, each
+// with a serial part), else 2^5 (one item per lane, no serial part), so a
+// small bucket set (quantised scalars: 2^8 buckets) spreads over several
+// teams instead of one team walking all of them.  The schedule depends only
+// on log2 of the bucket count, which the device may lower (short scalars),
+// so every kernel derives it from the job's logB.
 //
 // Within a segment, lane l owns the q = seg / 32 consecutive items
 // k = l q + t and runs the suffix form  w_l = sum_t t X_{lq+t}  (adding the
 // running sum r of the later items before each new item), r_l = sum_t X;
 // then sum_k k X_k = sum_l (w_l + q l r_l) and sum_l l r_l = sum_{l >= 1}
 // R_l with R the suffix scan of r over the lanes.
-constexpr int kSegLog = 8;
-constexpr uint32_t kSeg = 1u << kSegLog;
-constexpr int kMaxLevels = 3;
-// Level-1 outputs per MSM that level 2 reads: 2^(logB - 2 kSegLog) <= kL2Per.
-constexpr uint32_t kL2Per = 8;
-static_assert(kMaxWindow - 1 <= 3 * kSegLog && (1u << (kMaxWindow - 1 - 2 * kSegLog)) <= kL2Per,
-              "reduction levels");
+struct RedSched {
+    uint32_t levels;
+    uint32_t mlog[kMaxLevels];  // log2 of the items at each level
+    uint32_t glog[kMaxLevels];  // log2 of the segment (the final level: all items)
+};
+
+__host__ __device__ constexpr RedSched red_sched(uint32_t logB) {
+    RedSched r{};
+    uint32_t m = logB;
+    for (uint32_t L = 0; L < (uint32_t)kMaxLevels; L++) {
+        r.mlog[L] = m;
+        if (m <= 5 || L + 1 == (uint32_t)kMaxLevels) {
+            r.glog[L] = m;
+            r.levels = L + 1;
+            break;
+        }
+        r.glog[L] = m >= 13 ? 8 : 5;
+        m -= r.glog[L];
+    }
+    return r;
+}
+static_assert(kMaxWindow - 1 <= 8 + 5 + 5 + 5, "reduction levels");
+
+// Item buffers of levels 1 .. kMaxLevels - 1 (V and S); job j's items of
+// level L start at jobs[j].lbase[L - 1].
+struct RedBufs {
+    Xyzz *v[kMaxLevels];
+    Xyzz *s[kMaxLevels];
+};
 
 // Shared-memory slots of the reduction team (points take four slots).
 constexpr int kSlR = 0, kSlW = 4, kSlYA = 8, kSlIn = 12, kSlYIn = 16, kSlTmp = 20, kSlT = 24;
 constexpr int kSlots = kSlT + kTeamTemps;
 
 __global__ void __launch_bounds__(kTeamThreads)
-    k_reduce_team(const Xyzz *__restrict__ buckets, Xyzz *__restrict__ v1, Xyzz *__restrict__ s1,
-                  Xyzz *__restrict__ v2, Xyzz *__restrict__ s2, DevJobs dj, uint32_t level) {
+    k_reduce_team(const Xyzz *__restrict__ buckets, RedBufs rb, DevJobs dj, uint32_t level) {
     __shared__ uint32_t f[kSlots * 8 * 32];
     const uint32_t job = blockIdx.y;
-    const uint32_t logB = dj.jobs[job].logB;
-    if (level > 0 && logB <= kSegLog * level) return;  // final at an earlier level
-    const uint32_t m = 1u << (logB - kSegLog * level);
-    const uint32_t seg = min(m, kSeg);
-    if (blockIdx.x >= m / seg) return;
-    const bool final_level = m <= kSeg;
+    const JobDesc &J = dj.jobs[job];
+    const RedSched r = red_sched(J.logB);
+    if (level >= r.levels) return;  // final at an earlier level
+    const bool final_level = level + 1 == r.levels;
+    const uint32_t seg = 1u << r.glog[level];
+    if (blockIdx.x >= (1u << (r.mlog[level] - r.glog[level]))) return;
+    uint32_t fl = 0;  // f: doublings of this level's weights
+    for (uint32_t L = 0; L < level; L++) fl += r.glog[L];
     const Xyzz *X, *Y;
     if (level == 0) {
         X = buckets + dj.bbase[job];
         Y = nullptr;
-    } else if (level == 1) {
-        X = s1 + dj.kbase[job];
-        Y = v1 + dj.kbase[job];
     } else {
-        X = s2 + (size_t)kL2Per * job;
-        Y = v2 + (size_t)kL2Per * job;
+        X = rb.s[level] + J.lbase[level - 1];
+        Y = rb.v[level] + J.lbase[level - 1];
     }
     X += (size_t)blockIdx.x * seg;
     if (Y) Y += (size_t)blockIdx.x * seg;
     const uint32_t l = team_lane(), w = team_warp();
     const uint32_t q = seg >= 32 ? seg / 32 : 1;
 
-    team_set_inf_nosync(f, kSlR);
-    team_set_inf_nosync(f, kSlW);
-    team_set_inf_nosync(f, kSlYA);
     // Serial part, items t = q - 1 .. 0 of this lane; the next item's
-    // coordinate is fetched while the current one is added.
+    // coordinate is fetched while the current one is added.  The first item
+    // starts the running sums (w stays infinity).
+    team_set_inf_nosync(f, kSlW);
     uint32_t k = l * q + (q - 1);
-    Fq nx = team_fetch(X + k, k < seg);
-    Fq ny = Y ? team_fetch(Y + k, k < seg) : fe_zero<FqP>();
-    for (uint32_t t = q; t-- > 0;) {
+    tf_store(f, kSlR + w, team_fetch(X + k, k < seg));
+    if (Y) tf_store(f, kSlYA + w, team_fetch(Y + k, k < seg));
+    if (!Y) team_set_inf_nosync(f, kSlYA);
+    Fq nx = fe_zero<FqP>(), ny = fe_zero<FqP>();
+    if (q > 1) {
+        k = l * q + (q - 2);
+        nx = team_fetch(X + k, k < seg);
+        if (Y) ny = team_fetch(Y + k, k < seg);
+    }
+    __syncthreads();
+    for (uint32_t t = q - 1; t-- > 0;) {
         tf_store(f, kSlIn + w, nx);
         if (Y) tf_store(f, kSlYIn + w, ny);
         if (t > 0) {
@@ -525,47 +793,66 @@ __global__ void __launch_bounds__(kTeamThreads)
         team_add(f, kSlR, kSlIn, kSlR, kSlT);
         if (Y) team_add(f, kSlYA, kSlYIn, kSlYA, kSlT);
     }
-    // Inclusive suffix scan of r over the lanes: R_l = sum_{l' >= l} r_l'.
-    for (int d = 1; d < 32; d <<= 1) {
-        team_shift(f, kSlR, kSlTmp, d);
+    // Inclusive suffix scan of r over the lanes: R_l = sum_{l' >= l} r_l'
+    // (lanes past the segment hold infinity).
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        if (d >= seg) break;
+        team_shift(f, kSlR, kSlTmp, (int)d);
         team_add(f, kSlR, kSlTmp, kSlR, kSlT);
     }
     // term_l = w_l + q R_l (l >= 1), then u_l = y_l + 2^f term_l.
     team_copy(f, kSlR, kSlTmp, l >= 1);
     for (uint32_t e = q; e > 1; e >>= 1) team_dbl(f, kSlTmp, kSlTmp, kSlT);
     team_add(f, kSlW, kSlTmp, kSlW, kSlT);
-    for (uint32_t e = 0; e < kSegLog * level; e++) team_dbl(f, kSlW, kSlW, kSlT);
+    for (uint32_t e = 0; e < fl; e++) team_dbl(f, kSlW, kSlW, kSlT);
     if (Y) team_add(f, kSlW, kSlYA, kSlW, kSlT);
     // Sum over the lanes (lane 0), then sum_k Y_k = R_0 at level 0.
-    for (int d = 16; d >= 1; d >>= 1) {
-        team_shift(f, kSlW, kSlTmp, d);
+    for (uint32_t d = 16; d >= 1; d >>= 1) {
+        if (d >= seg) continue;
+        team_shift(f, kSlW, kSlTmp, (int)d);
         team_add(f, kSlW, kSlTmp, kSlW, kSlT);
     }
     if (!Y) team_add(f, kSlW, kSlR, kSlW, kSlT);
     if (final_level) {
-        const uint32_t sh = min(dj.jobs[job].shift, (uint32_t)kScalarBits);
-        for (uint32_t e = 0; e < sh; e++) team_dbl(f, kSlW, kSlW, kSlT);  // x 2^shift
-        if (threadIdx.x == 0) xyzz_store_canonical(dj.jobs[job].out, team_point(f, kSlW));
+        const uint32_t sh = min(J.dbl, (uint32_t)kScalarBits);
+        for (uint32_t e = 0; e < sh; e++) team_dbl(f, kSlW, kSlW, kSlT);  // x 2^dbl
+        if (threadIdx.x == 0) xyzz_store_canonical(J.out, team_point(f, kSlW));
     } else if (l == 0) {
-        const size_t o = (level == 0 ? dj.kbase[job] : (size_t)kL2Per * job) + blockIdx.x;
-        team_put(f, kSlW, (level == 0 ? v1 : v2) + o);
-        team_put(f, kSlR, (level == 0 ? s1 : s2) + o);
+        const size_t o = J.lbase[level] + blockIdx.x;
+        team_put(f, kSlW, rb.v[level + 1] + o);
+        team_put(f, kSlR, rb.s[level + 1] + o);
     }
 }
 
-// Launches the reduction levels for jobs whose bucket counts are 2^logB[k].
-int launch_reduce(const Xyzz *buckets, Xyzz *v1, Xyzz *s1, Xyzz *v2, Xyzz *s2, const DevJobs &dj,
-                  const uint32_t *logB, size_t count, cudaStream_t s) {
+// Item capacity of reduction level L (1 .. kMaxLevels - 1) and the teams of
+// level L (0 ..) for a job whose bucket count may be any 2^logB with
+// logB in [lo, hi] (the device lowers logB for short scalars).
+constexpr uint32_t red_cap(uint32_t lo, uint32_t hi, uint32_t L) {
+    uint32_t c = 0;
+    for (uint32_t b = lo; b <= hi; b++) {
+        const RedSched r = red_sched(b);
+        if (L < r.levels) c = std::max(c, 1u << r.mlog[L]);
+    }
+    return c;
+}
+constexpr uint32_t red_teams(uint32_t lo, uint32_t hi, uint32_t L) {
+    uint32_t t = 0;
+    for (uint32_t b = lo; b <= hi; b++) {
+        const RedSched r = red_sched(b);
+        if (L < r.levels) t = std::max(t, 1u << (r.mlog[L] - r.glog[L]));
+    }
+    return t;
+}
+
+// Launches the reduction levels for jobs whose bucket counts are 2^logB with
+// logB in [lo[k], hi[k]].
+int launch_reduce(const Xyzz *buckets, const RedBufs &rb, const DevJobs &dj, const uint32_t *lo,
+                  const uint32_t *hi, size_t count, cudaStream_t s) {
     for (uint32_t level = 0; level < (uint32_t)kMaxLevels; level++) {
         uint32_t gx = 0;
-        for (size_t k = 0; k < count; k++) {
-            if (level > 0 && logB[k] <= kSegLog * level) continue;
-            const uint32_t lm = logB[k] - kSegLog * level;
-            gx = std::max(gx, lm > (uint32_t)kSegLog ? 1u << (lm - kSegLog) : 1u);
-        }
+        for (size_t k = 0; k < count; k++) gx = std::max(gx, red_teams(lo[k], hi[k], level));
         if (!gx) break;
-        k_reduce_team<<<dim3(gx, (unsigned)count), kTeamThreads, 0, s>>>(buckets, v1, s1, v2, s2, dj,
-                                                                          level);
+        k_reduce_team<<<dim3(gx, (unsigned)count), kTeamThreads, 0, s>>>(buckets, rb, dj, level);
         ZK_LAUNCHED();
     }
     return ZK_OK;
@@ -576,8 +863,11 @@ int launch_recode_c(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscala
                     uint32_t table_n, uint32_t *counts, uint32_t *cursor, uint32_t *sorted,
                     cudaStream_t s) {
     if (nscalars == 0) return ZK_OK;
-    k_recode<C, SCATTER><<<(nscalars + 255) / 256, 256, 0, s>>>(dj, g0, g1, table_n, counts, cursor,
-                                                               sorted);
+    k_recode_short<SCATTER><<<(nscalars + kRecPer - 1) / kRecPer, kRecThreads, 0, s>>>(dj, g0, g1, counts,
+                                                                                      cursor, sorted);
+    ZK_LAUNCHED();
+    k_recode<C, SCATTER><<<(nscalars + kRecThreads - 1) / kRecThreads, kRecThreads, 0, s>>>(dj, g0, g1, table_n,
+                                                                                          counts, cursor, sorted);
     ZK_LAUNCHED();
     return ZK_OK;
 }
@@ -624,50 +914,6 @@ int msm_pick_window(zk_ctx *ctx, size_t n, size_t count) {
     return default_window(n);
 }
 
-// Reads, per job, the largest bit length and the fewest trailing zeros of
-// the recentred scalars (one pass over the scalars and a stream sync).
-static int scalar_stats(zk_ctx *ctx, const MsmJob *jobs, size_t count, std::vector<uint32_t> &len,
-                        std::vector<uint32_t> &tz, cudaStream_t s) {
-    int err = ZK_OK;
-    const size_t jd_bytes = align_up(count * sizeof(JobDesc), 256);
-    const size_t pre_bytes = align_up((count + 1) * 4, 256);
-    char *jt = (char *)scratch(ctx, "msm.statjobs", jd_bytes + pre_bytes, &err);
-    uint32_t *st = (uint32_t *)scratch(ctx, "msm.stats", 2 * align_up(count * 4, 256), &err);
-    if (!jt || !st) return err;
-    uint32_t *st_len = st, *st_tz = st + align_up(count * 4, 256) / 4;
-    std::vector<char> h(jd_bytes + pre_bytes, 0);
-    JobDesc *hd = (JobDesc *)h.data();
-    uint32_t *hs = (uint32_t *)(h.data() + jd_bytes);
-    for (size_t k = 0; k < count; k++) {
-        hd[k].scalars = jobs[k].scalars;
-        hd[k].n = jobs[k].n;
-        hs[k + 1] = hs[k] + jobs[k].n;
-    }
-    ZK_TRY(upload(ctx, jt, h.data(), h.size(), s));
-    ZK_CUDA_TRY(cudaMemsetAsync(st_len, 0, count * 4, s));
-    ZK_CUDA_TRY(cudaMemsetAsync(st_tz, 0xff, count * 4, s));
-    DevJobs dj;
-    dj.jobs = (const JobDesc *)jt;
-    dj.sbase = (const uint32_t *)(jt + jd_bytes);
-    dj.count = (uint32_t)count;
-    const uint32_t total = hs[count];
-    k_scalar_stats<<<(total + 255) / 256, 256, 0, s>>>(dj, total, st_len, st_tz);
-    ZK_LAUNCHED();
-    if (ctx->stat_cap < 2 * count) {
-        if (ctx->stat_host) cudaFreeHost(ctx->stat_host);
-        ctx->stat_host = nullptr;
-        ctx->stat_cap = 0;
-        ZK_CUDA_TRY(cudaHostAlloc((void **)&ctx->stat_host, 2 * count * 4, cudaHostAllocDefault));
-        ctx->stat_cap = 2 * count;
-    }
-    ZK_CUDA_TRY(cudaMemcpyAsync(ctx->stat_host, st_len, count * 4, cudaMemcpyDeviceToHost, s));
-    ZK_CUDA_TRY(cudaMemcpyAsync(ctx->stat_host + count, st_tz, count * 4, cudaMemcpyDeviceToHost, s));
-    ZK_CUDA_TRY(cudaStreamSynchronize(s));
-    len.assign(ctx->stat_host, ctx->stat_host + count);
-    tz.assign(ctx->stat_host + count, ctx->stat_host + 2 * count);
-    return ZK_OK;
-}
-
 int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed, cudaStream_t s) {
     if (count == 0) return ZK_OK;
     Shared &sh = *ctx->sh;
@@ -680,140 +926,164 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     }
     if (total_in >= (1ull << 32)) return ZK_EINVAL;
     // Small-scalar path: when the recentred scalars of a job are short (e.g.
-    // quantised int8 values times 2^16), shift out their common trailing
-    // zeros (the result is doubled back at the end) and use only the windows
-    // that can hold nonzero digits -- one window when the remaining width
-    // fits, read straight from the SRS.  Skipped while capturing a graph
-    // (it reads the statistics back to the host) and for tuning runs.
-    std::vector<uint32_t> len(count, kScalarBits - 1), tz(count, 0);
-    if (c_fixed == 0 && !ctx->capturing && total_in >= kStatsMin)
-        ZK_TRY(scalar_stats(ctx, jobs_in, count, len, tz, s));
+    // quantised int8 values times 2^16), its common trailing zeros are
+    // shifted out and only the windows that can hold digits are used -- one
+    // window when the rest fits, read straight from the base points.  A
+    // statistics pass and a plan kernel decide this on the device (k_msm_plan),
+    // so the host lays out every job for its full-width shape and nothing is
+    // read back; the same launches serve graph capture.  Skipped for tuning
+    // runs (fixed c) and for calls too small to pay for the pass.
+    const bool stats = c_fixed == 0 && total_in >= kStatsMin;
     struct J {
         MsmJob job;
         int c;
-        uint32_t shift, wins;
     };
     std::vector<J> jv(count);
-    size_t total64 = 0, entries64 = 0, nb64 = 0, nblk64 = 0;
+    size_t total64 = 0, entries64 = 0, nb64 = 0;
     for (size_t k = 0; k < count; k++) {
         const MsmJob &m = jobs_in[k];
         int c = c_fixed > 0 ? c_fixed : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
         if (c < kMinWindow || c > kMaxWindow) return ZK_EINVAL;
-        uint32_t shift = 0, wins = (uint32_t)windows_for(c);
-        if (len[k] > (uint32_t)kScalarBits - 1 || (len[k] && tz[k] >= len[k])) return ZK_ECUDA;
-        if (len[k] == 0) {  // all scalars zero
-            c = kMinWindow;
-            wins = 0;
-        } else if (len[k] < (uint32_t)kScalarBits - 1 || tz[k] > 0) {
-            shift = tz[k];
-            const uint32_t eff = len[k] - tz[k];  // bits left after the shift
-            if ((int)eff + 1 <= c) {
-                c = std::max<int>(kMinWindow, (int)eff + 1);
-                wins = 1;
-            } else {
-                wins = (eff + 1 + c - 1) / c;
-            }
-        }
-        jv[k] = {m, c, shift, wins};
+        jv[k] = {m, c};
         total64 += m.n;
-        entries64 += (size_t)m.n * wins;
+        entries64 += (size_t)m.n * windows_for(c);
         nb64 += (size_t)1 << (c - 1);
-        nblk64 += ((size_t)1 << (c - 1)) / kSeg;
     }
     if (nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
     std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) {
         if (a.c != b.c) return a.c < b.c;
-        if (a.job.basis != b.job.basis) return a.job.basis < b.job.basis;
-        return (a.wins > 1) < (b.wins > 1);
+        return a.job.basis < b.job.basis;
     });
-    // Point tables: the base points themselves (SRS, or the Lagrange basis
-    // of H for evaluation-form jobs) for one-window jobs, else the width's
-    // window table of that basis (built on first use, outside timed loops).
-    std::vector<const Affine *> tabs(count);
+    // Point tables: the base points (SRS, or the Lagrange basis of H for
+    // evaluation-form jobs) and the width's window table of that basis
+    // (built on first use, outside timed loops).
+    std::vector<const Affine *> bases(count), tabs(count);
     std::vector<uint32_t> tabn(count);
     for (size_t k = 0; k < count; k++) {
         const int basis = jv[k].job.basis;
         if (basis && (!sh.lag[basis].p || jv[k].job.n != (1u << basis))) return ZK_EINVAL;
-        if (jv[k].wins <= 1) {
-            tabs[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
-            tabn[k] = basis ? (1u << basis) : (uint32_t)sh.srs_n;
-            continue;
-        }
+        bases[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
         size_t need = 1;
         for (size_t j = 0; j < count; j++)
-            if (jv[j].c == jv[k].c && jv[j].job.basis == basis && jv[j].wins > 1)
-                need = std::max(need, (size_t)jv[j].job.n);
+            if (jv[j].c == jv[k].c && jv[j].job.basis == basis) need = std::max(need, (size_t)jv[j].job.n);
         const WindowTable *t;
         ZK_TRY(table_get(ctx, jv[k].c, need, basis, &t, s));
         tabs[k] = (const Affine *)t->buf.p;
         tabn[k] = (uint32_t)t->n;
     }
-    const uint32_t total = (uint32_t)total64;
+    // Width-16 tables that already exist (SRS loading builds the SRS's),
+    // for the single-window path of scalars with 16 or more trailing zeros.
+    std::vector<const Affine *> t16s(count, nullptr);
+    std::vector<uint32_t> t16n(count, 0);
+    if (stats) {
+        std::lock_guard<std::mutex> g(sh.mu);
+        for (size_t k = 0; k < count; k++)
+            for (auto &t : sh.tables)
+                if (t.c == 16 && t.basis == jv[k].job.basis && t.n >= jv[k].job.n) {
+                    t16s[k] = (const Affine *)t.buf.p;
+                    t16n[k] = (uint32_t)t.n;
+                    break;
+                }
+    }
     const uint32_t nb = (uint32_t)nb64;
     const size_t entries_max = entries64;
 
-    // Phase 3 shape: a bucket holds at most max_n W entries (all of a job's
+    // Phase 3 bounds: a bucket holds at most max_n W entries (all of a job's
     // digits in one bucket).
     size_t worst = 1;
     for (size_t k = 0; k < count; k++)
-        worst = std::max(worst, (size_t)jv[k].job.n * std::max<uint32_t>(jv[k].wins, 1));
+        worst = std::max(worst, (size_t)jv[k].job.n * windows_for(jv[k].c));
     const AccumShape shape = accum_shape(entries_max, worst, nb, sh.sms);
     const size_t piece_cap = shape.cap0;
+    // Reduction levels: a job's bucket count is 2^logB with logB between
+    // kMinWindow - 1 (short scalars, decided on the device) and c - 1.
+    std::vector<uint32_t> lo(count), hi(count);
+    size_t lvl_items[kMaxLevels] = {0, 0, 0, 0};
+    for (size_t k = 0; k < count; k++) {
+        hi[k] = (uint32_t)(jv[k].c - 1);
+        lo[k] = stats ? (uint32_t)(kMinWindow - 1) : hi[k];
+        for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++) lvl_items[L] += red_cap(lo[k], hi[k], L);
+    }
 
     // Workspace.
     int err = ZK_OK;
     const size_t jd_bytes = align_up(count * sizeof(JobDesc), 256);
     const size_t pre_bytes = align_up((count + 1) * 4, 256);
-    char *jt = (char *)scratch(ctx, "msm.jobs", jd_bytes + 3 * pre_bytes, &err);
+    char *jt = (char *)scratch(ctx, "msm.jobs", jd_bytes + 2 * pre_bytes, &err);
     uint32_t *counts = (uint32_t *)scratch(ctx, "msm.counts", (nb + 1) * 4, &err);
     uint32_t *off0 = (uint32_t *)scratch(ctx, "msm.off0", (nb + 1) * 4, &err);
     uint32_t *offa = (uint32_t *)scratch(ctx, "msm.offa", (nb + 1) * 4, &err);
     uint32_t *offb = (uint32_t *)scratch(ctx, "msm.offb", (nb + 1) * 4, &err);
     uint32_t *cursor = (uint32_t *)scratch(ctx, "msm.cursor", (nb + 1) * 4, &err);
+    uint32_t *offs = (uint32_t *)scratch(ctx, "msm.offs", (nb + 1) * 4, &err);
     uint32_t *sorted = (uint32_t *)scratch(ctx, "msm.sorted", std::max<size_t>(entries_max, 1) * 4, &err);
     Xyzz *pa = (Xyzz *)scratch(ctx, "msm.piecea", piece_cap * sizeof(Xyzz), &err);
     Xyzz *pb = (Xyzz *)scratch(ctx, "msm.pieceb", piece_cap * sizeof(Xyzz), &err);
     Xyzz *buckets = (Xyzz *)scratch(ctx, "msm.buckets", nb64 * sizeof(Xyzz), &err);
-    Xyzz *bval = (Xyzz *)scratch(ctx, "msm.bval", std::max<size_t>(nblk64, 1) * sizeof(Xyzz), &err);
-    Xyzz *bsum = (Xyzz *)scratch(ctx, "msm.bsum", std::max<size_t>(nblk64, 1) * sizeof(Xyzz), &err);
-    Xyzz *bv2 = (Xyzz *)scratch(ctx, "msm.bv2", count * kL2Per * sizeof(Xyzz), &err);
-    Xyzz *bs2 = (Xyzz *)scratch(ctx, "msm.bs2", count * kL2Per * sizeof(Xyzz), &err);
+    static const char *const kRedNames[kMaxLevels][2] = {
+        {"", ""}, {"msm.rv1", "msm.rs1"}, {"msm.rv2", "msm.rs2"}, {"msm.rv3", "msm.rs3"}};
+    RedBufs rb{};
+    bool red_ok = true;
+    for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++) {
+        const size_t bytes = std::max<size_t>(lvl_items[L], 1) * sizeof(Xyzz);
+        rb.v[L] = (Xyzz *)scratch(ctx, kRedNames[L][0], bytes, &err);
+        rb.s[L] = (Xyzz *)scratch(ctx, kRedNames[L][1], bytes, &err);
+        red_ok = red_ok && rb.v[L] && rb.s[L];
+    }
     void *scan_tmp = scratch(ctx, "msm.scantmp", scan_temp_bytes(nb), &err);
     char *plan = (char *)scratch(ctx, "msm.plan", 256 + sizeof(RoundPlan), &err);
-    if (!jt || !counts || !off0 || !offa || !offb || !cursor || !sorted || !pa || !pb || !buckets ||
-        !bval || !bsum || !bv2 || !bs2 || !scan_tmp || !plan)
+    uint32_t *st = (uint32_t *)scratch(ctx, "msm.stats", 2 * align_up(count * 4, 256), &err);
+    if (!jt || !counts || !off0 || !offa || !offb || !cursor || !offs || !sorted || !pa || !pb || !buckets ||
+        !red_ok || !scan_tmp || !plan || !st)
         return err;
 
-    // Job table: descriptors and the three prefix arrays.
-    std::vector<char> h(jd_bytes + 3 * pre_bytes, 0);
+    // Job table: descriptors and the two prefix arrays.
+    std::vector<char> h(jd_bytes + 2 * pre_bytes, 0);
     JobDesc *hd = (JobDesc *)h.data();
     uint32_t *hs = (uint32_t *)(h.data() + jd_bytes);
     uint32_t *hb = (uint32_t *)(h.data() + jd_bytes + pre_bytes);
-    uint32_t *hk = (uint32_t *)(h.data() + jd_bytes + 2 * pre_bytes);
-    std::vector<uint32_t> logBs(count);
+    uint32_t lb[kMaxLevels] = {0, 0, 0, 0};
     for (size_t k = 0; k < count; k++) {
         hd[k].scalars = jv[k].job.scalars;
         hd[k].out = jv[k].job.out;
         hd[k].table = tabs[k];
+        hd[k].base = bases[k];
+        hd[k].wtable = tabs[k];
         hd[k].n = jv[k].job.n;
         hd[k].logB = (uint32_t)(jv[k].c - 1);
-        hd[k].shift = jv[k].shift;
-        hd[k].wins = jv[k].wins;
+        hd[k].shift = 0;
+        hd[k].wins = (uint32_t)windows_for(jv[k].c);
+        hd[k].c = (uint32_t)jv[k].c;
+        hd[k].dbl = 0;
+        hd[k].t16 = t16s[k];
+        hd[k].t16n = t16n[k];
+        for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++) {
+            hd[k].lbase[L - 1] = lb[L];
+            lb[L] += red_cap(lo[k], hi[k], L);
+        }
         hs[k + 1] = hs[k] + jv[k].job.n;
         hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
-        hk[k + 1] = hk[k] + (1u << (jv[k].c - 1)) / kSeg;
-        logBs[k] = (uint32_t)(jv[k].c - 1);
     }
     ZK_TRY(upload(ctx, jt, h.data(), h.size(), s));
     DevJobs dj;
     dj.jobs = (const JobDesc *)jt;
     dj.sbase = (const uint32_t *)(jt + jd_bytes);
     dj.bbase = (const uint32_t *)(jt + jd_bytes + pre_bytes);
-    dj.kbase = (const uint32_t *)(jt + jd_bytes + 2 * pre_bytes);
     dj.count = (uint32_t)count;
 
-    // 1-2: histogram, offsets, scatter (one recode launch per window width).
+    // 1-2: width statistics and plan, histogram, offsets, scatter (one
+    // recode launch per window width and table).
     PhaseScope ph_sort(ctx, ZK_PHASE_MSM_SORT, s);
+    if (stats) {
+        uint32_t *st_len = st, *st_tz = st + align_up(count * 4, 256) / 4;
+        ZK_CUDA_TRY(cudaMemsetAsync(st_len, 0, count * 4, s));
+        ZK_CUDA_TRY(cudaMemsetAsync(st_tz, 0xff, count * 4, s));
+        const uint32_t tot = hs[count];
+        k_scalar_stats<<<(tot + kRecPer - 1) / kRecPer, kRecThreads, 0, s>>>(dj, tot, st_len, st_tz);
+        ZK_LAUNCHED();
+        k_msm_plan<<<(unsigned)((count + 127) / 128), 128, 0, s>>>((JobDesc *)jt, (uint32_t)count, st_len, st_tz);
+        ZK_LAUNCHED();
+    }
     ZK_CUDA_TRY(cudaMemsetAsync(counts, 0, (nb + 1) * 4, s));
     for (int pass = 0; pass < 2; pass++) {
         if (pass == 1) {
@@ -834,18 +1104,17 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
             g0 = g1;
         }
     }
-    (void)total;
     ph_sort.end();
 
     // 3: bucket sums.
     PhaseScope ph_accum(ctx, ZK_PHASE_MSM_ACCUM, s);
-    const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)plan, (RoundPlan *)(plan + 256), scan_tmp};
-    ZK_TRY(launch_accumulate(sorted, counts, off0, nb, entries_max, shape, dj, ab, buckets, sh.sms, s));
+    const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)plan, (RoundPlan *)(plan + 256), scan_tmp, offs};
+    ZK_TRY(launch_accumulate(sorted, counts, off0, nb, shape, dj, ab, buckets, sh.sms, s));
     ph_accum.end();
 
     // 4-5: bucket reduction and output.
     PhaseScope ph_reduce(ctx, ZK_PHASE_MSM_REDUCE, s);
-    return launch_reduce(buckets, bval, bsum, bv2, bs2, dj, logBs.data(), count, s);
+    return launch_reduce(buckets, rb, dj, lo.data(), hi.data(), count, s);
 }
 
 }  // namespace zk
@@ -873,24 +1142,30 @@ constexpr uint32_t kNoAllocB = 1u << (kNoAllocC - 1);
 constexpr uint32_t kNoAllocW = (kScalarBits + kNoAllocC - 1) / kNoAllocC;
 constexpr size_t kNoAllocEntries = (size_t)kNoAllocMaxN * kNoAllocW;
 constexpr size_t kNoAllocPieces = kNoAllocEntries / kP0Min + kNoAllocB + 1;
-constexpr size_t kNoAllocBlk = kNoAllocB / kSeg;
+// Reduction items of levels 1 and 2 (2^15 buckets: levels of 2^15, 2^7 and 2^2 items).
+constexpr size_t kNoAllocL1 = red_cap(kNoAllocC - 1, kNoAllocC - 1, 1);
+constexpr size_t kNoAllocL2 = red_cap(kNoAllocC - 1, kNoAllocC - 1, 2);
+static_assert(red_cap(kNoAllocC - 1, kNoAllocC - 1, 3) == 0, "no-alloc reduction levels");
 constexpr size_t kNoAllocPre = 256;  // one prefix array of the job table
 
 constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 // Workspace layout (byte offsets).
-constexpr size_t kNaJobs = 0;                                          // JobDesc + 3 prefixes
-constexpr size_t kNaCounts = kNaJobs + 256 + 3 * kNoAllocPre;
+constexpr size_t kNaJobs = 0;                                          // JobDesc + 2 prefixes
+constexpr size_t kNaCounts = kNaJobs + 256 + 2 * kNoAllocPre;
 constexpr size_t kNaOff0 = kNaCounts + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaOffA = kNaOff0 + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaOffB = kNaOffA + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaCursor = kNaOffB + na_align((kNoAllocB + 1) * 4);
-constexpr size_t kNaSorted = kNaCursor + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaOffS = kNaCursor + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaSorted = kNaOffS + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaPieceA = kNaSorted + na_align(kNoAllocEntries * 4);
 constexpr size_t kNaPieceB = kNaPieceA + na_align(kNoAllocPieces * sizeof(Xyzz));
 constexpr size_t kNaBuckets = kNaPieceB + na_align(kNoAllocPieces * sizeof(Xyzz));
-constexpr size_t kNaBval = kNaBuckets + na_align(kNoAllocB * sizeof(Xyzz));
-constexpr size_t kNaBsum = kNaBval + na_align(kNoAllocBlk * sizeof(Xyzz));
-constexpr size_t kNaScan = kNaBsum + na_align(kNoAllocBlk * sizeof(Xyzz));
+constexpr size_t kNaV1 = kNaBuckets + na_align(kNoAllocB * sizeof(Xyzz));
+constexpr size_t kNaS1 = kNaV1 + na_align(kNoAllocL1 * sizeof(Xyzz));
+constexpr size_t kNaV2 = kNaS1 + na_align(kNoAllocL1 * sizeof(Xyzz));
+constexpr size_t kNaS2 = kNaV2 + na_align(kNoAllocL2 * sizeof(Xyzz));
+constexpr size_t kNaScan = kNaS2 + na_align(kNoAllocL2 * sizeof(Xyzz));
 constexpr size_t kNaPlan = kNaScan + na_align(((size_t)kNoAllocB / 2048 + 2) * 4);
 constexpr size_t kNoAllocBytes = kNaPlan + 256 + na_align(sizeof(RoundPlan));
 
@@ -928,19 +1203,23 @@ __global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint3
     d->scalars = scalars;
     d->out = out;
     d->table = table;
+    d->base = nullptr;  // no plan kernel runs: always the full-width shape
+    d->wtable = table;
+    d->t16 = nullptr;
+    d->t16n = 0;
     d->n = n;
     d->logB = kNoAllocC - 1;
     d->shift = 0;
     d->wins = kNoAllocW;
+    d->c = kNoAllocC;
+    d->dbl = 0;
+    for (int L = 0; L < kMaxLevels - 1; L++) d->lbase[L] = 0;
     uint32_t *sb = reinterpret_cast<uint32_t *>(ws + kNaJobs + 256);
     uint32_t *bb = sb + kNoAllocPre / 4;
-    uint32_t *kb = bb + kNoAllocPre / 4;
     sb[0] = 0;
     sb[1] = n;
     bb[0] = 0;
     bb[1] = kNoAllocB;
-    kb[0] = 0;
-    kb[1] = (uint32_t)kNoAllocBlk;
 }
 
 }  // namespace
@@ -988,8 +1267,11 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     Xyzz *pa = (Xyzz *)(ws + kNaPieceA);
     Xyzz *pb = (Xyzz *)(ws + kNaPieceB);
     Xyzz *buckets = (Xyzz *)(ws + kNaBuckets);
-    Xyzz *bval = (Xyzz *)(ws + kNaBval);
-    Xyzz *bsum = (Xyzz *)(ws + kNaBsum);
+    RedBufs rb{};
+    rb.v[1] = (Xyzz *)(ws + kNaV1);
+    rb.s[1] = (Xyzz *)(ws + kNaS1);
+    rb.v[2] = (Xyzz *)(ws + kNaV2);
+    rb.s[2] = (Xyzz *)(ws + kNaS2);  // level 3 never runs (2^15 buckets)
     void *scan_tmp = ws + kNaScan;
 
     k_noalloc_jobs<<<1, 1, 0, s>>>(ws, (const uint32_t *)coeffs, (uint32_t)n, out,
@@ -999,7 +1281,6 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     dj.jobs = (const JobDesc *)(ws + kNaJobs);
     dj.sbase = (const uint32_t *)(ws + kNaJobs + 256);
     dj.bbase = dj.sbase + kNoAllocPre / 4;
-    dj.kbase = dj.bbase + kNoAllocPre / 4;
     dj.count = 1;
     const uint32_t total = (uint32_t)n;
     // The workspace keeps the previous call's contents: the histogram must
@@ -1014,12 +1295,8 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     const AccumShape shape = accum_shape((size_t)n * kNoAllocW, (size_t)n * kNoAllocW, nb, sh.sms);
     if (shape.cap0 > kNoAllocPieces) return ZK_EINVAL;  // cannot happen: p0 >= kP0Min
     const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)(ws + kNaPlan), (RoundPlan *)(ws + kNaPlan + 256),
-                       scan_tmp};
-    ZK_TRY(launch_accumulate(sorted, counts, off0, nb, (size_t)n * kNoAllocW, shape, dj, ab, buckets, sh.sms,
-                             s));
-    // Two reduction levels (2^15 buckets); level 2 never runs, so its
-    // outputs can point anywhere.
+                       scan_tmp, (uint32_t *)(ws + kNaOffS)};
+    ZK_TRY(launch_accumulate(sorted, counts, off0, nb, shape, dj, ab, buckets, sh.sms, s));
     const uint32_t logB = kNoAllocC - 1;
-    static_assert(kNoAllocC - 1 <= 2 * kSegLog, "no-alloc reduction levels");
-    return launch_reduce(buckets, bval, bsum, bval, bsum, dj, &logB, 1, s);
+    return launch_reduce(buckets, rb, dj, &logB, &logB, 1, s);
 }

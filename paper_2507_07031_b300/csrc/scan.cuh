@@ -57,8 +57,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 }
 
 __global__ void k_tile_sums(const uint32_t *__restrict__ in, uint32_t n, int K,
-                            uint32_t *__restrict__ sums, const uint32_t *gate) {
+                            uint32_t *__restrict__ sums, const uint32_t *gate, const int *Kp,
+                            const uint32_t *const *in_p) {
     if (gate && !*gate) return;
+    if (Kp) K = *Kp;
+    if (in_p) in = *in_p;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t s = 0;
 #pragma unroll
@@ -86,8 +89,11 @@ __global__ void k_scan_sums(uint32_t *__restrict__ sums, uint32_t tiles, const u
 
 __global__ void k_tile_scan(const uint32_t *__restrict__ in, uint32_t n, int K,
                             const uint32_t *__restrict__ sums, uint32_t tiles,
-                            uint32_t *__restrict__ out, const uint32_t *gate) {
+                            uint32_t *__restrict__ out, const uint32_t *gate, const int *Kp,
+                            const uint32_t *const *in_p) {
     if (gate && !*gate) return;
+    if (Kp) K = *Kp;
+    if (in_p) in = *in_p;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t v[kPer];
     uint32_t s = 0;
@@ -114,16 +120,19 @@ inline size_t scan_temp_bytes(uint32_t n) {
 
 // out[b] = sum_{b' < b} elem(b'), out[n] = total.  `in` may equal neither
 // `out` nor `tmp`.  With a `gate` (device word), the scan does nothing when
-// the word is zero at execution time.
+// the word is zero at execution time.  With `Kp` (device word), K is read
+// from it at execution time instead, and with `in_p` (a device word holding
+// a pointer), the input array.
 inline int scan_exclusive(const uint32_t *in, uint32_t *out, uint32_t n, int K, void *tmp,
-                          cudaStream_t s, const uint32_t *gate = nullptr) {
+                          cudaStream_t s, const uint32_t *gate = nullptr, const int *Kp = nullptr,
+                          const uint32_t *const *in_p = nullptr) {
     using namespace scan_detail;
     uint32_t tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) tiles = 1;
     uint32_t *sums = (uint32_t *)tmp;
-    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate);
+    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate, Kp, in_p);
     k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, gate);
-    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate);
+    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate, Kp, in_p);
     count_launches(3);
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
