@@ -1,12 +1,17 @@
 """Benchmark of the BN254 prover hot path on B300.
 
-One step = one pass over the plain single ops at scale: KZG commitment MSMs
-of n = 2^20 points (scalars uniform in F_r, and quantised int8 * 2^16 values),
-and F_r NTT + INTT of lengths 2^20 and 2^22, all inputs resident in HBM.
-The headline value is MSM throughput (Mpts/s) at 2^20 with uniform scalars;
-the JSON line also carries every op's throughput, the batched-vs-plain
-comparisons (256-polynomial CNN commitment batch, 1024-leaf fold tree), the
-roofline of the dominant kernel, the end-to-end number through the C ABI
+One step = one pass of the whole hot path over its synthetic inputs, all
+resident in HBM: KZG commitment MSMs of n = 2^20 points (scalars uniform in
+F_r, and quantised int8 * 2^16 values), F_r NTT + INTT of lengths 2^20 and
+2^22, the batched commitment of a CNN's 256 witness polynomials (2^24
+evaluations: INTT + MSM each, one batch), and the parallel fold tree of 1024
+accumulators of n = 2^16 (1023 generalised-Mira folds: cross terms, their
+commitments, witness and instance combinations).  L2 is flushed before every
+op.  The headline value is MSM throughput (Mpts/s) at 2^20 with uniform
+scalars; the JSON line also carries every op's time and roofline (IMAD pipe
+against the live mad.lo probe, HBM against the measured copy bandwidth), the
+batched-vs-plain comparisons, the small-task regime of the graph plans, the
+serving loop at its stated load, the end-to-end commitment through the C ABI
 with host buffers, and the CPU oracle timed on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -31,7 +36,8 @@ import zkinputs as Z  # noqa: E402
 
 METRIC = "BN254 MSM Mpts/s & Fr NTT Melem/s at 2^20; batched folds/s vs plain; % roofline"
 UNIT = "Mpts/s"
-WORKLOAD = "plain single ops at scale: MSM 2^20 (uniform F_r; int8*2^16), NTT/INTT 2^20 and 2^22"
+WORKLOAD = ("hot path at scale: MSM 2^20 (uniform F_r; int8*2^16), NTT/INTT 2^20 and 2^22, "
+            "256-poly CNN commitment batch (2^24 evaluations), fold tree 1024 x 2^16")
 L2_FLUSH_BYTES = 512 << 20
 SRS_LOG = 22
 # Per mixed addition (madd-2008-s): 8 multiplications + 2 squarings in F_q;
@@ -39,10 +45,14 @@ SRS_LOG = 22
 FQ_MUL_PER_MADD = 10
 IMAD_PER_MUL = 264
 IMAD_LO, IMAD_HI = 136, 128  # mad.lo (incl. the 8 m = t n0 products) and mad.hi per product
+FOLD_MULS = 11               # F_r products per element of the degree-2 witness pass
+FOLD_BYTES = 512             # bytes per element of the witness pass (10 vectors read, 6 written)
+NTT_BYTES_PER_ELEM = 2 * 64  # two passes, each reading and writing 32 B per element
+HBM_FALLBACK = 6400.0        # GB/s, used only when MEASURED_PEAKS.json is absent
 # DRAM bytes (read + write) of one k_pieces_first launch, uniform 2^20, c = 17,
 # from an ncu capture of that launch (dram__bytes_read.sum +
 # dram__bytes_write.sum); None when the kernel has changed since.
-ACCUM_TRAFFIC = 2.060e9
+ACCUM_TRAFFIC = None
 CPU_SAMPLE_LOG = 15  # oracle MSM sample: 2^15 points, ~10-15 s on 16 cores
 
 
@@ -52,7 +62,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-extras", action="store_true", help="skip batch / fold-tree comparisons")
+    ap.add_argument("--no-extras", action="store_true", help="skip the comparisons and the serving run")
+    ap.add_argument("--serving-jobs", type=int, default=1200, help="jobs of the serving run (Poisson, 20/s)")
     ap.add_argument("--case", default=None, choices=["msm", "ntt", "fold", "open"],
                     help="profiling case: two calls of one op at --log2n (for ncu captures)")
     ap.add_argument("--log2n", type=int, default=18)
@@ -216,6 +227,9 @@ def oracle_msm_rate(sample_n: int):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: each step is an affine
+    double-and-add MSM over a power-of-two sample sized so that the whole
+    --steps K --warmup W run takes about a minute."""
     rank, world, _ = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -225,7 +239,10 @@ def run_reference(args):
             return
     import oracle as orc
     orc.lib()
-    sample = 1 << max(args.cpu_sample_log - 1, 1)  # default: each step ~5-7 s on 16 cores
+    probe_rate, _, _ = oracle_msm_rate(1 << 10)  # Mpts/s of this host
+    per_step_s = 60.0 / max(args.steps + args.warmup, 1)
+    lg = int(np.clip(np.floor(np.log2(max(probe_rate * 1e6 * per_step_s, 1.0))), 8, args.cpu_sample_log))
+    sample = 1 << lg
     rates, times = [], []
     for _ in range(args.warmup):
         oracle_msm_rate(sample)
@@ -240,7 +257,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "MSM of %d points" % sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "affine double-and-add MSM, %d points, SRS from seeded tau" % sample},
+                         "sample": "affine double-and-add MSM, %d points per step, SRS from seeded tau" % sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -252,6 +269,37 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json copy benchmark)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK, "of fallback (6.4 TB/s, one earlier B300 measurement)"
+
+
+def imad_roof(imads, ms, rates):
+    """IMAD-pipe roofline entry: algorithmic IMADs per op over its time,
+    against the live mad.lo issue rate; the product-mix ceiling (136 mad.lo +
+    128 mad.hi per product at the measured lo and hi rates) as an extra."""
+    achieved = imads / (ms * 1e-3) / 1e12
+    lo, hi = rates["mad_lo"] / 1e12, rates["mad_hi"] / 1e12
+    mix = IMAD_PER_MUL / (IMAD_LO / lo + IMAD_HI / hi)
+    return {"bound": "alu", "achieved": achieved, "peak": lo, "unit": "TIMAD/s", "frac": achieved / lo,
+            "peak_source": "of measured: live mad.lo.u32 issue rate (zk_probe_pipes)",
+            "mix_ceiling": mix, "frac_of_mix_ceiling": achieved / mix, "algorithmic_imad": imads}
+
+
+def hbm_roof(nbytes, ms, hbm, src):
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "peak_source": src, "algorithmic_bytes": nbytes}
+
+
+def ntt_imads(n):
+    return (n // 2) * (n.bit_length() - 1) * IMAD_PER_MUL
+
 
 def main():
     args = parse()
@@ -284,6 +332,14 @@ def main():
     out = torch.zeros((2, 8), dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    # CNN batch: 256 evaluation vectors (int8 * 2^16), INTT + commit each.
+    cnn_sizes = Z.cnn_poly_sizes(8)
+    cnn = [dev(Z.zkml_scalars(7_000_000 + i, int(s))) for i, s in enumerate(cnn_sizes)]
+    cnn_out = torch.zeros((len(cnn), 8), dtype=torch.int64, device="cuda")
+    # Fold tree: 1024 leaves of 2^16 (matmul block, 4 witness vectors); the
+    # tree overwrites its leaves, so every step restores them first.
+    tree = FoldTree(zk, ctx, dev, torch)
+    tree.init_leaves()
 
     ops = [
         ("msm_2^20_uniform", n20, lambda: zk.zk_commit(ctx, sc_uni, out[0])),
@@ -292,11 +348,16 @@ def main():
         ("intt_2^20", n20, lambda: zk.zk_intt(ctx, x20)),
         ("ntt_2^22", n22, lambda: zk.zk_ntt(ctx, x22)),
         ("intt_2^22", n22, lambda: zk.zk_intt(ctx, x22)),
+        ("cnn_batch_commit", int(cnn_sizes.sum()),
+         lambda: zk.zk_commit_batch(ctx, cnn, cnn_out, flags=zk.ZK_EVALS)),
+        ("fold_tree_1024x2^16", tree.count - 1, tree.run),
     ]
     ev = {name: [] for name, _, _ in ops}
 
     def step(record):
         for name, _, fn in ops:
+            if name.startswith("fold_tree"):
+                tree.restore()  # not part of the op's interval
             flush.fill_(1)  # evict L2 (512 MiB > 126 MB) between ops
             if record:
                 a = torch.cuda.Event(enable_timing=True)
@@ -309,6 +370,7 @@ def main():
                 ev[name].append((a, b))
             else:
                 fn()
+        zk.zk_timing_enable(ctx, False)
 
     for _ in range(args.warmup):
         step(False)
@@ -332,44 +394,79 @@ def main():
     launches = zk.zk_kernel_launches() - launches0
     sampler.stop()
     phases = zk.zk_timing_read(ctx)
-    zk.zk_timing_enable(ctx, False)
     total_ms = max_over_ranks(t0.elapsed_time(t1), dist)
+    same_tree = tree.root_matches_last()
 
     per_op = {}
     for name, n, _ in ops:
-        ms = [a.elapsed_time(b) for a, b in ev[name]]
-        med = statistics.median(ms)
-        unit = "Mpts/s" if name.startswith("msm") else "Melem/s"
-        per_op[name] = {"ms": med, unit: n / (med * 1e-3) / 1e6}
-    msm_ms = statistics.median([a.elapsed_time(b) for a, b in ev["msm_2^20_uniform"]])
+        ms = statistics.median([a.elapsed_time(b) for a, b in ev[name]])
+        unit = ("Mpts/s" if name.startswith("msm") else "Mcoef/s" if name.startswith("cnn")
+                else "folds/s" if name.startswith("fold") else "Melem/s")
+        per_op[name] = {"ms": ms, unit: (n / (ms * 1e-3) / 1e6) if unit != "folds/s" else n / (ms * 1e-3)}
+    msm_ms = per_op["msm_2^20_uniform"]["ms"]
     value = whole_job_rate(n20, msm_ms * 1e-3, world, dist) / 1e6
 
-    # Roofline of the dominant kernel class: bucket accumulation of the
-    # uniform 2^20 MSM (k_pieces_first and the short rounds after it).
-    imad_peak, fq_mul_peak = zk.zk_probe_rates(local)
+    # Per-op phase split, from one extra untimed pass with phase timing on.
+    phase_split = {}
+    for name, _, fn in ops:
+        if name.startswith("fold_tree"):
+            tree.restore()
+        torch.cuda.synchronize()
+        zk.zk_timing_read(ctx)
+        zk.zk_timing_enable(ctx, True)
+        fn()
+        zk.zk_timing_enable(ctx, False)
+        torch.cuda.synchronize()
+        phase_split[name] = {k: round(v[0], 4) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
+
+    # Rooflines.  Denominators: the live probes of this run (IMAD) and the
+    # measured copy bandwidth (HBM).
+    rates = zk.zk_probe_pipes(local)
+    hbm, hbm_src = measured_peaks()
+    c20 = zk.zk_tune_get(ctx, zk.ZK_TUNE_MSM_WINDOW, 20)
+    W = -(-254 // c20)
+    madd = FQ_MUL_PER_MADD * IMAD_PER_MUL
+    roofs = {}
+    roofs["msm_2^20_uniform"] = imad_roof(n20 * W * madd, msm_ms, rates)
+    # int8 * 2^16: one 9-bit window after the shift, one mixed addition per point
+    roofs["msm_2^20_int8x2^16"] = imad_roof(n20 * madd, per_op["msm_2^20_int8x2^16"]["ms"], rates)
+    for name, n in (("ntt_2^20", n20), ("intt_2^20", n20), ("ntt_2^22", n22), ("intt_2^22", n22)):
+        ms = per_op[name]["ms"]
+        roofs[name] = {"imad": imad_roof(ntt_imads(n), ms, rates),
+                       "hbm": hbm_roof(n * NTT_BYTES_PER_ELEM, ms, hbm, hbm_src)}
+    # CNN batch: INTT of every polynomial, then full-width MSMs of its
+    # coefficients (ceil(254 / c) windows at each length's window width).
+    cnn_imad = 0
+    for s_ in cnn_sizes:
+        lg = int(s_).bit_length() - 1
+        cnn_imad += ntt_imads(int(s_)) + int(s_) * (-(-254 // zk.zk_tune_get(ctx, zk.ZK_TUNE_MSM_WINDOW, lg))) * madd
+    roofs["cnn_batch_commit"] = imad_roof(cnn_imad, per_op["cnn_batch_commit"]["ms"], rates)
+    # Fold tree: witness passes (11 F_r products, 512 B per element), the
+    # cross terms' INTTs and full-width MSMs; instance combinations excluded.
+    folds, nf = tree.count - 1, tree.n
+    wit_ms = phase_split["fold_tree_1024x2^16"].get("fold_witness", 0.0)
+    c16 = zk.zk_tune_get(ctx, zk.ZK_TUNE_MSM_WINDOW, 16)
+    tree_imad = folds * (nf * FOLD_MULS * IMAD_PER_MUL + ntt_imads(nf) + nf * (-(-254 // c16)) * madd)
+    roofs["fold_tree_1024x2^16"] = imad_roof(tree_imad, per_op["fold_tree_1024x2^16"]["ms"], rates)
+    if wit_ms:
+        roofs["fold_witness_pass"] = {"imad": imad_roof(folds * nf * FOLD_MULS * IMAD_PER_MUL, wit_ms, rates),
+                                      "hbm": hbm_roof(folds * nf * FOLD_BYTES, wit_ms, hbm, hbm_src),
+                                      "ms_per_tree": wit_ms}
+
+    # Dominant kernel: bucket accumulation of the uniform 2^20 MSM
+    # (k_pieces_first and the device-gated rounds after it).
     acc_ms, acc_cnt = phases["msm_accum"]
-    c = zk.zk_tune_get(ctx, zk.ZK_TUNE_MSM_WINDOW, 20)
-    W = -(-254 // c)
-    madds = n20 * W * args.steps  # one mixed addition per nonzero signed digit
-    achieved = madds * FQ_MUL_PER_MADD * IMAD_PER_MUL / (acc_ms * 1e-3) / 1e12 if acc_ms else None
-    # The IMAD pipe's ceiling for the product's instruction mix: mad.hi issues
-    # at half the mad.lo rate, so the 136 lo + 128 hi IMADs of a product take
-    # 136 + 2 * 128 mad.lo issue slots.
-    mix_peak = imad_peak * IMAD_PER_MUL / (IMAD_LO + 2 * IMAD_HI) / 1e12
-    roofline = {
-        "bound": "alu", "kernel": "MSM bucket accumulation (k_pieces_first + rounds + k_buckets_final), "
-                                  "uniform 2^20, c=%d" % c,
-        "achieved": achieved, "peak": mix_peak, "unit": "TIMAD/s",
-        "frac": (achieved / mix_peak) if achieved else None,
-        "peak_source": "of measured: live mad.lo issue rate (zk_probe_rates) x 264 / (136 + 2 x 128), "
-                       "mad.hi at half rate",
-        "mad_lo_peak": imad_peak / 1e12, "frac_of_mad_lo_peak": (achieved / (imad_peak / 1e12)) if achieved else None,
-        "product_loop_peak": fq_mul_peak * IMAD_PER_MUL / 1e12,
+    adds = n20 * W * args.steps  # one mixed addition per nonzero signed digit
+    acc = imad_roof(adds * madd, acc_ms, rates)
+    roofline = dict(acc)
+    roofline.update({
+        "kernel": "MSM bucket accumulation (k_pieces_first + gated rounds + tail), uniform 2^20, c=%d" % c20,
         "algorithmic": "%d mixed additions x 10 F_q products x 264 IMADs per MSM" % (n20 * W),
         "traffic": ACCUM_TRAFFIC, "traffic_kernel": "k_pieces_first (ncu, bytes per launch)",
         "ms_per_launch": acc_ms / max(acc_cnt, 1),
-        "phase_ms_per_msm": {k: v[0] / args.steps for k, v in phases.items()},
-    }
+        "phase_ms_per_msm": {k: v[0] / args.steps for k, v in phases.items() if v[1]},
+        "probes_per_s": rates,
+    })
 
     # End to end through the C ABI with host buffers (pinned): H2D of the
     # scalars and D2H of the commitment inside the timed region.
@@ -379,7 +476,7 @@ def main():
         zk.zk_commit(ctx, h_sc, h_out)
     torch.cuda.synchronize()
     e2e_t = []
-    for _ in range(args.steps):
+    for _ in range(max(args.steps, 5)):
         s0 = time.perf_counter()
         zk.zk_commit(ctx, h_sc, h_out)
         e2e_t.append(time.perf_counter() - s0)
@@ -389,7 +486,8 @@ def main():
 
     extras = {}
     if not args.no_extras:
-        extras = run_extras(zk, ctx, dev, torch)
+        extras = run_extras(zk, ctx, dev, torch, cnn, cnn_sizes, cnn_out, tree, args)
+    del tree
 
     cpu = None
     if rank == 0:
@@ -408,172 +506,216 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded SplitMix64; SRS from seeded tau)",
-        "config": {"workload": WORKLOAD, "srs": "2^22 points, window tables c=16",
-                   "l2": "flushed (512 MiB write) before every op", "parallelism": "replicas" if world > 1 else "single"},
-        "ops": per_op, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": sampler.summary(), **extras,
+        "config": {"workload": WORKLOAD, "srs": "2^22 points, window tables c=16 and per-length widths",
+                   "routes": "evaluation-form commitments by INTT + MSM (the paper's encoding)",
+                   "l2": "flushed (512 MiB write) before every op",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "ops": per_op, "phases_ms": phase_split, "roofline": roofline, "rooflines": roofs,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
+        "fold_tree_root_repeatable": same_tree, **extras,
     }
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_extras(zk, ctx, dev, torch):
-    """Batched vs plain: the 256-polynomial CNN commitment batch and the
-    1024-leaf fold tree."""
-    res = {}
-    # CNN batch: 256 evaluation vectors (int8 * 2^16), INTT + commit each.
-    sizes = Z.cnn_poly_sizes(8)
-    vecs = [dev(Z.zkml_scalars(7_000_000 + i, int(s))) for i, s in enumerate(sizes)]
-    outb = torch.zeros((len(vecs), 8), dtype=torch.int64, device="cuda")
-    outp = torch.zeros((len(vecs), 8), dtype=torch.int64, device="cuda")
+class FoldTree:
+    """The fold-tree workload: 1024 leaf accumulators of n = 2^16 (m1, m2, m4
+    int8 * 2^16, stream 9 * 2^20 + 4 j + i), level-major gammas, and a saved
+    copy of the initialised leaves that restores them before each run."""
 
-    def batched():
-        zk.zk_commit_batch(ctx, vecs, outb, flags=zk.ZK_EVALS)
+    def __init__(self, zk, ctx, dev, torch, count=1024, n=1 << 16):
+        self.zk, self.ctx, self.torch = zk, ctx, torch
+        self.count, self.n = count, n
+        self.m = torch.zeros((count, 4, n, 4), dtype=torch.int64, device="cuda")
+        self.e = torch.zeros((count, n, 4), dtype=torch.int64, device="cuda")
+        self.x = torch.zeros((count, 44), dtype=torch.int64, device="cuda")
+        for j in range(count):
+            base = (9 << 20) + 4 * j
+            self.m[j, 0].copy_(dev(Z.zkml_scalars(base, n)))
+            self.m[j, 1].copy_(dev(Z.zkml_scalars(base + 1, n)))
+            self.m[j, 3].copy_(dev(Z.zkml_scalars(base + 3, n)))
+        self.descs = [zk.make_acc(self.m[j], self.e[j], self.x[j]) for j in range(count)]
+        self.gam = dev(np.concatenate([Z.gammas(l, count >> l) for l in range(1, count.bit_length())]))
+        self.root = (torch.zeros((4, n, 4), dtype=torch.int64, device="cuda"),
+                     torch.zeros((n, 4), dtype=torch.int64, device="cuda"),
+                     torch.zeros(44, dtype=torch.int64, device="cuda"))
+        self.rdesc = zk.make_acc(*self.root)
+        self.saved = None
+        self.first_root = None
+
+    def init_leaves(self):
+        self.zk.zk_leaf_init(self.ctx, self.descs)
+        self.saved = (self.m.clone(), self.e.clone(), self.x.clone())
+
+    def restore(self):
+        self.m.copy_(self.saved[0])
+        self.e.copy_(self.saved[1])
+        self.x.copy_(self.saved[2])
+
+    def run(self):
+        self.zk.zk_fold_tree(self.ctx, self.descs, self.gam, self.rdesc)
+        if self.first_root is None:
+            self.first_root = [r.clone() for r in self.root]
+
+    def root_matches_last(self):
+        return bool(self.first_root is not None and
+                    all(self.torch.equal(a, b) for a, b in zip(self.first_root, self.root)))
+
+    def plain(self):
+        width, goff, span = self.count, 0, 2
+        while span <= self.count:
+            for j in range(width // 2):
+                L = self.descs[j * span + span // 2 - 1]
+                R = self.descs[j * span + span - 1]
+                self.zk.zk_fold(self.ctx, L, R, self.gam[goff + j], R)
+            goff += width // 2
+            width //= 2
+            span *= 2
+
+    def last_slot(self):
+        return (self.m[self.count - 1], self.e[self.count - 1], self.x[self.count - 1])
+
+
+def run_extras(zk, ctx, dev, torch, cnn, cnn_sizes, cnn_out, tree, args):
+    """Batched vs plain vs graph vs Lagrange route for the CNN batch and the
+    fold tree, the small-task regime, openings, and the serving loop."""
+    res = {}
+    ref = cnn_out.clone()
+    outp = torch.zeros_like(cnn_out)
+
+    def plain():
+        for i, v in enumerate(cnn):
+            zk.zk_commit_batch(ctx, [v], outp[i:i + 1], flags=zk.ZK_EVALS)
+
+    plain()
+    torch.cuda.synchronize()
+    tp = _time(torch, plain, 3)
+    outl = torch.zeros_like(cnn_out)
+    zk.zk_commit_batch(ctx, cnn, outl, flags=zk.ZK_LAGRANGE)  # builds the bases
+    tl = _time(torch, lambda: zk.zk_commit_batch(ctx, cnn, outl, flags=zk.ZK_LAGRANGE), 3)
+    outg = torch.zeros_like(cnn_out)
+    plan = zk.zk_plan_commit_batch(ctx, cnn, outg, flags=zk.ZK_EVALS)
+    tg = _time(torch, lambda: zk.zk_plan_launch(plan), 3)
+    nodes = zk.zk_plan_nodes(plan)
+    zk.zk_plan_destroy(plan)
+    outgl = torch.zeros_like(cnn_out)
+    plan = zk.zk_plan_commit_batch(ctx, cnn, outgl, flags=zk.ZK_LAGRANGE)
+    tgl = _time(torch, lambda: zk.zk_plan_launch(plan), 3)
+    zk.zk_plan_destroy(plan)
+    tb = _time(torch, lambda: zk.zk_commit_batch(ctx, cnn, cnn_out, flags=zk.ZK_EVALS), 3)
+    res["cnn_batch_commit"] = {"polys": len(cnn), "coeffs": int(cnn_sizes.sum()), "batched_ms": tb,
+                               "plain_ms": tp, "graph_ms": tg, "graph_nodes": nodes,
+                               "lagrange_batched_ms": tl, "lagrange_graph_ms": tgl, "speedup": tp / tb,
+                               "identical": bool(torch.equal(ref, outp) and torch.equal(outg, ref)
+                                                 and torch.equal(outl, ref) and torch.equal(outgl, ref))}
+    # Fold tree: batched (the step's op) vs per-fold calls vs one graph, and
+    # the Lagrange route; degree 3 on the Lagrange route.
+    tree.restore()
+    tree.run()
+    root_b = [r.clone() for r in tree.root]
+    tree.restore()
+    tree.plain()
+    tree.restore()
+    torch.cuda.synchronize()
+    t_plain = _time(torch, tree.plain, 1)
+    same = all(torch.equal(a, b) for a, b in zip(tree.last_slot(), root_b))
+    tree.restore()
+    torch.cuda.synchronize()
+    plan = zk.zk_plan_fold_tree(ctx, tree.descs, tree.gam, tree.rdesc)  # its warm-up consumes the leaves
+    tree.restore()
+    torch.cuda.synchronize()
+    t_graph = _time(torch, lambda: zk.zk_plan_launch(plan), 1)
+    same = same and all(torch.equal(a, b) for a, b in zip(tree.root, root_b))
+    zk.zk_plan_destroy(plan)
+    tree.restore()
+    t_batched = _time(torch, tree.run, 1)
+    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
+    m0 = tree.saved[0]
+    tree.m.copy_(m0)
+    zk.zk_leaf_init(ctx, tree.descs)  # builds the 2^16 basis
+    torch.cuda.synchronize()
+    t_leaf_l = _time(torch, lambda: zk.zk_leaf_init(ctx, tree.descs), 1)
+    leaf_same = torch.equal(tree.x, tree.saved[2])
+    tree.restore()
+    tree.run()
+    tree.restore()
+    torch.cuda.synchronize()
+    t_lag = _time(torch, tree.run, 1)
+    same = same and leaf_same and all(torch.equal(a, b) for a, b in zip(tree.root, root_b))
+    # Degree 3 (m1 o m2 o m3 - mu^2 m4 = e, two cross terms), Lagrange route:
+    # m3 := the degree-2 leaves' fourth int8 vector; leaf init computes m4.
+    zk.zk_set_fold_degree(ctx, 3)
+    tree.m.copy_(m0)
+    tree.m[:, 2].copy_(m0[:, 3])
+    tree.e.zero_()
+    zk.zk_leaf_init(ctx, tree.descs)
+    tree.saved = (tree.m.clone(), tree.e.clone(), tree.x.clone())
+    tree.run()
+    tree.restore()
+    torch.cuda.synchronize()
+    t3 = _time(torch, tree.run, 1)
+    zk.zk_set_fold_degree(ctx, 2)
+    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
+    folds = tree.count - 1
+    res["fold_tree"] = {"leaves": tree.count, "n": tree.n, "folds": folds,
+                        "batched_ms": t_batched, "plain_ms": t_plain, "graph_ms": t_graph,
+                        "batched_folds_per_s": folds / (t_batched * 1e-3),
+                        "plain_folds_per_s": folds / (t_plain * 1e-3),
+                        "graph_folds_per_s": folds / (t_graph * 1e-3), "speedup": t_plain / t_batched,
+                        "lagrange_ms": t_lag, "lagrange_folds_per_s": folds / (t_lag * 1e-3),
+                        "lagrange_leaf_commit_ms": t_leaf_l,
+                        "degree3_lagrange_ms": t3, "degree3_lagrange_folds_per_s": folds / (t3 * 1e-3),
+                        "identical": bool(same)}
+    tree.m = tree.e = tree.x = tree.saved = None
+    torch.cuda.empty_cache()
+    res["small_tasks"] = run_small_tasks(zk, ctx, dev, torch)
+    res["kzg_open_and_quotient"] = run_openings(zk, ctx, dev, torch)
+    if args.serving_jobs > 0:
+        zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
+        res["serving"] = run_serving(zk, ctx, dev, torch, jobs=args.serving_jobs)
+        res["serving"]["route"] = "lagrange"
+        zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
+        res["serving_intt"] = run_serving(zk, ctx, dev, torch, jobs=args.serving_jobs)
+        res["serving_intt"]["route"] = "intt"
+    return res
+
+
+def run_small_tasks(zk, ctx, dev, torch, count=4096, seed=12):
+    """Many tiny uneven tasks: 4096 evaluation vectors of 2^8 .. 2^12 (INTT +
+    commit each), as per-task calls, one batched call, and one graph."""
+    rng = np.random.default_rng(seed)
+    sizes = (1 << rng.integers(8, 13, count)).astype(np.int64)
+    vecs = [dev(Z.zkml_scalars(8_000_000 + i, int(s))) for i, s in enumerate(sizes)]
+    outb = torch.zeros((count, 8), dtype=torch.int64, device="cuda")
+    outp = torch.zeros_like(outb)
+    outg = torch.zeros_like(outb)
 
     def plain():
         for i, v in enumerate(vecs):
             zk.zk_commit_batch(ctx, [v], outp[i:i + 1], flags=zk.ZK_EVALS)
 
-    for f in (batched, plain):
-        f()
+    def batched():
+        zk.zk_commit_batch(ctx, vecs, outb, flags=zk.ZK_EVALS)
+
+    plain()
+    batched()
+    tp = _time(torch, plain, 3)
+    tb = _time(torch, batched, 3)
     torch.cuda.synchronize()
     zk.zk_timing_read(ctx)
     zk.zk_timing_enable(ctx, True)
-    tb = _time(torch, batched, 3)
-    ph_b = {k: round(v[0] / 3, 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
-    tp = _time(torch, plain, 3)
-    ph_p = {k: round(v[0] / 3, 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
+    batched()
     zk.zk_timing_enable(ctx, False)
-    outl = torch.zeros_like(outb)
-    zk.zk_commit_batch(ctx, vecs, outl, flags=zk.ZK_LAGRANGE)  # builds the bases
-    tl = _time(torch, lambda: zk.zk_commit_batch(ctx, vecs, outl, flags=zk.ZK_LAGRANGE), 3)
-    outg = torch.zeros_like(outb)
+    torch.cuda.synchronize()
+    ph = {k: round(v[0], 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
     plan = zk.zk_plan_commit_batch(ctx, vecs, outg, flags=zk.ZK_EVALS)
     tg = _time(torch, lambda: zk.zk_plan_launch(plan), 3)
-    nodes = zk.zk_plan_nodes(plan)
     zk.zk_plan_destroy(plan)
-    res["cnn_batch_commit"] = {"polys": len(vecs), "coeffs": int(sizes.sum()),
-                               "batched_ms": tb, "plain_ms": tp, "graph_ms": tg, "graph_nodes": nodes,
-                               "lagrange_batched_ms": tl, "speedup": tp / tb,
-                               "identical": bool(torch.equal(outb, outp) and torch.equal(outg, outb)
-                                                 and torch.equal(outl, outb)),
-                               "batched_phase_ms": ph_b, "plain_phase_ms": ph_p}
-    del vecs
-    # Fold tree: 1024 leaves of 2^16 (config: matmul block, 4 witness vectors).
-    count, n = 1024, 1 << 16
-    accs = []
-    for j in range(count):
-        m = torch.zeros((4, n, 4), dtype=torch.int64, device="cuda")
-        base = (9 << 20) + 4 * j
-        m[0].copy_(dev(Z.zkml_scalars(base, n)))
-        m[1].copy_(dev(Z.zkml_scalars(base + 1, n)))
-        m[3].copy_(dev(Z.zkml_scalars(base + 3, n)))
-        e = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
-        x = torch.zeros(44, dtype=torch.int64, device="cuda")
-        accs.append((m, e, x))
-    descs = [zk.make_acc(*a) for a in accs]
-    t_leaf = _time(torch, lambda: zk.zk_leaf_init(ctx, descs), 1)
-    leaf_state = [(a[0].clone(), a[1].clone(), a[2].clone()) for a in accs]
-    gam = dev(np.concatenate([Z.gammas(l, count >> l) for l in range(1, 11)]))
-    root = (torch.zeros((4, n, 4), dtype=torch.int64, device="cuda"),
-            torch.zeros((n, 4), dtype=torch.int64, device="cuda"),
-            torch.zeros(44, dtype=torch.int64, device="cuda"))
-    rdesc = zk.make_acc(*root)
-
-    def restore():
-        for a, s in zip(accs, leaf_state):
-            for t, u in zip(a, s):
-                t.copy_(u)
-
-    def tree():
-        zk.zk_fold_tree(ctx, descs, gam, rdesc)
-
-    def plain_tree():
-        width, goff, span = count, 0, 2
-        while span <= count:
-            for j in range(width // 2):
-                L = descs[j * span + span // 2 - 1]
-                R = descs[j * span + span - 1]
-                zk.zk_fold(ctx, L, R, gam[goff + j], R)
-            goff += width // 2
-            width //= 2
-            span *= 2
-
-    restore()
-    tree()  # warm-up (sizes workspaces)
-    restore()
-    torch.cuda.synchronize()
-    zk.zk_timing_read(ctx)
-    zk.zk_timing_enable(ctx, True)
-    tt = _time(torch, tree, 1)
-    ph_tree = {k: round(v[0], 3) for k, v in zk.zk_timing_read(ctx).items() if v[1]}
-    zk.zk_timing_enable(ctx, False)
-    root_batched = [r.clone() for r in root]
-    restore()
-    plain_tree()  # warm-up
-    restore()
-    torch.cuda.synchronize()
-    tp = _time(torch, plain_tree, 1)
-    same = all(torch.equal(a, b) for a, b in zip(accs[count - 1], root_batched))
-    restore()
-    torch.cuda.synchronize()
-    plan = zk.zk_plan_fold_tree(ctx, descs, gam, rdesc)  # its warm-up consumes the leaves
-    restore()
-    torch.cuda.synchronize()
-    tg = _time(torch, lambda: zk.zk_plan_launch(plan), 1)
-    same = same and all(torch.equal(a, b) for a, b in zip(root, root_batched))
-    zk.zk_plan_destroy(plan)
-    # Lagrange route: leaf commitments and cross terms without INTTs.
-    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
-    restore()
-    zk.zk_leaf_init(ctx, descs)  # builds the 2^16 basis
-    torch.cuda.synchronize()
-    t_leaf_l = _time(torch, lambda: zk.zk_leaf_init(ctx, descs), 1)
-    leaf_same = all(torch.equal(a[2], s_[2]) for a, s_ in zip(accs, leaf_state))
-    restore()
-    tree()
-    restore()
-    torch.cuda.synchronize()
-    tl = _time(torch, tree, 1)
-    same = same and leaf_same and all(torch.equal(a, b) for a, b in zip(root, root_batched))
-    # Degree 3 (m1 o m2 o m3 - mu^2 m4 = e, two cross terms), Lagrange route,
-    # over the same 1024 leaves: m1, m2 as before and m3 := the degree-2
-    # leaves' fourth int8 vector; leaf init computes m4 = m1 o m2 o m3.
-    zk.zk_set_fold_degree(ctx, 3)
-    for (m, e, x), (m0, e0, x0) in zip(accs, leaf_state):
-        m.copy_(m0)
-        m[2].copy_(m0[3])
-    zk.zk_leaf_init(ctx, descs)
-    state3 = [(a[0].clone(), a[1].clone(), a[2].clone()) for a in accs]
-    tree()  # warm-up
-    for a, s_ in zip(accs, state3):
-        for t, u in zip(a, s_):
-            t.copy_(u)
-    torch.cuda.synchronize()
-    t3 = _time(torch, tree, 1)
-    zk.zk_set_fold_degree(ctx, 2)
-    del state3
-    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
-    res["fold_tree"] = {"leaves": count, "n": n, "folds": count - 1,
-                        "degree3_lagrange_folds_per_s": (count - 1) / (t3 * 1e-3), "degree3_lagrange_ms": t3,
-                        "batched_folds_per_s": (count - 1) / (tt * 1e-3),
-                        "plain_folds_per_s": (count - 1) / (tp * 1e-3),
-                        "graph_folds_per_s": (count - 1) / (tg * 1e-3),
-                        "lagrange_folds_per_s": (count - 1) / (tl * 1e-3), "lagrange_ms": tl,
-                        "lagrange_leaf_commit_ms": t_leaf_l,
-                        "batched_ms": tt, "plain_ms": tp, "graph_ms": tg, "speedup": tp / tt,
-                        "leaf_commit_ms": t_leaf, "identical": bool(same),
-                        "batched_phase_ms": ph_tree}
-    del accs, leaf_state, descs
-    torch.cuda.empty_cache()
-    res["kzg_open_and_quotient"] = run_openings(zk, ctx, dev, torch)
-    res["serving"] = run_serving(zk, ctx, dev, torch)
-    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_LAGRANGE)
-    res["serving_lagrange"] = run_serving(zk, ctx, dev, torch)
-    zk.zk_set_commit_route(ctx, zk.ZK_ROUTE_INTT)
-    return res
-
+    return {"tasks": count, "sizes": "2^8 .. 2^12 (uniform log2)", "coeffs": int(sizes.sum()),
+            "plain_ms": tp, "batched_ms": tb, "graph_ms": tg, "batched_speedup": tp / tb, "batched_phase_ms": ph,
+            "graph_vs_batched": tb / tg,
+            "identical": bool(torch.equal(outb, outp) and torch.equal(outg, outb))}
 
 def run_openings(zk, ctx, dev, torch, reps=5):
     """KZG opening (Sec. 2.1) at 2^20: one polynomial (division + MSM of the
@@ -624,13 +766,17 @@ def run_openings(zk, ctx, dev, torch, reps=5):
             "open_batch_16x2^16_ms": batch, "mul_quotient_2^20_ms": mq}
 
 
-def run_serving(zk, ctx, dev, torch, lanes=4, layers=12, rate_hz=20.0):
-    """Poisson stream of the basic-block jobs of a 12-layer, width-768
-    transformer (sequence 128): each job commits to its witness (three int8 *
-    2^16 vectors, as a leaf accumulator) and folds it into the resident
-    accumulator of its size.  Jobs reuse a pool of output buffers per size."""
+def run_serving(zk, ctx, dev, torch, jobs=1200, lanes=4, rate_hz=20.0):
+    """Poisson stream (20 jobs/s) of the basic-block jobs of a 12-layer,
+    width-768 transformer (sequence 128), inference after inference: each job
+    commits to its witness (three int8 * 2^16 vectors, as a leaf accumulator)
+    and folds it into the resident accumulator of its size.  Jobs reuse a pool
+    of output buffers per size.  Latency = end - arrival; it splits into the
+    submission delay (the driver loop was late), the wait in the server's
+    queue (submit -> start) and the run on a lane (start -> end)."""
     import time as _t
-    sizes = [1 << lg for lg in Z.transformer_job_sizes()] * layers
+    per_inf = [1 << lg for lg in Z.transformer_job_sizes()] * 12
+    sizes = [per_inf[i % len(per_inf)] for i in range(jobs)]
     arrivals = Z.poisson_arrivals(10, len(sizes), rate_hz)
     pool = {}
 
@@ -675,13 +821,29 @@ def run_serving(zk, ctx, dev, torch, lanes=4, layers=12, rate_hz=20.0):
     st = zk.zk_server_stats(srv)
     zk.zk_server_destroy(srv)
     ok = all(i.status == zk.ZK_JOB_DONE for i in infos)
-    lat = np.array([i.end_ms - i.submit_ms + d for i, d in zip(infos, delays)])
+    delay = np.array(delays)
+    queue = np.array([i.start_ms - i.submit_ms for i in infos])
+    run = np.array([i.end_ms - i.start_ms for i in infos])
+    lat = delay + queue + run
     span_s = (max(i.end_ms for i in infos) - min(i.submit_ms for i in infos)) / 1e3
+
+    def pct(a):
+        return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "mean": float(a.mean())}
+
+    by_size = {}
+    for lg in sorted(set(n.bit_length() - 1 for n in sizes)):
+        sel = np.array([n.bit_length() - 1 == lg for n in sizes])
+        by_size[str(lg)] = {"jobs": int(sel.sum()), "run_p50_ms": float(np.percentile(run[sel], 50)),
+                            "latency_p99_ms": float(np.percentile(lat[sel], 99))}
+    worst = int(np.argmax(lat))
     return {"jobs": len(sizes), "rate_hz": rate_hz, "lanes": lanes, "all_done": ok,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "jobs_per_s": len(sizes) / span_s,
-            "peak_reserved_gb": st.peak_reserved_bytes / 2 ** 30,
-            "sizes_log2": sorted(set(Z.transformer_job_sizes()))}
+            "latency_ms": pct(lat), "submit_delay_ms": pct(delay), "queue_ms": pct(queue), "run_ms": pct(run),
+            "worst_job": {"log2n": sizes[worst].bit_length() - 1, "queue_ms": float(queue[worst]),
+                          "run_ms": float(run[worst]), "delay_ms": float(delay[worst])},
+            "by_log2n": by_size, "peak_reserved_gb": st.peak_reserved_bytes / 2 ** 30,
+            "budget_gb": 150, "sizes_log2": sorted(set(Z.transformer_job_sizes()))}
 
 
 def _time(torch, fn, reps):

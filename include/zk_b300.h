@@ -274,8 +274,8 @@ int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, z
 int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
                  zk_stream stream);
 
-/* Autotuning (the window width of the MSM and the largest NTT pass radix, per
- * length).  op = ZK_TUNE_MSM_WINDOW: value = window width c in [9, 20] for
+/* Autotuning (the window width and bucket layout of the MSM and the largest
+ * NTT pass radix, per length).  op = ZK_TUNE_MSM_WINDOW: value = window width c in [9, 20] for
  * MSMs of length in (2^(log2n-1), 2^log2n]; op = ZK_TUNE_NTT_RADIX: value =
  * log2 of the largest pass radix in [1, 11] for transforms of length 2^log2n.
  * value 0 restores the built-in choice (the winners of a tuning sweep on
@@ -287,6 +287,20 @@ int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas,
  * winners in a JSON table. */
 #define ZK_TUNE_MSM_WINDOW 0
 #define ZK_TUNE_NTT_RADIX 1
+/* Bucket layout of the MSM, per length (value 0 = built-in):
+ *   ZK_TUNE_MSM_CHUNK  : 1 + log2 of the round-0 chunk multiplier used when
+ *                        few buckets (<= 4096) are in use, value in [1, 4];
+ *   ZK_TUNE_MSM_TAIL   : 1 + log2 of the items each lane sums in a slice of
+ *                        the team tail (few, full buckets), value in [1, 4];
+ *   ZK_TUNE_MSM_SEG    : log2 of the bucket-reduction segment of levels with
+ *                        fewer than 2^13 items, value in [3, 5];
+ *   ZK_TUNE_MSM_SEGBIG : log2 of the segment of larger levels, in [6, 8].
+ * zk_tune_measure times these on quantised int8 x 2^16 scalars (CHUNK,
+ * TAIL, SEG) or uniform scalars (SEGBIG) through the default MSM path. */
+#define ZK_TUNE_MSM_CHUNK 2
+#define ZK_TUNE_MSM_TAIL 3
+#define ZK_TUNE_MSM_SEG 4
+#define ZK_TUNE_MSM_SEGBIG 5
 int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value);
 int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value);
 int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double *ms);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "field.cuh"
 
 namespace zk {
 
@@ -191,6 +192,23 @@ __global__ void k_fill_random(uint64_t *out, size_t n, uint64_t seed) {
     }
 }
 
+// Quantised scalars q 2^16 mod r, q a uniform int8 from the same hash (the
+// width-tuning data of the MSM's bucket layout).
+__global__ void k_fill_quant(uint64_t *out, size_t n, uint64_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const int q = (int)(int8_t)(z & 0xff);
+        Fr v = fe_zero<FrP>();
+        v.v[0] = (uint32_t)((q < 0 ? -q : q) << 16);
+        if (q < 0) v = fe_neg<FrP>(v);
+        for (int l = 0; l < 4; l++) out[4 * i + l] = ((uint64_t)v.v[2 * l + 1] << 32) | v.v[2 * l];
+    }
+}
+
 size_t next_pow2(size_t n) {
     size_t p = 1;
     while (p < n) p <<= 1;
@@ -247,6 +265,16 @@ int zk_init(zk_ctx **out, int device, size_t hbm_budget_bytes) {
     return ZK_OK;
 }
 
+static bool layout_value_ok(int op, int value) {
+    switch (op) {
+        case ZK_TUNE_MSM_CHUNK:
+        case ZK_TUNE_MSM_TAIL: return value >= 1 && value <= 4;
+        case ZK_TUNE_MSM_SEG: return value >= 3 && value <= 5;
+        case ZK_TUNE_MSM_SEGBIG: return value >= 6 && value <= 8;
+        default: return false;
+    }
+}
+
 int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value) {
     if (!ctx || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
     Shared &sh = *ctx->sh;
@@ -257,6 +285,9 @@ int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value) {
     } else if (op == ZK_TUNE_NTT_RADIX) {
         if (value < 0 || value > 11) return ZK_EINVAL;
         sh.tuned_radix[log2n] = value;
+    } else if (op >= ZK_TUNE_MSM_CHUNK && op <= ZK_TUNE_MSM_SEGBIG) {
+        if (value != 0 && !layout_value_ok(op, value)) return ZK_EINVAL;
+        sh.tuned_layout[op - ZK_TUNE_MSM_CHUNK][log2n] = value;
     } else {
         return ZK_EINVAL;
     }
@@ -265,9 +296,17 @@ int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value) {
 
 int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value) {
     if (!ctx || !value || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
-    if (op == ZK_TUNE_MSM_WINDOW) *value = msm_pick_window(const_cast<zk_ctx *>(ctx), (size_t)1 << log2n, 1);
-    else if (op == ZK_TUNE_NTT_RADIX) *value = ntt_pass_radix(*ctx->sh, log2n);
-    else return ZK_EINVAL;
+    if (op == ZK_TUNE_MSM_WINDOW) {
+        *value = msm_pick_window(const_cast<zk_ctx *>(ctx), (size_t)1 << log2n, 1);
+    } else if (op == ZK_TUNE_NTT_RADIX) {
+        *value = ntt_pass_radix(*ctx->sh, log2n);
+    } else if (op >= ZK_TUNE_MSM_CHUNK && op <= ZK_TUNE_MSM_SEGBIG) {
+        const MsmLayout m = msm_layout(*ctx->sh, log2n);
+        const uint32_t v[4] = {m.chunk_log + 1, m.tail_log + 1, m.seg_small, m.seg_big};
+        *value = (int)v[op - ZK_TUNE_MSM_CHUNK];
+    } else {
+        return ZK_EINVAL;
+    }
     return ZK_OK;
 }
 
@@ -280,7 +319,11 @@ int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double 
     uint32_t *out = (uint32_t *)scratch(ctx, "tune.out", 64, &err);
     if (!data || !out) return err;
     cudaStream_t s = 0;
-    k_fill_random<<<1024, 256, 0, s>>>(data, n, 0x5eed0000ull + (uint64_t)log2n);
+    const bool layout = op >= ZK_TUNE_MSM_CHUNK && op <= ZK_TUNE_MSM_SEGBIG;
+    if (layout && op != ZK_TUNE_MSM_SEGBIG)
+        k_fill_quant<<<1024, 256, 0, s>>>(data, n, 0x5eed0000ull + (uint64_t)log2n);
+    else
+        k_fill_random<<<1024, 256, 0, s>>>(data, n, 0x5eed0000ull + (uint64_t)log2n);
     ZK_LAUNCHED();
     std::vector<float> t;
     cudaEvent_t e0, e1;
@@ -292,17 +335,21 @@ int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double 
         if (value < 1 || value > 11) rc = ZK_EINVAL;
         saved = ctx->sh->tuned_radix[log2n];
         ctx->sh->tuned_radix[log2n] = value;
+    } else if (layout) {
+        if (!layout_value_ok(op, value)) rc = ZK_EINVAL;
+        saved = ctx->sh->tuned_layout[op - ZK_TUNE_MSM_CHUNK][log2n];
+        ctx->sh->tuned_layout[op - ZK_TUNE_MSM_CHUNK][log2n] = value;
     } else if (op != ZK_TUNE_MSM_WINDOW || value < kMinWindow || value > kMaxWindow) {
         rc = ZK_EINVAL;
     }
     for (int r = 0; rc == ZK_OK && r <= reps; r++) {  // run 0 warms up (tables, twiddles)
         cudaEventRecord(e0, s);
-        if (op == ZK_TUNE_MSM_WINDOW) {
+        if (op == ZK_TUNE_MSM_WINDOW || layout) {
             MsmJob j;
             j.scalars = (const uint32_t *)data;
             j.n = (uint32_t)n;
             j.out = out;
-            rc = msm_batch_impl(ctx, &j, 1, value, s);
+            rc = msm_batch_impl(ctx, &j, 1, layout ? 0 : value, s);
         } else {
             rc = ntt_impl(ctx, (uint32_t *)data, n, false, s);
         }
@@ -313,6 +360,7 @@ int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double 
         if (r > 0) t.push_back(x);
     }
     if (op == ZK_TUNE_NTT_RADIX) ctx->sh->tuned_radix[log2n] = saved;
+    if (layout && layout_value_ok(op, value)) ctx->sh->tuned_layout[op - ZK_TUNE_MSM_CHUNK][log2n] = saved;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != ZK_OK) return rc;
@@ -379,7 +427,6 @@ int zk_destroy(zk_ctx *ctx) {
         }
         ctx->marks.clear();
         if (ctx->side) cudaStreamDestroy(ctx->side);
-        if (ctx->stat_host) cudaFreeHost(ctx->stat_host);
         for (auto &e : ctx->side_ev)
             if (e) cudaEventDestroy(e);
         for (auto &r : ctx->up.inflight) cudaEventDestroy(r.ev);

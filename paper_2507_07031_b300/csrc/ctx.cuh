@@ -57,6 +57,7 @@ struct Shared {
     int fold_degree = 2;         // folded relation: 2 (m1 o m2 - mu m3 = e) or 3 (m1 o m2 o m3 - mu^2 m4 = e)
     int tuned_window[29] = {};   // MSM window width per log2 length (0 = built-in)
     int tuned_radix[29] = {};    // largest NTT pass radix (log2) per log2 length (0 = built-in)
+    int tuned_layout[4][29] = {};  // MSM bucket layout per log2 length (0 = built-in): see MsmLayout
     ~Shared();
 };
 
@@ -99,8 +100,6 @@ struct zk_ctx {
     zk::Uploader up;
     bool capturing = false;  // inside a plan's graph capture: no allocation allowed
     cudaStream_t side = nullptr;         // fold tree: instance passes overlap the next level
-    uint32_t *stat_host = nullptr;       // pinned: per-job scalar widths read back by the MSM
-    size_t stat_cap = 0;
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
     int last_error = 0;
 };
@@ -189,6 +188,18 @@ int ntt_batch_impl(zk_ctx *ctx, uint32_t *const *data, const size_t *lens, size_
                    bool inverse, cudaStream_t s);
 int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s);
 int ntt_pass_radix(const Shared &sh, int L);  // tuned or built-in largest pass radix (log2)
+
+// Bucket layout of the MSM (tuned per log2 length, zk_tune_set ops
+// ZK_TUNE_MSM_CHUNK .. ZK_TUNE_MSM_SEGBIG):
+//   chunk_log : round-0 chunks are 2^chunk_log times longer when few buckets
+//               are in use (fewer partial sums for the tail to combine);
+//   tail_log  : a team-tail slice gives each lane 2^tail_log items;
+//   seg_small, seg_big : log2 of the bucket-reduction segments (seg_big
+//               while a level holds at least 2^13 items).
+struct MsmLayout {
+    uint32_t chunk_log, tail_log, seg_small, seg_big;
+};
+MsmLayout msm_layout(const Shared &sh, int log2n);
 
 // MSM (msm.cu).  Each job: scalars (device, canonical, 32 B each), length n,
 // output 64-byte canonical affine point (device).  c > 0 fixes the window

@@ -406,16 +406,20 @@ __global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, ui
 // Shape of phase 3 from the actual entries (their count at off0[nb], the
 // largest bucket and the nonempty buckets in stat): round 0 gives every
 // resident thread one chunk of p0 = ceil(entries / resident) entries (at
-// least kP0Min), so it runs as one wave; round rd runs while the largest
+// least kP0Min; 2^chunk_log times more when few buckets are in use), so it
+// runs as one wave; round rd runs while the largest
 // bucket still holds more than `thr` items (kPiece, or kTailItems when few
 // buckets are in use and the last stage may run on teams).
-__global__ void k_round_plan(const uint32_t *stat, const uint32_t *total, uint32_t resident,
+__global__ void k_round_plan(const uint32_t *stat, const uint32_t *total, uint32_t resident, uint32_t chunk_log,
                              uint32_t rounds, const uint32_t *off0, const uint32_t *offa, const uint32_t *offb,
                              Xyzz *pa, Xyzz *pb, RoundPlan *plan) {
     if (threadIdx.x || blockIdx.x) return;
     const uint32_t entries = *total;
-    const uint32_t p0 = max(kP0Min, (uint32_t)(((uint64_t)entries + resident - 1) / resident));
     const bool tail = stat[1] <= kTailBuckets;
+    // Few buckets in use: longer chunks (chunk_log) leave fewer partial sums
+    // for the team tail; the chunks still fill the GPU when it runs.
+    const uint32_t p0 = max(kP0Min, (uint32_t)(((uint64_t)entries + resident - 1) / resident))
+                        << (tail ? chunk_log : 0u);
     uint32_t x = stat[0], last = 0;
     const uint32_t thr = tail ? kTailItems : kPiece;
     for (uint32_t rd = 0; rd < (uint32_t)kMaxRounds; rd++) {
@@ -517,22 +521,22 @@ __global__ void k_buckets_final(FinalItems fi, DevJobs dj, uint32_t nb,
 
 // Last stage on teams (few buckets in use, each with up to kTailItems
 // items), in two levels.  Level A: team g sums slice g of the items, at most
-// kSlice of them (two per lane, then a tree over the lanes); bucket b's
-// slices are off_s[b] .. off_s[b + 1] - 1 (a scan of ceil(items / kSlice)),
-// and slice k covers its items kSlice k .. kSlice (k + 1) - 1.  Level B: a
-// team per bucket adds its at most kTailItems / kSlice partial sums in a
-// tree.  Every team operation spreads one point addition over the block's
-// four warps (team.cuh), so the depth is about ten additions.
-constexpr uint32_t kSlice = 64;
+// 32 L of them (lane l adds items l, l + 32, ..., then a tree over the
+// lanes; L = 2^tail_log); bucket b's slices are off_s[b] .. off_s[b + 1] - 1
+// (a scan of ceil(items / 32 L)), and slice k covers its items 32 L k ..
+// 32 L (k + 1) - 1.  Level B: a team per bucket adds its partial sums (at
+// most kTailItems / 32) in a tree.  Every team operation spreads one point
+// addition over the block's four warps (team.cuh).
 constexpr int kBtAcc = 0, kBtIn = 4, kBtTmp = 8, kBtT = 12;
-static_assert(kTailItems / kSlice <= 32, "level B sums one partial per lane");
+static_assert(kTailItems / 32 <= 32, "level B sums one partial per lane");
 
 __global__ void __launch_bounds__(kTeamThreads)
-    k_tail_slices(FinalItems fi, DevJobs dj, uint32_t nb, const uint32_t *__restrict__ off_s,
+    k_tail_slices(FinalItems fi, DevJobs dj, uint32_t nb, uint32_t tail_log, const uint32_t *__restrict__ off_s,
                   const RoundPlan *__restrict__ plan) {
     __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
     if (!plan->team) return;
     const uint32_t l = team_lane(), w = team_warp();
+    const uint32_t slice = 32u << tail_log;
     const bool entries = plan->last == 0;
     const uint32_t *off = plan->off;
     const Xyzz *in = entries ? nullptr : (((plan->last - 1) & 1) ? fi.in1 : fi.in0);
@@ -540,8 +544,8 @@ __global__ void __launch_bounds__(kTeamThreads)
     const uint32_t nslices = off_s[nb];
     for (uint32_t g = blockIdx.x; g < nslices; g += gridDim.x) {  // block-uniform
         const uint32_t b = upper_index(off_s, nb, g);
-        const uint32_t lo = off[b] + (g - off_s[b]) * kSlice;
-        const uint32_t hi = min(lo + kSlice, off[b + 1]);
+        const uint32_t lo = off[b] + (g - off_s[b]) * slice;
+        const uint32_t hi = min(lo + slice, off[b + 1]);
         const Affine *table = entries ? dj.jobs[search(dj.bbase, 0, dj.count, b)].table : nullptr;
         // Coordinate w of item j (a table point with sign, or a partial sum).
         auto fetch = [&](uint32_t j) -> Fq {
@@ -553,9 +557,12 @@ __global__ void __launch_bounds__(kTeamThreads)
             return (w == 1 && (v & 1)) ? fe_neg<FqP>(c) : c;
         };
         tf_store(f, kBtAcc + w, fetch(lo + l));
-        tf_store(f, kBtIn + w, fetch(lo + 32 + l));
+        for (uint32_t j = lo + 32; j < hi; j += 32) {
+            tf_store(f, kBtIn + w, fetch(j + l));
+            __syncthreads();
+            team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
+        }
         __syncthreads();
-        if (hi - lo > 32) team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
         for (uint32_t d = 16; d >= 1; d >>= 1) {
             if (d >= hi - lo) continue;  // lanes d.. hold infinity
             team_shift(f, kBtAcc, kBtTmp, (int)d);
@@ -599,9 +606,10 @@ struct AccumShape {
     size_t cap0;       // items after round 0 (bound)
     uint32_t resident; // threads of one wave of k_pieces_first
     uint32_t blocks;   // its grid
+    MsmLayout layout;  // bucket layout (chunk multiplier, tail slices)
 };
 
-AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms) {
+AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms, const MsmLayout &layout) {
     static const int per_sm = [] {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pieces_first, 128, 0) != cudaSuccess || b < 1) {
@@ -611,6 +619,7 @@ AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms) {
         return b;
     }();
     AccumShape a;
+    a.layout = layout;
     a.blocks = (uint32_t)std::max(sms, 1) * (uint32_t)per_sm;
     a.resident = a.blocks * 128;
     // p0 >= kP0Min bounds the rounds; p0 >= entries / resident bounds the
@@ -619,9 +628,9 @@ AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms) {
     for (size_t x = worst; x > kPiece && a.rounds < kMaxRounds; a.rounds++)
         x = (x + (a.rounds ? kPiece : kP0Min) - 1) / (a.rounds ? kPiece : kP0Min);
     const size_t chunks = std::min<size_t>(a.resident, (total + kP0Min - 1) / kP0Min);
-    // The team tail's partial sums (at most entries / kSlice + nb) reuse a
+    // The team tail's partial sums (at most entries / 32 + nb) reuse a
     // piece buffer.
-    a.cap0 = std::max<size_t>(chunks, (total + kSlice - 1) / kSlice) + nb + 1;
+    a.cap0 = std::max<size_t>(chunks, (total + 31) / 32) + nb + 1;
     return a;
 }
 
@@ -643,8 +652,8 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
     const unsigned mb = (unsigned)std::min<size_t>((nb + 255) / 256, (size_t)sms * 4);
     k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, w.stat);
     ZK_LAUNCHED();
-    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, (uint32_t)a.rounds, off0, w.offa, w.offb, w.pa,
-                                  w.pb, w.plan);
+    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, a.layout.chunk_log, (uint32_t)a.rounds, off0,
+                                  w.offa, w.offb, w.pa, w.pb, w.plan);
     ZK_LAUNCHED();
     const uint32_t *off_prev = off0;
     size_t cap = a.cap0;
@@ -670,9 +679,10 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
     ZK_LAUNCHED();
     // Gated on the device: runs when few buckets are in use and they still
     // hold many items (the round plan's `team`).
-    ZK_TRY(scan_exclusive(nullptr, w.offs, nb, (int)kSlice, w.scan_tmp, s, &w.plan->team, nullptr, &w.plan->off));
+    ZK_TRY(scan_exclusive(nullptr, w.offs, nb, (int)(32u << a.layout.tail_log), w.scan_tmp, s, &w.plan->team,
+                          nullptr, &w.plan->off));
     const unsigned tb = (unsigned)std::min<size_t>(std::max<uint32_t>(nb, 1), (size_t)sms * 8);
-    k_tail_slices<<<tb, kTeamThreads, 0, s>>>(fi, dj, nb, w.offs, w.plan);
+    k_tail_slices<<<tb, kTeamThreads, 0, s>>>(fi, dj, nb, a.layout.tail_log, w.offs, w.plan);
     ZK_LAUNCHED();
     k_tail_buckets<<<tb, kTeamThreads, 0, s>>>(nb, w.offs, w.plan, buckets);
     ZK_LAUNCHED();
@@ -712,22 +722,21 @@ struct RedSched {
     uint32_t glog[kMaxLevels];  // log2 of the segment (the final level: all items)
 };
 
-__host__ __device__ constexpr RedSched red_sched(uint32_t logB) {
+__host__ __device__ constexpr RedSched red_sched(uint32_t logB, uint32_t gbig = 8, uint32_t gsmall = 5) {
     RedSched r{};
     uint32_t m = logB;
     for (uint32_t L = 0; L < (uint32_t)kMaxLevels; L++) {
         r.mlog[L] = m;
-        if (m <= 5 || L + 1 == (uint32_t)kMaxLevels) {
+        if (m <= 5 || L + 1 == (uint32_t)kMaxLevels) {  // the last level takes what is left
             r.glog[L] = m;
             r.levels = L + 1;
             break;
         }
-        r.glog[L] = m >= 13 ? 8 : 5;
+        r.glog[L] = m >= 13 ? gbig : gsmall;
         m -= r.glog[L];
     }
     return r;
 }
-static_assert(kMaxWindow - 1 <= 8 + 5 + 5 + 5, "reduction levels");
 
 // Item buffers of levels 1 .. kMaxLevels - 1 (V and S); job j's items of
 // level L start at jobs[j].lbase[L - 1].
@@ -741,11 +750,12 @@ constexpr int kSlR = 0, kSlW = 4, kSlYA = 8, kSlIn = 12, kSlYIn = 16, kSlTmp = 2
 constexpr int kSlots = kSlT + kTeamTemps;
 
 __global__ void __launch_bounds__(kTeamThreads)
-    k_reduce_team(const Xyzz *__restrict__ buckets, RedBufs rb, DevJobs dj, uint32_t level) {
+    k_reduce_team(const Xyzz *__restrict__ buckets, RedBufs rb, DevJobs dj, uint32_t level, uint32_t gbig,
+                  uint32_t gsmall) {
     __shared__ uint32_t f[kSlots * 8 * 32];
     const uint32_t job = blockIdx.y;
     const JobDesc &J = dj.jobs[job];
-    const RedSched r = red_sched(J.logB);
+    const RedSched r = red_sched(J.logB, gbig, gsmall);
     if (level >= r.levels) return;  // final at an earlier level
     const bool final_level = level + 1 == r.levels;
     const uint32_t seg = 1u << r.glog[level];
@@ -827,18 +837,18 @@ __global__ void __launch_bounds__(kTeamThreads)
 // Item capacity of reduction level L (1 .. kMaxLevels - 1) and the teams of
 // level L (0 ..) for a job whose bucket count may be any 2^logB with
 // logB in [lo, hi] (the device lowers logB for short scalars).
-constexpr uint32_t red_cap(uint32_t lo, uint32_t hi, uint32_t L) {
+constexpr uint32_t red_cap(uint32_t lo, uint32_t hi, uint32_t L, uint32_t gbig = 8, uint32_t gsmall = 5) {
     uint32_t c = 0;
     for (uint32_t b = lo; b <= hi; b++) {
-        const RedSched r = red_sched(b);
+        const RedSched r = red_sched(b, gbig, gsmall);
         if (L < r.levels) c = std::max(c, 1u << r.mlog[L]);
     }
     return c;
 }
-constexpr uint32_t red_teams(uint32_t lo, uint32_t hi, uint32_t L) {
+constexpr uint32_t red_teams(uint32_t lo, uint32_t hi, uint32_t L, uint32_t gbig = 8, uint32_t gsmall = 5) {
     uint32_t t = 0;
     for (uint32_t b = lo; b <= hi; b++) {
-        const RedSched r = red_sched(b);
+        const RedSched r = red_sched(b, gbig, gsmall);
         if (L < r.levels) t = std::max(t, 1u << (r.mlog[L] - r.glog[L]));
     }
     return t;
@@ -847,12 +857,14 @@ constexpr uint32_t red_teams(uint32_t lo, uint32_t hi, uint32_t L) {
 // Launches the reduction levels for jobs whose bucket counts are 2^logB with
 // logB in [lo[k], hi[k]].
 int launch_reduce(const Xyzz *buckets, const RedBufs &rb, const DevJobs &dj, const uint32_t *lo,
-                  const uint32_t *hi, size_t count, cudaStream_t s) {
+                  const uint32_t *hi, size_t count, const MsmLayout &ly, cudaStream_t s) {
     for (uint32_t level = 0; level < (uint32_t)kMaxLevels; level++) {
         uint32_t gx = 0;
-        for (size_t k = 0; k < count; k++) gx = std::max(gx, red_teams(lo[k], hi[k], level));
+        for (size_t k = 0; k < count; k++)
+            gx = std::max(gx, red_teams(lo[k], hi[k], level, ly.seg_big, ly.seg_small));
         if (!gx) break;
-        k_reduce_team<<<dim3(gx, (unsigned)count), kTeamThreads, 0, s>>>(buckets, rb, dj, level);
+        k_reduce_team<<<dim3(gx, (unsigned)count), kTeamThreads, 0, s>>>(buckets, rb, dj, level, ly.seg_big,
+                                                                          ly.seg_small);
         ZK_LAUNCHED();
     }
     return ZK_OK;
@@ -904,6 +916,20 @@ int default_window(size_t n) {
 }
 
 }  // namespace
+
+// Built-in bucket layout, the winners of a tuning sweep on B300 (int8 x 2^16
+// and uniform scalars, 2^16 .. 2^20): chunk multiplier 1, eight items per
+// lane in a tail slice, reduction segments of 2^4 and 2^6 (2^8 above 2^18
+// points).
+MsmLayout msm_layout(const Shared &sh, int lg) {
+    MsmLayout m{0, 3, 4, lg <= 18 ? 6u : 8u};
+    if (lg < 0 || lg > kMaxLogN) return m;
+    if (sh.tuned_layout[0][lg]) m.chunk_log = (uint32_t)sh.tuned_layout[0][lg] - 1;
+    if (sh.tuned_layout[1][lg]) m.tail_log = (uint32_t)sh.tuned_layout[1][lg] - 1;
+    if (sh.tuned_layout[2][lg]) m.seg_small = (uint32_t)sh.tuned_layout[2][lg];
+    if (sh.tuned_layout[3][lg]) m.seg_big = (uint32_t)sh.tuned_layout[3][lg];
+    return m;
+}
 
 int msm_pick_window(zk_ctx *ctx, size_t n, size_t count) {
     (void)count;
@@ -993,7 +1019,28 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     size_t worst = 1;
     for (size_t k = 0; k < count; k++)
         worst = std::max(worst, (size_t)jv[k].job.n * windows_for(jv[k].c));
-    const AccumShape shape = accum_shape(entries_max, worst, nb, sh.sms);
+    // Bucket layout of the call: tuned for the longest job.
+    uint32_t maxn = 1;
+    for (size_t k = 0; k < count; k++) maxn = std::max(maxn, jv[k].job.n);
+    int lgmax = 0;
+    while (((size_t)1 << lgmax) < maxn) lgmax++;
+    MsmLayout ly = msm_layout(sh, lgmax);
+    // The tuned segments suit one MSM, whose reduction is latency bound.  A
+    // batch of many MSMs (a fold-tree level: 512 of them) keeps every SM
+    // busy instead; there larger segments amortise each team's scans, so the
+    // large segment grows while level 0 would still hold far more teams than
+    // the GPU keeps resident (about six per SM).
+    {
+        auto teams0 = [&](uint32_t g) {
+            size_t t = 0;
+            for (size_t k = 0; k < count; k++)
+                if (jv[k].c - 1 >= 13) t += (size_t)1 << (jv[k].c - 1 - (int)g);
+            return t;
+        };
+        const size_t resident = (size_t)std::max(sh.sms, 1) * 6;
+        while (ly.seg_big < 8 && teams0(ly.seg_big) > 4 * resident) ly.seg_big++;
+    }
+    const AccumShape shape = accum_shape(entries_max, worst, nb, sh.sms, ly);
     const size_t piece_cap = shape.cap0;
     // Reduction levels: a job's bucket count is 2^logB with logB between
     // kMinWindow - 1 (short scalars, decided on the device) and c - 1.
@@ -1002,7 +1049,8 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     for (size_t k = 0; k < count; k++) {
         hi[k] = (uint32_t)(jv[k].c - 1);
         lo[k] = stats ? (uint32_t)(kMinWindow - 1) : hi[k];
-        for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++) lvl_items[L] += red_cap(lo[k], hi[k], L);
+        for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++)
+            lvl_items[L] += red_cap(lo[k], hi[k], L, ly.seg_big, ly.seg_small);
     }
 
     // Workspace.
@@ -1059,7 +1107,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hd[k].t16n = t16n[k];
         for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++) {
             hd[k].lbase[L - 1] = lb[L];
-            lb[L] += red_cap(lo[k], hi[k], L);
+            lb[L] += red_cap(lo[k], hi[k], L, ly.seg_big, ly.seg_small);
         }
         hs[k + 1] = hs[k] + jv[k].job.n;
         hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
@@ -1114,7 +1162,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
 
     // 4-5: bucket reduction and output.
     PhaseScope ph_reduce(ctx, ZK_PHASE_MSM_REDUCE, s);
-    return launch_reduce(buckets, rb, dj, lo.data(), hi.data(), count, s);
+    return launch_reduce(buckets, rb, dj, lo.data(), hi.data(), count, ly, s);
 }
 
 }  // namespace zk
@@ -1292,11 +1340,13 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
     ZK_TRY((launch_recode_c<kNoAllocC, true>(dj, 0, 1, total, (uint32_t)tab->n, nullptr, cursor,
                                               sorted, s)));
-    const AccumShape shape = accum_shape((size_t)n * kNoAllocW, (size_t)n * kNoAllocW, nb, sh.sms);
+    // The built-in layout (the workspace is sized for it).
+    const MsmLayout ly{0, 1, 5, 8};
+    const AccumShape shape = accum_shape((size_t)n * kNoAllocW, (size_t)n * kNoAllocW, nb, sh.sms, ly);
     if (shape.cap0 > kNoAllocPieces) return ZK_EINVAL;  // cannot happen: p0 >= kP0Min
     const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)(ws + kNaPlan), (RoundPlan *)(ws + kNaPlan + 256),
                        scan_tmp, (uint32_t *)(ws + kNaOffS)};
     ZK_TRY(launch_accumulate(sorted, counts, off0, nb, shape, dj, ab, buckets, sh.sms, s));
     const uint32_t logB = kNoAllocC - 1;
-    return launch_reduce(buckets, rb, dj, &logB, &logB, 1, s);
+    return launch_reduce(buckets, rb, dj, &logB, &logB, 1, ly, s);
 }

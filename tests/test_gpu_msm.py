@@ -176,14 +176,46 @@ def test_autotune_table(zk, ctx_small, tmp_path):
     from paper_2507_07031_b300 import autotune
     path = str(tmp_path / "tune.json")
     table = autotune.tune(ctx_small, msm_logs=[10, 12], ntt_logs=[10, 12], reps=1,
-                          windows=range(10, 14), radices=range(5, 12), path=path)
+                          windows=range(10, 14), radices=range(5, 12), path=path, layout_logs=[12])
     assert set(table["msm_window"]) == {"10", "12"} and set(table["ntt_radix"]) == {"10", "12"}
     for lg, e in table["msm_window"].items():
         assert zk.zk_tune_get(ctx_small, zk.ZK_TUNE_MSM_WINDOW, int(lg)) == e["best"]
+    for name, (op, values) in autotune.MSM_LAYOUT.items():
+        e = table["msm_layout"][name]["12"]
+        assert set(e["ms"]) == {str(v) for v in values}
+        assert zk.zk_tune_get(ctx_small, op, 12) == e["best"]
     autotune.apply(ctx_small, path)
     for lg in (10, 12):
         zk.zk_tune_set(ctx_small, zk.ZK_TUNE_MSM_WINDOW, lg, 0)
         zk.zk_tune_set(ctx_small, zk.ZK_TUNE_NTT_RADIX, lg, 0)
+        for op, _ in autotune.MSM_LAYOUT.values():
+            zk.zk_tune_set(ctx_small, op, lg, 0)
+    assert zk.zk_tune_get(ctx_small, zk.ZK_TUNE_MSM_TAIL, 12) == 4  # built-in: eight items per lane
+
+
+@pytest.fixture(scope="module")
+def layout_case():
+    n = 1 << 18
+    return {"int8": Z.zkml_scalars(31, n), "uniform": Z.fr_uniform(32, n)}
+
+
+@pytest.mark.parametrize("op,value", [("CHUNK", v) for v in range(1, 5)] + [("TAIL", v) for v in range(1, 5)]
+                         + [("SEG", v) for v in range(3, 6)] + [("SEGBIG", v) for v in range(6, 9)])
+def test_msm_every_bucket_layout(zk, orc, ctx_big, tau, layout_case, op, value):
+    """Every value of every bucket-layout knob gives the closed form, on
+    quantised scalars (2^18 entries in 128 buckets: round 0, the team tail,
+    small reduction segments) and uniform ones (many buckets, large
+    segments)."""
+    code = getattr(zk, "ZK_TUNE_MSM_" + op)
+    try:
+        zk.zk_tune_set(ctx_big, code, 18, value)
+        assert zk.zk_tune_get(ctx_big, code, 18) == value
+        for name, c in layout_case.items():
+            assert pts_equal(_commit(zk, ctx_big, c), orc.commit_coeffs_tau(c, tau)), name
+    finally:
+        zk.zk_tune_set(ctx_big, code, 18, 0)
+    with pytest.raises(zk.ZkError):
+        zk.zk_tune_set(ctx_big, code, 18, 99)
 
 
 def test_msm_small_scalar_path(zk, orc, ctx_small, tau):
