@@ -192,28 +192,37 @@ __global__ void __launch_bounds__(kTeamThreads) k_fold_instance(const FoldDesc *
     xyzz_store_canonical(d.Ox + 16 * out, r);
 }
 
-// Leaf: out = m1 o m2 (degree 2: out = m3) or m1 o m2 o m3 (degree 3, m3 given:
-// out = m4), e = 0, mu = 1, E = infinity (C_i are written by the MSM).
-__global__ void k_leaf(const uint32_t *m1, const uint32_t *m2, const uint32_t *m3, uint32_t *out,
-                       uint32_t *e, uint32_t *x, uint32_t n) {
+// Leaves: out = m1 o m2 (degree 2: out = m3) or m1 o m2 o m3 (degree 3, m3
+// given: out = m4), e = 0, mu = 1, E = infinity (C_i are written by the MSM).
+// A group of leaves in one launch (blockIdx.y = leaf): the k_leaf work, and
+// on the INTT route a copy of the four witness vectors (the derived one as
+// just computed) into the workspace the batched INTT transforms in place.
+struct LeafDesc {
+    const uint32_t *m[4];
+    uint32_t *out;  // the derived vector: m[2] (degree 2) or m[3] (degree 3)
+    uint32_t *e, *x;
+    uint32_t *ws;   // 4 n elements, or null (Lagrange route: commit in place)
+};
+
+__global__ void k_leaf_batch(const LeafDesc *__restrict__ descs, uint32_t n, int degree) {
+    const LeafDesc &L = descs[blockIdx.y];
+    const int derived = degree == 3 ? 3 : 2;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const size_t o = 8 * (size_t)k;
-        Fr a = fe_to_mont<FrP>(fe_load<FrP>(m1 + o));
-        Fr p = fe_mul<FrP>(a, fe_load<FrP>(m2 + o));  // canonical m1 m2
-        if (m3) p = fe_mul<FrP>(fe_to_mont<FrP>(p), fe_load<FrP>(m3 + o));
-        fe_store<FrP>(out + o, p);
-        fe_store<FrP>(e + o, fe_zero<FrP>());
+        Fr p = fe_mul<FrP>(fe_to_mont<FrP>(fe_load<FrP>(L.m[0] + o)), fe_load<FrP>(L.m[1] + o));  // canonical m1 m2
+        if (degree == 3) p = fe_mul<FrP>(fe_to_mont<FrP>(p), fe_load<FrP>(L.m[2] + o));
+        fe_store<FrP>(L.out + o, p);
+        fe_store<FrP>(L.e + o, fe_zero<FrP>());
+        if (L.ws) {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                fe_store<FrP>(L.ws + (size_t)i * n * 8 + o, i == derived ? p : fe_load<FrP>(L.m[i] + o));
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x < 16) {
-        x[64 + threadIdx.x] = 0;                        // E = infinity
-        if (threadIdx.x < 8) x[kInstMu + threadIdx.x] = threadIdx.x == 0 ? 1u : 0u;  // mu = 1
+        L.x[64 + threadIdx.x] = 0;                        // E = infinity
+        if (threadIdx.x < 8) L.x[kInstMu + threadIdx.x] = threadIdx.x == 0 ? 1u : 0u;  // mu = 1
     }
-}
-
-// Copy one vector (workspace staging for INTT before a commitment).
-__global__ void k_copy(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = src[i];
 }
 
 bool pow2(size_t n) { return n && !(n & (n - 1)); }
@@ -446,14 +455,16 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
         std::vector<uint32_t *> vecs;
         std::vector<size_t> lens;
         std::vector<MsmJob> jobs;
+        std::vector<LeafDesc> hd(G);
+        const int degree = ctx->sh->fold_degree;
         for (size_t a = a0; a < a1; a++) {
             const zk_acc &A = accs[a];
-            const bool three = ctx->sh->fold_degree == 3;
-            k_leaf<<<elem_blocks((uint32_t)n), 256, 0, s>>>(
-                (const uint32_t *)A.m[0], (const uint32_t *)A.m[1],
-                three ? (const uint32_t *)A.m[2] : nullptr, (uint32_t *)(three ? A.m[3] : A.m[2]),
-                (uint32_t *)A.e, (uint32_t *)A.x, (uint32_t)n);
-            ZK_LAUNCHED();
+            LeafDesc &d = hd[a - a0];
+            for (int i = 0; i < 4; i++) d.m[i] = (const uint32_t *)A.m[i];
+            d.out = (uint32_t *)(degree == 3 ? A.m[3] : A.m[2]);
+            d.e = (uint32_t *)A.e;
+            d.x = (uint32_t *)A.x;
+            d.ws = lagrange ? nullptr : ws + (a - a0) * 4 * n * 8;
             for (int i = 0; i < 4; i++) {
                 MsmJob j;
                 j.n = (uint32_t)n;
@@ -461,11 +472,8 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
                 if (lagrange) {  // commit the evaluations in place
                     j.scalars = (const uint32_t *)A.m[i];
                     j.basis = lg;
-                } else {         // interpolate a copy, then commit over the SRS
-                    uint32_t *dst = ws + ((a - a0) * 4 + i) * n * 8;
-                    k_copy<<<elem_blocks((uint32_t)n), 256, 0, s>>>((const uint4 *)A.m[i],
-                                                                    (uint4 *)dst, n * 2);
-                    ZK_LAUNCHED();
+                } else {         // interpolate the workspace copy, then commit over the SRS
+                    uint32_t *dst = d.ws + (size_t)i * n * 8;
                     vecs.push_back(dst);
                     lens.push_back(n);
                     j.scalars = dst;
@@ -473,6 +481,12 @@ int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s
                 jobs.push_back(j);
             }
         }
+        LeafDesc *dd = (LeafDesc *)scratch(ctx, "leaf.descs", G * sizeof(LeafDesc), &err);
+        if (!dd) return err;
+        ZK_TRY(upload(ctx, dd, hd.data(), G * sizeof(LeafDesc), s));
+        const unsigned bx = std::max(1u, std::min(elem_blocks((uint32_t)n), (unsigned)(4 * ctx->sh->sms / G + 1)));
+        k_leaf_batch<<<dim3(bx, (unsigned)G), 256, 0, s>>>(dd, (uint32_t)n, degree);
+        ZK_LAUNCHED();
         if (!lagrange) ZK_TRY(ntt_batch_impl(ctx, vecs.data(), lens.data(), vecs.size(), true, s));
         ZK_TRY(msm_batch_impl(ctx, jobs.data(), jobs.size(), 0, s));
     }

@@ -727,13 +727,16 @@ __host__ __device__ constexpr RedSched red_sched(uint32_t logB, uint32_t gbig = 
     uint32_t m = logB;
     for (uint32_t L = 0; L < (uint32_t)kMaxLevels; L++) {
         r.mlog[L] = m;
-        if (m <= 5 || L + 1 == (uint32_t)kMaxLevels) {  // the last level takes what is left
+        const uint32_t g = m >= 13 ? gbig : gsmall;
+        // A level whose items fit one team, or one segment, is final; so is
+        // the last level, which takes what is left.
+        if (m <= 5 || g >= m || L + 1 == (uint32_t)kMaxLevels) {
             r.glog[L] = m;
             r.levels = L + 1;
             break;
         }
-        r.glog[L] = m >= 13 ? gbig : gsmall;
-        m -= r.glog[L];
+        r.glog[L] = g;
+        m -= g;
     }
     return r;
 }
@@ -1026,19 +1029,28 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     while (((size_t)1 << lgmax) < maxn) lgmax++;
     MsmLayout ly = msm_layout(sh, lgmax);
     // The tuned segments suit one MSM, whose reduction is latency bound.  A
-    // batch of many MSMs (a fold-tree level: 512 of them) keeps every SM
-    // busy instead; there larger segments amortise each team's scans, so the
-    // large segment grows while level 0 would still hold far more teams than
-    // the GPU keeps resident (about six per SM).
+    // batch of many MSMs (a fold-tree level: 512 of them; a model's tiny
+    // commitments: thousands) keeps every SM busy instead; there larger
+    // segments amortise each team's scans, so the segments grow (the small
+    // one first, if any job uses it) while level 0 would still hold far more
+    // teams than the GPU keeps resident (about six per SM).
     {
-        auto teams0 = [&](uint32_t g) {
+        auto teams0 = [&](uint32_t gb, uint32_t gs) {
             size_t t = 0;
-            for (size_t k = 0; k < count; k++)
-                if (jv[k].c - 1 >= 13) t += (size_t)1 << (jv[k].c - 1 - (int)g);
+            for (size_t k = 0; k < count; k++) {
+                const uint32_t lb = (uint32_t)jv[k].c - 1, g = lb >= 13 ? gb : gs;
+                t += lb > g ? (size_t)1 << (lb - g) : 1;
+            }
             return t;
         };
+        bool small_used = false;
+        for (size_t k = 0; k < count; k++) small_used |= jv[k].c - 1 < 13;
         const size_t resident = (size_t)std::max(sh.sms, 1) * 6;
-        while (ly.seg_big < 8 && teams0(ly.seg_big) > 4 * resident) ly.seg_big++;
+        while (teams0(ly.seg_big, ly.seg_small) > 4 * resident) {
+            if (small_used && ly.seg_small < 8) ly.seg_small++;
+            else if (ly.seg_big < 8) ly.seg_big++;
+            else break;
+        }
     }
     const AccumShape shape = accum_shape(entries_max, worst, nb, sh.sms, ly);
     const size_t piece_cap = shape.cap0;

@@ -193,6 +193,23 @@ def test_autotune_table(zk, ctx_small, tmp_path):
     assert zk.zk_tune_get(ctx_small, zk.ZK_TUNE_MSM_TAIL, 12) == 4  # built-in: eight items per lane
 
 
+def test_large_mixed_batch(zk, orc, ctx_big, tau):
+    """A batch of many small and some large MSMs (as a model's witness
+    commitments): the bucket reduction then widens its segments to amortise
+    each team's scans, down to levels whose items fit one segment."""
+    import torch
+    rng = np.random.default_rng(5)
+    lens = [int(x) for x in (1 << rng.integers(6, 13, 600))] + [1 << 14] * 6 + [3000, 1 << 15]
+    vecs = [Z.zkml_scalars(40_000 + i, l) if i % 3 else Z.fr_uniform(40_000 + i, l)
+            for i, l in enumerate(lens)]
+    out = torch.zeros((len(lens), 8), dtype=torch.int64, device="cuda")
+    zk.zk_commit_batch(ctx_big, [to_dev(v) for v in vecs], out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    for k, v in enumerate(vecs):
+        assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (k, lens[k])
+
+
 @pytest.fixture(scope="module")
 def layout_case():
     n = 1 << 18
