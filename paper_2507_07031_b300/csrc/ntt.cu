@@ -35,6 +35,9 @@ namespace {
 constexpr int kMaxRadixLog = 11;
 constexpr int kMaxJ = 4;
 constexpr size_t kMaxSmem = (size_t)128 << 10;  // J R 32 bytes per CTA
+constexpr uint32_t kMaxRegJR = 1u << kMaxRadixLog;  // largest J R of the register-tiled pass (R alone can reach it)
+constexpr uint32_t kRegJR = 1024;               // its J R where the length allows
+constexpr int kRegMinLog = 9;                   // smallest radix (log2) on the register-tiled pass
 
 // w = 5^((r - 1) / 2^lg), the primitive 2^lg-th root of unity (5 generates
 // the 2-Sylow subgroup of F_r^*: it is a quadratic non-residue).
@@ -175,6 +178,180 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     }
 }
 
+// Register-tiled pass for sub-transforms of R = 2^LR >= 8 points, J = 2^logJ
+// of them per CTA (the host picks J R = 1024 where it can), T = J R / 4
+// threads.  Each thread holds E = 4 elements of one sub-transform in
+// registers and runs the radix-2 DIF stages two at a time: for stages
+// s0 .. s0 + ne - 1 (half-sizes h = R / 2^(s + 1)) the
+// pairs (r, r + h) of a thread are its own elements when it holds
+//     r = blk 2^ne S + kk S + b,   kk < 2^ne,  S = R / 2^(s0 + ne)
+// (b < S, blk < 2^s0), so one shared-memory exchange per group of two
+// stages (instead of one per stage) re-deals the elements between groups.
+// Four elements per thread measured faster than eight (more resident warps)
+// at 2^20 and 2^22.
+// Shared memory is limb-planar with one padding word per 32 (word of
+// element i of sub-transform jj at l P + pad(i J + jj)), which keeps the
+// strided exchanges free of bank conflicts.  Inter-pass twiddles, the
+// output permutation and the final n^-1 scaling are as in k_ntt_pass.
+constexpr int kRegLE = 2;  // log2 elements per thread
+
+__device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
+
+template <int LR>
+__global__ void __launch_bounds__(512) k_ntt_reg(PassArgs a) {
+    extern __shared__ uint32_t sm[];
+    constexpr uint32_t R = 1u << LR, E = 1u << kRegLE;
+    const uint32_t LJ = a.logJ, J = 1u << LJ, JR = J * R;
+    const uint32_t T = JR / E;            // threads doing work
+    const uint32_t P = JR + JR / 32;      // padded words per limb plane
+    constexpr int G = (LR + kRegLE - 1) / kRegLE;  // stage groups
+    const uint64_t n = 1ull << a.logn;
+    const uint32_t Ns = 1u << a.logNs;
+    const uint64_t stride = n >> LR;  // n / R
+    const uint32_t *in = a.in_tab[blockIdx.y];
+    uint32_t *out = a.out_tab[blockIdx.y];
+    const uint64_t j0 = (uint64_t)blockIdx.x * J;
+    const uint32_t tshift = a.logn - a.logNs - LR;
+    const uint32_t t = threadIdx.x;
+    const bool worker = t < T;
+    const uint32_t jj = t & (J - 1), rest = t >> LJ;
+    Fr x[E];
+
+    // Element k of this thread in stage group g (ne stages starting at s0).
+    auto elem_r = [&](int g, uint32_t k) -> uint32_t {
+        const int s0 = g * kRegLE;
+        const int ne = LR - s0 < kRegLE ? LR - s0 : kRegLE;
+        const int lS = LR - s0 - ne;
+        const uint32_t gi = (rest << (kRegLE - ne)) + (k >> ne);
+        const uint32_t blk = gi >> lS, b = gi & ((1u << lS) - 1);
+        return (blk << (ne + lS)) + ((k & ((1u << ne) - 1)) << lS) + b;
+    };
+
+    // Load group 0's elements with the inter-pass twiddle omega_{Ns R}^{r (j mod Ns)}.
+    if (worker) {
+        const uint64_t j = j0 + jj;
+        const uint64_t m = j & (Ns - 1);
+#pragma unroll
+        for (uint32_t k = 0; k < E; k++) {
+            const uint32_t r = elem_r(0, k);
+            Fr v = fe_load<FrP>(in + 8 * (j + (uint64_t)r * stride));
+            const uint64_t ex = ((uint64_t)r * m) << tshift;
+            if (ex) v = fe_mul<FrP>(v, fe_ldg<FrP>(a.tw_n + (a.inverse ? n - ex : ex)));
+            x[k] = v;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const int s0 = g * kRegLE;
+        const int ne = LR - s0 < kRegLE ? LR - s0 : kRegLE;
+        if (g > 0) {  // re-deal: write by group g-1's layout, read by group g's
+            if (worker) {
+#pragma unroll
+                for (uint32_t k = 0; k < E; k++) {
+                    const uint32_t w = pad32(elem_r(g - 1, k) * J + jj);
+#pragma unroll
+                    for (int l = 0; l < 8; l++) sm[l * P + w] = x[k].v[l];
+                }
+            }
+            __syncthreads();
+            if (worker) {
+#pragma unroll
+                for (uint32_t k = 0; k < E; k++) {
+                    const uint32_t w = pad32(elem_r(g, k) * J + jj);
+#pragma unroll
+                    for (int l = 0; l < 8; l++) x[k].v[l] = sm[l * P + w];
+                }
+            }
+            __syncthreads();
+        }
+        if (!worker) continue;
+#pragma unroll
+        for (int ls = 0; ls < ne; ls++) {
+            const int s = s0 + ls;
+            const uint32_t hk = 1u << (ne - 1 - ls);  // pair distance in k
+#pragma unroll
+            for (uint32_t k = 0; k < E; k++) {
+                if (k & hk) continue;
+                const uint32_t k2 = k + hk;
+                const Fr u = x[k], v = x[k2];
+                x[k] = fe_add<FrP>(u, v);
+                Fr d = fe_sub<FrP>(u, v);
+                // pos = r mod h with h = S 2^(ne - 1 - ls)
+                const uint32_t pos = elem_r(g, k) & ((R >> (s + 1)) - 1);
+                if (pos) {
+                    uint32_t idx = pos << s;
+                    if (a.inverse) idx = R - idx;
+                    d = fe_mul<FrP>(d, fe_ldg<FrP>(a.tw_R + idx));
+                }
+                x[k2] = d;
+            }
+        }
+    }
+    // Natural-order output: element at position i holds V_{bitrev(i)}.
+    if (worker) {
+#pragma unroll
+        for (uint32_t k = 0; k < E; k++) {
+            const uint32_t w = pad32(elem_r(G - 1, k) * J + jj);
+#pragma unroll
+            for (int l = 0; l < 8; l++) sm[l * P + w] = x[k].v[l];
+        }
+    }
+    __syncthreads();
+    Fr sc;
+    if (a.scale) sc = fe_ldg<FrP>(a.tw_n + n);
+    for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
+        uint32_t r, jx;
+        if (Ns >= J) {
+            r = e >> LJ;
+            jx = e & (J - 1);
+        } else {
+            uint32_t q = e >> (a.logNs + LR);
+            uint32_t rem = e & ((Ns << LR) - 1);
+            r = rem >> a.logNs;
+            jx = q * Ns + (rem & (Ns - 1));
+        }
+        const uint64_t j = j0 + jx;
+        const uint32_t src = __brev(r) >> (32 - LR);
+        const uint32_t w = pad32(src * J + jx);
+        Fr v;
+#pragma unroll
+        for (int l = 0; l < 8; l++) v.v[l] = sm[l * P + w];
+        if (a.scale) v = fe_mul<FrP>(v, sc);
+        const uint64_t dst = ((j >> a.logNs) << (a.logNs + LR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
+        fe_store<FrP>(out + 8 * dst, v);
+    }
+}
+
+template <int LR>
+int launch_reg_t(dim3 grid, cudaStream_t s, const PassArgs &a) {
+    const uint32_t JR = 1u << (LR + a.logJ);
+    const uint32_t threads = std::max<uint32_t>(32, JR >> kRegLE);
+    const size_t smem = (size_t)8 * (JR + JR / 32) * 4;
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    ZK_CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0;
+    if (!bit || !(attr_set.load() & bit)) {
+        ZK_CUDA_TRY(cudaFuncSetAttribute(k_ntt_reg<LR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)8 * (kMaxRegJR + kMaxRegJR / 32) * 4)));
+        attr_set.fetch_or(bit);
+    }
+    k_ntt_reg<LR><<<grid, threads, smem, s>>>(a);
+    ZK_LAUNCHED();
+    return ZK_OK;
+}
+
+// Register-tiled pass for kRegMinLog <= logR <= 11.
+int launch_reg(uint32_t logR, dim3 grid, cudaStream_t s, const PassArgs &a) {
+    static_assert(kRegMinLog == 9, "instances below");
+    switch (logR) {
+        case 9: return launch_reg_t<9>(grid, s, a);
+        case 10: return launch_reg_t<10>(grid, s, a);
+        case 11: return launch_reg_t<11>(grid, s, a);
+        default: return ZK_EINVAL;
+    }
+}
+
 template <int LJR>
 int launch_pass_t(dim3 grid, uint32_t threads, size_t smem, cudaStream_t s, const PassArgs &a) {
     // The shared-memory limit is a per-device attribute of the kernel: set it
@@ -255,13 +432,16 @@ int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
 }
 
 // Built-in largest pass radix (log2) when none is tuned: the fastest choices
-// of an autotuner sweep on B300.  Smaller radices mean more passes but smaller
-// CTAs (more resident per SM, fewer block-wide barriers per element).
+// of an autotuner sweep on B300.  Up to 2^19 the shared-memory pass with
+// radices 2^6 .. 2^8 wins (small CTAs, many resident per SM); from 2^20 on,
+// two register-tiled passes of radix 2^10 .. 2^11 (half the DRAM passes and
+// inter-pass twiddles of four).
 static int default_radix(int L) {
     if (L <= 9) return L ? L : 1;
     if (L <= 16) return 6;
-    if (L <= 21) return 8;
-    return 6;
+    if (L == 17 || L == 19) return 8;
+    if (L == 18) return 7;
+    return 11;  // 2^20 .. : two register-tiled passes
 }
 
 static int radix_for(const Shared &sh, int L) {
@@ -318,8 +498,13 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         a.logR = (uint32_t)logR;
         a.logNs = (uint32_t)logNs;
         const uint64_t subs = (uint64_t)n >> logR;
-        a.J = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(kMaxJ, subs),
-                                           kMaxSmem / ((size_t)32 << logR));
+        // Radices of 2^9 and more: register-tiled pass (J R = 1024 elements
+        // per CTA where the length allows); smaller ones: shared-memory pass
+        // (J <= 4, J R 32 bytes <= 128 KiB), which measured faster there.
+        const bool reg = logR >= kRegMinLog;
+        a.J = reg ? (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, kRegJR >> logR), subs)
+                  : (uint32_t)std::min<uint64_t>(std::min<uint64_t>(kMaxJ, subs),
+                                                 kMaxSmem / ((size_t)32 << logR));
         a.logJ = 0;
         while ((1u << a.logJ) < a.J) a.logJ++;
         a.tw_n = (const Fr *)tw_n;
@@ -327,10 +512,14 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         a.inverse = inverse ? 1 : 0;
         a.scale = (inverse && p == P - 1) ? 1 : 0;
         const uint32_t JR = a.J << logR;
-        const uint32_t threads = std::min<uint32_t>(512, std::max<uint32_t>(32, JR / 2));
-        const size_t smem = (size_t)JR * 32;
         dim3 grid((unsigned)(subs / a.J), (unsigned)count);
-        ZK_TRY(launch_pass(a.logJ + (uint32_t)logR, grid, threads, smem, s, a));
+        if (reg) {
+            ZK_TRY(launch_reg((uint32_t)logR, grid, s, a));
+        } else {
+            const uint32_t threads = std::min<uint32_t>(512, std::max<uint32_t>(32, JR / 2));
+            const size_t smem = (size_t)JR * 32;
+            ZK_TRY(launch_pass(a.logJ + (uint32_t)logR, grid, threads, smem, s, a));
+        }
         logNs += logR;
     }
     return ZK_OK;
