@@ -40,7 +40,8 @@ __global__ void k_probe_imad(uint32_t *sink, uint32_t iters, uint32_t seed) {
 // independent chains per thread (kChains * kUnroll instructions, or pairs,
 // per iteration):
 //   HI   mad.hi.u32                  (the high half of a limb product)
-//   WIDE mad.wide.u32 with a 64-bit addend (both halves in one instruction)
+//   WIDE mad.wide.u32 with a 64-bit addend (both halves in one instruction),
+//        its multiplicand the accumulator's low word
 //   PAIR mad.lo.cc.u32 + madc.hi.u32 (one limb product of a carry chain)
 //   ADD  add.cc.u32 + addc.u32        (integer ALU carry chain)
 enum ProbeForm { kHi = 0, kWide = 1, kPair = 2, kAdd = 3 };
@@ -63,8 +64,9 @@ __global__ void k_probe_form(uint32_t *sink, uint32_t iters, uint32_t seed) {
             for (int j = 0; j < kChains; j++) {
                 if (F == kHi)
                     asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[j]) : "r"(b), "r"(a[(j + 1) % kChains]));
-                else if (F == kWide)
-                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[j]) : "r"(a[j]), "r"(b));
+                else if (F == kWide)  // multiplicand from the accumulator: nothing to hoist
+                    asm volatile("{\n\t.reg .u32 t;\n\tcvt.u32.u64 t, %0;\n\tmad.wide.u32 %0, t, %1, %0;\n\t}"
+                                 : "+l"(w[j]) : "r"(b));
                 else if (F == kPair)
                     asm volatile("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
                                  : "+r"(a[j]), "+r"(h[j]) : "r"(a[(j + 1) % kChains]), "r"(b));
