@@ -9,7 +9,6 @@
 #include <vector>
 
 #include "ctx.cuh"
-#include "curve.cuh"
 #include "field.cuh"
 
 namespace zk {
@@ -208,13 +207,6 @@ __global__ void k_fill_quant(uint64_t *out, size_t n, uint64_t seed) {
         if (q < 0) v = fe_neg<FrP>(v);
         for (int l = 0; l < 4; l++) out[4 * i + l] = ((uint64_t)v.v[2 * l + 1] << 32) | v.v[2 * l];
     }
-}
-
-// out = a + b for two canonical affine points (the halves of a split
-// commitment).
-__global__ void k_point_add(const uint32_t *a, const uint32_t *b, uint32_t *out) {
-    if (threadIdx.x || blockIdx.x) return;
-    xyzz_store_canonical(out, xyzz_add(xyzz_load_canonical(a), xyzz_load_canonical(b)));
 }
 
 size_t next_pow2(size_t n) {
@@ -435,9 +427,6 @@ int zk_destroy(zk_ctx *ctx) {
         }
         ctx->marks.clear();
         if (ctx->side) cudaStreamDestroy(ctx->side);
-        if (ctx->copy) cudaStreamDestroy(ctx->copy);
-        for (auto &e : ctx->copy_ev)
-            if (e) cudaEventDestroy(e);
         for (auto &e : ctx->side_ev)
             if (e) cudaEventDestroy(e);
         for (auto &r : ctx->up.inflight) cudaEventDestroy(r.ev);
@@ -619,60 +608,8 @@ int zk_commit_hiding(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *s,
     return ZK_OK;
 }
 
-// A long commitment from host memory: the copy over the host link takes about
-// a quarter of the MSM's time, and the MSM needs every scalar before it
-// starts (the width statistics).  So the scalars are committed as two halves
-// at the full length's window width: the second half is copied on a side
-// stream while the first half's MSM runs, and one point addition joins the
-// two results.  The extra cost is one more bucket reduction.
-static int commit_host_split(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, cudaStream_t s) {
-    const Shared &sh = *ctx->sh;
-    if (n > sh.srs_n) return ZK_ESRS;
-    int err = ZK_OK;
-    uint32_t *ws = (uint32_t *)scratch(ctx, "commit.ws", n * 32, &err);
-    uint32_t *parts = (uint32_t *)scratch(ctx, "commit.parts", 3 * 64, &err);
-    if (!ws || !parts) return err;
-    if (!ctx->copy) {
-        ZK_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
-        ZK_CUDA_TRY(cudaEventCreateWithFlags(&ctx->copy_ev[0], cudaEventDisableTiming));
-        ZK_CUDA_TRY(cudaEventCreateWithFlags(&ctx->copy_ev[1], cudaEventDisableTiming));
-    }
-    const size_t h = n / 2;
-    const uint32_t *src = (const uint32_t *)coeffs;
-    // The workspace may still be read by work queued earlier on s.
-    ZK_CUDA_TRY(cudaEventRecord(ctx->copy_ev[0], s));
-    ZK_CUDA_TRY(cudaStreamWaitEvent(ctx->copy, ctx->copy_ev[0], 0));
-    ZK_CUDA_TRY(cudaMemcpyAsync(ws, src, h * 32, cudaMemcpyHostToDevice, s));
-    ZK_CUDA_TRY(cudaMemcpyAsync(ws + 8 * h, src + 8 * h, (n - h) * 32, cudaMemcpyHostToDevice, ctx->copy));
-    ZK_CUDA_TRY(cudaEventRecord(ctx->copy_ev[1], ctx->copy));
-    MsmJob j;
-    j.c = msm_pick_window(ctx, n, 1);
-    j.scalars = ws;
-    j.n = (uint32_t)h;
-    j.out = parts;
-    ZK_TRY(msm_batch_impl(ctx, &j, 1, 0, s));
-    ZK_CUDA_TRY(cudaStreamWaitEvent(s, ctx->copy_ev[1], 0));
-    j.scalars = ws + 8 * h;
-    j.n = (uint32_t)(n - h);
-    j.first = (uint32_t)h;  // its points are SRS[h ..]
-    j.out = parts + 16;
-    ZK_TRY(msm_batch_impl(ctx, &j, 1, 0, s));
-    k_point_add<<<1, 1, 0, s>>>(parts, parts + 16, parts + 32);
-    ZK_LAUNCHED();
-    ZK_CUDA_TRY(cudaMemcpyAsync(out, parts + 32, 64, is_device_ptr(out) ? cudaMemcpyDeviceToDevice
-                                                                          : cudaMemcpyDeviceToHost, s));
-    if (!is_device_ptr(out)) ZK_CUDA_TRY(cudaStreamSynchronize(s));
-    return ZK_OK;
-}
-
-constexpr size_t kSplitMin = (size_t)1 << 19;  // host commitments at least this long are split
-
 int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream) {
     if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
-    if (n >= kSplitMin && !is_device_ptr(coeffs) && !ctx->capturing) {
-        DeviceGuard g(ctx);
-        return commit_host_split(ctx, coeffs, n, out, (cudaStream_t)stream);
-    }
     const size_t lens[1] = {n};
     const zk_fr *const vecs[1] = {coeffs};
     return zk_commit_batch(ctx, vecs, lens, 1, 0, out, stream);

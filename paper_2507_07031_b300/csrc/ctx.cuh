@@ -101,8 +101,6 @@ struct zk_ctx {
     bool capturing = false;  // inside a plan's graph capture: no allocation allowed
     cudaStream_t side = nullptr;         // fold tree: instance passes overlap the next level
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
-    cudaStream_t copy = nullptr;          // host-buffer commitments: second half's copy
-    cudaEvent_t copy_ev[2] = {nullptr, nullptr};
     int last_error = 0;
 };
 
@@ -212,8 +210,6 @@ struct MsmJob {
     uint32_t n;
     void *out;
     int basis = 0;  // 0: scalars are coefficients (SRS); lg: evaluations over H, n = 2^lg (Lagrange basis)
-    int c = 0;      // window width, 0 = the tuned or built-in width for n
-    uint32_t first = 0;  // index of the base point of scalar 0 (coefficient jobs)
 };
 int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs, size_t count, int c, cudaStream_t s);
 

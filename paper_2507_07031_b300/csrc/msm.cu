@@ -56,7 +56,6 @@ struct JobDesc {
     const Affine *t16;        // window table of width 16 over the base points, or null
     uint32_t t16n;            // its points per window
     uint32_t n;
-    uint32_t first;           // base point of scalar 0 (its index in each window of the tables)
     uint32_t logB;            // buckets in use: 2^logB (2^(c - 1), or fewer for short scalars)
     uint32_t shift;           // every scalar of the job is a multiple of 2^shift
     uint32_t wins;            // windows that can hold nonzero digits (after the shift)
@@ -182,7 +181,7 @@ __global__ void __launch_bounds__(kRecThreads)
             const uint32_t d = sc[0];
             if (d) {
                 key[e] = d - 1u;
-                word[e] = ((J.first + gid - sb) << 1) | (neg ? 1u : 0u);
+                word[e] = ((gid - sb) << 1) | (neg ? 1u : 0u);
                 atomicAdd(&hist[d - 1u], 1u);
             }
         }
@@ -219,7 +218,6 @@ __global__ void __launch_bounds__(kRecThreads)
         bb = dj.bbase[job];
         neg = load_recentred(dj.jobs[job].scalars + 8 * (size_t)i, sc);
         shr256(sc, dj.jobs[job].shift);
-        i += dj.jobs[job].first;  // the point's index in a window of the table
     }
     const uint32_t wins = live ? dj.jobs[job].wins : 0;
     // Windows past every lane's last one hold no digits: stop before them.
@@ -952,8 +950,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     for (size_t k = 0; k < count; k++) {
         const MsmJob &m = jobs_in[k];
         if (!m.out || (m.n && !m.scalars)) return ZK_EINVAL;
-        if ((size_t)m.first + m.n > sh.srs_n) return ZK_ESRS;
-        if (m.basis && m.first) return ZK_EINVAL;
+        if (m.n > sh.srs_n) return ZK_ESRS;
         total_in += m.n;
     }
     if (total_in >= (1ull << 32)) return ZK_EINVAL;
@@ -974,7 +971,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     size_t total64 = 0, entries64 = 0, nb64 = 0;
     for (size_t k = 0; k < count; k++) {
         const MsmJob &m = jobs_in[k];
-        int c = c_fixed > 0 ? c_fixed : m.c > 0 ? m.c : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
+        int c = c_fixed > 0 ? c_fixed : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
         if (c < kMinWindow || c > kMaxWindow) return ZK_EINVAL;
         jv[k] = {m, c};
         total64 += m.n;
@@ -997,8 +994,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         bases[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
         size_t need = 1;
         for (size_t j = 0; j < count; j++)
-            if (jv[j].c == jv[k].c && jv[j].job.basis == basis)
-                need = std::max(need, (size_t)jv[j].job.first + jv[j].job.n);
+            if (jv[j].c == jv[k].c && jv[j].job.basis == basis) need = std::max(need, (size_t)jv[j].job.n);
         const WindowTable *t;
         ZK_TRY(table_get(ctx, jv[k].c, need, basis, &t, s));
         tabs[k] = (const Affine *)t->buf.p;
@@ -1012,7 +1008,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         std::lock_guard<std::mutex> g(sh.mu);
         for (size_t k = 0; k < count; k++)
             for (auto &t : sh.tables)
-                if (t.c == 16 && t.basis == jv[k].job.basis && t.n >= (size_t)jv[k].job.first + jv[k].job.n) {
+                if (t.c == 16 && t.basis == jv[k].job.basis && t.n >= jv[k].job.n) {
                     t16s[k] = (const Affine *)t.buf.p;
                     t16n[k] = (uint32_t)t.n;
                     break;
@@ -1114,7 +1110,6 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hd[k].base = bases[k];
         hd[k].wtable = tabs[k];
         hd[k].n = jv[k].job.n;
-        hd[k].first = jv[k].job.first;
         hd[k].logB = (uint32_t)(jv[k].c - 1);
         hd[k].shift = 0;
         hd[k].wins = (uint32_t)windows_for(jv[k].c);
@@ -1273,7 +1268,6 @@ __global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint3
     d->t16 = nullptr;
     d->t16n = 0;
     d->n = n;
-    d->first = 0;
     d->logB = kNoAllocC - 1;
     d->shift = 0;
     d->wins = kNoAllocW;

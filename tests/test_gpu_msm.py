@@ -285,21 +285,3 @@ def test_msm_repeated_and_opposite_points(zk, orc):
             assert pts_equal(_commit(zk, ctx, c), want), name
     finally:
         zk.zk_destroy(ctx)
-
-
-@pytest.mark.parametrize("dist", ["fr", "zkml"])
-def test_host_buffer_commit_is_split_and_exact(zk, orc, ctx_big, tau, dist):
-    """Long commitments from host memory run as two halves whose second copy
-    overlaps the first MSM; the joined point equals the closed form, into a
-    host or a device output, with an odd length too."""
-    import torch
-    for n in ((1 << 20) if dist == "fr" else (1 << 20) + 77, (1 << 19) + 3):
-        c = np.ascontiguousarray(Z.fr_uniform(91, n) if dist == "fr" else Z.zkml_scalars(92, n))
-        want = orc.commit_coeffs_tau(c, tau)
-        h_out = np.zeros(8, dtype=np.uint64)
-        zk.zk_commit(ctx_big, c, h_out)
-        assert pts_equal(h_out, want), n
-        d_out = torch.zeros(8, dtype=torch.int64, device="cuda")
-        zk.zk_commit(ctx_big, c, d_out)
-        torch.cuda.synchronize()
-        assert pts_equal(to_host(d_out), want), n
