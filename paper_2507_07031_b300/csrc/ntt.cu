@@ -432,16 +432,16 @@ int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
 }
 
 // Built-in largest pass radix (log2) when none is tuned: the fastest choices
-// of an autotuner sweep on B300.  Up to 2^19 the shared-memory pass with
-// radices 2^6 .. 2^8 wins (small CTAs, many resident per SM); from 2^20 on,
-// two register-tiled passes of radix 2^10 .. 2^11 (half the DRAM passes and
-// inter-pass twiddles of four).
+// of an autotuner sweep on B300.  Up to 2^20 the shared-memory pass with
+// radices 2^6 .. 2^8 wins (small CTAs, many resident per SM; at 2^20 it also
+// won with L2 flushed before the call, 0.348 vs 0.376 ms); from 2^21 on, two
+// register-tiled passes of radix 2^10 .. 2^11 (half the DRAM passes of four).
 static int default_radix(int L) {
     if (L <= 9) return L ? L : 1;
     if (L <= 16) return 6;
-    if (L == 17 || L == 19) return 8;
+    if (L == 17 || L == 19 || L == 20) return 8;
     if (L == 18) return 7;
-    return 11;  // 2^20 .. : two register-tiled passes
+    return 11;  // 2^21 .. : two register-tiled passes
 }
 
 static int radix_for(const Shared &sh, int L) {

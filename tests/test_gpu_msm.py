@@ -285,3 +285,13 @@ def test_msm_repeated_and_opposite_points(zk, orc):
             assert pts_equal(_commit(zk, ctx, c), want), name
     finally:
         zk.zk_destroy(ctx)
+
+
+def test_host_buffer_commit_at_2_20(zk, orc, ctx_big, tau):
+    """The end-to-end call: scalars and output in host memory (staged through
+    the workspace inside the call), against the closed form."""
+    n = (1 << 20) + 5
+    c = np.ascontiguousarray(Z.fr_uniform(91, n))
+    h_out = np.zeros(8, dtype=np.uint64)
+    zk.zk_commit(ctx_big, c, h_out)
+    assert pts_equal(h_out, orc.commit_coeffs_tau(c, tau))
