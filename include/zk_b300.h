@@ -341,7 +341,8 @@ int zk_plan_destroy(zk_plan *plan);
  * remaining vector is derived by the leaf step); the degree in effect when
  * the scheduler starts a job applies to it, and the job's HBM reservation
  * covers its d - 1 cross terms.  zk_submit returns ZK_EBUSY when 65536 jobs
- * wait, ZK_ENOMEM when one job's estimate exceeds the budget.  zk_wait
+ * wait, ZK_ENOMEM when one job's estimate exceeds the budget; zk_cancel
+ * takes a job out of the queue before it runs.  zk_wait
  * returns ZK_ETIMEOUT after timeout_ms.  Times are ms since server creation.
  * Every ticket stays queryable until zk_server_destroy, so the server keeps
  * a small record (about 200 bytes) per job submitted.  zk_server_create
@@ -359,6 +360,7 @@ typedef struct {
 #define ZK_JOB_RUNNING 1
 #define ZK_JOB_DONE 2
 #define ZK_JOB_FAILED 3
+#define ZK_JOB_CANCELLED 4
 typedef struct {
     int status;       /* ZK_JOB_* */
     int error;        /* ZK_OK or the failing call's code */
@@ -370,12 +372,19 @@ typedef struct {
     size_t queued;
     size_t reserved_bytes, peak_reserved_bytes;
     int busy_lanes;
+    unsigned long long cancelled;
 } zk_server_info;
 int zk_server_create(zk_ctx *ctx, int lanes, size_t hbm_budget_bytes, zk_server **out);
 int zk_submit(zk_server *srv, const zk_job *job, uint64_t *ticket);
 int zk_poll(zk_server *srv, uint64_t ticket, zk_ticket_info *info);
 int zk_wait(zk_server *srv, uint64_t ticket, int timeout_ms, zk_ticket_info *info);
 int zk_server_stats(zk_server *srv, zk_server_info *info);
+/* Cancel a job that is still queued: it leaves the queue unrun, its status
+ * becomes ZK_JOB_CANCELLED (waiters return at once) and its buffers are
+ * never touched.  ZK_EBUSY when the job was already admitted (running) or
+ * has finished; ZK_EINVAL for an unknown ticket.  The paper has no serving
+ * loop; this is part of the deployment wrapper around its prover steps. */
+int zk_cancel(zk_server *srv, uint64_t ticket);
 int zk_server_destroy(zk_server *srv);
 
 /* Static description of an error code. */
@@ -438,6 +447,24 @@ int zk_probe_pipes(int device, double *rates);
 #define ZK_FOP_SUB 4
 #define ZK_FOP_MULSUB 5
 int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk_fr *out, size_t n, zk_stream stream);
+
+/* Checked build.  Compiled with -DZK_CHECK (`python
+ * paper_2507_07031_b300/build.py --check` writes libzkb300_check.so), the
+ * kernels check the invariants their gathers and scatters rely on and, on a
+ * failure, set a flag bit and skip the access instead of trapping:
+ *   ZK_CHECK_SCALAR  a scalar >= r reached the MSM (a precondition of the API)
+ *   ZK_CHECK_BUCKET  a bucket key outside its job's bucket range
+ *   ZK_CHECK_ENTRY   a sorted-entry position outside its bucket
+ *   ZK_CHECK_NTT_IDX an NTT gather or scatter outside the vector
+ * zk_check_status synchronises the device, returns the flags raised since the
+ * last call (then clears them) and *checked = 1 in the checked build (in the
+ * normal build the checks compile to nothing: flags 0, *checked = 0).
+ * The paper has no counterpart; this stands in for a memory sanitizer. */
+#define ZK_CHECK_SCALAR 1u
+#define ZK_CHECK_BUCKET 2u
+#define ZK_CHECK_ENTRY 4u
+#define ZK_CHECK_NTT_IDX 8u
+int zk_check_status(zk_ctx *ctx, unsigned *flags, int *checked);
 
 /* Phase timing: with timing on, each call brackets its phases with CUDA events
  * on its stream; zk_timing_read waits for them, adds up the device time (ms)

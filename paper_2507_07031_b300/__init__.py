@@ -48,10 +48,10 @@ class ZkTicketInfo(ctypes.Structure):
 class ZkServerInfo(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_ulonglong), ("queued", ctypes.c_size_t),
                 ("reserved_bytes", ctypes.c_size_t), ("peak_reserved_bytes", ctypes.c_size_t),
-                ("busy_lanes", ctypes.c_int)]
+                ("busy_lanes", ctypes.c_int), ("cancelled", ctypes.c_ulonglong)]
 
 
-ZK_JOB_QUEUED, ZK_JOB_RUNNING, ZK_JOB_DONE, ZK_JOB_FAILED = range(4)
+ZK_JOB_QUEUED, ZK_JOB_RUNNING, ZK_JOB_DONE, ZK_JOB_FAILED, ZK_JOB_CANCELLED = range(5)
 
 
 _VP = ctypes.c_void_p
@@ -59,11 +59,13 @@ _SZ = ctypes.c_size_t
 _SZP = ctypes.POINTER(ctypes.c_size_t)
 
 
-def _load():
-    if not os.path.exists(LIB_PATH):
-        raise ImportError("libzkb300.so not built: run `python paper_2507_07031_b300/build.py` "
-                          "(or __graft_entry__.build())")
-    L = ctypes.CDLL(LIB_PATH)
+def _load(path: str = LIB_PATH):
+    """Loads the library at `path` (the in-tree build by default) and declares
+    every entry point's argument types."""
+    if not os.path.exists(path):
+        raise ImportError("%s not built: run `python paper_2507_07031_b300/build.py` "
+                          "(or __graft_entry__.build())" % os.path.basename(path))
+    L = ctypes.CDLL(path)
     sig = {
         "zk_init": [ctypes.POINTER(_VP), ctypes.c_int, _SZ],
         "zk_destroy": [_VP],
@@ -95,6 +97,8 @@ def _load():
         "zk_wait": [_VP, ctypes.c_uint64, ctypes.c_int, _VP],
         "zk_server_stats": [_VP, _VP],
         "zk_server_destroy": [_VP],
+        "zk_cancel": [_VP, ctypes.c_uint64],
+        "zk_check_status": [_VP, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int)],
         "zk_tune_get": [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "zk_tune_measure": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_double)],
@@ -131,7 +135,7 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
             "zk_kernel_launches", "zk_probe_rates", "zk_probe_pipes", "zk_timing_enable", "zk_timing_read",
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
-            "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats",
+            "zk_server_create", "zk_submit", "zk_poll", "zk_wait", "zk_server_stats", "zk_cancel", "zk_check_status",
             "zk_server_destroy", "zk_set_commit_route", "zk_field_op", "zk_open", "zk_open_batch",
             "zk_mul_quotient", "zk_set_hiding_base", "zk_commit_hiding", "zk_set_fold_degree"]
 
@@ -448,6 +452,28 @@ def zk_server_stats(srv: int) -> ZkServerInfo:
     info = ZkServerInfo()
     _check(lib.zk_server_stats(srv, ctypes.byref(info)), "zk_server_stats")
     return info
+
+
+ZK_CHECK_SCALAR, ZK_CHECK_BUCKET, ZK_CHECK_ENTRY, ZK_CHECK_NTT_IDX = 1, 2, 4, 8
+
+
+def zk_check_status(ctx: int):
+    """(flags raised since the last call, whether this is the checked build)."""
+    f, c = ctypes.c_uint(), ctypes.c_int()
+    _check(lib.zk_check_status(ctx, ctypes.byref(f), ctypes.byref(c)), "zk_check_status")
+    return f.value, bool(c.value)
+
+
+def load_checked():
+    """The checked build (libzkb300_check.so, built by `build.py --check`) as
+    a raw ctypes library with the same entry points: call it as `lib.zk_...`
+    with the pointer arguments the functions above pass."""
+    return _load(os.path.join(_HERE, "libzkb300_check.so"))
+
+
+def zk_cancel(srv: int, ticket: int) -> None:
+    """Takes a still-queued job out of the queue (ZK_EBUSY if it already ran)."""
+    _check(lib.zk_cancel(srv, int(ticket)), "zk_cancel")
 
 
 def zk_server_destroy(srv: int) -> None:

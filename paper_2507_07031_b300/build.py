@@ -16,6 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libzkb300.so")
 OBJ = os.path.join(HERE, "_build")
+# The checked build (-DZK_CHECK: in-kernel bounds checks that set flags read
+# by zk_check_status) goes to its own library and object directory.
+LIB_CHECK = os.path.join(HERE, "libzkb300_check.so")
+OBJ_CHECK = os.path.join(HERE, "_build_check")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -32,8 +36,8 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OBJ, src[:-3] + ".o")
+def _compile(src: str, extra, objdir: str = OBJ) -> str:
+    obj = os.path.join(objdir, src[:-3] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime():
         return obj
     cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
@@ -45,22 +49,23 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
+    lib, objdir = (LIB_CHECK, OBJ_CHECK) if checked else (LIB, OBJ)
+    os.makedirs(objdir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DZK_CHECK"] if checked else [])
     if force:
-        for f in os.listdir(OBJ):
-            os.remove(os.path.join(OBJ, f))
+        for f in os.listdir(objdir):
+            os.remove(os.path.join(objdir, f))
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), sources()))
-    tmp = LIB + ".tmp%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, extra, objdir), sources()))
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checked="--check" in sys.argv))

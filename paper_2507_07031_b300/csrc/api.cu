@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "check.cuh"
 #include "ctx.cuh"
 #include "field.cuh"
 
@@ -275,6 +276,18 @@ static bool layout_value_ok(int op, int value) {
     }
 }
 
+int zk_check_status(zk_ctx *ctx, unsigned *flags, int *checked) {
+    if (!ctx || !flags || !checked) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    ZK_CUDA_TRY(cudaDeviceSynchronize());
+    uint32_t a = 0, b = 0;
+    ZK_TRY(msm_check_read(&a));
+    ZK_TRY(ntt_check_read(&b));
+    *flags = a | b;
+    *checked = kChecked ? 1 : 0;
+    return ZK_OK;
+}
+
 int zk_tune_set(zk_ctx *ctx, int op, int log2n, int value) {
     if (!ctx || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
     Shared &sh = *ctx->sh;
@@ -311,6 +324,7 @@ int zk_tune_get(const zk_ctx *ctx, int op, int log2n, int *value) {
 }
 
 int zk_tune_measure(zk_ctx *ctx, int op, int log2n, int value, int reps, double *ms) {
+    ZK_NVTX("zk_tune_measure");
     if (!ctx || !ms || reps < 1 || log2n < 0 || log2n > kMaxLogN) return ZK_EINVAL;
     DeviceGuard g(ctx);
     const size_t n = (size_t)1 << log2n;
@@ -442,12 +456,14 @@ int zk_destroy(zk_ctx *ctx) {
 }
 
 int zk_srs_load(zk_ctx *ctx, const zk_g1 *pts, size_t n) {
+    ZK_NVTX("zk_srs_load");
     if (!ctx) return ZK_EINVAL;
     DeviceGuard g(ctx);
     return srs_load_impl(ctx, pts, n, 0);
 }
 
 int zk_srs_generate(zk_ctx *ctx, const zk_fr *tau, size_t n) {
+    ZK_NVTX("zk_srs_generate");
     if (!ctx) return ZK_EINVAL;
     DeviceGuard g(ctx);
     return srs_generate_impl(ctx, tau, n, 0);
@@ -490,6 +506,7 @@ struct OutBuf {
 
 int zk_open(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *x, zk_fr *y, zk_g1 *proof, zk_fr *quotient,
             zk_stream stream) {
+    ZK_NVTX("zk_open");
     if (!ctx || !coeffs || !x || !y || !proof || n == 0) return ZK_EINVAL;
     DeviceGuard g(ctx);
     cudaStream_t s = (cudaStream_t)stream;
@@ -514,6 +531,7 @@ int zk_open(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *x, zk_fr *y
 
 int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, size_t count, const zk_fr *x,
                   const zk_fr *gamma, zk_fr *ys, zk_g1 *proof, zk_stream stream) {
+    ZK_NVTX("zk_open_batch");
     if (!ctx || !polys || !lens || !x || !gamma || !ys || !proof || count == 0) return ZK_EINVAL;
     DeviceGuard g(ctx);
     cudaStream_t s = (cudaStream_t)stream;
@@ -558,6 +576,7 @@ int zk_open_batch(zk_ctx *ctx, const zk_fr *const *polys, const size_t *lens, si
 
 int zk_mul_quotient(zk_ctx *ctx, const zk_fr *a, const zk_fr *b, size_t n, zk_fr *t, zk_g1 *com,
                     zk_stream stream) {
+    ZK_NVTX("zk_mul_quotient");
     if (!ctx || !a || !b || !com || n == 0) return ZK_EINVAL;
     DeviceGuard g(ctx);
     cudaStream_t s = (cudaStream_t)stream;
@@ -583,6 +602,7 @@ int zk_set_fold_degree(zk_ctx *ctx, int degree) {
 }
 
 int zk_set_hiding_base(zk_ctx *ctx, const zk_g1 *H) {
+    ZK_NVTX("zk_set_hiding_base");
     if (!ctx || !H) return ZK_EINVAL;
     DeviceGuard g(ctx);
     const void *dh = nullptr;
@@ -592,6 +612,7 @@ int zk_set_hiding_base(zk_ctx *ctx, const zk_g1 *H) {
 
 int zk_commit_hiding(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *s, zk_g1 *out,
                      zk_stream stream) {
+    ZK_NVTX("zk_commit_hiding");
     if (!ctx || !coeffs || !s || !out || n == 0) return ZK_EINVAL;
     DeviceGuard g(ctx);
     cudaStream_t st = (cudaStream_t)stream;
@@ -609,6 +630,7 @@ int zk_commit_hiding(zk_ctx *ctx, const zk_fr *coeffs, size_t n, const zk_fr *s,
 }
 
 int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream stream) {
+    ZK_NVTX("zk_commit");
     if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
     const size_t lens[1] = {n};
     const zk_fr *const vecs[1] = {coeffs};
@@ -617,6 +639,7 @@ int zk_commit(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out, zk_stream 
 
 int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, size_t count,
                     unsigned flags, zk_g1 *out, zk_stream stream) {
+    ZK_NVTX("zk_commit_batch");
     if (!ctx || !vecs || !lens || !out) return ZK_EINVAL;
     if (count == 0) return ZK_OK;
     if (flags & ~(ZK_EVALS | ZK_LAGRANGE)) return ZK_EINVAL;
@@ -710,6 +733,7 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
 }
 
 static int ntt_entry(zk_ctx *ctx, zk_fr *data, size_t n, bool inverse, zk_stream stream) {
+    ZK_NVTX(inverse ? "zk_intt" : "zk_ntt");
     if (!ctx || !data) return ZK_EINVAL;
     if (!n || (n & (n - 1)) || n > ((size_t)1 << kMaxLogN)) return ZK_EINVAL;
     DeviceGuard g(ctx);
@@ -733,6 +757,7 @@ int zk_intt(zk_ctx *ctx, zk_fr *data, size_t n, zk_stream stream) {
 
 int zk_ntt_batch(zk_ctx *ctx, zk_fr *const *data, const size_t *lens, size_t count, int inverse,
                  zk_stream stream) {
+    ZK_NVTX("zk_ntt_batch");
     if (!ctx || (count && (!data || !lens))) return ZK_EINVAL;
     DeviceGuard g(ctx);
     for (size_t k = 0; k < count; k++)
@@ -742,6 +767,7 @@ int zk_ntt_batch(zk_ctx *ctx, zk_fr *const *data, const size_t *lens, size_t cou
 }
 
 int zk_leaf_init(zk_ctx *ctx, const zk_acc *accs, size_t count, zk_stream stream) {
+    ZK_NVTX("zk_leaf_init");
     if (!ctx) return ZK_EINVAL;
     DeviceGuard g(ctx);
     return leaf_init_impl(ctx, accs, count, (cudaStream_t)stream);
@@ -749,6 +775,7 @@ int zk_leaf_init(zk_ctx *ctx, const zk_acc *accs, size_t count, zk_stream stream
 
 int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
             zk_g1 *E1_out, zk_stream stream) {
+    ZK_NVTX("zk_fold");
     if (!ctx) return ZK_EINVAL;
     DeviceGuard g(ctx);
     return fold_impl(ctx, L, R, gamma, out, E1_out, (cudaStream_t)stream);
@@ -756,6 +783,7 @@ int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, z
 
 int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
                  zk_stream stream) {
+    ZK_NVTX("zk_fold_tree");
     if (!ctx) return ZK_EINVAL;
     DeviceGuard g(ctx);
     return fold_tree_impl(ctx, leaves, count, gammas, root, (cudaStream_t)stream);

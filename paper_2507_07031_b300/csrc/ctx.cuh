@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/zk_b300.h"
 
 namespace zk {
@@ -146,6 +148,17 @@ void count_launches(unsigned k);
         if (_r != ZK_OK) return _r;                         \
     } while (0)
 
+// A named NVTX range over one public entry point, so that a profiler's
+// timeline shows each call by task type (commit, NTT, fold, ...); with no
+// tool attached the push and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define ZK_NVTX(name) ::zk::NvtxRange zk_nvtx_range_(name)
+
 // Brackets one phase of a call with CUDA events on its stream when the
 // context's timing is on (kernel durations for the roofline report).
 struct PhaseScope {
@@ -171,6 +184,10 @@ struct PhaseScope {
 };
 
 // --- internal entry points between translation units ----------------------
+
+// Check flags of the ZK_CHECK build (check.cuh), read and cleared per unit.
+int msm_check_read(uint32_t *flags);
+int ntt_check_read(uint32_t *flags);
 
 // SRS (srs.cu)
 int srs_load_impl(zk_ctx *ctx, const zk_g1 *pts, size_t n, cudaStream_t s);

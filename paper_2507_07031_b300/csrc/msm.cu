@@ -28,12 +28,15 @@
 #include <cstring>
 #include <vector>
 
+#include "check.cuh"
 #include "ctx.cuh"
 #include "curve.cuh"
 #include "scan.cuh"
 #include "team.cuh"
 
 namespace zk {
+
+ZK_CHECK_UNIT()
 
 namespace {
 
@@ -114,6 +117,7 @@ __device__ __forceinline__ void shr256(uint32_t (&s)[8], uint32_t k) {
 // Loads a scalar, recentres it, and returns the negation flag.
 __device__ __forceinline__ bool load_recentred(const uint32_t *p, uint32_t (&s)[8]) {
     Fr x = fe_load<FrP>(p);
+    if (ZK_FAILED(!fe_ge_modulus<FrP>(x), kCheckScalar)) x = fe_zero<FrP>();
     bool neg = fe_gt_half<FrP>(x);
     if (neg) x = fe_neg<FrP>(x);
 #pragma unroll
@@ -160,7 +164,7 @@ __device__ __forceinline__ Chunk rec_chunk(const DevJobs &dj, uint32_t g0, uint3
 template <bool SCATTER>
 __global__ void __launch_bounds__(kRecThreads)
     k_recode_short(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t *__restrict__ counts,
-                   uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted) {
+                   uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted, const uint32_t *off0) {
     __shared__ uint32_t hist[kSmemBuckets];
     const Chunk ch = rec_chunk(dj, g0, g1, blockIdx.x);
     if (!ch.smem) return;  // block-uniform
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(kRecThreads)
             shr256(sc, J.shift);
             // One window: the shifted scalar is its own digit (below 2^(c' - 1)).
             const uint32_t d = sc[0];
+            if (d && ZK_FAILED(d <= nbj, kCheckBucket)) continue;
             if (d) {
                 key[e] = d - 1u;
                 word[e] = ((gid - sb) << 1) | (neg ? 1u : 0u);
@@ -195,15 +200,19 @@ __global__ void __launch_bounds__(kRecThreads)
             if (hist[b]) hist[b] = atomicAdd(&cursor[bb + b], hist[b]);
         __syncthreads();
 #pragma unroll
-        for (uint32_t e = 0; e < kRecEach; e++)
-            if (key[e] != kInvalid) sorted[atomicAdd(&hist[key[e]], 1u)] = word[e];
+        for (uint32_t e = 0; e < kRecEach; e++) {
+            if (key[e] == kInvalid) continue;
+            const uint32_t pos = atomicAdd(&hist[key[e]], 1u);
+            if (ZK_FAILED(!off0 || pos < off0[bb + key[e] + 1], kCheckEntry)) continue;
+            sorted[pos] = word[e];
+        }
     }
 }
 
 template <int C, bool SCATTER>
 __global__ void __launch_bounds__(kRecThreads)
     k_recode(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n, uint32_t *__restrict__ counts,
-             uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted) {
+             uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted, const uint32_t *off0) {
     constexpr int W = (kScalarBits + C - 1) / C;
     static_assert(kRecPer % kRecThreads == 0, "a block lies in one chunk");
     if (rec_chunk(dj, g0, g1, blockIdx.x / kRecEach).smem) return;  // block-uniform
@@ -231,6 +240,7 @@ __global__ void __launch_bounds__(kRecThreads)
         carry = d > (1u << (C - 1)) ? 1u : 0u;
         int sd = carry ? (int)d - (1 << C) : (int)d;
         uint32_t key = (live && sd != 0) ? bb + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
+        if (key != kInvalid && ZK_FAILED(key < dj.bbase[job + 1], kCheckBucket)) key = kInvalid;
         uint32_t group = __match_any_sync(0xffffffffu, key);
         uint32_t leader = (uint32_t)(__ffs(group) - 1);
         if (!SCATTER) {
@@ -242,7 +252,9 @@ __global__ void __launch_bounds__(kRecThreads)
             base = __shfl_sync(0xffffffffu, base, leader);
             if (key != kInvalid) {
                 uint32_t sign = ((sd < 0) ? 1u : 0u) ^ (neg ? 1u : 0u);
-                sorted[base + __popc(group & lt_mask)] = (((uint32_t)w * table_n + i) << 1) | sign;
+                const uint32_t pos = base + __popc(group & lt_mask);
+                if (!ZK_FAILED(!off0 || pos < off0[key + 1], kCheckEntry))
+                    sorted[pos] = (((uint32_t)w * table_n + i) << 1) | sign;
             }
         }
     }
@@ -873,25 +885,28 @@ int launch_reduce(const Xyzz *buckets, const RedBufs &rb, const DevJobs &dj, con
     return ZK_OK;
 }
 
+// off0: the bucket offsets (scatter pass; the checked build bounds each
+// sorted-entry position by its bucket's end).
 template <int C, bool SCATTER>
 int launch_recode_c(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscalars,
                     uint32_t table_n, uint32_t *counts, uint32_t *cursor, uint32_t *sorted,
-                    cudaStream_t s) {
+                    const uint32_t *off0, cudaStream_t s) {
     if (nscalars == 0) return ZK_OK;
     k_recode_short<SCATTER><<<(nscalars + kRecPer - 1) / kRecPer, kRecThreads, 0, s>>>(dj, g0, g1, counts,
-                                                                                      cursor, sorted);
+                                                                                      cursor, sorted, off0);
     ZK_LAUNCHED();
     k_recode<C, SCATTER><<<(nscalars + kRecThreads - 1) / kRecThreads, kRecThreads, 0, s>>>(dj, g0, g1, table_n,
-                                                                                          counts, cursor, sorted);
+                                                                                          counts, cursor, sorted,
+                                                                                          off0);
     ZK_LAUNCHED();
     return ZK_OK;
 }
 
 template <bool SCATTER>
 int recode(int c, const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscalars, uint32_t table_n,
-           uint32_t *counts, uint32_t *cursor, uint32_t *sorted, cudaStream_t s) {
+           uint32_t *counts, uint32_t *cursor, uint32_t *sorted, const uint32_t *off0, cudaStream_t s) {
 #define ZK_RECODE_CASE(C) \
-    case C: return launch_recode_c<C, SCATTER>(dj, g0, g1, nscalars, table_n, counts, cursor, sorted, s);
+    case C: return launch_recode_c<C, SCATTER>(dj, g0, g1, nscalars, table_n, counts, cursor, sorted, off0, s);
     switch (c) {
         ZK_RECODE_CASE(9) ZK_RECODE_CASE(10) ZK_RECODE_CASE(11) ZK_RECODE_CASE(12)
         ZK_RECODE_CASE(13) ZK_RECODE_CASE(14) ZK_RECODE_CASE(15) ZK_RECODE_CASE(16)
@@ -932,6 +947,18 @@ MsmLayout msm_layout(const Shared &sh, int lg) {
     if (sh.tuned_layout[2][lg]) m.seg_small = (uint32_t)sh.tuned_layout[2][lg];
     if (sh.tuned_layout[3][lg]) m.seg_big = (uint32_t)sh.tuned_layout[3][lg];
     return m;
+}
+
+// Reads and clears this translation unit's check flags (always 0 in the
+// normal build).
+int msm_check_read(uint32_t *flags) {
+    *flags = 0;
+#ifdef ZK_CHECK
+    ZK_CUDA_TRY(cudaMemcpyFromSymbol(flags, g_zk_check_flags, sizeof(uint32_t)));
+    const uint32_t zero = 0;
+    ZK_CUDA_TRY(cudaMemcpyToSymbol(g_zk_check_flags, &zero, sizeof(uint32_t)));
+#endif
+    return ZK_OK;
 }
 
 int msm_pick_window(zk_ctx *ctx, size_t n, size_t count) {
@@ -1157,10 +1184,10 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
             const uint32_t tn = tabn[g0];
             if (pass == 0)
                 ZK_TRY(recode<false>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, counts, nullptr,
-                                     nullptr, s));
+                                     nullptr, nullptr, s));
             else
                 ZK_TRY(recode<true>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, nullptr, cursor,
-                                    sorted, s));
+                                    sorted, off0, s));
             g0 = g1;
         }
     }
@@ -1288,6 +1315,7 @@ __global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint3
 
 extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_g1 *out,
                                  zk_stream stream) {
+    ZK_NVTX("zk_commit_noalloc");
     using namespace zk;
     if (!ctx || !coeffs || !out || n == 0) return ZK_EINVAL;
     if (n > kNoAllocMaxN) return ZK_EINVAL;
@@ -1347,11 +1375,11 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     // start at zero; every other region is fully written before it is read.
     ZK_CUDA_TRY(cudaMemsetAsync(counts, 0, (nb + 1) * 4, s));
     ZK_TRY((launch_recode_c<kNoAllocC, false>(dj, 0, 1, total, (uint32_t)tab->n, counts, nullptr,
-                                               nullptr, s)));
+                                               nullptr, nullptr, s)));
     ZK_TRY(scan_exclusive(counts, off0, nb, 0, scan_tmp, s));
     ZK_CUDA_TRY(cudaMemcpyAsync(cursor, off0, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
     ZK_TRY((launch_recode_c<kNoAllocC, true>(dj, 0, 1, total, (uint32_t)tab->n, nullptr, cursor,
-                                              sorted, s)));
+                                              sorted, off0, s)));
     // The built-in layout (the workspace is sized for it).
     const MsmLayout ly{0, 1, 5, 8};
     const AccumShape shape = accum_shape((size_t)n * kNoAllocW, (size_t)n * kNoAllocW, nb, sh.sms, ly);

@@ -25,10 +25,13 @@
 #include <map>
 #include <vector>
 
+#include "check.cuh"
 #include "ctx.cuh"
 #include "field.cuh"
 
 namespace zk {
+
+ZK_CHECK_UNIT()
 
 namespace {
 
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
         uint32_t r = e >> a.logJ, jj = e & (J - 1);
         uint64_t j = j0 + jj;
+        if (ZK_FAILED(j + (uint64_t)r * stride < n, kCheckNttIdx)) continue;
         Fr x = fe_load<FrP>(in + 8 * (j + (uint64_t)r * stride));
         uint64_t m = j & (Ns - 1);
         uint64_t ex = ((uint64_t)r * m) << tshift;
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
         for (int l = 0; l < 8; l++) x.v[l] = sm[l * JR + src * J + jj];
         if (a.scale) x = fe_mul<FrP>(x, sc);
         uint64_t dst = ((j >> a.logNs) << (a.logNs + a.logR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
+        if (ZK_FAILED(dst < n, kCheckNttIdx)) continue;
         fe_store<FrP>(out + 8 * dst, x);
     }
 }
@@ -234,6 +239,10 @@ __global__ void __launch_bounds__(512) k_ntt_reg(PassArgs a) {
 #pragma unroll
         for (uint32_t k = 0; k < E; k++) {
             const uint32_t r = elem_r(0, k);
+            if (ZK_FAILED(j + (uint64_t)r * stride < n, kCheckNttIdx)) {
+                x[k] = fe_zero<FrP>();
+                continue;
+            }
             Fr v = fe_load<FrP>(in + 8 * (j + (uint64_t)r * stride));
             const uint64_t ex = ((uint64_t)r * m) << tshift;
             if (ex) v = fe_mul<FrP>(v, fe_ldg<FrP>(a.tw_n + (a.inverse ? n - ex : ex)));
@@ -318,6 +327,7 @@ __global__ void __launch_bounds__(512) k_ntt_reg(PassArgs a) {
         for (int l = 0; l < 8; l++) v.v[l] = sm[l * P + w];
         if (a.scale) v = fe_mul<FrP>(v, sc);
         const uint64_t dst = ((j >> a.logNs) << (a.logNs + LR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
+        if (ZK_FAILED(dst < n, kCheckNttIdx)) continue;
         fe_store<FrP>(out + 8 * dst, v);
     }
 }
@@ -408,6 +418,18 @@ int ilog2(size_t n) {
 bool is_pow2(size_t n) { return n && !(n & (n - 1)); }
 
 }  // namespace
+
+// Reads and clears this translation unit's check flags (always 0 in the
+// normal build).
+int ntt_check_read(uint32_t *flags) {
+    *flags = 0;
+#ifdef ZK_CHECK
+    ZK_CUDA_TRY(cudaMemcpyFromSymbol(flags, g_zk_check_flags, sizeof(uint32_t)));
+    const uint32_t zero = 0;
+    ZK_CUDA_TRY(cudaMemcpyToSymbol(g_zk_check_flags, &zero, sizeof(uint32_t)));
+#endif
+    return ZK_OK;
+}
 
 int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
     Shared &sh = *ctx->sh;

@@ -109,6 +109,7 @@ extern "C" {
 
 int zk_plan_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, size_t count,
                          unsigned flags, zk_g1 *out, zk_plan **plan) {
+    ZK_NVTX("zk_plan_commit_batch");
     if (!ctx || !vecs || !lens || !out || !plan || count == 0) return ZK_EINVAL;
     std::vector<const void *> ptrs(vecs, vecs + count);
     ptrs.push_back(out);
@@ -125,6 +126,7 @@ int zk_plan_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *le
 
 int zk_plan_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
                       zk_plan **plan) {
+    ZK_NVTX("zk_plan_fold_tree");
     if (!ctx || !leaves || !gammas || !root || !plan) return ZK_EINVAL;
     if (!is_device_ptr(gammas)) return ZK_EINVAL;
     std::vector<zk_acc> lv(leaves, leaves + count);
@@ -138,6 +140,7 @@ int zk_plan_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *ga
 }
 
 int zk_plan_launch(zk_plan *plan, zk_stream stream) {
+    ZK_NVTX("zk_plan_launch");
     if (!plan || !plan->exec) return ZK_EINVAL;
     if (cudaGraphLaunch(plan->exec, (cudaStream_t)stream) != cudaSuccess) {
         cudaGetLastError();

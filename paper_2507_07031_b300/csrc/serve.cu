@@ -69,6 +69,7 @@ struct zk_server {
     std::unordered_map<uint64_t, zk::Ticket> tickets;
     uint64_t next = 1;
     uint64_t completed = 0;
+    uint64_t cancelled = 0;
     bool stop = false;
     std::thread sched;
     zk::Clock::time_point t0;
@@ -250,6 +251,7 @@ int zk_server_create(zk_ctx *ctx, int lanes, size_t hbm_budget_bytes, zk_server 
 }
 
 int zk_submit(zk_server *srv, const zk_job *job, uint64_t *ticket) {
+    ZK_NVTX("zk_submit");
     if (!srv || !job || !ticket) return ZK_EINVAL;
     const size_t n = job->n;
     if (!pow2(n) || n < 2 || n > srv->ctx->sh->srs_n) return ZK_EINVAL;
@@ -308,10 +310,32 @@ int zk_wait(zk_server *srv, uint64_t ticket, int timeout_ms, zk_ticket_info *inf
     return zk_poll(srv, ticket, info);
 }
 
+int zk_cancel(zk_server *srv, uint64_t ticket) {
+    if (!srv) return ZK_EINVAL;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        auto it = srv->tickets.find(ticket);
+        if (it == srv->tickets.end()) return ZK_EINVAL;
+        Ticket &t = it->second;
+        if (t.status != ZK_JOB_QUEUED) return ZK_EBUSY;  // admitted (running) or finished
+        for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+            if (*q == ticket) {
+                srv->queue.erase(q);
+                break;
+            }
+        t.status = ZK_JOB_CANCELLED;
+        t.t_end = Clock::now();
+        srv->cancelled++;
+    }
+    srv->cv.notify_all();
+    return ZK_OK;
+}
+
 int zk_server_stats(zk_server *srv, zk_server_info *info) {
     if (!srv || !info) return ZK_EINVAL;
     std::lock_guard<std::mutex> g(srv->mu);
     info->completed = srv->completed;
+    info->cancelled = srv->cancelled;
     info->queued = srv->queue.size();
     info->reserved_bytes = srv->reserved;
     info->peak_reserved_bytes = srv->peak_reserved;

@@ -193,3 +193,40 @@ def test_wait_times_out_on_a_queued_job(zk, ctx_big):
             assert zk.zk_wait(srv, t, 120000).status == zk.ZK_JOB_DONE
     finally:
         zk.zk_server_destroy(srv)
+
+
+def test_cancel_a_queued_job(zk, ctx_big):
+    """A job still waiting in the queue can be cancelled: it never runs (its
+    output buffer stays untouched), waiters return at once; running or
+    finished jobs cannot be cancelled."""
+    import torch
+    n = 1 << 18
+    res = _resident(zk, ctx_big, n, 9500)
+    slots = [Slot(zk, n, 9600 + 10 * i) for i in range(3)]
+    gam = to_dev(Z.gammas(5, 3))
+    jobs = [zk.make_job(n, s.w, s.leaf, res.leaf, s.out, gam[i]) for i, s in enumerate(slots)]
+    slots[2].out_t[0].fill_(7)
+    torch.cuda.synchronize()
+    srv = zk.zk_server_create(ctx_big, lanes=1)
+    try:
+        tickets = [zk.zk_submit(srv, j) for j in jobs]
+        zk.zk_cancel(srv, tickets[2])
+        info = zk.zk_wait(srv, tickets[2], 1000)
+        assert info.status == zk.ZK_JOB_CANCELLED
+        with pytest.raises(zk.ZkError) as ei:
+            zk.zk_cancel(srv, tickets[2])  # no longer queued
+        assert ei.value.code == zk.ZK_EBUSY
+        with pytest.raises(zk.ZkError) as ei:
+            zk.zk_cancel(srv, 10 ** 9)
+        assert ei.value.code == zk.ZK_EINVAL
+        for t in tickets[:2]:
+            assert zk.zk_wait(srv, t, 120000).status == zk.ZK_JOB_DONE
+        with pytest.raises(zk.ZkError) as ei:
+            zk.zk_cancel(srv, tickets[0])  # finished
+        assert ei.value.code == zk.ZK_EBUSY
+        st = zk.zk_server_stats(srv)
+        assert st.cancelled == 1 and st.completed == 2 and st.queued == 0
+        torch.cuda.synchronize()
+        assert bool((slots[2].out_t[0] == 7).all())  # never written
+    finally:
+        zk.zk_server_destroy(srv)
