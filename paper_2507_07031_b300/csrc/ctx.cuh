@@ -212,9 +212,13 @@ int ntt_pass_radix(const Shared &sh, int L);  // tuned or built-in largest pass 
 //               are in use (fewer partial sums for the tail to combine);
 //   tail_log  : a team-tail slice gives each lane 2^tail_log items;
 //   seg_small, seg_big : log2 of the bucket-reduction segments (seg_big
-//               while a level holds at least 2^13 items).
+//               while a level holds at least 2^13 items);
+//   seq_log   : not tuned; set per call for large batches: the reduction's
+//               first level runs one thread per 2^seq_log buckets (running
+//               sums, two additions per bucket) instead of teams (0 = off).
 struct MsmLayout {
     uint32_t chunk_log, tail_log, seg_small, seg_big;
+    uint32_t seq_log = 0;
 };
 MsmLayout msm_layout(const Shared &sh, int log2n);
 

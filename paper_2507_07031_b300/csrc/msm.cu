@@ -734,10 +734,22 @@ struct RedSched {
     uint32_t glog[kMaxLevels];  // log2 of the segment (the final level: all items)
 };
 
-__host__ __device__ constexpr RedSched red_sched(uint32_t logB, uint32_t gbig = 8, uint32_t gsmall = 5) {
+// With gseq > 0 (large batches), level 0 instead cuts the buckets into
+// segments of 2^gseq that one thread each reduces by running sums (k_reduce_seq:
+// two additions per bucket, none of the teams' scans and trees); the team
+// levels follow.  gseq < kMinWindow - 1 <= logB, so level 0 is never final.
+__host__ __device__ constexpr RedSched red_sched(uint32_t logB, uint32_t gbig = 8, uint32_t gsmall = 5,
+                                                 uint32_t gseq = 0) {
     RedSched r{};
     uint32_t m = logB;
-    for (uint32_t L = 0; L < (uint32_t)kMaxLevels; L++) {
+    uint32_t L0 = 0;
+    if (gseq) {
+        r.mlog[0] = m;
+        r.glog[0] = gseq;
+        m -= gseq;
+        L0 = 1;
+    }
+    for (uint32_t L = L0; L < (uint32_t)kMaxLevels; L++) {
         r.mlog[L] = m;
         const uint32_t g = m >= 13 ? gbig : gsmall;
         // A level whose items fit one team, or one segment, is final; so is
@@ -753,6 +765,12 @@ __host__ __device__ constexpr RedSched red_sched(uint32_t logB, uint32_t gbig = 
     return r;
 }
 
+// k_reduce_seq: threads resident per SM (its occupancy at 128 threads per
+// block, rounded down) and the longest segment (log2; below kMinWindow - 1).
+constexpr uint32_t kSeqThreadsPerSm = 512;
+constexpr uint32_t kMaxSeqLog = 5;
+static_assert(kMaxSeqLog < (uint32_t)kMinWindow - 1, "level 0 of the sequential schedule is never final");
+
 // Item buffers of levels 1 .. kMaxLevels - 1 (V and S); job j's items of
 // level L start at jobs[j].lbase[L - 1].
 struct RedBufs {
@@ -766,11 +784,11 @@ constexpr int kSlots = kSlT + kTeamTemps;
 
 __global__ void __launch_bounds__(kTeamThreads)
     k_reduce_team(const Xyzz *__restrict__ buckets, RedBufs rb, DevJobs dj, uint32_t level, uint32_t gbig,
-                  uint32_t gsmall) {
+                  uint32_t gsmall, uint32_t gseq) {
     __shared__ uint32_t f[kSlots * 8 * 32];
     const uint32_t job = blockIdx.y;
     const JobDesc &J = dj.jobs[job];
-    const RedSched r = red_sched(J.logB, gbig, gsmall);
+    const RedSched r = red_sched(J.logB, gbig, gsmall, gseq);
     if (level >= r.levels) return;  // final at an earlier level
     const bool final_level = level + 1 == r.levels;
     const uint32_t seg = 1u << r.glog[level];
@@ -849,37 +867,78 @@ __global__ void __launch_bounds__(kTeamThreads)
     }
 }
 
+// Level 0 of a large batch's reduction (red_sched with gseq > 0): thread t
+// takes buckets q t .. q t + q - 1 (q = 2^gseq, in the bucket array's
+// layout, jobs at dj.bbase) and, from the top, keeps the running sum r and
+// the sum w of the running sums:
+//     r = sum_k X_k,   w = sum_j sum_{k >= j} X_k = sum_k (k + 1) X_k,
+// i.e. S and V of the segment for f = 0 (Y = X), in 2q - 2 additions.  The
+// threads of a job's buckets beyond its device-side 2^logB exit.
+__global__ void __launch_bounds__(128, 4)
+    k_reduce_seq(const Xyzz *__restrict__ buckets, RedBufs rb, DevJobs dj, uint32_t gseq, uint32_t segs) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= segs) return;
+    const uint32_t q = 1u << gseq, b = t << gseq;
+    const uint32_t job = search(dj.bbase, 0, dj.count, b);
+    const JobDesc &J = dj.jobs[job];
+    const uint32_t local = b - dj.bbase[job];
+    if (local >= (1u << J.logB)) return;
+    // w waits in shared memory while r takes the next bucket, so that one
+    // point is live across each addition (the register budget of four
+    // blocks per SM).
+    __shared__ Xyzz ws[128];
+    const Xyzz *X = buckets + b;
+    Xyzz r = X[q - 1];
+    ws[threadIdx.x] = r;
+    for (uint32_t k = q - 1; k-- > 0;) {
+        r = xyzz_add(r, X[k]);
+        ws[threadIdx.x] = xyzz_add(ws[threadIdx.x], r);
+    }
+    const size_t o = J.lbase[0] + (local >> gseq);
+    rb.v[1][o] = ws[threadIdx.x];
+    rb.s[1][o] = r;
+}
+
 // Item capacity of reduction level L (1 .. kMaxLevels - 1) and the teams of
 // level L (0 ..) for a job whose bucket count may be any 2^logB with
 // logB in [lo, hi] (the device lowers logB for short scalars).
-constexpr uint32_t red_cap(uint32_t lo, uint32_t hi, uint32_t L, uint32_t gbig = 8, uint32_t gsmall = 5) {
+constexpr uint32_t red_cap(uint32_t lo, uint32_t hi, uint32_t L, uint32_t gbig = 8, uint32_t gsmall = 5,
+                           uint32_t gseq = 0) {
     uint32_t c = 0;
     for (uint32_t b = lo; b <= hi; b++) {
-        const RedSched r = red_sched(b, gbig, gsmall);
+        const RedSched r = red_sched(b, gbig, gsmall, gseq);
         if (L < r.levels) c = std::max(c, 1u << r.mlog[L]);
     }
     return c;
 }
-constexpr uint32_t red_teams(uint32_t lo, uint32_t hi, uint32_t L, uint32_t gbig = 8, uint32_t gsmall = 5) {
+constexpr uint32_t red_teams(uint32_t lo, uint32_t hi, uint32_t L, uint32_t gbig = 8, uint32_t gsmall = 5,
+                             uint32_t gseq = 0) {
     uint32_t t = 0;
     for (uint32_t b = lo; b <= hi; b++) {
-        const RedSched r = red_sched(b, gbig, gsmall);
+        const RedSched r = red_sched(b, gbig, gsmall, gseq);
         if (L < r.levels) t = std::max(t, 1u << (r.mlog[L] - r.glog[L]));
     }
     return t;
 }
 
 // Launches the reduction levels for jobs whose bucket counts are 2^logB with
-// logB in [lo[k], hi[k]].
+// logB in [lo[k], hi[k]] (nb buckets in all, in the bucket array's layout).
 int launch_reduce(const Xyzz *buckets, const RedBufs &rb, const DevJobs &dj, const uint32_t *lo,
-                  const uint32_t *hi, size_t count, const MsmLayout &ly, cudaStream_t s) {
-    for (uint32_t level = 0; level < (uint32_t)kMaxLevels; level++) {
+                  const uint32_t *hi, size_t count, uint32_t nb, const MsmLayout &ly, cudaStream_t s) {
+    uint32_t level = 0;
+    if (ly.seq_log) {
+        const uint32_t segs = nb >> ly.seq_log;
+        k_reduce_seq<<<(segs + 127) / 128, 128, 0, s>>>(buckets, rb, dj, ly.seq_log, segs);
+        ZK_LAUNCHED();
+        level = 1;
+    }
+    for (; level < (uint32_t)kMaxLevels; level++) {
         uint32_t gx = 0;
         for (size_t k = 0; k < count; k++)
-            gx = std::max(gx, red_teams(lo[k], hi[k], level, ly.seg_big, ly.seg_small));
+            gx = std::max(gx, red_teams(lo[k], hi[k], level, ly.seg_big, ly.seg_small, ly.seq_log));
         if (!gx) break;
         k_reduce_team<<<dim3(gx, (unsigned)count), kTeamThreads, 0, s>>>(buckets, rb, dj, level, ly.seg_big,
-                                                                          ly.seg_small);
+                                                                          ly.seg_small, ly.seq_log);
         ZK_LAUNCHED();
     }
     return ZK_OK;
@@ -1057,21 +1116,35 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     MsmLayout ly = msm_layout(sh, lgmax);
     // The tuned segments suit one MSM, whose reduction is latency bound.  A
     // batch of many MSMs (a fold-tree level: 512 of them; a model's tiny
-    // commitments: thousands) keeps every SM busy instead; there larger
-    // segments amortise each team's scans, so the segments grow (the small
-    // one first, if any job uses it) while level 0 would still hold far more
-    // teams than the GPU keeps resident (about six per SM).
+    // commitments: thousands) keeps every SM busy instead, and there the
+    // work of the teams' scans and trees (several additions per bucket)
+    // dominates.  When the buckets give every resident thread at least two
+    // segments of 2^g (g <= kMaxSeqLog), level 0 runs one thread per segment
+    // (two additions per bucket, k_reduce_seq) with the largest such g.
+    ly.seq_log = 0;
+    {
+        const size_t threads = (size_t)std::max(sh.sms, 1) * kSeqThreadsPerSm;
+        for (uint32_t g = kMaxSeqLog; g >= 1; g--)
+            if ((nb64 >> g) >= 2 * threads) {
+                ly.seq_log = g;
+                break;
+            }
+    }
+    // Then the team levels' segments grow (the small one first, if any job
+    // uses it) while their first level would still hold far more teams than
+    // the GPU keeps resident (about six per SM): larger segments amortise
+    // each team's scans.
     {
         auto teams0 = [&](uint32_t gb, uint32_t gs) {
             size_t t = 0;
             for (size_t k = 0; k < count; k++) {
-                const uint32_t lb = (uint32_t)jv[k].c - 1, g = lb >= 13 ? gb : gs;
+                const uint32_t lb = (uint32_t)jv[k].c - 1 - ly.seq_log, g = lb >= 13 ? gb : gs;
                 t += lb > g ? (size_t)1 << (lb - g) : 1;
             }
             return t;
         };
         bool small_used = false;
-        for (size_t k = 0; k < count; k++) small_used |= jv[k].c - 1 < 13;
+        for (size_t k = 0; k < count; k++) small_used |= jv[k].c - 1 - (int)ly.seq_log < 13;
         const size_t resident = (size_t)std::max(sh.sms, 1) * 6;
         while (teams0(ly.seg_big, ly.seg_small) > 4 * resident) {
             if (small_used && ly.seg_small < 8) ly.seg_small++;
@@ -1089,7 +1162,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hi[k] = (uint32_t)(jv[k].c - 1);
         lo[k] = stats ? (uint32_t)(kMinWindow - 1) : hi[k];
         for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++)
-            lvl_items[L] += red_cap(lo[k], hi[k], L, ly.seg_big, ly.seg_small);
+            lvl_items[L] += red_cap(lo[k], hi[k], L, ly.seg_big, ly.seg_small, ly.seq_log);
     }
 
     // Workspace.
@@ -1146,7 +1219,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hd[k].t16n = t16n[k];
         for (uint32_t L = 1; L < (uint32_t)kMaxLevels; L++) {
             hd[k].lbase[L - 1] = lb[L];
-            lb[L] += red_cap(lo[k], hi[k], L, ly.seg_big, ly.seg_small);
+            lb[L] += red_cap(lo[k], hi[k], L, ly.seg_big, ly.seg_small, ly.seq_log);
         }
         hs[k + 1] = hs[k] + jv[k].job.n;
         hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
@@ -1201,7 +1274,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
 
     // 4-5: bucket reduction and output.
     PhaseScope ph_reduce(ctx, ZK_PHASE_MSM_REDUCE, s);
-    return launch_reduce(buckets, rb, dj, lo.data(), hi.data(), count, ly, s);
+    return launch_reduce(buckets, rb, dj, lo.data(), hi.data(), count, nb, ly, s);
 }
 
 }  // namespace zk
@@ -1388,5 +1461,5 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
                        scan_tmp, (uint32_t *)(ws + kNaOffS)};
     ZK_TRY(launch_accumulate(sorted, counts, off0, nb, shape, dj, ab, buckets, sh.sms, s));
     const uint32_t logB = kNoAllocC - 1;
-    return launch_reduce(buckets, rb, dj, &logB, &logB, 1, ly, s);
+    return launch_reduce(buckets, rb, dj, &logB, &logB, 1, kNoAllocB, ly, s);
 }

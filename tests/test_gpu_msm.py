@@ -210,6 +210,35 @@ def test_large_mixed_batch(zk, orc, ctx_big, tau):
         assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (k, lens[k])
 
 
+@pytest.mark.parametrize("g", [1, 2, 3, 4, 5])
+def test_batch_sequential_reduction_level(zk, orc, ctx_big, tau, g):
+    """A large batch runs the first level of its bucket reduction one thread
+    per 2^g buckets (running sums), g the largest value up to 5 for which the
+    batch's buckets give every resident thread (512 per SM) two segments.
+    Batches of 2^12-point jobs (4096 buckets each) are sized here for each g.
+    Every third job has quantised scalars, for which the device lowers the
+    bucket count to 2^8 (the threads past it exit); one job is all zero."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 1 << 12
+    count = (2 * sms * 512 << g) // 4096 + 1
+    vecs = []
+    for i in range(count):
+        if i == 1:
+            vecs.append(np.zeros((n, 4), dtype=np.uint64))
+        elif i % 3 == 0:
+            vecs.append(Z.zkml_scalars(50_000 + i, n))
+        else:
+            vecs.append(Z.fr_uniform(50_000 + i, n))
+    out = torch.zeros((count, 8), dtype=torch.int64, device="cuda")
+    zk.zk_commit_batch(ctx_big, [to_dev(v) for v in vecs], out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    assert not got[1].any()  # the zero job commits to infinity
+    for k, v in enumerate(vecs):
+        assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (g, k)
+
+
 @pytest.fixture(scope="module")
 def layout_case():
     n = 1 << 18
