@@ -71,6 +71,7 @@ struct DevJobs {
     const JobDesc *jobs;     // count entries
     const uint32_t *sbase;   // scalar prefix over jobs, count + 1
     const uint32_t *bbase;   // first global bucket of each job, count + 1
+    const uint32_t *cbase;   // prefix of the jobs' wide-recode chunks (0 for the others), count + 1
     uint32_t count;
 };
 
@@ -257,6 +258,78 @@ __global__ void __launch_bounds__(kRecThreads)
                     sorted[pos] = (((uint32_t)w * table_n + i) << 1) | sign;
             }
         }
+    }
+}
+
+// Phases 1 and 2 for the large jobs of a big batch (a fold-tree level: 512
+// jobs of 2^16 scalars): one block per chunk of kWidePer scalars of one job,
+// counting the chunk's digits in a shared-memory histogram of the job's
+// 2^logB buckets (c <= 16: at most 128 KB), so that one global atomic per
+// bucket stands for the chunk's ~kWidePer W / 2^logB digits of that bucket
+// instead of one per digit.  With SCATTER the block counts again, reserves
+// each bucket's range with one atomic on its cursor, and places the entries
+// through shared-memory atomics.  The digits (signed windows) are those of
+// k_recode.  Chunk k of jobs [g0, g1) is k - cbase[job] of that job.
+constexpr uint32_t kWidePer = 8192;
+constexpr uint32_t kWideThreads = 1024;
+constexpr uint32_t kWideMaxLogB = 15;
+// Shared memory every block requests (at least its histogram): more than half
+// of an SM's, so that one block runs per SM.  With three blocks per SM the
+// chunks in flight (their scalars, which the scatter pass reads twice, and
+// their entries' write ranges) overflowed L2 and the sort of a 512 x 2^16
+// batch at width 15 took three times as long (16.7 against 5.4 ms, B300).
+constexpr int kWideSmemMin = 128 << 10;
+constexpr uint32_t kWideMinN = 1u << 14;  // shorter jobs stay on k_recode / k_recode_short
+
+template <int C>
+__device__ __forceinline__ void wide_digits(const JobDesc &J, uint32_t i, uint32_t table_n, uint32_t nbj,
+                                            uint32_t *hist, bool place, uint32_t *sorted, const uint32_t *end) {
+    constexpr int W = (kScalarBits + C - 1) / C;
+    uint32_t sc[8];
+    const bool neg = load_recentred(J.scalars + 8 * (size_t)i, sc);
+    shr256(sc, J.shift);
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        if ((uint32_t)w >= J.wins) break;
+        const uint32_t d = window_bits<C>(sc, w) + carry;
+        carry = d > (1u << (C - 1)) ? 1u : 0u;
+        const int sd = carry ? (int)d - (1 << C) : (int)d;
+        if (sd == 0) continue;
+        const uint32_t key = (uint32_t)(sd < 0 ? -sd : sd) - 1u;
+        if (ZK_FAILED(key < nbj, kCheckBucket)) continue;
+        const uint32_t pos = atomicAdd(&hist[key], 1u);
+        if (place && !ZK_FAILED(!end || pos < end[key + 1], kCheckEntry)) {
+            const uint32_t sign = ((sd < 0) ? 1u : 0u) ^ (neg ? 1u : 0u);
+            sorted[pos] = (((uint32_t)w * table_n + i) << 1) | sign;
+        }
+    }
+}
+
+template <int C, bool SCATTER>
+__global__ void __launch_bounds__(kWideThreads)
+    k_recode_wide(DevJobs dj, uint32_t g0, uint32_t g1, uint32_t table_n, uint32_t *__restrict__ counts,
+                  uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted, const uint32_t *off0) {
+    extern __shared__ uint32_t hist[];
+    const uint32_t k = dj.cbase[g0] + blockIdx.x;
+    const uint32_t job = search(dj.cbase, g0, g1, k);
+    const JobDesc &J = dj.jobs[job];
+    const uint32_t first = (k - dj.cbase[job]) * kWidePer, last = min(first + kWidePer, J.n);
+    const uint32_t nbj = 1u << J.logB, bb = dj.bbase[job];
+    for (uint32_t b = threadIdx.x; b < nbj; b += kWideThreads) hist[b] = 0;
+    __syncthreads();
+    for (uint32_t i = first + threadIdx.x; i < last; i += kWideThreads)
+        wide_digits<C>(J, i, table_n, nbj, hist, false, nullptr, nullptr);
+    __syncthreads();
+    if constexpr (!SCATTER) {
+        for (uint32_t b = threadIdx.x; b < nbj; b += kWideThreads)
+            if (hist[b]) atomicAdd(&counts[bb + b], hist[b]);
+    } else {
+        for (uint32_t b = threadIdx.x; b < nbj; b += kWideThreads)
+            if (hist[b]) hist[b] = atomicAdd(&cursor[bb + b], hist[b]);
+        __syncthreads();
+        for (uint32_t i = first + threadIdx.x; i < last; i += kWideThreads)
+            wide_digits<C>(J, i, table_n, nbj, hist, true, sorted, off0 ? off0 + bb : nullptr);
     }
 }
 
@@ -559,18 +632,27 @@ __global__ void __launch_bounds__(kTeamThreads)
         const uint32_t lo = off[b] + (g - off_s[b]) * slice;
         const uint32_t hi = min(lo + slice, off[b + 1]);
         const Affine *table = entries ? dj.jobs[search(dj.bbase, 0, dj.count, b)].table : nullptr;
-        // Coordinate w of item j (a table point with sign, or a partial sum).
-        auto fetch = [&](uint32_t j) -> Fq {
-            if (j >= hi) return fe_zero<FqP>();
-            if (!entries) return team_fetch(in + j, true);
-            const uint32_t v = fi.sorted[j];
-            if (w >= 2) return fe_mont_one<FqP>();
-            const Fq c = fe_ldg<FqP>(reinterpret_cast<const char *>(table + (v >> 1)) + 32 * w);
-            return (w == 1 && (v & 1)) ? fe_neg<FqP>(c) : c;
+        // Coordinate w of item j (a table point, or a partial sum) and whether
+        // it is negated (a table point's Y with the sign bit) when stored, so
+        // that a prefetch does not wait for its loads.
+        struct Coord {
+            Fq c;
+            bool neg;
         };
-        tf_store(f, kBtAcc + w, fetch(lo + l));
+        auto fetch = [&](uint32_t j) -> Coord {
+            if (j >= hi) return {fe_zero<FqP>(), false};
+            if (!entries) return {team_fetch(in + j, true), false};
+            if (w >= 2) return {fe_mont_one<FqP>(), false};
+            const uint32_t v = fi.sorted[j];
+            return {fe_ldg<FqP>(reinterpret_cast<const char *>(table + (v >> 1)) + 32 * w), w == 1 && (v & 1)};
+        };
+        auto put = [&](int slot, const Coord &x) { tf_store(f, slot + w, x.neg ? fe_neg<FqP>(x.c) : x.c); };
+        put(kBtAcc, fetch(lo + l));
+        // The next item's loads are issued before the current addition.
+        Coord nx = fetch(lo + 32 + l);
         for (uint32_t j = lo + 32; j < hi; j += 32) {
-            tf_store(f, kBtIn + w, fetch(j + l));
+            put(kBtIn, nx);
+            nx = fetch(j + 32 + l);
             __syncthreads();
             team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
         }
@@ -591,22 +673,37 @@ __global__ void __launch_bounds__(kTeamThreads)
     __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
     if (!plan->team) return;
     const uint32_t l = team_lane(), w = team_warp();
+    __shared__ uint32_t multi[kTeamThreads], nmulti;
     const Xyzz *parts = plan->parts;
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {  // block-uniform
-        const uint32_t lo = off_s[b], cnt = off_s[b + 1] - lo;
-        if (cnt <= 1) {
-            if (threadIdx.x == 0) buckets[b] = cnt ? parts[lo] : xyzz_inf();
-            continue;
-        }
-        tf_store(f, kBtAcc + w, team_fetch(parts + lo + l, l < cnt));
+    // Block k takes buckets k, k + G, k + 2G, ... (G blocks), 128 at a time:
+    // one thread per bucket writes those with at most one partial sum, and
+    // the others (a few per block) are summed by the team one by one.
+    const uint32_t mine = blockIdx.x < nb ? (nb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    for (uint32_t j0 = 0; j0 < mine; j0 += kTeamThreads) {  // block-uniform
+        if (threadIdx.x == 0) nmulti = 0;
         __syncthreads();
-        for (uint32_t d = 16; d >= 1; d >>= 1) {
-            if (d >= cnt) continue;
-            team_shift(f, kBtAcc, kBtTmp, (int)d);
-            team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
+        const uint32_t j = j0 + threadIdx.x;
+        if (j < mine) {
+            const uint32_t b = blockIdx.x + j * gridDim.x;
+            const uint32_t lo = off_s[b], cnt = off_s[b + 1] - lo;
+            if (cnt <= 1) buckets[b] = cnt ? parts[lo] : xyzz_inf();
+            else multi[atomicAdd(&nmulti, 1u)] = b;
         }
-        if (l == 0) team_put(f, kBtAcc, buckets + b);
         __syncthreads();
+        const uint32_t nm = nmulti;
+        for (uint32_t i = 0; i < nm; i++) {  // block-uniform
+            const uint32_t b = multi[i];
+            const uint32_t lo = off_s[b], cnt = off_s[b + 1] - lo;
+            tf_store(f, kBtAcc + w, team_fetch(parts + lo + l, l < cnt));
+            __syncthreads();
+            for (uint32_t d = 16; d >= 1; d >>= 1) {
+                if (d >= cnt) continue;
+                team_shift(f, kBtAcc, kBtTmp, (int)d);
+                team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
+            }
+            if (l == 0) team_put(f, kBtAcc, buckets + b);
+            __syncthreads();
+        }
     }
 }
 
@@ -961,6 +1058,45 @@ int launch_recode_c(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscala
     return ZK_OK;
 }
 
+// Jobs [g0, g1) of width C, all on the wide path: `chunks` chunks of
+// kWidePer scalars (C <= kWideMaxLogB + 1).
+template <int C, bool SCATTER>
+int launch_recode_wide_c(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t chunks, uint32_t table_n,
+                         uint32_t *counts, uint32_t *cursor, uint32_t *sorted, const uint32_t *off0,
+                         cudaStream_t s) {
+    if constexpr (C - 1 > (int)kWideMaxLogB) {
+        return ZK_EINVAL;
+    } else {
+        if (chunks == 0) return ZK_OK;
+        constexpr int kSmem = std::max((1 << (C - 1)) * 4, kWideSmemMin);
+        static const bool attr = [] {
+            const bool ok = cudaFuncSetAttribute(k_recode_wide<C, SCATTER>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) == cudaSuccess;
+            if (!ok) cudaGetLastError();
+            return ok;
+        }();
+        if (!attr) return ZK_ECUDA;
+        k_recode_wide<C, SCATTER><<<chunks, kWideThreads, kSmem, s>>>(dj, g0, g1, table_n, counts, cursor, sorted,
+                                                                     off0);
+        ZK_LAUNCHED();
+        return ZK_OK;
+    }
+}
+
+template <bool SCATTER>
+int recode_wide(int c, const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t chunks, uint32_t table_n,
+                uint32_t *counts, uint32_t *cursor, uint32_t *sorted, const uint32_t *off0, cudaStream_t s) {
+    if (chunks == 0) return ZK_OK;
+#define ZK_RECODE_WIDE_CASE(C) \
+    case C: return launch_recode_wide_c<C, SCATTER>(dj, g0, g1, chunks, table_n, counts, cursor, sorted, off0, s);
+    switch (c) {
+        ZK_RECODE_WIDE_CASE(9) ZK_RECODE_WIDE_CASE(10) ZK_RECODE_WIDE_CASE(11) ZK_RECODE_WIDE_CASE(12)
+        ZK_RECODE_WIDE_CASE(13) ZK_RECODE_WIDE_CASE(14) ZK_RECODE_WIDE_CASE(15) ZK_RECODE_WIDE_CASE(16)
+        default: return ZK_EINVAL;
+    }
+#undef ZK_RECODE_WIDE_CASE
+}
+
 template <bool SCATTER>
 int recode(int c, const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t nscalars, uint32_t table_n,
            uint32_t *counts, uint32_t *cursor, uint32_t *sorted, const uint32_t *off0, cudaStream_t s) {
@@ -1052,6 +1188,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     struct J {
         MsmJob job;
         int c;
+        bool big;  // may take the wide recode path (long enough, histogram fits)
     };
     std::vector<J> jv(count);
     size_t total64 = 0, entries64 = 0, nb64 = 0;
@@ -1059,7 +1196,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         const MsmJob &m = jobs_in[k];
         int c = c_fixed > 0 ? c_fixed : msm_pick_window(ctx, std::max<uint32_t>(m.n, 1), count);
         if (c < kMinWindow || c > kMaxWindow) return ZK_EINVAL;
-        jv[k] = {m, c};
+        jv[k] = {m, c, m.n >= kWideMinN && (uint32_t)c - 1 <= kWideMaxLogB};
         total64 += m.n;
         entries64 += (size_t)m.n * windows_for(c);
         nb64 += (size_t)1 << (c - 1);
@@ -1067,7 +1204,8 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     if (nb64 >= (1ull << 31) || entries64 >= (1ull << 32)) return ZK_EINVAL;
     std::stable_sort(jv.begin(), jv.end(), [](const J &a, const J &b) {
         if (a.c != b.c) return a.c < b.c;
-        return a.job.basis < b.job.basis;
+        if (a.job.basis != b.job.basis) return a.job.basis < b.job.basis;
+        return a.big < b.big;
     });
     // Point tables: the base points (SRS, or the Lagrange basis of H for
     // evaluation-form jobs) and the width's window table of that basis
@@ -1169,7 +1307,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     int err = ZK_OK;
     const size_t jd_bytes = align_up(count * sizeof(JobDesc), 256);
     const size_t pre_bytes = align_up((count + 1) * 4, 256);
-    char *jt = (char *)scratch(ctx, "msm.jobs", jd_bytes + 2 * pre_bytes, &err);
+    char *jt = (char *)scratch(ctx, "msm.jobs", jd_bytes + 3 * pre_bytes, &err);
     uint32_t *counts = (uint32_t *)scratch(ctx, "msm.counts", (nb + 1) * 4, &err);
     uint32_t *off0 = (uint32_t *)scratch(ctx, "msm.off0", (nb + 1) * 4, &err);
     uint32_t *offa = (uint32_t *)scratch(ctx, "msm.offa", (nb + 1) * 4, &err);
@@ -1198,10 +1336,24 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         return err;
 
     // Job table: descriptors and the two prefix arrays.
-    std::vector<char> h(jd_bytes + 2 * pre_bytes, 0);
+    std::vector<char> h(jd_bytes + 3 * pre_bytes, 0);
     JobDesc *hd = (JobDesc *)h.data();
     uint32_t *hs = (uint32_t *)(h.data() + jd_bytes);
     uint32_t *hb = (uint32_t *)(h.data() + jd_bytes + pre_bytes);
+    uint32_t *hc = (uint32_t *)(h.data() + jd_bytes + 2 * pre_bytes);
+    // Wide recode path: per group of one width and table, its big jobs (at
+    // the group's end) when their chunks give every SM at least two.
+    std::vector<bool> wide(count, false);
+    for (size_t g0 = 0; g0 < count;) {
+        size_t g1 = g0;
+        while (g1 < count && jv[g1].c == jv[g0].c && tabs[g1] == tabs[g0]) g1++;
+        size_t chunks = 0;
+        for (size_t k = g0; k < g1; k++)
+            if (jv[k].big) chunks += (jv[k].job.n + kWidePer - 1) / kWidePer;
+        if (chunks >= 2 * (size_t)std::max(sh.sms, 1))
+            for (size_t k = g0; k < g1; k++) wide[k] = jv[k].big;
+        g0 = g1;
+    }
     uint32_t lb[kMaxLevels] = {0, 0, 0, 0};
     for (size_t k = 0; k < count; k++) {
         hd[k].scalars = jv[k].job.scalars;
@@ -1223,12 +1375,14 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         }
         hs[k + 1] = hs[k] + jv[k].job.n;
         hb[k + 1] = hb[k] + (1u << (jv[k].c - 1));
+        hc[k + 1] = hc[k] + (wide[k] ? (jv[k].job.n + kWidePer - 1) / kWidePer : 0u);
     }
     ZK_TRY(upload(ctx, jt, h.data(), h.size(), s));
     DevJobs dj;
     dj.jobs = (const JobDesc *)jt;
     dj.sbase = (const uint32_t *)(jt + jd_bytes);
     dj.bbase = (const uint32_t *)(jt + jd_bytes + pre_bytes);
+    dj.cbase = (const uint32_t *)(jt + jd_bytes + 2 * pre_bytes);
     dj.count = (uint32_t)count;
 
     // 1-2: width statistics and plan, histogram, offsets, scatter (one
@@ -1253,14 +1407,18 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         for (size_t g0 = 0; g0 < count;) {
             size_t g1 = g0;
             while (g1 < count && jv[g1].c == jv[g0].c && tabs[g1] == tabs[g0]) g1++;
-            const uint32_t ns = hs[g1] - hs[g0];
+            size_t gw = g0;  // the group's wide jobs are [gw, g1)
+            while (gw < g1 && !wide[gw]) gw++;
+            const uint32_t ns = hs[gw] - hs[g0], nc = hc[g1] - hc[gw];
             const uint32_t tn = tabn[g0];
-            if (pass == 0)
-                ZK_TRY(recode<false>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, counts, nullptr,
-                                     nullptr, nullptr, s));
-            else
-                ZK_TRY(recode<true>(jv[g0].c, dj, (uint32_t)g0, (uint32_t)g1, ns, tn, nullptr, cursor,
-                                    sorted, off0, s));
+            const uint32_t a = (uint32_t)g0, m = (uint32_t)gw, b = (uint32_t)g1;
+            if (pass == 0) {
+                ZK_TRY(recode<false>(jv[g0].c, dj, a, m, ns, tn, counts, nullptr, nullptr, nullptr, s));
+                ZK_TRY(recode_wide<false>(jv[g0].c, dj, m, b, nc, tn, counts, nullptr, nullptr, nullptr, s));
+            } else {
+                ZK_TRY(recode<true>(jv[g0].c, dj, a, m, ns, tn, nullptr, cursor, sorted, off0, s));
+                ZK_TRY(recode_wide<true>(jv[g0].c, dj, m, b, nc, tn, nullptr, cursor, sorted, off0, s));
+            }
             g0 = g1;
         }
     }
@@ -1442,6 +1600,7 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     dj.jobs = (const JobDesc *)(ws + kNaJobs);
     dj.sbase = (const uint32_t *)(ws + kNaJobs + 256);
     dj.bbase = dj.sbase + kNoAllocPre / 4;
+    dj.cbase = nullptr;  // no wide recode chunks
     dj.count = 1;
     const uint32_t total = (uint32_t)n;
     // The workspace keeps the previous call's contents: the histogram must

@@ -239,6 +239,34 @@ def test_batch_sequential_reduction_level(zk, orc, ctx_big, tau, g):
         assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (g, k)
 
 
+def test_batch_wide_recode(zk, orc, ctx_big, tau):
+    """In a batch whose long jobs (2^14 points or more, window width <= 16)
+    give every SM at least two chunks of 8192 scalars, those jobs are sorted
+    through shared-memory histograms (one block per chunk).  Here: 2^16-point
+    jobs at width 15 (uniform, and every fourth quantised), two ragged long
+    jobs (2^14 + 3, 2^15 - 1), an all-zero long job, a shorter job of the same
+    width (10000 points, on the per-scalar path) and one of another width."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nbig = (2 * sms + 7) // 8 + 2
+    lens = [1 << 16] * nbig + [(1 << 14) + 3, (1 << 15) - 1, 1 << 16, 10000, 3000]
+    vecs = []
+    for i, n in enumerate(lens):
+        if i == nbig + 2:
+            vecs.append(np.zeros((n, 4), dtype=np.uint64))
+        elif i % 4 == 3:
+            vecs.append(Z.zkml_scalars(60_000 + i, n))
+        else:
+            vecs.append(Z.fr_uniform(60_000 + i, n))
+    out = torch.zeros((len(lens), 8), dtype=torch.int64, device="cuda")
+    zk.zk_commit_batch(ctx_big, [to_dev(v) for v in vecs], out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    assert not got[nbig + 2].any()
+    for k, v in enumerate(vecs):
+        assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (k, lens[k])
+
+
 @pytest.fixture(scope="module")
 def layout_case():
     n = 1 << 18
