@@ -440,42 +440,33 @@ __global__ void k_msm_plan(JobDesc *__restrict__ jobs, uint32_t count, const uin
     }
 }
 
-__device__ __forceinline__ Affine table_point(const DevJobs &dj, uint32_t b, uint32_t v) {
-    uint32_t job = search(dj.bbase, 0, dj.count, b);
-    Affine a = affine_ldg(dj.jobs[job].table + (v >> 1));
-    if (v & 1) a = affine_neg(a);
-    return a;
-}
-
 // Phase 3: bucket sums.  Round 0 cuts the sorted entries into fixed chunks
 // of p0 consecutive entries (whatever the bucket boundaries, so every thread
-// does the same work) and emits one partial sum per bucket a chunk meets.
-// Rounds 1, 2, ... add each bucket's items kPiece at a time.  The rounds are
-// launched for the worst case (every entry of a job in one bucket), but a
-// round plan computed on the device from the largest bucket skips, at
-// execution time, the rounds (and their scans) that the actual buckets do not
-// need.  The last stage sums what is left per bucket: one thread per bucket,
-// or, for small bucket sets whose buckets still hold more than a few items
-// (quantised scalars put many entries in few buckets), one team per bucket.
-constexpr uint32_t kPiece = 32;             // items per thread in rounds >= 1
+// does the same work) and emits one partial sum (piece) per bucket a chunk
+// meets; bucket b's pieces are off1[b] .. off1[b + 1] - 1, in chunk order.
+// What completes a bucket depends on its piece count m:
+//   m = 1:                the piece is the bucket sum, stored as such;
+//   2 <= m <= kThreadMax: one thread per bucket (k_buckets_final);
+//   m > kThreadMax:       teams (k_tail_slices, k_tail_buckets): small bucket
+//                         sets with many entries each (quantised scalars put
+//                         2^20 entries in about a hundred buckets), or a
+//                         skewed bucket.
+// Empty buckets are set to infinity by k_buckets_final.  (Completing buckets
+// of a few pieces inside round 0 instead -- the last thread to finish one,
+// found by a per-bucket counter, adding the others -- made a 2^20 MSM of
+// uniform scalars 2 % slower on B300: the fences, atomics and extra registers
+// cost the loop more than the separate pass.)
 constexpr uint32_t kP0Min = 8;              // smallest round-0 chunk
-constexpr int kMaxRounds = 8;
-constexpr uint32_t kTailBuckets = 4096;     // bucket sets that may end on teams
-constexpr uint32_t kTailItems = 1024;       // items a team sums per bucket (32 per lane)
-constexpr uint32_t kTailMin = 4;            // fewer items per bucket: one thread
+constexpr uint32_t kThreadMax = 32;
+constexpr uint32_t kTailBuckets = 4096;     // bucket sets that take longer round-0 chunks (chunk_log)
 
 struct RoundPlan {
-    uint32_t run[kMaxRounds];  // round rd executes
-    uint32_t last;             // rounds that execute (a prefix of 0 .. rounds-1)
-    uint32_t team;             // the last stage runs on teams
-    uint32_t p0;               // round-0 chunk (entries per thread)
-    int p0neg;                 // -p0 (the scan's chunk-count mode)
-    const uint32_t *off;       // offsets of the items the last stage sums
-    Xyzz *parts;               // a piece buffer the last round does not hold (team tail partials)
+    uint32_t p0;  // round-0 chunk (entries per thread)
+    int p0neg;    // -p0 (the scan's chunk-count mode)
 };
 
-// Largest bucket (entries) into stat[0] and the number of nonempty buckets
-// into stat[1] (both zeroed by the caller).
+// The number of nonempty buckets into stat[1] and the largest bucket into
+// stat[0] (both zeroed by the caller).
 __global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, uint32_t *stat) {
     uint32_t m = 0, used = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
@@ -488,49 +479,34 @@ __global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, ui
     if (lane_id() == 0 && used) atomicAdd(&stat[1], used);
 }
 
-// Shape of phase 3 from the actual entries (their count at off0[nb], the
-// largest bucket and the nonempty buckets in stat): round 0 gives every
-// resident thread one chunk of p0 = ceil(entries / resident) entries (at
-// least kP0Min; 2^chunk_log times more when few buckets are in use), so it
-// runs as one wave; round rd runs while the largest
-// bucket still holds more than `thr` items (kPiece, or kTailItems when few
-// buckets are in use and the last stage may run on teams).
+// Round-0 chunk from the actual entries (their count at off0[nb]): every
+// resident thread gets one chunk of p0 = ceil(entries / resident) entries (at
+// least kP0Min), so round 0 runs as one wave; 2^chunk_log times more when few
+// buckets are in use (fewer pieces for the team tail).
 __global__ void k_round_plan(const uint32_t *stat, const uint32_t *total, uint32_t resident, uint32_t chunk_log,
-                             uint32_t rounds, const uint32_t *off0, const uint32_t *offa, const uint32_t *offb,
-                             Xyzz *pa, Xyzz *pb, RoundPlan *plan) {
+                             RoundPlan *plan) {
     if (threadIdx.x || blockIdx.x) return;
     const uint32_t entries = *total;
-    const bool tail = stat[1] <= kTailBuckets;
-    // Few buckets in use: longer chunks (chunk_log) leave fewer partial sums
-    // for the team tail; the chunks still fill the GPU when it runs.
+    const bool few = stat[1] <= kTailBuckets;
     const uint32_t p0 = max(kP0Min, (uint32_t)(((uint64_t)entries + resident - 1) / resident))
-                        << (tail ? chunk_log : 0u);
-    uint32_t x = stat[0], last = 0;
-    const uint32_t thr = tail ? kTailItems : kPiece;
-    for (uint32_t rd = 0; rd < (uint32_t)kMaxRounds; rd++) {
-        const bool run = rd < rounds && x > thr;
-        plan->run[rd] = run;
-        if (run) {
-            const uint32_t k = rd ? kPiece : p0;
-            x = (x + k - 1) / k;
-            last = rd + 1;
-        }
-    }
-    plan->last = last;
-    plan->team = tail && x > kTailMin;
+                        << (few ? chunk_log : 0u);
     plan->p0 = p0;
     plan->p0neg = -(int)p0;
-    // Round rd writes buffer rd % 2 (pa, pb).
-    plan->off = last == 0 ? off0 : (((last - 1) & 1) ? offb : offa);
-    plan->parts = (last == 0 || ((last - 1) & 1)) ? pa : pb;
 }
 
-// Round 0.  Thread c adds entries [c p0, (c + 1) p0); bucket b's items are
-// off1[b] .. off1[b + 1] - 1, one per chunk its entries meet, in chunk order.
+// Stores piece j of bucket b (of m pieces): the bucket sum itself when it is
+// the only one.
+__device__ __forceinline__ void piece_out(const Xyzz &acc, uint32_t b, uint32_t j, uint32_t m, Xyzz *pieces,
+                                          Xyzz *buckets) {
+    if (m == 1) buckets[b] = acc;
+    else pieces[j] = acc;
+}
+
+// Round 0.  Thread c adds entries [c p0, (c + 1) p0).
 __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32_t *__restrict__ off0,
                                const uint32_t *__restrict__ off1, uint32_t nb, DevJobs dj,
-                               const RoundPlan *__restrict__ plan, Xyzz *__restrict__ pieces) {
-    if (!plan->run[0]) return;
+                               const RoundPlan *__restrict__ plan, Xyzz *__restrict__ pieces,
+                               Xyzz *__restrict__ buckets) {
     const uint32_t p0 = plan->p0;
     const uint32_t total = off0[nb];  // entries (zero digits have none)
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,7 +520,8 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
     Xyzz acc = xyzz_inf();
     for (uint32_t j = lo; j < hi; j++) {
         if (j >= end) {  // bucket b ends inside the chunk
-            pieces[off1[b] + c - off0[b] / p0] = acc;
+            const uint32_t plo = off1[b];
+            piece_out(acc, b, plo + c - off0[b] / p0, off1[b + 1] - plo, pieces, buckets);
             acc = xyzz_inf();
             do b++; while (off0[b + 1] <= j);  // skip empty buckets
             end = off0[b + 1];
@@ -559,125 +536,82 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
         if (v & 1) a = affine_neg(a);
         acc = xyzz_add_affine(acc, a);
     }
-    pieces[off1[b] + c - off0[b] / p0] = acc;
+    const uint32_t plo = off1[b];
+    piece_out(acc, b, plo + c - off0[b] / p0, off1[b + 1] - plo, pieces, buckets);
 }
 
-// Round rd >= 1 over partial sums.
-__global__ void k_pieces_next(const Xyzz *__restrict__ in, const uint32_t *__restrict__ off_in,
-                              const uint32_t *__restrict__ off_out, uint32_t nb,
-                              const RoundPlan *__restrict__ plan, uint32_t rd, Xyzz *__restrict__ out) {
-    if (!plan->run[rd]) return;
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= off_out[nb]) return;
-    uint32_t b = upper_index(off_out, nb, p);
-    uint32_t k = p - off_out[b];
-    uint32_t lo = off_in[b] + k * kPiece;
-    uint32_t hi = min(lo + kPiece, off_in[b + 1]);
-    Xyzz acc = xyzz_inf();
-    for (uint32_t j = lo; j < hi; j++) acc = xyzz_add(acc, in[j]);
-    out[p] = acc;
-}
-
-// Where the last executed round left its items (round rd writes buffer
-// rd % 2); no round: the sorted entries themselves.
-struct FinalItems {
-    const uint32_t *sorted, *off0;
-    const Xyzz *in0, *in1;
-    const uint32_t *off_a, *off_b;
-};
-
-// Last stage, one thread per bucket.
-__global__ void k_buckets_final(FinalItems fi, DevJobs dj, uint32_t nb,
-                                const RoundPlan *__restrict__ plan, Xyzz *__restrict__ buckets) {
-    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb || plan->team) return;
-    const uint32_t last = plan->last;
-    Xyzz acc = xyzz_inf();
-    if (last == 0) {
-        for (uint32_t j = fi.off0[b]; j < fi.off0[b + 1]; j++)
-            acc = xyzz_add_affine(acc, table_point(dj, b, fi.sorted[j]));
-    } else {
-        const Xyzz *in = ((last - 1) & 1) ? fi.in1 : fi.in0;
-        const uint32_t *off = ((last - 1) & 1) ? fi.off_b : fi.off_a;
-        for (uint32_t j = off[b]; j < off[b + 1]; j++) acc = xyzz_add(acc, in[j]);
+// Empty buckets (infinity) and buckets of 2 <= m <= kThreadMax pieces, one
+// thread per bucket.
+__global__ void k_buckets_final(const Xyzz *__restrict__ pieces, const uint32_t *__restrict__ off1, uint32_t nb,
+                                Xyzz *__restrict__ buckets) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const uint32_t lo = off1[b], m = off1[b + 1] - lo;
+    if (m == 0) {
+        buckets[b] = xyzz_inf();
+        return;
     }
+    if (m == 1 || m > kThreadMax) return;
+    Xyzz acc = pieces[lo];
+    for (uint32_t j = lo + 1; j < lo + m; j++) acc = xyzz_add(acc, pieces[j]);
     buckets[b] = acc;
 }
 
-// Last stage on teams (few buckets in use, each with up to kTailItems
-// items), in two levels.  Level A: team g sums slice g of the items, at most
-// 32 L of them (lane l adds items l, l + 32, ..., then a tree over the
-// lanes; L = 2^tail_log); bucket b's slices are off_s[b] .. off_s[b + 1] - 1
-// (a scan of ceil(items / 32 L)), and slice k covers its items 32 L k ..
-// 32 L (k + 1) - 1.  Level B: a team per bucket adds its partial sums (at
-// most kTailItems / 32) in a tree.  Every team operation spreads one point
-// addition over the block's four warps (team.cuh).
+// Buckets of more than kThreadMax pieces, on teams, in two levels.  Level A:
+// team g sums slice g of a bucket's pieces, at most 32 L of them (lane l adds
+// pieces l, l + 32, ..., then a tree over the lanes; L = 2^tail_log);
+// bucket b's slices are off_s[b] .. off_s[b + 1] - 1 (a scan of
+// ceil(m / 32 L) over those buckets, 0 for the others), and slice k covers
+// its pieces 32 L k .. 32 L (k + 1) - 1.  Level B: a team per bucket adds its
+// slice sums the same way.  Every team operation spreads one point addition
+// over the block's four warps (team.cuh).
 constexpr int kBtAcc = 0, kBtIn = 4, kBtTmp = 8, kBtT = 12;
-static_assert(kTailItems / 32 <= 32, "level B sums one partial per lane");
+
+// Team sum of the points src[0 .. cnt - 1] into slots kBtAcc of lane 0
+// (block-uniform cnt >= 1; the next point is fetched during each addition).
+__device__ __forceinline__ void team_sum(uint32_t *f, const Xyzz *src, uint32_t cnt) {
+    const uint32_t l = team_lane();
+    tf_store(f, kBtAcc + team_warp(), team_fetch(src + l, l < cnt));
+    Fq nx = team_fetch(src + 32 + l, 32 + l < cnt);
+    for (uint32_t j = 32; j < cnt; j += 32) {
+        tf_store(f, kBtIn + team_warp(), nx);
+        nx = team_fetch(src + j + 32 + l, j + 32 + l < cnt);
+        __syncthreads();
+        team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
+    }
+    __syncthreads();
+    for (uint32_t d = 16; d >= 1; d >>= 1) {
+        if (d >= cnt) continue;  // lanes d.. hold infinity
+        team_shift(f, kBtAcc, kBtTmp, (int)d);
+        team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
+    }
+}
 
 __global__ void __launch_bounds__(kTeamThreads)
-    k_tail_slices(FinalItems fi, DevJobs dj, uint32_t nb, uint32_t tail_log, const uint32_t *__restrict__ off_s,
-                  const RoundPlan *__restrict__ plan) {
+    k_tail_slices(const Xyzz *__restrict__ pieces, const uint32_t *__restrict__ off1, uint32_t nb,
+                  uint32_t tail_log, const uint32_t *__restrict__ off_s, Xyzz *__restrict__ parts) {
     __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
-    if (!plan->team) return;
-    const uint32_t l = team_lane(), w = team_warp();
     const uint32_t slice = 32u << tail_log;
-    const bool entries = plan->last == 0;
-    const uint32_t *off = plan->off;
-    const Xyzz *in = entries ? nullptr : (((plan->last - 1) & 1) ? fi.in1 : fi.in0);
-    Xyzz *parts = plan->parts;
     const uint32_t nslices = off_s[nb];
     for (uint32_t g = blockIdx.x; g < nslices; g += gridDim.x) {  // block-uniform
         const uint32_t b = upper_index(off_s, nb, g);
-        const uint32_t lo = off[b] + (g - off_s[b]) * slice;
-        const uint32_t hi = min(lo + slice, off[b + 1]);
-        const Affine *table = entries ? dj.jobs[search(dj.bbase, 0, dj.count, b)].table : nullptr;
-        // Coordinate w of item j (a table point, or a partial sum) and whether
-        // it is negated (a table point's Y with the sign bit) when stored, so
-        // that a prefetch does not wait for its loads.
-        struct Coord {
-            Fq c;
-            bool neg;
-        };
-        auto fetch = [&](uint32_t j) -> Coord {
-            if (j >= hi) return {fe_zero<FqP>(), false};
-            if (!entries) return {team_fetch(in + j, true), false};
-            if (w >= 2) return {fe_mont_one<FqP>(), false};
-            const uint32_t v = fi.sorted[j];
-            return {fe_ldg<FqP>(reinterpret_cast<const char *>(table + (v >> 1)) + 32 * w), w == 1 && (v & 1)};
-        };
-        auto put = [&](int slot, const Coord &x) { tf_store(f, slot + w, x.neg ? fe_neg<FqP>(x.c) : x.c); };
-        put(kBtAcc, fetch(lo + l));
-        // The next item's loads are issued before the current addition.
-        Coord nx = fetch(lo + 32 + l);
-        for (uint32_t j = lo + 32; j < hi; j += 32) {
-            put(kBtIn, nx);
-            nx = fetch(j + 32 + l);
-            __syncthreads();
-            team_add(f, kBtAcc, kBtIn, kBtAcc, kBtT);
-        }
-        __syncthreads();
-        for (uint32_t d = 16; d >= 1; d >>= 1) {
-            if (d >= hi - lo) continue;  // lanes d.. hold infinity
-            team_shift(f, kBtAcc, kBtTmp, (int)d);
-            team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
-        }
-        if (l == 0) team_put(f, kBtAcc, parts + g);
+        const uint32_t lo = off1[b] + (g - off_s[b]) * slice;
+        const uint32_t hi = min(lo + slice, off1[b + 1]);
+        team_sum(f, pieces + lo, hi - lo);
+        if (team_lane() == 0) team_put(f, kBtAcc, parts + g);
         __syncthreads();  // the slots are reused by the next slice
     }
 }
 
 __global__ void __launch_bounds__(kTeamThreads)
-    k_tail_buckets(uint32_t nb, const uint32_t *__restrict__ off_s, const RoundPlan *__restrict__ plan,
+    k_tail_buckets(uint32_t nb, const uint32_t *__restrict__ off_s, const Xyzz *__restrict__ parts,
                    Xyzz *__restrict__ buckets) {
     __shared__ uint32_t f[(kBtT + kTeamTemps) * 8 * 32];
-    if (!plan->team) return;
-    const uint32_t l = team_lane(), w = team_warp();
     __shared__ uint32_t multi[kTeamThreads], nmulti;
-    const Xyzz *parts = plan->parts;
     // Block k takes buckets k, k + G, k + 2G, ... (G blocks), 128 at a time:
-    // one thread per bucket writes those with at most one partial sum, and
-    // the others (a few per block) are summed by the team one by one.
+    // one thread per bucket copies a single slice sum, and the buckets with
+    // several (a few per block) are summed by the team one by one.  Buckets
+    // without slices are complete already.
     const uint32_t mine = blockIdx.x < nb ? (nb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     for (uint32_t j0 = 0; j0 < mine; j0 += kTeamThreads) {  // block-uniform
         if (threadIdx.x == 0) nmulti = 0;
@@ -686,39 +620,31 @@ __global__ void __launch_bounds__(kTeamThreads)
         if (j < mine) {
             const uint32_t b = blockIdx.x + j * gridDim.x;
             const uint32_t lo = off_s[b], cnt = off_s[b + 1] - lo;
-            if (cnt <= 1) buckets[b] = cnt ? parts[lo] : xyzz_inf();
-            else multi[atomicAdd(&nmulti, 1u)] = b;
+            if (cnt == 1) buckets[b] = parts[lo];
+            else if (cnt > 1) multi[atomicAdd(&nmulti, 1u)] = b;
         }
         __syncthreads();
         const uint32_t nm = nmulti;
         for (uint32_t i = 0; i < nm; i++) {  // block-uniform
             const uint32_t b = multi[i];
-            const uint32_t lo = off_s[b], cnt = off_s[b + 1] - lo;
-            tf_store(f, kBtAcc + w, team_fetch(parts + lo + l, l < cnt));
-            __syncthreads();
-            for (uint32_t d = 16; d >= 1; d >>= 1) {
-                if (d >= cnt) continue;
-                team_shift(f, kBtAcc, kBtTmp, (int)d);
-                team_add(f, kBtAcc, kBtTmp, kBtAcc, kBtT);
-            }
-            if (l == 0) team_put(f, kBtAcc, buckets + b);
+            const uint32_t lo = off_s[b];
+            team_sum(f, parts + lo, off_s[b + 1] - lo);
+            if (team_lane() == 0) team_put(f, kBtAcc, buckets + b);
             __syncthreads();
         }
     }
 }
 
-// Host bounds of phase 3 for at most `total` entries in `nb` buckets with
-// at most `worst` entries in one bucket; the actual chunk size and the
-// rounds that run are decided on the device (k_round_plan).
+// Host bounds of phase 3 for at most `total` entries in `nb` buckets; the
+// actual chunk is decided on the device (k_round_plan).
 struct AccumShape {
-    int rounds;        // rounds launched (the worst case; gated on the device)
-    size_t cap0;       // items after round 0 (bound)
+    size_t cap0;       // pieces of round 0 (bound); also the team tail's slice sums
     uint32_t resident; // threads of one wave of k_pieces_first
     uint32_t blocks;   // its grid
     MsmLayout layout;  // bucket layout (chunk multiplier, tail slices)
 };
 
-AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms, const MsmLayout &layout) {
+AccumShape accum_shape(size_t total, uint32_t nb, int sms, const MsmLayout &layout) {
     static const int per_sm = [] {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pieces_first, 128, 0) != cudaSuccess || b < 1) {
@@ -731,29 +657,26 @@ AccumShape accum_shape(size_t total, size_t worst, uint32_t nb, int sms, const M
     a.layout = layout;
     a.blocks = (uint32_t)std::max(sms, 1) * (uint32_t)per_sm;
     a.resident = a.blocks * 128;
-    // p0 >= kP0Min bounds the rounds; p0 >= entries / resident bounds the
-    // chunks, and every chunk emits one item per bucket it meets.
-    a.rounds = 0;
-    for (size_t x = worst; x > kPiece && a.rounds < kMaxRounds; a.rounds++)
-        x = (x + (a.rounds ? kPiece : kP0Min) - 1) / (a.rounds ? kPiece : kP0Min);
+    // p0 >= entries / resident and p0 >= kP0Min bound the chunks, and every
+    // chunk emits one piece per bucket it meets.
     const size_t chunks = std::min<size_t>(a.resident, (total + kP0Min - 1) / kP0Min);
-    // The team tail's partial sums (at most entries / 32 + nb) reuse a
-    // piece buffer.
-    a.cap0 = std::max<size_t>(chunks, (total + 31) / 32) + nb + 1;
+    // The team tail's slice sums (at most pieces / 32 + nb) go to a second
+    // buffer of the same size.
+    a.cap0 = chunks + nb + 1;
     return a;
 }
 
 struct AccumBufs {
-    uint32_t *offa, *offb;
-    Xyzz *pa, *pb;
-    uint32_t *stat;  // two words
+    uint32_t *off1;   // nb + 1 words: piece offsets
+    Xyzz *pieces, *parts;
+    uint32_t *stat;   // two words
     RoundPlan *plan;
     void *scan_tmp;
-    uint32_t *offs;  // nb + 1 words: slice offsets of the team tail
+    uint32_t *offs;   // nb + 1 words: slice offsets of the team tail
 };
 
-// Phase 3 launches: sorted entries (offsets off0, histogram counts; at most
-// `total` entries) -> one point per bucket.
+// Phase 3 launches: sorted entries (offsets off0, histogram counts) -> one
+// point per bucket.
 int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint32_t *off0, uint32_t nb,
                       const AccumShape &a, const DevJobs &dj, const AccumBufs &w, Xyzz *buckets, int sms,
                       cudaStream_t s) {
@@ -761,39 +684,20 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
     const unsigned mb = (unsigned)std::min<size_t>((nb + 255) / 256, (size_t)sms * 4);
     k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, w.stat);
     ZK_LAUNCHED();
-    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, a.layout.chunk_log, (uint32_t)a.rounds, off0,
-                                  w.offa, w.offb, w.pa, w.pb, w.plan);
+    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, a.layout.chunk_log, w.plan);
     ZK_LAUNCHED();
-    const uint32_t *off_prev = off0;
-    size_t cap = a.cap0;
-    for (int rd = 0; rd < a.rounds; rd++) {
-        uint32_t *off_new = (rd % 2 == 0) ? w.offa : w.offb;
-        Xyzz *out = (rd % 2 == 0) ? w.pa : w.pb;
-        const uint32_t *gate = &w.plan->run[rd];
-        if (rd == 0) {
-            ZK_TRY(scan_exclusive(off_prev, off_new, nb, -(int)kP0Min, w.scan_tmp, s, gate, &w.plan->p0neg));
-            k_pieces_first<<<a.blocks, 128, 0, s>>>(sorted, off_prev, off_new, nb, dj, w.plan, out);
-        } else {
-            ZK_TRY(scan_exclusive(off_prev, off_new, nb, (int)kPiece, w.scan_tmp, s, gate));
-            const Xyzz *in = (rd % 2 == 1) ? w.pa : w.pb;
-            cap = cap / kPiece + nb + 1;  // bound on this round's items
-            k_pieces_next<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(in, off_prev, off_new, nb, w.plan,
-                                                                       (uint32_t)rd, out);
-        }
-        ZK_LAUNCHED();
-        off_prev = off_new;
-    }
-    const FinalItems fi{sorted, off0, w.pa, w.pb, w.offa, w.offb};
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(fi, dj, nb, w.plan, buckets);
+    ZK_TRY(scan_exclusive(off0, w.off1, nb, -(int)kP0Min, w.scan_tmp, s, nullptr, &w.plan->p0neg));
+    k_pieces_first<<<a.blocks, 128, 0, s>>>(sorted, off0, w.off1, nb, dj, w.plan, w.pieces, buckets);
     ZK_LAUNCHED();
-    // Gated on the device: runs when few buckets are in use and they still
-    // hold many items (the round plan's `team`).
-    ZK_TRY(scan_exclusive(nullptr, w.offs, nb, (int)(32u << a.layout.tail_log), w.scan_tmp, s, &w.plan->team,
-                          nullptr, &w.plan->off));
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(w.pieces, w.off1, nb, buckets);
+    ZK_LAUNCHED();
+    // Buckets of more than kThreadMax pieces: slices of 32 L pieces.
+    ZK_TRY(scan_exclusive(w.off1, w.offs, nb, (int)(32u << a.layout.tail_log), w.scan_tmp, s, nullptr, nullptr,
+                          nullptr, kThreadMax));
     const unsigned tb = (unsigned)std::min<size_t>(std::max<uint32_t>(nb, 1), (size_t)sms * 8);
-    k_tail_slices<<<tb, kTeamThreads, 0, s>>>(fi, dj, nb, a.layout.tail_log, w.offs, w.plan);
+    k_tail_slices<<<tb, kTeamThreads, 0, s>>>(w.pieces, w.off1, nb, a.layout.tail_log, w.offs, w.parts);
     ZK_LAUNCHED();
-    k_tail_buckets<<<tb, kTeamThreads, 0, s>>>(nb, w.offs, w.plan, buckets);
+    k_tail_buckets<<<tb, kTeamThreads, 0, s>>>(nb, w.offs, w.parts, buckets);
     ZK_LAUNCHED();
     return ZK_OK;
 }
@@ -1241,11 +1145,6 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     const uint32_t nb = (uint32_t)nb64;
     const size_t entries_max = entries64;
 
-    // Phase 3 bounds: a bucket holds at most max_n W entries (all of a job's
-    // digits in one bucket).
-    size_t worst = 1;
-    for (size_t k = 0; k < count; k++)
-        worst = std::max(worst, (size_t)jv[k].job.n * windows_for(jv[k].c));
     // Bucket layout of the call: tuned for the longest job.
     uint32_t maxn = 1;
     for (size_t k = 0; k < count; k++) maxn = std::max(maxn, jv[k].job.n);
@@ -1290,7 +1189,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
             else break;
         }
     }
-    const AccumShape shape = accum_shape(entries_max, worst, nb, sh.sms, ly);
+    const AccumShape shape = accum_shape(entries_max, nb, sh.sms, ly);
     const size_t piece_cap = shape.cap0;
     // Reduction levels: a job's bucket count is 2^logB with logB between
     // kMinWindow - 1 (short scalars, decided on the device) and c - 1.
@@ -1310,8 +1209,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     char *jt = (char *)scratch(ctx, "msm.jobs", jd_bytes + 3 * pre_bytes, &err);
     uint32_t *counts = (uint32_t *)scratch(ctx, "msm.counts", (nb + 1) * 4, &err);
     uint32_t *off0 = (uint32_t *)scratch(ctx, "msm.off0", (nb + 1) * 4, &err);
-    uint32_t *offa = (uint32_t *)scratch(ctx, "msm.offa", (nb + 1) * 4, &err);
-    uint32_t *offb = (uint32_t *)scratch(ctx, "msm.offb", (nb + 1) * 4, &err);
+    uint32_t *off1 = (uint32_t *)scratch(ctx, "msm.off1", (nb + 1) * 4, &err);
     uint32_t *cursor = (uint32_t *)scratch(ctx, "msm.cursor", (nb + 1) * 4, &err);
     uint32_t *offs = (uint32_t *)scratch(ctx, "msm.offs", (nb + 1) * 4, &err);
     uint32_t *sorted = (uint32_t *)scratch(ctx, "msm.sorted", std::max<size_t>(entries_max, 1) * 4, &err);
@@ -1331,7 +1229,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     void *scan_tmp = scratch(ctx, "msm.scantmp", scan_temp_bytes(nb), &err);
     char *plan = (char *)scratch(ctx, "msm.plan", 256 + sizeof(RoundPlan), &err);
     uint32_t *st = (uint32_t *)scratch(ctx, "msm.stats", 2 * align_up(count * 4, 256), &err);
-    if (!jt || !counts || !off0 || !offa || !offb || !cursor || !offs || !sorted || !pa || !pb || !buckets ||
+    if (!jt || !counts || !off0 || !off1 || !cursor || !offs || !sorted || !pa || !pb || !buckets ||
         !red_ok || !scan_tmp || !plan || !st)
         return err;
 
@@ -1426,7 +1324,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
 
     // 3: bucket sums.
     PhaseScope ph_accum(ctx, ZK_PHASE_MSM_ACCUM, s);
-    const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)plan, (RoundPlan *)(plan + 256), scan_tmp, offs};
+    const AccumBufs ab{off1, pa, pb, (uint32_t *)plan, (RoundPlan *)(plan + 256), scan_tmp, offs};
     ZK_TRY(launch_accumulate(sorted, counts, off0, nb, shape, dj, ab, buckets, sh.sms, s));
     ph_accum.end();
 
@@ -1471,9 +1369,8 @@ constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kNaJobs = 0;                                          // JobDesc + 2 prefixes
 constexpr size_t kNaCounts = kNaJobs + 256 + 2 * kNoAllocPre;
 constexpr size_t kNaOff0 = kNaCounts + na_align((kNoAllocB + 1) * 4);
-constexpr size_t kNaOffA = kNaOff0 + na_align((kNoAllocB + 1) * 4);
-constexpr size_t kNaOffB = kNaOffA + na_align((kNoAllocB + 1) * 4);
-constexpr size_t kNaCursor = kNaOffB + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaOff1 = kNaOff0 + na_align((kNoAllocB + 1) * 4);
+constexpr size_t kNaCursor = kNaOff1 + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaOffS = kNaCursor + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaSorted = kNaOffS + na_align((kNoAllocB + 1) * 4);
 constexpr size_t kNaPieceA = kNaSorted + na_align(kNoAllocEntries * 4);
@@ -1579,8 +1476,7 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     const uint32_t nb = kNoAllocB;
     uint32_t *counts = (uint32_t *)(ws + kNaCounts);
     uint32_t *off0 = (uint32_t *)(ws + kNaOff0);
-    uint32_t *offa = (uint32_t *)(ws + kNaOffA);
-    uint32_t *offb = (uint32_t *)(ws + kNaOffB);
+    uint32_t *off1 = (uint32_t *)(ws + kNaOff1);
     uint32_t *cursor = (uint32_t *)(ws + kNaCursor);
     uint32_t *sorted = (uint32_t *)(ws + kNaSorted);
     Xyzz *pa = (Xyzz *)(ws + kNaPieceA);
@@ -1614,9 +1510,9 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
                                               sorted, off0, s)));
     // The built-in layout (the workspace is sized for it).
     const MsmLayout ly{0, 1, 5, 8};
-    const AccumShape shape = accum_shape((size_t)n * kNoAllocW, (size_t)n * kNoAllocW, nb, sh.sms, ly);
+    const AccumShape shape = accum_shape((size_t)n * kNoAllocW, nb, sh.sms, ly);
     if (shape.cap0 > kNoAllocPieces) return ZK_EINVAL;  // cannot happen: p0 >= kP0Min
-    const AccumBufs ab{offa, offb, pa, pb, (uint32_t *)(ws + kNaPlan), (RoundPlan *)(ws + kNaPlan + 256),
+    const AccumBufs ab{off1, pa, pb, (uint32_t *)(ws + kNaPlan), (RoundPlan *)(ws + kNaPlan + 256),
                        scan_tmp, (uint32_t *)(ws + kNaOffS)};
     ZK_TRY(launch_accumulate(sorted, counts, off0, nb, shape, dj, ab, buckets, sh.sms, s));
     const uint32_t logB = kNoAllocC - 1;

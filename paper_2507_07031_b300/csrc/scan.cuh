@@ -17,14 +17,14 @@ constexpr int kPer = 8;
 constexpr int kTile = kThreads * kPer;
 
 // Element b of the scanned sequence: in[b] when K = 0; for bucket offsets
-// `in`, the item count of bucket b after one round of K-way pieces,
-// ceil((in[b+1] - in[b]) / K), when K > 0; and the number of fixed chunks of
-// -K consecutive entries that bucket b's entries meet, when K < 0.
-__device__ __forceinline__ uint32_t elem(const uint32_t *in, uint32_t b, uint32_t n, int K) {
+// `in`, the number of K-item slices of bucket b, ceil((in[b+1] - in[b]) / K),
+// when K > 0 (0 for buckets of at most `thr` items); and the number of fixed
+// chunks of -K consecutive entries that bucket b's entries meet, when K < 0.
+__device__ __forceinline__ uint32_t elem(const uint32_t *in, uint32_t b, uint32_t n, int K, uint32_t thr) {
     if (b >= n) return 0;
     if (K == 0) return in[b];
     const uint32_t lo = in[b], hi = in[b + 1];
-    if (K > 0) return (hi - lo + (uint32_t)K - 1) / (uint32_t)K;
+    if (K > 0) return hi - lo > thr ? (hi - lo + (uint32_t)K - 1) / (uint32_t)K : 0u;
     const uint32_t c = (uint32_t)(-K);
     return hi > lo ? (hi - 1) / c - lo / c + 1 : 0u;
 }
@@ -58,14 +58,14 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 
 __global__ void k_tile_sums(const uint32_t *__restrict__ in, uint32_t n, int K,
                             uint32_t *__restrict__ sums, const uint32_t *gate, const int *Kp,
-                            const uint32_t *const *in_p) {
+                            const uint32_t *const *in_p, uint32_t thr) {
     if (gate && !*gate) return;
     if (Kp) K = *Kp;
     if (in_p) in = *in_p;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t s = 0;
 #pragma unroll
-    for (int i = 0; i < kPer; i++) s += elem(in, base + i, n, K);
+    for (int i = 0; i < kPer; i++) s += elem(in, base + i, n, K, thr);
     uint32_t tot;
     block_excl_scan(s, &tot);
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -90,7 +90,7 @@ __global__ void k_scan_sums(uint32_t *__restrict__ sums, uint32_t tiles, const u
 __global__ void k_tile_scan(const uint32_t *__restrict__ in, uint32_t n, int K,
                             const uint32_t *__restrict__ sums, uint32_t tiles,
                             uint32_t *__restrict__ out, const uint32_t *gate, const int *Kp,
-                            const uint32_t *const *in_p) {
+                            const uint32_t *const *in_p, uint32_t thr) {
     if (gate && !*gate) return;
     if (Kp) K = *Kp;
     if (in_p) in = *in_p;
@@ -99,7 +99,7 @@ __global__ void k_tile_scan(const uint32_t *__restrict__ in, uint32_t n, int K,
     uint32_t s = 0;
 #pragma unroll
     for (int i = 0; i < kPer; i++) {
-        v[i] = elem(in, base + i, n, K);
+        v[i] = elem(in, base + i, n, K, thr);
         s += v[i];
     }
     uint32_t tot;
@@ -122,17 +122,17 @@ inline size_t scan_temp_bytes(uint32_t n) {
 // `out` nor `tmp`.  With a `gate` (device word), the scan does nothing when
 // the word is zero at execution time.  With `Kp` (device word), K is read
 // from it at execution time instead, and with `in_p` (a device word holding
-// a pointer), the input array.
+// a pointer), the input array.  `thr`: see elem().
 inline int scan_exclusive(const uint32_t *in, uint32_t *out, uint32_t n, int K, void *tmp,
                           cudaStream_t s, const uint32_t *gate = nullptr, const int *Kp = nullptr,
-                          const uint32_t *const *in_p = nullptr) {
+                          const uint32_t *const *in_p = nullptr, uint32_t thr = 0) {
     using namespace scan_detail;
     uint32_t tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) tiles = 1;
     uint32_t *sums = (uint32_t *)tmp;
-    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate, Kp, in_p);
+    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate, Kp, in_p, thr);
     k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, gate);
-    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate, Kp, in_p);
+    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate, Kp, in_p, thr);
     count_launches(3);
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
