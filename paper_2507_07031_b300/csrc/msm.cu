@@ -144,6 +144,7 @@ constexpr uint32_t kRecPer = 2048;
 constexpr uint32_t kRecEach = kRecPer / kRecThreads;
 constexpr uint32_t kSmemBucketsLog = 12;
 constexpr uint32_t kSmemBuckets = 1u << kSmemBucketsLog;
+constexpr uint32_t kAggLogB = 11;  // bucket sets up to 2^11: warp-aggregated atomics in k_recode
 
 struct Chunk {
     uint32_t first, last, job;
@@ -233,6 +234,10 @@ __global__ void __launch_bounds__(kRecThreads)
     // Windows past every lane's last one hold no digits: stop before them.
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, wins);
     const uint32_t lt_mask = (1u << lane_id()) - 1u;
+    // Lanes with equal keys share one atomic only where keys do collide:
+    // when the warp holds a job of at most 2^kAggLogB buckets (32 lanes among
+    // 2^16 buckets almost never meet, and the match costs every window).
+    const bool agg = __any_sync(0xffffffffu, live && dj.jobs[job].logB <= kAggLogB);
     uint32_t carry = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) {
@@ -242,6 +247,18 @@ __global__ void __launch_bounds__(kRecThreads)
         int sd = carry ? (int)d - (1 << C) : (int)d;
         uint32_t key = (live && sd != 0) ? bb + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
         if (key != kInvalid && ZK_FAILED(key < dj.bbase[job + 1], kCheckBucket)) key = kInvalid;
+        if (!agg) {  // warp-uniform
+            if (key == kInvalid) continue;
+            if (!SCATTER) {
+                atomicAdd(&counts[key], 1u);
+            } else {
+                const uint32_t pos = atomicAdd(&cursor[key], 1u);
+                const uint32_t sign = ((sd < 0) ? 1u : 0u) ^ (neg ? 1u : 0u);
+                if (!ZK_FAILED(!off0 || pos < off0[key + 1], kCheckEntry))
+                    sorted[pos] = (((uint32_t)w * table_n + i) << 1) | sign;
+            }
+            continue;
+        }
         uint32_t group = __match_any_sync(0xffffffffu, key);
         uint32_t leader = (uint32_t)(__ffs(group) - 1);
         if (!SCATTER) {
