@@ -570,6 +570,43 @@ template <class P> ZK_DEV Wide wide_sub_lift(const Wide &x, const Wide &y) {
     return t;
 }
 
+// x + y over 512 bits (the caller keeps the sum below 2^512: a few products
+// of values below p < 2^254).
+template <class P> ZK_DEV Wide wide_add(const Wide &x, const Wide &y) {
+    Wide t;
+    uint32_t c;
+    asm("add.cc.u32  %0, %9, %17;\n\t"
+        "addc.cc.u32 %1, %10, %18;\n\t"
+        "addc.cc.u32 %2, %11, %19;\n\t"
+        "addc.cc.u32 %3, %12, %20;\n\t"
+        "addc.cc.u32 %4, %13, %21;\n\t"
+        "addc.cc.u32 %5, %14, %22;\n\t"
+        "addc.cc.u32 %6, %15, %23;\n\t"
+        "addc.cc.u32 %7, %16, %24;\n\t"
+        "addc.u32    %8, 0, 0;"
+        : "=r"(t.w[0]), "=r"(t.w[1]), "=r"(t.w[2]), "=r"(t.w[3]), "=r"(t.w[4]), "=r"(t.w[5]), "=r"(t.w[6]),
+          "=r"(t.w[7]), "=r"(c)
+        : "r"(x.w[0]), "r"(x.w[1]), "r"(x.w[2]), "r"(x.w[3]), "r"(x.w[4]), "r"(x.w[5]), "r"(x.w[6]), "r"(x.w[7]),
+          "r"(y.w[0]), "r"(y.w[1]), "r"(y.w[2]), "r"(y.w[3]), "r"(y.w[4]), "r"(y.w[5]), "r"(y.w[6]), "r"(y.w[7]));
+#pragma unroll
+    for (int i = 8; i < 16; i++) t.w[i] = x.w[i];
+    asm("{\n\t.reg .u32 z;\n\t"
+        "add.cc.u32  z, %16, 0xffffffff;\n\t"  // carry flag <- (c != 0)
+        "addc.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32    %7, %7, %15;\n\t}"
+        : "+r"(t.w[8]), "+r"(t.w[9]), "+r"(t.w[10]), "+r"(t.w[11]), "+r"(t.w[12]), "+r"(t.w[13]),
+          "+r"(t.w[14]), "+r"(t.w[15])
+        : "r"(y.w[8]), "r"(y.w[9]), "r"(y.w[10]), "r"(y.w[11]), "r"(y.w[12]), "r"(y.w[13]), "r"(y.w[14]),
+          "r"(y.w[15]), "r"(c));
+    return t;
+}
+
 // Montgomery reduction of x < p 2^256: the 8 rows t += m p 2^(32 i), then
 // (x + M p) / 2^256 < 2p (p < 2^254, so no carry leaves word 15) and one
 // conditional subtraction.

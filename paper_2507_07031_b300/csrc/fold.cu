@@ -62,48 +62,72 @@ __global__ void __launch_bounds__(256, 2)
     const Fr muL = fe_to_mont<FrP>(fe_load<FrP>(d.Lx + kInstMu));
     const Fr muR = fe_to_mont<FrP>(fe_load<FrP>(d.Rx + kInstMu));
     if constexpr (DEG == 3) {
-        // mu_L^2 R, 2 mu_L mu_R R, mu_R^2 R, gamma^3 R
-        const Fr mLL = fe_mul<FrP>(muL, muL), mRR = fe_mul<FrP>(muR, muR);
-        const Fr mLR = fe_dbl<FrP>(fe_mul<FrP>(muL, muR));
+        // Sums of products share one Montgomery reduction (see the degree-2
+        // branch).  The pair products enter as x R^-1 (a Montgomery product
+        // of canonical values), so each cross term is a sum of four products
+        // of values below r whose reduction is e R^-2; a product with R^3
+        // gives the canonical e.  The mu coefficients are prepared the same
+        // way: -mu_L^2 R^-1, -2 mu_L mu_R R^-1, -mu_R^2 R^-1 (canonical).
+        using namespace detail;
+        (void)muL;
+        (void)muR;
+        const Fr uL = fe_load<FrP>(d.Lx + kInstMu), uR = fe_load<FrP>(d.Rx + kInstMu);
+        const Fr cLL = fe_neg<FrP>(fe_mul<FrP>(uL, uL)), cRR = fe_neg<FrP>(fe_mul<FrP>(uR, uR));
+        const Fr cLR = fe_neg<FrP>(fe_dbl<FrP>(fe_mul<FrP>(uL, uR)));
         const Fr g3 = fe_mul<FrP>(g2, g);
+        Fr r3;
+#pragma unroll
+        for (int i = 0; i < 8; i++) r3.v[i] = FrP::r3(i);
         for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
             const size_t o = 8 * (size_t)k;
             // Consumed in three groups, each finished (its RLC outputs
             // stored) before the next is loaded, to keep the live set small.
-            Fr sx, paa, pbb;  // a1 b2 + b1 a2, a1 a2, b1 b2
+            Fr sx, paa, pbb;  // (a1 b2 + b1 a2, a1 a2, b1 b2) R^-1
             {
                 const Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
                 const Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
-                const Fr A1 = fe_to_mont<FrP>(a1), B1 = fe_to_mont<FrP>(b1);
-                paa = fe_mul<FrP>(A1, a2);
-                pbb = fe_mul<FrP>(B1, b2);
-                sx = fe_add<FrP>(fe_mul<FrP>(A1, b2), fe_mul<FrP>(B1, a2));
+                paa = fe_mul<FrP>(a1, a2);
+                pbb = fe_mul<FrP>(b1, b2);
+                sx = redc_wide<FrP>(wide_add<FrP>(wide_mul<FrP>(a1, b2), wide_mul<FrP>(b1, a2)));
                 fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
                 fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
             }
-            Fr e1, e2;
+            Wide w2, w1;
             {
                 const Fr a3 = fe_load<FrP>(d.Lm[2] + o), b3 = fe_load<FrP>(d.Rm[2] + o);
-                const Fr A3 = fe_to_mont<FrP>(a3), B3 = fe_to_mont<FrP>(b3);
                 // gamma^2: a1 a2 b3 + (a1 b2 + b1 a2) a3;  gamma^1: (a1 b2 + b1 a2) b3 + b1 b2 a3
-                e2 = fe_add<FrP>(fe_mul<FrP>(paa, B3), fe_mul<FrP>(sx, A3));
-                e1 = fe_add<FrP>(fe_mul<FrP>(sx, B3), fe_mul<FrP>(pbb, A3));
+                w2 = wide_add<FrP>(wide_mul<FrP>(paa, b3), wide_mul<FrP>(sx, a3));
+                w1 = wide_add<FrP>(wide_mul<FrP>(sx, b3), wide_mul<FrP>(pbb, a3));
                 fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
             }
+            Fr e1, e2;
             {
                 const Fr a4 = fe_load<FrP>(d.Lm[3] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
                 // - mu_L^2 b4 - 2 mu_L mu_R a4 (gamma^2), - 2 mu_L mu_R b4 - mu_R^2 a4 (gamma^1)
-                e2 = fe_sub<FrP>(e2, fe_add<FrP>(fe_mul<FrP>(b4, mLL), fe_mul<FrP>(a4, mLR)));
-                e1 = fe_sub<FrP>(e1, fe_add<FrP>(fe_mul<FrP>(b4, mLR), fe_mul<FrP>(a4, mRR)));
+                w2 = wide_add<FrP>(w2, wide_add<FrP>(wide_mul<FrP>(b4, cLL), wide_mul<FrP>(a4, cLR)));
+                w1 = wide_add<FrP>(w1, wide_add<FrP>(wide_mul<FrP>(b4, cLR), wide_mul<FrP>(a4, cRR)));
+                e2 = fe_mul<FrP>(redc_wide<FrP>(w2), r3);
+                e1 = fe_mul<FrP>(redc_wide<FrP>(w1), r3);
                 fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
             }
             fe_store<FrP>(d.e1 + o, e1);
             fe_store<FrP>(d.e2 + o, e2);
             const Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
-            Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(e2, g2)));
-            fe_store<FrP>(d.Oe + o, fe_add<FrP>(eo, fe_mul<FrP>(eL, g3)));
+            // e'' = e' + gamma e1 + gamma^2 e2 + gamma^3 e (three products, one reduction)
+            const Fr t = redc_wide<FrP>(wide_add<FrP>(wide_add<FrP>(wide_mul<FrP>(e1, g), wide_mul<FrP>(e2, g2)),
+                                                      wide_mul<FrP>(eL, g3)));
+            fe_store<FrP>(d.Oe + o, fe_add<FrP>(eR, t));
         }
     } else {
+        // Sums of products share one Montgomery reduction (lazy reduction):
+        // a sum of at most four products of values below r is below
+        // 4 r^2 < r 2^256, the reduction's bound.  The mu terms enter with
+        // the canonical negations r - mu, so every term is a plain product.
+        using namespace detail;
+        (void)muL;
+        (void)muR;
+        const Fr nmuL = fe_neg<FrP>(fe_load<FrP>(d.Lx + kInstMu));
+        const Fr nmuR = fe_neg<FrP>(fe_load<FrP>(d.Rx + kInstMu));
         for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
             const size_t o = 8 * (size_t)k;
             Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
@@ -111,18 +135,19 @@ __global__ void __launch_bounds__(256, 2)
             Fr b1 = fe_load<FrP>(d.Rm[0] + o), b2 = fe_load<FrP>(d.Rm[1] + o);
             Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
             Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
-            // (m1 m2' + m1' m2) R^-1, then * R^2 R^-1 -> canonical
-            Fr x = fe_add<FrP>(fe_mul<FrP>(a1, b2), fe_mul<FrP>(b1, a2));
-            x = fe_mul<FrP>(x, r2);
-            Fr y = fe_add<FrP>(fe_mul<FrP>(b3, muL), fe_mul<FrP>(a3, muR));
-            Fr e1 = fe_sub<FrP>(x, y);
+            // e1 = m1 m2' + m1' m2 - mu m3' - mu' m3: one reduction gives
+            // e1 R^-1, a product with R^2 the canonical value.
+            const Wide w = wide_add<FrP>(wide_add<FrP>(wide_mul<FrP>(a1, b2), wide_mul<FrP>(b1, a2)),
+                                         wide_add<FrP>(wide_mul<FrP>(b3, nmuL), wide_mul<FrP>(a3, nmuR)));
+            const Fr e1 = fe_mul<FrP>(redc_wide<FrP>(w), r2);
             fe_store<FrP>(d.e1 + o, e1);
             fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
             fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
             fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
             fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
-            Fr eo = fe_add<FrP>(eR, fe_add<FrP>(fe_mul<FrP>(e1, g), fe_mul<FrP>(eL, g2)));
-            fe_store<FrP>(d.Oe + o, eo);
+            // e'' = e' + gamma e1 + gamma^2 e (g, g2 in Montgomery form)
+            const Fr t = redc_wide<FrP>(wide_add<FrP>(wide_mul<FrP>(e1, g), wide_mul<FrP>(eL, g2)));
+            fe_store<FrP>(d.Oe + o, fe_add<FrP>(eR, t));
         }
     }
 }
