@@ -267,6 +267,22 @@ def test_batch_wide_recode(zk, orc, ctx_big, tau):
         assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (k, lens[k])
 
 
+def test_batch_window_rule(zk, orc, ctx_big, tau):
+    """Calls of 64 jobs or more give 2^17- and 2^18-point jobs window width
+    16 (single MSMs take 15): three such jobs, one ragged, among 67 short
+    ones, against the closed form."""
+    import torch
+    lens = [1 << 17, 1 << 18, (1 << 17) + 5] + [1 << 10] * 67
+    vecs = [Z.fr_uniform(70_000 + i, n) if i % 2 == 0 else Z.zkml_scalars(70_000 + i, n)
+            for i, n in enumerate(lens)]
+    out = torch.zeros((len(lens), 8), dtype=torch.int64, device="cuda")
+    zk.zk_commit_batch(ctx_big, [to_dev(v) for v in vecs], out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    for k, v in enumerate(vecs):
+        assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), (k, lens[k])
+
+
 @pytest.fixture(scope="module")
 def layout_case():
     n = 1 << 18
