@@ -540,7 +540,11 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
             const uint32_t plo = off1[b];
             piece_out(acc, b, plo + c - off0[b] / p0, off1[b + 1] - plo, pieces, buckets);
             acc = xyzz_inf();
-            do b++; while (off0[b + 1] <= j);  // skip empty buckets
+            // The next nonempty bucket: usually b + 1; past a run of empty
+            // ones (a short-scalar job uses 2^8 of its 2^(c-1) buckets, so a
+            // chunk entering the next job would walk the rest), a search.
+            b++;
+            if (off0[b + 1] <= j) b = search(off0, b, nb, j);
             end = off0[b + 1];
             if (b >= jend) {
                 job = search(dj.bbase, 0, dj.count, b);
@@ -558,11 +562,14 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
 }
 
 // Empty buckets (infinity) and buckets of 2 <= m <= kThreadMax pieces, one
-// thread per bucket.
+// thread per bucket.  Buckets past a job's 2^logB (short scalars) are never
+// read and are left alone.
 __global__ void k_buckets_final(const Xyzz *__restrict__ pieces, const uint32_t *__restrict__ off1, uint32_t nb,
-                                Xyzz *__restrict__ buckets) {
+                                DevJobs dj, Xyzz *__restrict__ buckets) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
+    const uint32_t job = search(dj.bbase, 0, dj.count, b);
+    if (b - dj.bbase[job] >= (1u << dj.jobs[job].logB)) return;
     const uint32_t lo = off1[b], m = off1[b + 1] - lo;
     if (m == 0) {
         buckets[b] = xyzz_inf();
@@ -706,7 +713,7 @@ int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint
     ZK_TRY(scan_exclusive(off0, w.off1, nb, -(int)kP0Min, w.scan_tmp, s, nullptr, &w.plan->p0neg));
     k_pieces_first<<<a.blocks, 128, 0, s>>>(sorted, off0, w.off1, nb, dj, w.plan, w.pieces, buckets);
     ZK_LAUNCHED();
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(w.pieces, w.off1, nb, buckets);
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(w.pieces, w.off1, nb, dj, buckets);
     ZK_LAUNCHED();
     // Buckets of more than kThreadMax pieces: slices of 32 L pieces.
     ZK_TRY(scan_exclusive(w.off1, w.offs, nb, (int)(32u << a.layout.tail_log), w.scan_tmp, s, nullptr, nullptr,
