@@ -62,6 +62,31 @@ def test_hot_path_passes_every_check(zk, orc, checked, tau):
     assert _status(L, ctx) == (0, 1)
 
 
+def test_batch_paths_pass_every_check(zk, orc, checked, tau):
+    """A batch on the batch-only paths (shared-memory histogram sort, the
+    thread-level first reduction level, the team tail of quantised jobs)
+    through the checked build: every check passes, results equal the
+    oracle's."""
+    import torch
+    L, ctx = checked
+    stream = torch.cuda.current_stream().cuda_stream
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 1 << 16
+    count = (2 * sms + 7) // 8 + 2  # chunks of 8192 scalars: two per SM
+    vecs = [Z.zkml_scalars(80 + i, n) if i % 4 == 3 else Z.fr_uniform(80 + i, n) for i in range(count)]
+    devs = [to_dev(v) for v in vecs]
+    ptrs = (ctypes.c_void_p * count)(*[d.data_ptr() for d in devs])
+    lens = (ctypes.c_size_t * count)(*[n] * count)
+    out = torch.zeros((count, 8), dtype=torch.int64, device="cuda")
+    assert L.zk_commit_batch(ctx, ctypes.addressof(ptrs), ctypes.addressof(lens), count, 0, out.data_ptr(),
+                             stream) == 0
+    torch.cuda.synchronize()
+    got = to_host(out)
+    for k, v in enumerate(vecs):
+        assert pts_equal(got[k], orc.commit_coeffs_tau(v, tau)), k
+    assert _status(L, ctx) == (0, 1)
+
+
 def test_non_canonical_scalar_raises_its_flag(zk, checked):
     import torch
     L, ctx = checked
