@@ -235,9 +235,12 @@ __global__ void __launch_bounds__(kRecThreads)
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, wins);
     const uint32_t lt_mask = (1u << lane_id()) - 1u;
     // Lanes with equal keys share one atomic only where keys do collide:
-    // when the warp holds a job of at most 2^kAggLogB buckets (32 lanes among
-    // 2^16 buckets almost never meet, and the match costs every window).
-    const bool agg = __any_sync(0xffffffffu, live && dj.jobs[job].logB <= kAggLogB);
+    // when the warp holds a job of at most 2^kAggLogB buckets, and in the
+    // warp's last window, which may hold only a few bits (254 = 14 x 18 + 2:
+    // at width 18 every scalar's top digit lands in three buckets).  Elsewhere
+    // 32 lanes among 2^16 buckets almost never meet, and the match costs
+    // every window.
+    const bool agg_all = __any_sync(0xffffffffu, live && dj.jobs[job].logB <= kAggLogB);
     uint32_t carry = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) {
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(kRecThreads)
         int sd = carry ? (int)d - (1 << C) : (int)d;
         uint32_t key = (live && sd != 0) ? bb + (uint32_t)(sd < 0 ? -sd : sd) - 1u : kInvalid;
         if (key != kInvalid && ZK_FAILED(key < dj.bbase[job + 1], kCheckBucket)) key = kInvalid;
+        const bool agg = agg_all || (uint32_t)w + 1 == wmax;
         if (!agg) {  // warp-uniform
             if (key == kInvalid) continue;
             if (!SCATTER) {
