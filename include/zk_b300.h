@@ -274,6 +274,20 @@ int zk_fold(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, z
 int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
                  zk_stream stream);
 
+/* The first `levels` levels of the fold tree above (1 <= levels <= log2
+ * count), for checkpointing: the tree's accumulators are the natural
+ * checkpoint of the parallel accumulation (Sec. 4.2, tree reduction; each
+ * level's accumulators carry everything the rest of the tree needs).  After
+ * the call, level-`levels` accumulator j (j < count / 2^levels) is in
+ * leaves[j 2^levels + 2^levels - 1]; gammas holds the first count -
+ * count/2^levels challenges of the level-major array.  The caller may copy
+ * those accumulators (m, e: device vectors; x: the instance) anywhere,
+ * and later resume with zk_fold_tree over them and the remaining challenges
+ * (gammas + count - count/2^levels), which gives the root of the whole tree.
+ * Errors as zk_fold_tree; ZK_EINVAL for levels = 0 or > log2 count. */
+int zk_fold_tree_levels(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, size_t levels,
+                        zk_stream stream);
+
 /* Autotuning (the window width and bucket layout of the MSM and the largest
  * NTT pass radix, per length).  op = ZK_TUNE_MSM_WINDOW: value = window width c in [9, 20] for
  * MSMs of length in (2^(log2n-1), 2^log2n]; op = ZK_TUNE_NTT_RADIX: value =

@@ -83,6 +83,7 @@ def _load(path: str = LIB_PATH):
         "zk_leaf_init": [_VP, _VP, _SZ, _VP],
         "zk_fold": [_VP, _VP, _VP, _VP, _VP, _VP, _VP],
         "zk_fold_tree": [_VP, _VP, _SZ, _VP, _VP, _VP],
+        "zk_fold_tree_levels": [_VP, _VP, _SZ, _VP, _SZ, _VP],
         "zk_timing_enable": [_VP, ctypes.c_int],
         "zk_set_commit_route": [_VP, ctypes.c_int],
         "zk_tune_set": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
@@ -131,7 +132,7 @@ lib = _load()
 
 EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_generate",
             "zk_srs_size", "zk_srs_export", "zk_commit", "zk_commit_noalloc", "zk_commit_batch", "zk_ntt", "zk_intt",
-            "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_strerror",
+            "zk_ntt_batch", "zk_leaf_init", "zk_fold", "zk_fold_tree", "zk_fold_tree_levels", "zk_strerror",
             "zk_kernel_launches", "zk_probe_rates", "zk_probe_pipes", "zk_timing_enable", "zk_timing_read",
             "zk_tune_set", "zk_tune_get", "zk_tune_measure", "zk_plan_commit_batch",
             "zk_plan_fold_tree", "zk_plan_launch", "zk_plan_nodes", "zk_plan_destroy",
@@ -507,3 +508,13 @@ def zk_fold_tree(ctx: int, leaves, gammas, root: ZkAcc, stream=None) -> None:
     arr = (ZkAcc * len(leaves))(*leaves)
     _check(lib.zk_fold_tree(ctx, arr, len(leaves), _ptr(gammas), ctypes.byref(root), _stream(stream)),
            "zk_fold_tree")
+
+
+def zk_fold_tree_levels(ctx: int, leaves, gammas, levels: int, stream=None) -> list:
+    """The first `levels` levels of the fold tree; returns the indices of the
+    leaves that now hold that level's accumulators (the checkpoint)."""
+    arr = (ZkAcc * len(leaves))(*leaves)
+    _check(lib.zk_fold_tree_levels(ctx, arr, len(leaves), _ptr(gammas), int(levels), _stream(stream)),
+           "zk_fold_tree_levels")
+    span = 1 << int(levels)
+    return [j * span + span - 1 for j in range(len(leaves) // span)]

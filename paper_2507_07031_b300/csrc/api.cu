@@ -789,4 +789,12 @@ int zk_fold_tree(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas,
     return fold_tree_impl(ctx, leaves, count, gammas, root, (cudaStream_t)stream);
 }
 
+int zk_fold_tree_levels(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, size_t levels,
+                        zk_stream stream) {
+    ZK_NVTX("zk_fold_tree_levels");
+    if (!ctx || levels == 0) return ZK_EINVAL;
+    DeviceGuard g(ctx);
+    return fold_tree_impl(ctx, leaves, count, gammas, nullptr, (cudaStream_t)stream, levels);
+}
+
 }  // extern "C"

@@ -255,8 +255,10 @@ int msm_pick_window(zk_ctx *ctx, size_t max_n, size_t count);
 // Fold (fold.cu)
 int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma, zk_acc *out,
               zk_g1 *E1_out, cudaStream_t s);
+// levels = 0: the whole tree, root copied to *root; else the first `levels`
+// levels only (their accumulators left in the leaves' slots), root may be null.
 int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
-                   cudaStream_t s);
+                   cudaStream_t s, size_t levels = 0);
 int leaf_init_impl(zk_ctx *ctx, const zk_acc *accs, size_t count, cudaStream_t s);
 
 }  // namespace zk

@@ -392,20 +392,26 @@ int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma,
 }
 
 int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gammas, zk_acc *root,
-                   cudaStream_t s) {
-    if (!leaves || !gammas || !root || !pow2(count) || count < 2) return ZK_EINVAL;
+                   cudaStream_t s, size_t levels) {
+    if (!leaves || !gammas || !pow2(count) || count < 2) return ZK_EINVAL;
+    size_t all = 0;
+    while (((size_t)1 << all) < count) all++;
+    if (levels == 0) levels = all;
+    if (levels > all || (levels == all && !root)) return ZK_EINVAL;
     const size_t n = leaves[0].n;
     if (!pow2(n) || n < 2 || n > ((size_t)1 << kMaxSrsLog)) return ZK_EINVAL;
     for (size_t i = 0; i < count; i++)
         if (!acc_ok(&leaves[i], n)) return ZK_EINVAL;
-    if (!acc_ok(root, n)) return ZK_EINVAL;
+    if (root && !acc_ok(root, n)) return ZK_EINVAL;
     if (n > ctx->sh->srs_n) return ZK_ESRS;
     int err = ZK_OK;
+    // The challenges of the levels that run: a prefix of the level-major array.
+    const size_t used = count - (count >> levels);
     const uint32_t *g = (const uint32_t *)gammas;
     if (!is_device_ptr(gammas)) {
-        uint32_t *gd = (uint32_t *)scratch(ctx, "fold.gammas", (count - 1) * 32, &err);
+        uint32_t *gd = (uint32_t *)scratch(ctx, "fold.gammas", used * 32, &err);
         if (!gd) return err;
-        ZK_TRY(upload(ctx, gd, gammas, (count - 1) * 32, s));
+        ZK_TRY(upload(ctx, gd, gammas, used * 32, s));
         g = gd;
     }
     // Per-fold descriptor slots and E1 points for the whole tree, so that a
@@ -429,7 +435,7 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
     // Level l accumulator j lives in leaf slot j 2^l + 2^l - 1 (the fold
     // output overwrites its R operand).
     size_t width = count, goff = 0;
-    for (size_t span = 2; span <= count; span <<= 1) {
+    for (size_t span = 2; span <= ((size_t)1 << levels); span <<= 1) {
         std::vector<FoldDesc> d;
         d.reserve(width / 2);
         for (size_t j = 0; j < width / 2; j++) {
@@ -442,9 +448,11 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
         goff += width / 2;
         width /= 2;
     }
-    // Join the side stream before the root's instance is copied.
+    // Join the side stream before the root's instance is copied (or, after
+    // a partial tree, before the caller reads the level's accumulators).
     ZK_CUDA_TRY(cudaEventRecord(ctx->side_ev[1], ctx->side));
     ZK_CUDA_TRY(cudaStreamWaitEvent(s, ctx->side_ev[1], 0));
+    if (levels < all) return ZK_OK;
     const zk_acc &top = leaves[count - 1];
     for (int i = 0; i < 4; i++)
         ZK_CUDA_TRY(cudaMemcpyAsync(root->m[i], top.m[i], n * 32, cudaMemcpyDeviceToDevice, s));

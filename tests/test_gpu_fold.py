@@ -104,6 +104,46 @@ def test_fold_tree_small(zk, orc, ctx_small, tau, count, n):
     assert _same_acc(root.oracle(orc), want)
 
 
+def test_fold_tree_checkpoint_resume(zk, orc, ctx_small, tau):
+    """Checkpoint and resume of the fold tree: 16 leaves of 2^10 folded two
+    levels (zk_fold_tree_levels), the four level-2 accumulators copied to
+    host memory and the device state dropped; a fresh context with the same
+    SRS restores them and folds the remaining levels with the remaining
+    challenges.  The root equals the oracle's uninterrupted tree."""
+    import torch
+    count, n = 16, 1 << 10
+    devs, orcs = _leaves(zk, ctx_small, orc, tau, count, n)
+    gam = np.ascontiguousarray(np.concatenate([Z.gammas(l, count >> l) for l in range(1, count.bit_length())]))
+    want = orc.fold_tree(orcs, gam, orc.COMMIT_TAU, tau=tau)
+    for bad in (0, 5):
+        with pytest.raises(zk.ZkError) as ei:
+            zk.zk_fold_tree_levels(ctx_small, [d.desc for d in devs], gam, bad)
+        assert ei.value.code == zk.ZK_EINVAL
+    slots = zk.zk_fold_tree_levels(ctx_small, [d.desc for d in devs], gam, 2)
+    torch.cuda.synchronize()
+    assert slots == [3, 7, 11, 15]
+    saved = [(devs[k].m.cpu(), devs[k].e.cpu(), devs[k].x.cpu()) for k in slots]
+    del devs
+    torch.cuda.empty_cache()
+    ctx = zk.zk_init(0)
+    try:
+        zk.zk_srs_generate(ctx, tau, n)
+        restored = []
+        for m, e, x in saved:
+            d = DevAcc(zk, n)
+            d.m.copy_(m)
+            d.e.copy_(e)
+            d.x.copy_(x)
+            restored.append(d)
+        root = DevAcc(zk, n)
+        used = count - (count >> 2)
+        zk.zk_fold_tree(ctx, [d.desc for d in restored], np.ascontiguousarray(gam[used:]), root.desc)
+        torch.cuda.synchronize()
+        assert _same_acc(root.oracle(orc), want)
+    finally:
+        zk.zk_destroy(ctx)
+
+
 def test_fold_tree_paper_scale(zk, orc, ctx_big, tau):
     """1024 leaves of n = 2^16 (about 10 GiB resident), 10 levels, 1023 folds."""
     import torch
