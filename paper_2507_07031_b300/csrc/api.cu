@@ -178,6 +178,33 @@ __global__ void k_zero_pad(uint4 *dst, size_t from16, size_t to16) {
         dst[i] = make_uint4(0, 0, 0, 0);
 }
 
+// Workspace copies of many device vectors in one launch (a batch of small
+// commitments would otherwise issue a copy and a padding launch per vector):
+// vector k (len elements at src) goes to dst, zero-padded to `padded`
+// elements.  ebase: prefix of the padded lengths (count + 1 words, elements);
+// the grid strides over all 16-byte words.
+struct GatherDesc {
+    const uint4 *src;
+    uint4 *dst;
+    uint32_t len, padded;  // elements (32 bytes, two words)
+};
+
+__global__ void k_gather_pad(const GatherDesc *__restrict__ d, const uint32_t *__restrict__ ebase, uint32_t count) {
+    const size_t words = 2 * (size_t)ebase[count];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t e = (uint32_t)(i >> 1);
+        uint32_t lo = 0, hi = count;  // largest k with ebase[k] <= e
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (ebase[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const GatherDesc g = d[lo];
+        const size_t w = i - 2 * (size_t)ebase[lo];
+        g.dst[w] = w < 2 * (size_t)g.len ? g.src[w] : make_uint4(0, 0, 0, 0);
+    }
+}
+
 // Synthetic canonical F_r elements (253-bit values, so always < r) for
 // tuning runs: a SplitMix64-style hash of the index.
 __global__ void k_fill_random(uint64_t *out, size_t n, uint64_t seed) {
@@ -661,6 +688,7 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
         if (evals && padded[k] > ((size_t)1 << kMaxLogN)) return ZK_EINVAL;
         total += padded[k];
     }
+    if (total >= ((size_t)1 << 32)) return ZK_EINVAL;  // 32-bit element offsets (workspace, MSM)
     // Inputs: staged (host sources, or a workspace copy for the INTT).
     int err = ZK_OK;
     bool any_host = false;
@@ -680,18 +708,20 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
     std::vector<MsmJob> jobs(count);
     std::vector<uint32_t *> ntt_vecs;
     std::vector<size_t> ntt_lens;
+    std::vector<GatherDesc> gather;  // device sources copied to the workspace
     size_t off = 0;
     for (size_t k = 0; k < count; k++) {
         const uint32_t *src = (const uint32_t *)vecs[k];
         if ((evals && (!lagrange || padded[k] != lens[k])) || !dev_in[k]) {
             uint32_t *dst = ws + off * 8;
-            if (lens[k]) {
-                cudaMemcpyKind kind = dev_in[k] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-                ZK_CUDA_TRY(cudaMemcpyAsync(dst, src, lens[k] * 32, kind, s));
-            }
-            if (padded[k] > lens[k]) {
-                k_zero_pad<<<64, 256, 0, s>>>((uint4 *)dst, lens[k] * 2, padded[k] * 2);
-                ZK_LAUNCHED();
+            if (dev_in[k] && padded[k]) {
+                gather.push_back({(const uint4 *)src, (uint4 *)dst, (uint32_t)lens[k], (uint32_t)padded[k]});
+            } else {
+                if (lens[k]) ZK_CUDA_TRY(cudaMemcpyAsync(dst, src, lens[k] * 32, cudaMemcpyHostToDevice, s));
+                if (padded[k] > lens[k]) {
+                    k_zero_pad<<<64, 256, 0, s>>>((uint4 *)dst, lens[k] * 2, padded[k] * 2);
+                    ZK_LAUNCHED();
+                }
             }
             if (evals && !lagrange && padded[k]) {
                 ntt_vecs.push_back(dst);
@@ -709,6 +739,22 @@ int zk_commit_batch(zk_ctx *ctx, const zk_fr *const *vecs, const size_t *lens, s
             jobs[k].basis = lg;
         }
         off += padded[k];
+    }
+    if (!gather.empty()) {
+        const size_t gn = gather.size();
+        const size_t dbytes = (gn * sizeof(GatherDesc) + 255) / 256 * 256;
+        char *gt = (char *)scratch(ctx, "commit.gather", dbytes + (gn + 1) * 4, &err);
+        if (!gt) return err;
+        std::vector<char> h(dbytes + (gn + 1) * 4, 0);
+        std::memcpy(h.data(), gather.data(), gn * sizeof(GatherDesc));
+        uint32_t *eb = (uint32_t *)(h.data() + dbytes);
+        for (size_t k = 0; k < gn; k++) eb[k + 1] = eb[k] + gather[k].padded;
+        ZK_TRY(upload(ctx, gt, h.data(), h.size(), s));
+        const size_t words = 2 * (size_t)eb[gn];
+        const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, (size_t)sh.sms * 16);
+        k_gather_pad<<<std::max(blocks, 1u), 256, 0, s>>>((const GatherDesc *)gt, (const uint32_t *)(gt + dbytes),
+                                                         (uint32_t)gn);
+        ZK_LAUNCHED();
     }
     if (!ntt_vecs.empty())
         ZK_TRY(ntt_batch_impl(ctx, ntt_vecs.data(), ntt_lens.data(), ntt_vecs.size(), true, s));

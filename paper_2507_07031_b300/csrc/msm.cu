@@ -1151,19 +1151,25 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     // Point tables: the base points (SRS, or the Lagrange basis of H for
     // evaluation-form jobs) and the width's window table of that basis
     // (built on first use, outside timed loops).
+    // (The jobs are sorted by width and basis, so each pair's jobs are
+    // contiguous: one table lookup per group, sized for its longest job.)
     std::vector<const Affine *> bases(count), tabs(count);
     std::vector<uint32_t> tabn(count);
-    for (size_t k = 0; k < count; k++) {
-        const int basis = jv[k].job.basis;
-        if (basis && (!sh.lag[basis].p || jv[k].job.n != (1u << basis))) return ZK_EINVAL;
-        bases[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
-        size_t need = 1;
-        for (size_t j = 0; j < count; j++)
-            if (jv[j].c == jv[k].c && jv[j].job.basis == basis) need = std::max(need, (size_t)jv[j].job.n);
+    for (size_t g0 = 0; g0 < count;) {
+        const int basis = jv[g0].job.basis;
+        size_t g1 = g0, need = 1;
+        for (; g1 < count && jv[g1].c == jv[g0].c && jv[g1].job.basis == basis; g1++) {
+            if (basis && (!sh.lag[basis].p || jv[g1].job.n != (1u << basis))) return ZK_EINVAL;
+            need = std::max(need, (size_t)jv[g1].job.n);
+        }
         const WindowTable *t;
-        ZK_TRY(table_get(ctx, jv[k].c, need, basis, &t, s));
-        tabs[k] = (const Affine *)t->buf.p;
-        tabn[k] = (uint32_t)t->n;
+        ZK_TRY(table_get(ctx, jv[g0].c, need, basis, &t, s));
+        for (size_t k = g0; k < g1; k++) {
+            bases[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
+            tabs[k] = (const Affine *)t->buf.p;
+            tabn[k] = (uint32_t)t->n;
+        }
+        g0 = g1;
     }
     // Width-16 tables that already exist (SRS loading builds the SRS's),
     // for the single-window path of scalars with 16 or more trailing zeros.
