@@ -171,15 +171,24 @@ __global__ void k_fold_mu(const FoldDesc *__restrict__ descs, uint32_t folds) {
 // Every product of a scalar and a point is its own lane of a team (four warps
 // sharing each point operation): per fold, lanes C_1..C_4 (gamma), gamma E1,
 // then gamma^2 E (degree 2) or gamma^2 E2, gamma^3 E (degree 3).  A lane runs
-// double-and-add over its 254 scalar bits; the lanes of one fold then meet in
+// a fixed-window product over its 254 scalar bits: a table of d P for
+// d < 16 (each lane its own, in shared memory), then per 4-bit digit from
+// the top four doublings and one addition of its table entry: 252 doublings
+// and 64 additions instead of 254 of each (a team addition costs four
+// product latencies, a doubling three).  The lanes of one fold then meet in
 // one thread per output point, which adds the primed point and normalises.
+constexpr int kInstWin = 4;
+constexpr int kInstAcc = 0, kInstTmp = 4, kInstT = 8, kInstTab = kInstT + kTeamTemps;
+constexpr int kInstSlots = kInstTab + 4 * (1 << kInstWin);
+constexpr size_t kInstSmem = (size_t)kInstSlots * 8 * 32 * sizeof(uint32_t);
+
 template <int DEG>
 __global__ void __launch_bounds__(kTeamThreads) k_fold_instance(const FoldDesc *__restrict__ descs,
                                                                 uint32_t folds) {
     constexpr int kOps = DEG == 3 ? 7 : 6;  // scalar-point products per fold
     constexpr int kFolds = 32 / kOps;       // folds per team
-    constexpr int kAcc = 0, kBase = 4, kTmp = 8, kT = 12;
-    __shared__ uint32_t f[(kT + kTeamTemps) * 8 * 32];
+    constexpr int kAcc = kInstAcc, kTmp = kInstTmp, kT = kInstT, kTab = kInstTab;
+    extern __shared__ uint32_t f[];  // kInstSlots slots
     const uint32_t l = team_lane(), w = team_warp();
     const uint32_t fl = blockIdx.x * kFolds + l / kOps, op = l % kOps;
     const bool valid = l < kFolds * kOps && fl < folds;
@@ -197,12 +206,24 @@ __global__ void __launch_bounds__(kTeamThreads) k_fold_instance(const FoldDesc *
         const uint32_t *src = op < 4 ? d.Lx + 16 * op : op == 4 ? d.E1 : (DEG == 3 && op == 5) ? d.E2 : d.Lx + 64;
         base = xyzz_load_canonical(src);
     }
-    tf_store(f, kBase + w, w == 0 ? base.X : w == 1 ? base.Y : w == 2 ? base.ZZ : base.ZZZ);
+    // Table: T[0] = infinity, T[1] = base, T[2d] = 2 T[d], T[2d+1] = T[2d] + T[1].
+    team_set_inf_nosync(f, kTab);
+    tf_store(f, kTab + 4 + w, w == 0 ? base.X : w == 1 ? base.Y : w == 2 ? base.ZZ : base.ZZZ);
+    __syncthreads();
+    for (int d = 2; d < (1 << kInstWin); d++) {
+        if (d & 1) team_add(f, kTab + 4 * (d - 1), kTab + 4, kTab + 4 * d, kT);
+        else team_dbl(f, kTab + 4 * (d / 2), kTab + 4 * d, kT);
+    }
     team_set_inf_nosync(f, kAcc);
     __syncthreads();
-    for (int i = 253; i >= 0; i--) {
-        team_dbl(f, kAcc, kAcc, kT);
-        team_copy(f, kBase, kTmp, (k[i >> 5] >> (i & 31)) & 1);
+    constexpr int kWins = (256 + kInstWin - 1) / kInstWin;  // bits 254, 255 are zero
+    for (int i = kWins - 1; i >= 0; i--) {
+        if (i != kWins - 1)
+            for (int r = 0; r < kInstWin; r++) team_dbl(f, kAcc, kAcc, kT);
+        const int bit = i * kInstWin;  // windows do not cross words (32 % kInstWin == 0)
+        const uint32_t dgt = (k[bit >> 5] >> (bit & 31)) & ((1u << kInstWin) - 1u);
+        tf_store(f, kTmp + w, tf_load(f, kTab + 4 * (int)dgt + w));  // this lane's entry
+        __syncthreads();
         team_add(f, kAcc, kTmp, kAcc, kT);
     }
     // One thread per output point: C_1..C_4 and E of each fold.
@@ -326,8 +347,17 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     }
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s_inst);
-        if (three) k_fold_instance<3><<<(unsigned)((F + 3) / 4), kTeamThreads, 0, s_inst>>>(dd, (uint32_t)F);
-        else k_fold_instance<2><<<(unsigned)((F + 4) / 5), kTeamThreads, 0, s_inst>>>(dd, (uint32_t)F);
+        static const bool attr = [] {
+            const bool ok = cudaFuncSetAttribute(k_fold_instance<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kInstSmem) == cudaSuccess &&
+                            cudaFuncSetAttribute(k_fold_instance<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kInstSmem) == cudaSuccess;
+            if (!ok) cudaGetLastError();
+            return ok;
+        }();
+        if (!attr) return ZK_ECUDA;
+        if (three) k_fold_instance<3><<<(unsigned)((F + 3) / 4), kTeamThreads, kInstSmem, s_inst>>>(dd, (uint32_t)F);
+        else k_fold_instance<2><<<(unsigned)((F + 4) / 5), kTeamThreads, kInstSmem, s_inst>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();
     }
     return ZK_OK;
