@@ -235,4 +235,166 @@ ZK_DEV Xyzz xyzz_mul(const Xyzz &p, const uint32_t (&k)[8]) {
     return acc;
 }
 
+// ---------------------------------------------------------------------------
+// GLV (Gallant, Lambert, Vanstone, CRYPTO 2001) on BN254 G1.  The map
+// phi(x, y) = (beta x, y), beta a primitive cube root of unity in F_q, is an
+// endomorphism of the curve that acts as multiplication by lambda, a primitive
+// cube root of unity in F_r (the pair with phi(G) = lambda G).  A scalar k
+// splits as k = k1 + k2 lambda (mod r) with |k1|, |k2| < 2^130 using the short
+// basis (a1, b1), (a2, b2) of the lattice {(x, y): x + y lambda = 0 (mod r)}
+// (extended Euclid on r and lambda, stopped at sqrt(r)):
+//   c1 = floor(k G1 / 2^256), c2 = floor(k G2 / 2^256), with
+//   G1 = floor(b2 2^256 / r) and G2 = floor(-b1 2^256 / r) (each c within 2 of
+//   the rounded k b2 / r and -k b1 / r),
+//   k1 = k - c1 a1 - c2 a2,  k2 = -c1 b1 - c2 b2 = c1 |b1| - c2 b2  (b1 < 0).
+// Then k P = k1 P + k2 phi(P): two half-length scalars share one chain of
+// doublings.  (k1, k2) = e1 (a1, b1) + e2 (a2, b2) with 0 <= e1, e2 < 2 bounds
+// |k1| <= 2 (|a1| + |a2|) < 2^129 and |k2| <= 2 (|b1| + |b2|) < 2^129.
+// ---------------------------------------------------------------------------
+struct Glv {
+    static ZK_HD constexpr uint32_t beta_mont(int i) {  // beta R mod q
+        constexpr uint32_t v[8] = {0xd782e155u, 0x71930c11u, 0xffbe3323u, 0xa6bb947cu,
+                                   0xd4741444u, 0xaa303344u, 0x26594943u, 0x2c3b3f0du};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t a1(int i) {
+        constexpr uint32_t v[8] = {0x94d213e3u, 0x89d32568u, 0, 0, 0, 0, 0, 0};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t b1_abs(int i) {  // -b1
+        constexpr uint32_t v[8] = {0x7d4f1128u, 0x8211bbebu, 0xeeb859fcu, 0x6f4d8248u, 0, 0, 0, 0};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t a2(int i) {
+        constexpr uint32_t v[8] = {0x1221250bu, 0x0be4e154u, 0xeeb859fdu, 0x6f4d8248u, 0, 0, 0, 0};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t b2(int i) {
+        constexpr uint32_t v[8] = {0x94d213e3u, 0x89d32568u, 0, 0, 0, 0, 0, 0};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t g1(int i) {
+        constexpr uint32_t v[8] = {0xc7e0b3d7u, 0xd91d232eu, 0x00000002u, 0, 0, 0, 0, 0};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t g2(int i) {
+        constexpr uint32_t v[8] = {0x391eb18du, 0x7a7bd9d4u, 0xa773d2cfu, 0x4ccef014u, 0x00000002u, 0, 0, 0};
+        return v[i];
+    }
+};
+
+constexpr int kGlvWords = 5;  // |k1|, |k2| < 2^130 fit 160 bits
+
+namespace detail {
+// x y for 8-word operands, low 9 words (both small enough that the product
+// fits: the callers' products stay below 2^288).
+ZK_DEV void glv_mul9(const uint32_t (&x)[8], const uint32_t (&y)[8], uint32_t (&out)[9]) {
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        uint64_t carry = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (i + j >= 9) break;
+            const uint64_t p = (uint64_t)x[i] * y[j] + t[i + j] + carry;
+            t[i + j] = (uint32_t)p;
+            carry = p >> 32;
+        }
+        if (i + 8 < 9) t[i + 8] = (uint32_t)carry;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) out[i] = t[i];
+}
+// floor(x y / 2^256) for an 8-word x and constant y, 8 words.
+ZK_DEV void glv_mulhi(const uint32_t (&x)[8], const uint32_t (&y)[8], uint32_t (&out)[8]) {
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        uint64_t carry = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const uint64_t p = (uint64_t)x[i] * y[j] + t[i + j] + carry;
+            t[i + j] = (uint32_t)p;
+            carry = p >> 32;
+        }
+        t[i + 8] = (uint32_t)carry;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i] = t[8 + i];
+}
+// a - b over 9 words (two's complement).
+ZK_DEV void glv_sub9(uint32_t (&a)[9], const uint32_t (&b)[9]) {
+    uint64_t borrow = 0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const uint64_t d = (uint64_t)a[i] - b[i] - borrow;
+        a[i] = (uint32_t)d;
+        borrow = (d >> 32) & 1;
+    }
+}
+// Sign and magnitude (kGlvWords words) of a 9-word two's complement value.
+ZK_DEV bool glv_abs(const uint32_t (&a)[9], uint32_t (&m)[kGlvWords]) {
+    const bool neg = (a[8] >> 31) != 0;
+    uint64_t c = 1;
+#pragma unroll
+    for (int i = 0; i < kGlvWords; i++) {
+        if (neg) {
+            const uint64_t v = (uint64_t)(~a[i]) + c;
+            m[i] = (uint32_t)v;
+            c = v >> 32;
+        } else {
+            m[i] = a[i];
+        }
+    }
+    return neg;
+}
+}  // namespace detail
+
+// k (canonical, < r) -> |k1|, |k2| (kGlvWords words each) and their signs,
+// with k = k1 + k2 lambda (mod r).
+ZK_DEV void glv_split(const uint32_t (&k)[8], uint32_t (&k1)[kGlvWords], bool &neg1, uint32_t (&k2)[kGlvWords],
+                      bool &neg2) {
+    using namespace detail;
+    uint32_t g1[8], g2[8], a1[8], a2[8], b1[8], b2[8], c1[8], c2[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        g1[i] = Glv::g1(i);
+        g2[i] = Glv::g2(i);
+        a1[i] = Glv::a1(i);
+        a2[i] = Glv::a2(i);
+        b1[i] = Glv::b1_abs(i);
+        b2[i] = Glv::b2(i);
+    }
+    glv_mulhi(k, g1, c1);  // < 2^66
+    glv_mulhi(k, g2, c2);  // < 2^130
+    uint32_t x[9], t[9];
+    // k1 = k - c1 a1 - c2 a2
+#pragma unroll
+    for (int i = 0; i < 9; i++) x[i] = i < 8 ? k[i] : 0u;
+    glv_mul9(c1, a1, t);
+    glv_sub9(x, t);
+    glv_mul9(c2, a2, t);
+    glv_sub9(x, t);
+    neg1 = glv_abs(x, k1);
+    // k2 = c1 |b1| - c2 b2
+    glv_mul9(c1, b1, x);
+    glv_mul9(c2, b2, t);
+    glv_sub9(x, t);
+    neg2 = glv_abs(x, k2);
+}
+
+// phi(P) = (beta x, y) in XYZZ: (beta X, Y, ZZ, ZZZ).
+ZK_DEV Xyzz xyzz_phi(const Xyzz &p) {
+    Fq b;
+#pragma unroll
+    for (int i = 0; i < 8; i++) b.v[i] = Glv::beta_mont(i);
+    Xyzz r = p;
+    r.X = fe_mul<FqP>(p.X, b);
+    return r;
+}
+
 }  // namespace zk

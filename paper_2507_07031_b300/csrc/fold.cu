@@ -171,15 +171,18 @@ __global__ void k_fold_mu(const FoldDesc *__restrict__ descs, uint32_t folds) {
 // Every product of a scalar and a point is its own lane of a team (four warps
 // sharing each point operation): per fold, lanes C_1..C_4 (gamma), gamma E1,
 // then gamma^2 E (degree 2) or gamma^2 E2, gamma^3 E (degree 3).  A lane runs
-// a fixed-window product over its 254 scalar bits: a table of d P for
-// d < 16 (each lane its own, in shared memory), then per 4-bit digit from
-// the top four doublings and one addition of its table entry: 252 doublings
-// and 64 additions instead of 254 of each (a team addition costs four
-// product latencies, a doubling three).  The lanes of one fold then meet in
-// one thread per output point, which adds the primed point and normalises.
-constexpr int kInstWin = 4;
+// its scalar k as k1 P1 + k2 P2 with the GLV split k = k1 + k2 lambda
+// (curve.cuh; |k1|, |k2| < 2^130, P1 = sign(k1) P, P2 = sign(k2) phi(P)): a
+// table of d1 P1 + d2 P2 for d1, d2 < 4 (each lane its own, in shared
+// memory), then per 2-bit digit pair from the top two doublings and one
+// addition of its table entry.  About 130 doublings and 65 additions instead
+// of 254 of each for plain double-and-add (a team addition costs four
+// product latencies, a doubling three); a 4-bit window without the split took
+// 252 and 64, and 1.0 ms against 1.7 per fold.  The lanes of one fold then
+// meet in one thread per output point, which adds the primed point and
+// normalises.
 constexpr int kInstAcc = 0, kInstTmp = 4, kInstT = 8, kInstTab = kInstT + kTeamTemps;
-constexpr int kInstSlots = kInstTab + 4 * (1 << kInstWin);
+constexpr int kInstSlots = kInstTab + 4 * 16;
 constexpr size_t kInstSmem = (size_t)kInstSlots * 8 * 32 * sizeof(uint32_t);
 
 template <int DEG>
@@ -206,23 +209,38 @@ __global__ void __launch_bounds__(kTeamThreads) k_fold_instance(const FoldDesc *
         const uint32_t *src = op < 4 ? d.Lx + 16 * op : op == 4 ? d.E1 : (DEG == 3 && op == 5) ? d.E2 : d.Lx + 64;
         base = xyzz_load_canonical(src);
     }
-    // Table: T[0] = infinity, T[1] = base, T[2d] = 2 T[d], T[2d+1] = T[2d] + T[1].
+    uint32_t k1[kGlvWords], k2[kGlvWords];
+    bool n1, n2;
+    glv_split(k, k1, n1, k2, n2);
+    const Xyzz p1 = n1 ? xyzz_neg(base) : base;
+    Xyzz p2 = xyzz_phi(base);
+    if (n2) p2 = xyzz_neg(p2);
+    // Table T[d1 + 4 d2] = d1 P1 + d2 P2 (T[0] = infinity).
     team_set_inf_nosync(f, kTab);
-    tf_store(f, kTab + 4 + w, w == 0 ? base.X : w == 1 ? base.Y : w == 2 ? base.ZZ : base.ZZZ);
+    tf_store(f, kTab + 4 + w, w == 0 ? p1.X : w == 1 ? p1.Y : w == 2 ? p1.ZZ : p1.ZZZ);
+    tf_store(f, kTab + 16 + w, w == 0 ? p2.X : w == 1 ? p2.Y : w == 2 ? p2.ZZ : p2.ZZZ);
     __syncthreads();
-    for (int d = 2; d < (1 << kInstWin); d++) {
-        if (d & 1) team_add(f, kTab + 4 * (d - 1), kTab + 4, kTab + 4 * d, kT);
-        else team_dbl(f, kTab + 4 * (d / 2), kTab + 4 * d, kT);
-    }
+    team_dbl(f, kTab + 4, kTab + 8, kT);               // 2 P1
+    team_add(f, kTab + 8, kTab + 4, kTab + 12, kT);    // 3 P1
+    team_dbl(f, kTab + 16, kTab + 32, kT);             // 2 P2
+    team_add(f, kTab + 32, kTab + 16, kTab + 48, kT);  // 3 P2
+    for (int d2 = 1; d2 < 4; d2++)
+        for (int d1 = 1; d1 < 4; d1++) team_add(f, kTab + 4 * d1, kTab + 16 * d2, kTab + 4 * (d1 + 4 * d2), kT);
     team_set_inf_nosync(f, kAcc);
     __syncthreads();
-    constexpr int kWins = (256 + kInstWin - 1) / kInstWin;  // bits 254, 255 are zero
-    for (int i = kWins - 1; i >= 0; i--) {
-        if (i != kWins - 1)
-            for (int r = 0; r < kInstWin; r++) team_dbl(f, kAcc, kAcc, kT);
-        const int bit = i * kInstWin;  // windows do not cross words (32 % kInstWin == 0)
-        const uint32_t dgt = (k[bit >> 5] >> (bit & 31)) & ((1u << kInstWin) - 1u);
-        tf_store(f, kTmp + w, tf_load(f, kTab + 4 * (int)dgt + w));  // this lane's entry
+    // 2-bit digit pairs from bit 129 down; leading windows where no lane has
+    // a digit are skipped (block-uniform).
+    bool started = false;
+    for (int i = 16 * kGlvWords - 1; i >= 0; i--) {
+        const int bit = 2 * i;  // digits do not cross words
+        const uint32_t e = ((k1[bit >> 5] >> (bit & 31)) & 3u) + 4u * ((k2[bit >> 5] >> (bit & 31)) & 3u);
+        if (started) {
+            team_dbl(f, kAcc, kAcc, kT);
+            team_dbl(f, kAcc, kAcc, kT);
+        }
+        if (!__syncthreads_or(e != 0)) continue;
+        started = true;
+        tf_store(f, kTmp + w, tf_load(f, kTab + 4 * (int)e + w));  // this lane's entry
         __syncthreads();
         team_add(f, kAcc, kTmp, kAcc, kT);
     }
