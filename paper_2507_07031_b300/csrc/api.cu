@@ -6,6 +6,9 @@
 #include <atomic>
 #include <cstring>
 #include <new>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "check.cuh"
@@ -80,6 +83,24 @@ void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err) {
         }
     }
     return b.p;
+}
+
+int set_max_dynamic_smem(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count({dev, func})) return ZK_OK;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return ZK_ECUDA;
+    }
+    done.insert({dev, func});
+    return ZK_OK;
 }
 
 int upload(zk_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {

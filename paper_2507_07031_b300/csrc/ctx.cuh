@@ -124,6 +124,9 @@ void dev_free(Shared &sh, DevBuf &b);
 void *scratch(zk_ctx *ctx, const char *name, size_t bytes, int *err);
 
 bool is_device_ptr(const void *p);
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (device, kernel) pair (the attribute is per device).
+int set_max_dynamic_smem(const void *func, int bytes);
 // Asynchronous upload of `bytes` host bytes to `dst` on stream s (see Uploader).
 int upload(zk_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s);
 

@@ -365,15 +365,8 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     }
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_INSTANCE, s_inst);
-        static const bool attr = [] {
-            const bool ok = cudaFuncSetAttribute(k_fold_instance<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kInstSmem) == cudaSuccess &&
-                            cudaFuncSetAttribute(k_fold_instance<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kInstSmem) == cudaSuccess;
-            if (!ok) cudaGetLastError();
-            return ok;
-        }();
-        if (!attr) return ZK_ECUDA;
+        ZK_TRY(set_max_dynamic_smem(three ? (const void *)k_fold_instance<3> : (const void *)k_fold_instance<2>,
+                                    (int)kInstSmem));
         if (three) k_fold_instance<3><<<(unsigned)((F + 3) / 4), kTeamThreads, kInstSmem, s_inst>>>(dd, (uint32_t)F);
         else k_fold_instance<2><<<(unsigned)((F + 4) / 5), kTeamThreads, kInstSmem, s_inst>>>(dd, (uint32_t)F);
         ZK_LAUNCHED();

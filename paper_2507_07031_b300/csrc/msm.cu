@@ -1001,13 +1001,7 @@ int launch_recode_wide_c(const DevJobs &dj, uint32_t g0, uint32_t g1, uint32_t c
     } else {
         if (chunks == 0) return ZK_OK;
         constexpr int kSmem = std::max((1 << (C - 1)) * 4, kWideSmemMin);
-        static const bool attr = [] {
-            const bool ok = cudaFuncSetAttribute(k_recode_wide<C, SCATTER>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) == cudaSuccess;
-            if (!ok) cudaGetLastError();
-            return ok;
-        }();
-        if (!attr) return ZK_ECUDA;
+        ZK_TRY(set_max_dynamic_smem((const void *)k_recode_wide<C, SCATTER>, kSmem));
         k_recode_wide<C, SCATTER><<<chunks, kWideThreads, kSmem, s>>>(dj, g0, g1, table_n, counts, cursor, sorted,
                                                                      off0);
         ZK_LAUNCHED();
