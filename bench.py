@@ -454,13 +454,13 @@ def main():
                                       "ms_per_tree": wit_ms}
 
     # Dominant kernel: bucket accumulation of the uniform 2^20 MSM
-    # (k_pieces_first and the device-gated rounds after it).
+    # (round 0, k_pieces_first, and the bucket completion after it).
     acc_ms, acc_cnt = phases["msm_accum"]
     adds = n20 * W * args.steps  # one mixed addition per nonzero signed digit
     acc = imad_roof(adds * madd, acc_ms, rates)
     roofline = dict(acc)
     roofline.update({
-        "kernel": "MSM bucket accumulation (k_pieces_first + gated rounds + tail), uniform 2^20, c=%d" % c20,
+        "kernel": "MSM bucket accumulation (k_pieces_first + bucket completion), uniform 2^20, c=%d" % c20,
         "algorithmic": "%d mixed additions x 10 F_q products x 264 IMADs per MSM" % (n20 * W),
         "traffic": ACCUM_TRAFFIC, "traffic_kernel": "k_pieces_first (ncu, bytes per launch)",
         "ms_per_launch": acc_ms / max(acc_cnt, 1),
