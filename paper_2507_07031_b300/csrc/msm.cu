@@ -472,32 +472,52 @@ __global__ void k_msm_plan(JobDesc *__restrict__ jobs, uint32_t count, const uin
 //                         sets with many entries each (quantised scalars put
 //                         2^20 entries in about a hundred buckets), or a
 //                         skewed bucket.
-// Empty buckets are set to infinity by k_buckets_final.  (Completing buckets
+// Empty buckets are set to infinity by k_buckets_final.  The thread path's
+// limit is kThreadMax when many buckets hold several pieces (a throughput
+// matter), but only kThreadMaxFew when the buckets of more than that many
+// pieces fit one wave of tail teams: a small MSM of quantised values has a
+// few buckets of 20-30 pieces, whose one-thread chains of full additions set
+// its latency (190 us at 2^12 x 4) while a team sums them in a few steps.
+// (Completing buckets
 // of a few pieces inside round 0 instead -- the last thread to finish one,
 // found by a per-bucket counter, adding the others -- made a 2^20 MSM of
 // uniform scalars 2 % slower on B300: the fences, atomics and extra registers
 // cost the loop more than the separate pass.)
 constexpr uint32_t kP0Min = 8;              // smallest round-0 chunk
 constexpr uint32_t kThreadMax = 32;
+constexpr uint32_t kThreadMaxFew = 4;
 constexpr uint32_t kTailBuckets = 4096;     // bucket sets that take longer round-0 chunks (chunk_log)
 
 struct RoundPlan {
-    uint32_t p0;  // round-0 chunk (entries per thread)
-    int p0neg;    // -p0 (the scan's chunk-count mode)
+    uint32_t p0;   // round-0 chunk (entries per thread)
+    int p0neg;     // -p0 (the scan's chunk-count mode)
+    uint32_t thr;  // buckets of more pieces take the team tail
 };
 
-// The number of nonempty buckets into stat[1] and the largest bucket into
-// stat[0] (both zeroed by the caller).
-__global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, uint32_t *stat) {
-    uint32_t m = 0, used = 0;
+// Round-0 chunk before the few-bucket multiplier.
+__device__ __forceinline__ uint32_t p0_base(uint32_t entries, uint32_t resident) {
+    return max(kP0Min, (uint32_t)(((uint64_t)entries + resident - 1) / resident));
+}
+
+// Into stat (three words, zeroed by the caller): the largest bucket, the
+// number of nonempty buckets, and the number of buckets with more than
+// kThreadMaxFew - 1 chunks' worth of entries (about kThreadMaxFew pieces or
+// more; the few-bucket multiplier only makes pieces fewer).
+__global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, const uint32_t *total,
+                            uint32_t resident, uint32_t *stat) {
+    const uint32_t big = (kThreadMaxFew - 1) * p0_base(*total, resident);
+    uint32_t m = 0, used = 0, many = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
         m = max(m, counts[i]);
         used += counts[i] != 0;
+        many += counts[i] > big;
     }
     m = __reduce_max_sync(0xffffffffu, m);
     used = __reduce_add_sync(0xffffffffu, used);
+    many = __reduce_add_sync(0xffffffffu, many);
     if (lane_id() == 0 && m) atomicMax(&stat[0], m);
     if (lane_id() == 0 && used) atomicAdd(&stat[1], used);
+    if (lane_id() == 0 && many) atomicAdd(&stat[2], many);
 }
 
 // Round-0 chunk from the actual entries (their count at off0[nb]): every
@@ -505,14 +525,13 @@ __global__ void k_count_max(const uint32_t *__restrict__ counts, uint32_t nb, ui
 // least kP0Min), so round 0 runs as one wave; 2^chunk_log times more when few
 // buckets are in use (fewer pieces for the team tail).
 __global__ void k_round_plan(const uint32_t *stat, const uint32_t *total, uint32_t resident, uint32_t chunk_log,
-                             RoundPlan *plan) {
+                             uint32_t tail_teams, RoundPlan *plan) {
     if (threadIdx.x || blockIdx.x) return;
-    const uint32_t entries = *total;
     const bool few = stat[1] <= kTailBuckets;
-    const uint32_t p0 = max(kP0Min, (uint32_t)(((uint64_t)entries + resident - 1) / resident))
-                        << (few ? chunk_log : 0u);
+    const uint32_t p0 = p0_base(*total, resident) << (few ? chunk_log : 0u);
     plan->p0 = p0;
     plan->p0neg = -(int)p0;
+    plan->thr = stat[2] <= tail_teams ? kThreadMaxFew : kThreadMax;
 }
 
 // Stores piece j of bucket b (of m pieces): the bucket sum itself when it is
@@ -569,7 +588,7 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
 // thread per bucket.  Buckets past a job's 2^logB (short scalars) are never
 // read and are left alone.
 __global__ void k_buckets_final(const Xyzz *__restrict__ pieces, const uint32_t *__restrict__ off1, uint32_t nb,
-                                DevJobs dj, Xyzz *__restrict__ buckets) {
+                                DevJobs dj, const RoundPlan *__restrict__ plan, Xyzz *__restrict__ buckets) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     const uint32_t job = search(dj.bbase, 0, dj.count, b);
@@ -579,7 +598,7 @@ __global__ void k_buckets_final(const Xyzz *__restrict__ pieces, const uint32_t 
         buckets[b] = xyzz_inf();
         return;
     }
-    if (m == 1 || m > kThreadMax) return;
+    if (m == 1 || m > plan->thr) return;
     Xyzz acc = pieces[lo];
     for (uint32_t j = lo + 1; j < lo + m; j++) acc = xyzz_add(acc, pieces[j]);
     buckets[b] = acc;
@@ -697,7 +716,7 @@ AccumShape accum_shape(size_t total, uint32_t nb, int sms, const MsmLayout &layo
 struct AccumBufs {
     uint32_t *off1;   // nb + 1 words: piece offsets
     Xyzz *pieces, *parts;
-    uint32_t *stat;   // two words
+    uint32_t *stat;   // three words (k_count_max)
     RoundPlan *plan;
     void *scan_tmp;
     uint32_t *offs;   // nb + 1 words: slice offsets of the team tail
@@ -708,21 +727,21 @@ struct AccumBufs {
 int launch_accumulate(const uint32_t *sorted, const uint32_t *counts, const uint32_t *off0, uint32_t nb,
                       const AccumShape &a, const DevJobs &dj, const AccumBufs &w, Xyzz *buckets, int sms,
                       cudaStream_t s) {
-    ZK_CUDA_TRY(cudaMemsetAsync(w.stat, 0, 2 * sizeof(uint32_t), s));
+    ZK_CUDA_TRY(cudaMemsetAsync(w.stat, 0, 3 * sizeof(uint32_t), s));
     const unsigned mb = (unsigned)std::min<size_t>((nb + 255) / 256, (size_t)sms * 4);
-    k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, w.stat);
+    const unsigned tb = (unsigned)std::min<size_t>(std::max<uint32_t>(nb, 1), (size_t)sms * 8);  // tail teams
+    k_count_max<<<std::max(mb, 1u), 256, 0, s>>>(counts, nb, off0 + nb, a.resident, w.stat);
     ZK_LAUNCHED();
-    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, a.layout.chunk_log, w.plan);
+    k_round_plan<<<1, 32, 0, s>>>(w.stat, off0 + nb, a.resident, a.layout.chunk_log, tb, w.plan);
     ZK_LAUNCHED();
     ZK_TRY(scan_exclusive(off0, w.off1, nb, -(int)kP0Min, w.scan_tmp, s, nullptr, &w.plan->p0neg));
     k_pieces_first<<<a.blocks, 128, 0, s>>>(sorted, off0, w.off1, nb, dj, w.plan, w.pieces, buckets);
     ZK_LAUNCHED();
-    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(w.pieces, w.off1, nb, dj, buckets);
+    k_buckets_final<<<(nb + 127) / 128, 128, 0, s>>>(w.pieces, w.off1, nb, dj, w.plan, buckets);
     ZK_LAUNCHED();
-    // Buckets of more than kThreadMax pieces: slices of 32 L pieces.
+    // Buckets of more than plan->thr pieces: slices of 32 L pieces.
     ZK_TRY(scan_exclusive(w.off1, w.offs, nb, (int)(32u << a.layout.tail_log), w.scan_tmp, s, nullptr, nullptr,
-                          nullptr, kThreadMax));
-    const unsigned tb = (unsigned)std::min<size_t>(std::max<uint32_t>(nb, 1), (size_t)sms * 8);
+                          nullptr, kThreadMax, &w.plan->thr));
     k_tail_slices<<<tb, kTeamThreads, 0, s>>>(w.pieces, w.off1, nb, a.layout.tail_log, w.offs, w.parts);
     ZK_LAUNCHED();
     k_tail_buckets<<<tb, kTeamThreads, 0, s>>>(nb, w.offs, w.parts, buckets);

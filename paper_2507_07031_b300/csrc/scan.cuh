@@ -58,9 +58,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 
 __global__ void k_tile_sums(const uint32_t *__restrict__ in, uint32_t n, int K,
                             uint32_t *__restrict__ sums, const uint32_t *gate, const int *Kp,
-                            const uint32_t *const *in_p, uint32_t thr) {
+                            const uint32_t *const *in_p, uint32_t thr, const uint32_t *thr_p) {
     if (gate && !*gate) return;
     if (Kp) K = *Kp;
+    if (thr_p) thr = *thr_p;
     if (in_p) in = *in_p;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t s = 0;
@@ -90,9 +91,10 @@ __global__ void k_scan_sums(uint32_t *__restrict__ sums, uint32_t tiles, const u
 __global__ void k_tile_scan(const uint32_t *__restrict__ in, uint32_t n, int K,
                             const uint32_t *__restrict__ sums, uint32_t tiles,
                             uint32_t *__restrict__ out, const uint32_t *gate, const int *Kp,
-                            const uint32_t *const *in_p, uint32_t thr) {
+                            const uint32_t *const *in_p, uint32_t thr, const uint32_t *thr_p) {
     if (gate && !*gate) return;
     if (Kp) K = *Kp;
+    if (thr_p) thr = *thr_p;
     if (in_p) in = *in_p;
     uint32_t base = blockIdx.x * kTile + threadIdx.x * kPer;
     uint32_t v[kPer];
@@ -122,17 +124,19 @@ inline size_t scan_temp_bytes(uint32_t n) {
 // `out` nor `tmp`.  With a `gate` (device word), the scan does nothing when
 // the word is zero at execution time.  With `Kp` (device word), K is read
 // from it at execution time instead, and with `in_p` (a device word holding
-// a pointer), the input array.  `thr`: see elem().
+// a pointer), the input array.  `thr`: see elem(); with `thr_p` (device
+// word) it is read from there at execution time.
 inline int scan_exclusive(const uint32_t *in, uint32_t *out, uint32_t n, int K, void *tmp,
                           cudaStream_t s, const uint32_t *gate = nullptr, const int *Kp = nullptr,
-                          const uint32_t *const *in_p = nullptr, uint32_t thr = 0) {
+                          const uint32_t *const *in_p = nullptr, uint32_t thr = 0,
+                          const uint32_t *thr_p = nullptr) {
     using namespace scan_detail;
     uint32_t tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) tiles = 1;
     uint32_t *sums = (uint32_t *)tmp;
-    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate, Kp, in_p, thr);
+    k_tile_sums<<<tiles, kThreads, 0, s>>>(in, n, K, sums, gate, Kp, in_p, thr, thr_p);
     k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, gate);
-    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate, Kp, in_p, thr);
+    k_tile_scan<<<tiles, kThreads, 0, s>>>(in, n, K, sums, tiles, out, gate, Kp, in_p, thr, thr_p);
     count_launches(3);
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
