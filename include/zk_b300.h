@@ -304,8 +304,9 @@ int zk_fold_tree_levels(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *
 /* Bucket layout of the MSM, per length (value 0 = built-in):
  *   ZK_TUNE_MSM_CHUNK  : 1 + log2 of the round-0 chunk multiplier used when
  *                        few buckets (<= 4096) are in use, value in [1, 4];
- *   ZK_TUNE_MSM_TAIL   : 1 + log2 of the items each lane sums in a slice of
- *                        the team tail (few, full buckets), value in [1, 4];
+ *   ZK_TUNE_MSM_TAIL   : 1 + log2 of the partial sums each lane adds in a
+ *                        slice of the team tail (buckets of many partial
+ *                        sums, e.g. quantised scalars), value in [1, 4];
  *   ZK_TUNE_MSM_SEG    : log2 of the bucket-reduction segment of levels with
  *                        fewer than 2^13 items, value in [3, 5];
  *   ZK_TUNE_MSM_SEGBIG : log2 of the segment of larger levels, in [6, 8].
