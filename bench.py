@@ -64,8 +64,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the comparisons and the serving run")
     ap.add_argument("--serving-jobs", type=int, default=1200, help="jobs of the serving run (Poisson, 20/s)")
-    ap.add_argument("--case", default=None, choices=["msm", "ntt", "fold", "open"],
-                    help="profiling case: two calls of one op at --log2n (for ncu captures)")
+    ap.add_argument("--case", default=None, choices=["msm", "ntt", "fold", "open", "batch"],
+                    help="profiling case: two calls of one op at --log2n (for ncu captures); batch: "
+                         "two batched commitments of --count polynomials of 2^log2n (a fold-tree level)")
+    ap.add_argument("--count", type=int, default=512, help="polynomials of the batch case")
     ap.add_argument("--log2n", type=int, default=18)
     ap.add_argument("--cpu-sample-log", type=int, default=CPU_SAMPLE_LOG,
                     help="log2 points of the oracle MSM sample (cpu_baseline; the reference arm "
@@ -94,6 +96,12 @@ def run_case(args):
         x = dev(Z.fr_uniform(5, n))
         for _ in range(2):
             zk.zk_ntt(ctx, x)
+    elif args.case == "batch":
+        sc = dev(Z.fr_uniform(13, args.count * n)).view(args.count, n, 4)
+        vecs = [sc[i] for i in range(args.count)]
+        out = torch.zeros((args.count, 8), dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            zk.zk_commit_batch(ctx, vecs, out)
     elif args.case == "open":
         c = dev(Z.fr_uniform(11, n + 1))
         pt = dev(Z.fr_uniform(12, 1)[0])
