@@ -447,7 +447,12 @@ int zk_probe_pipes(int device, double *rates);
  *           (0 for 0), ZK_FOP_ADD out = a + b, ZK_FOP_SUB out = a - b,
  *           ZK_FOP_MULSUB out[i] = a[i] b[i] - a[n-1-i] b[n-1-i] (the
  *           difference of two products that point additions and doublings
- *           take for their Y coordinate; F_q reduces it once).
+ *           take for their Y coordinate; F_q reduces it once), ZK_FOP_MULC
+ *           out = a b through the product by a constant with a precomputed
+ *           quotient (the NTT's butterfly twiddles): floor(b 2^256 / p) is
+ *           computed on the device, and element i's first operand is the
+ *           representative a[i] + (i mod 4) p, so the inputs span [0, 4p),
+ *           the range the NTT's lazy butterflies pass it; out is canonical.
  *   a, b, out : DEVICE pointers to n canonical 32-byte little-endian elements
  *           (< modulus; not checked); b is ignored by SQR and INV; out may
  *           alias a or b.  Stream-ordered on `stream`.
@@ -461,6 +466,7 @@ int zk_probe_pipes(int device, double *rates);
 #define ZK_FOP_ADD 3
 #define ZK_FOP_SUB 4
 #define ZK_FOP_MULSUB 5
+#define ZK_FOP_MULC 6
 int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk_fr *out, size_t n, zk_stream stream);
 
 /* Checked build.  Compiled with -DZK_CHECK (`python

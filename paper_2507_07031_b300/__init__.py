@@ -143,7 +143,7 @@ EXPORTED = ["zk_init", "zk_destroy", "zk_lane_create", "zk_srs_load", "zk_srs_ge
 ZK_TUNE_MSM_WINDOW, ZK_TUNE_NTT_RADIX = 0, 1
 ZK_TUNE_MSM_CHUNK, ZK_TUNE_MSM_TAIL, ZK_TUNE_MSM_SEG, ZK_TUNE_MSM_SEGBIG = 2, 3, 4, 5
 ZK_FIELD_Q, ZK_FIELD_R = 0, 1
-ZK_FOP_MUL, ZK_FOP_SQR, ZK_FOP_INV, ZK_FOP_ADD, ZK_FOP_SUB, ZK_FOP_MULSUB = range(6)
+ZK_FOP_MUL, ZK_FOP_SQR, ZK_FOP_INV, ZK_FOP_ADD, ZK_FOP_SUB, ZK_FOP_MULSUB, ZK_FOP_MULC = range(7)
 
 PHASES = ["msm_sort", "msm_accum", "msm_reduce", "ntt", "fold_witness", "fold_instance"]
 

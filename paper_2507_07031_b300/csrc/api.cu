@@ -27,6 +27,8 @@ Shared::~Shared() {
     if (srs.p) cudaFree(srs.p);
     for (auto &b : tw)
         if (b.p) cudaFree(b.p);
+    for (auto &b : tws)
+        if (b.p) cudaFree(b.p);
     for (auto &b : lag)
         if (b.p) cudaFree(b.p);
     if (hide_tab.p) cudaFree(hide_tab.p);

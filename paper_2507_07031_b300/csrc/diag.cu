@@ -192,8 +192,9 @@ extern "C" int zk_probe_pipes(int device, double *rates) {
 // ---------------------------------------------------------------------------
 // zk_field_op: elementwise F_q / F_r arithmetic on canonical vectors, through
 // the same device code the prover uses (Montgomery conversions, product,
-// squaring, inversion, addition, subtraction, and the difference of two
-// products that point additions use), for tests of that code.
+// squaring, inversion, addition, subtraction, the difference of two
+// products that point additions use, and the NTT's product by a constant
+// with a precomputed quotient), for tests of that code.
 // ---------------------------------------------------------------------------
 
 namespace zk {
@@ -205,6 +206,14 @@ __global__ void k_field_op(int op, const uint32_t *__restrict__ a, const uint32_
                            uint32_t *__restrict__ out, size_t n) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (op == ZK_FOP_MULC) {  // plain residues: a + (i mod 4) p times the constant b
+        Fe<P> x = fe_load<P>(a + 8 * i);
+        const Fe<P> w = fe_load<P>(b + 8 * i);
+        const uint32_t pw[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
+        for (size_t m = 0; m < (i & 3); m++) detail::add_words(x.v, pw);
+        fe_store<P>(out + 8 * i, fe_mul_shoup<P>(x, w, fe_shoup_quotient<P>(w)));
+        return;
+    }
     const Fe<P> x = fe_to_mont<P>(fe_load<P>(a + 8 * i));
     Fe<P> y = fe_zero<P>();
     if (op != ZK_FOP_SQR && op != ZK_FOP_INV) y = fe_to_mont<P>(fe_load<P>(b + 8 * i));
@@ -232,7 +241,7 @@ extern "C" int zk_field_op(int field, int op, const zk_fr *a, const zk_fr *b, zk
                            zk_stream stream) {
     using namespace zk;
     if (field != ZK_FIELD_Q && field != ZK_FIELD_R) return ZK_EINVAL;
-    if (op < ZK_FOP_MUL || op > ZK_FOP_MULSUB) return ZK_EINVAL;
+    if (op < ZK_FOP_MUL || op > ZK_FOP_MULC) return ZK_EINVAL;
     if (n == 0) return ZK_OK;
     const bool binary = op != ZK_FOP_SQR && op != ZK_FOP_INV;
     if (!a || !out || (binary && !b) || n > ((size_t)1 << 31)) return ZK_EINVAL;

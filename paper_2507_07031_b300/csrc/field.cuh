@@ -724,6 +724,315 @@ template <class P> ZK_DEV Fe<P> fe_from_mont(const Fe<P> &a) {
 template <class P> ZK_DEV Fe<P> fe_mul3(const Fe<P> &a) { return fe_add<P>(fe_add<P>(a, a), a); }
 
 // ---------------------------------------------------------------------------
+// Products by a constant with a precomputed quotient (V. Shoup's method, as
+// used for NTT twiddles by D. Harvey, "Faster arithmetic for number-theoretic
+// transforms", J. Symb. Comp. 2014), on 256-bit words for a modulus p with
+// 3p < 2^256.  For a constant w < p and wq = floor(w 2^256 / p):
+//   a w mod p = a w - q p  with  q = floor(a wq / 2^256) in {Q - 1, Q},
+// Q = floor(a w / p), for every a < 2^256.  The quotient here is taken from
+// the columns >= 7 of a wq only (the dropped partial products sum to below
+// 2^228, so q loses at most one more unit): q in {Q - 2, Q - 1, Q}, and
+// a w - q p in [0, 3p) is exact in 256 bits, so a w mod 2^256 and q p mod
+// 2^256 (the lower triangles of their products) suffice.  Two conditional
+// subtractions give the canonical result.  207 word products (99 of them
+// high halves) against the Montgomery product's 264 (128).
+// ---------------------------------------------------------------------------
+
+namespace detail {
+
+// Runs of partial products into a word window, each one carry chain:
+//   lo_run: t[C .. C+K-1] += lo(x[XO .. XO+K-1] y); CARRY adds the carry out
+//           into t[C+K], otherwise it is dropped;
+//   hi_run: t[C .. C+K-1] += hi(x[XO .. XO+K-1] y), carry out dropped.
+// Callers drop a carry only where it leaves the window they keep or where
+// the window's bound rules it out.
+template <int C, int XO, int K, bool CARRY, int N>
+ZK_DEV void lo_run(uint32_t (&t)[N], const uint32_t (&x)[8], uint32_t y) {
+    static_assert(K >= 1 && K <= 8 && XO + K <= 8 && C + K + (CARRY ? 1 : 0) <= N, "run out of range");
+    if constexpr (K == 1 && !CARRY)
+        asm("mad.lo.u32 %0, %1, %2, %0;"
+            : "+r"(t[C + 0])
+            : "r"(x[XO + 0]), "r"(y));
+    else if constexpr (K == 1 && CARRY)
+        asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\taddc.u32 %1, %1, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1])
+            : "r"(x[XO + 0]), "r"(y));
+    else if constexpr (K == 2 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %2, %4, %0;\n\tmadc.lo.u32 %1, %3, %4, %1;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(y));
+    else if constexpr (K == 2 && CARRY)
+        asm("mad.lo.cc.u32 %0, %3, %5, %0;\n\tmadc.lo.cc.u32 %1, %4, %5, %1;\n\taddc.u32 %2, %2, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(y));
+    else if constexpr (K == 3 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %3, %6, %0;\n\tmadc.lo.cc.u32 %1, %4, %6, %1;\n\tmadc.lo.u32 %2, %5, %6, %2;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(y));
+    else if constexpr (K == 3 && CARRY)
+        asm("mad.lo.cc.u32 %0, %4, %7, %0;\n\tmadc.lo.cc.u32 %1, %5, %7, %1;\n\tmadc.lo.cc.u32 %2, %6, %7, %2;\n\taddc.u32 %3, %3, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(y));
+    else if constexpr (K == 4 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %4, %8, %0;\n\tmadc.lo.cc.u32 %1, %5, %8, %1;\n\tmadc.lo.cc.u32 %2, %6, %8, %2;\n\tmadc.lo.u32 %3, %7, %8, %3;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(y));
+    else if constexpr (K == 4 && CARRY)
+        asm("mad.lo.cc.u32 %0, %5, %9, %0;\n\tmadc.lo.cc.u32 %1, %6, %9, %1;\n\tmadc.lo.cc.u32 %2, %7, %9, %2;\n\tmadc.lo.cc.u32 %3, %8, %9, %3;\n\taddc.u32 %4, %4, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(y));
+    else if constexpr (K == 5 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %5, %10, %0;\n\tmadc.lo.cc.u32 %1, %6, %10, %1;\n\tmadc.lo.cc.u32 %2, %7, %10, %2;\n\tmadc.lo.cc.u32 %3, %8, %10, %3;\n\tmadc.lo.u32 %4, %9, %10, %4;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(y));
+    else if constexpr (K == 5 && CARRY)
+        asm("mad.lo.cc.u32 %0, %6, %11, %0;\n\tmadc.lo.cc.u32 %1, %7, %11, %1;\n\tmadc.lo.cc.u32 %2, %8, %11, %2;\n\tmadc.lo.cc.u32 %3, %9, %11, %3;\n\tmadc.lo.cc.u32 %4, %10, %11, %4;\n\taddc.u32 %5, %5, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(y));
+    else if constexpr (K == 6 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %6, %12, %0;\n\tmadc.lo.cc.u32 %1, %7, %12, %1;\n\tmadc.lo.cc.u32 %2, %8, %12, %2;\n\tmadc.lo.cc.u32 %3, %9, %12, %3;\n\tmadc.lo.cc.u32 %4, %10, %12, %4;\n\tmadc.lo.u32 %5, %11, %12, %5;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(y));
+    else if constexpr (K == 6 && CARRY)
+        asm("mad.lo.cc.u32 %0, %7, %13, %0;\n\tmadc.lo.cc.u32 %1, %8, %13, %1;\n\tmadc.lo.cc.u32 %2, %9, %13, %2;\n\tmadc.lo.cc.u32 %3, %10, %13, %3;\n\tmadc.lo.cc.u32 %4, %11, %13, %4;\n\tmadc.lo.cc.u32 %5, %12, %13, %5;\n\taddc.u32 %6, %6, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(y));
+    else if constexpr (K == 7 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %7, %14, %0;\n\tmadc.lo.cc.u32 %1, %8, %14, %1;\n\tmadc.lo.cc.u32 %2, %9, %14, %2;\n\tmadc.lo.cc.u32 %3, %10, %14, %3;\n\tmadc.lo.cc.u32 %4, %11, %14, %4;\n\tmadc.lo.cc.u32 %5, %12, %14, %5;\n\tmadc.lo.u32 %6, %13, %14, %6;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(x[XO + 6]), "r"(y));
+    else if constexpr (K == 7 && CARRY)
+        asm("mad.lo.cc.u32 %0, %8, %15, %0;\n\tmadc.lo.cc.u32 %1, %9, %15, %1;\n\tmadc.lo.cc.u32 %2, %10, %15, %2;\n\tmadc.lo.cc.u32 %3, %11, %15, %3;\n\tmadc.lo.cc.u32 %4, %12, %15, %4;\n\tmadc.lo.cc.u32 %5, %13, %15, %5;\n\tmadc.lo.cc.u32 %6, %14, %15, %6;\n\taddc.u32 %7, %7, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6]), "+r"(t[C + 7])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(x[XO + 6]), "r"(y));
+    else if constexpr (K == 8 && !CARRY)
+        asm("mad.lo.cc.u32 %0, %8, %16, %0;\n\tmadc.lo.cc.u32 %1, %9, %16, %1;\n\tmadc.lo.cc.u32 %2, %10, %16, %2;\n\tmadc.lo.cc.u32 %3, %11, %16, %3;\n\tmadc.lo.cc.u32 %4, %12, %16, %4;\n\tmadc.lo.cc.u32 %5, %13, %16, %5;\n\tmadc.lo.cc.u32 %6, %14, %16, %6;\n\tmadc.lo.u32 %7, %15, %16, %7;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6]), "+r"(t[C + 7])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(x[XO + 6]), "r"(x[XO + 7]), "r"(y));
+    else if constexpr (K == 8 && CARRY)
+        asm("mad.lo.cc.u32 %0, %9, %17, %0;\n\tmadc.lo.cc.u32 %1, %10, %17, %1;\n\tmadc.lo.cc.u32 %2, %11, %17, %2;\n\tmadc.lo.cc.u32 %3, %12, %17, %3;\n\tmadc.lo.cc.u32 %4, %13, %17, %4;\n\tmadc.lo.cc.u32 %5, %14, %17, %5;\n\tmadc.lo.cc.u32 %6, %15, %17, %6;\n\tmadc.lo.cc.u32 %7, %16, %17, %7;\n\taddc.u32 %8, %8, 0;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6]), "+r"(t[C + 7]), "+r"(t[C + 8])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(x[XO + 6]), "r"(x[XO + 7]), "r"(y));
+}
+
+template <int C, int XO, int K, int N>
+ZK_DEV void hi_run(uint32_t (&t)[N], const uint32_t (&x)[8], uint32_t y) {
+    static_assert(K >= 1 && K <= 8 && XO + K <= 8 && C + K <= N, "run out of range");
+    if constexpr (K == 1)
+        asm("mad.hi.u32 %0, %1, %2, %0;"
+            : "+r"(t[C + 0])
+            : "r"(x[XO + 0]), "r"(y));
+    else if constexpr (K == 2)
+        asm("mad.hi.cc.u32 %0, %2, %4, %0;\n\tmadc.hi.u32 %1, %3, %4, %1;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(y));
+    else if constexpr (K == 3)
+        asm("mad.hi.cc.u32 %0, %3, %6, %0;\n\tmadc.hi.cc.u32 %1, %4, %6, %1;\n\tmadc.hi.u32 %2, %5, %6, %2;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(y));
+    else if constexpr (K == 4)
+        asm("mad.hi.cc.u32 %0, %4, %8, %0;\n\tmadc.hi.cc.u32 %1, %5, %8, %1;\n\tmadc.hi.cc.u32 %2, %6, %8, %2;\n\tmadc.hi.u32 %3, %7, %8, %3;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(y));
+    else if constexpr (K == 5)
+        asm("mad.hi.cc.u32 %0, %5, %10, %0;\n\tmadc.hi.cc.u32 %1, %6, %10, %1;\n\tmadc.hi.cc.u32 %2, %7, %10, %2;\n\tmadc.hi.cc.u32 %3, %8, %10, %3;\n\tmadc.hi.u32 %4, %9, %10, %4;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(y));
+    else if constexpr (K == 6)
+        asm("mad.hi.cc.u32 %0, %6, %12, %0;\n\tmadc.hi.cc.u32 %1, %7, %12, %1;\n\tmadc.hi.cc.u32 %2, %8, %12, %2;\n\tmadc.hi.cc.u32 %3, %9, %12, %3;\n\tmadc.hi.cc.u32 %4, %10, %12, %4;\n\tmadc.hi.u32 %5, %11, %12, %5;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(y));
+    else if constexpr (K == 7)
+        asm("mad.hi.cc.u32 %0, %7, %14, %0;\n\tmadc.hi.cc.u32 %1, %8, %14, %1;\n\tmadc.hi.cc.u32 %2, %9, %14, %2;\n\tmadc.hi.cc.u32 %3, %10, %14, %3;\n\tmadc.hi.cc.u32 %4, %11, %14, %4;\n\tmadc.hi.cc.u32 %5, %12, %14, %5;\n\tmadc.hi.u32 %6, %13, %14, %6;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(x[XO + 6]), "r"(y));
+    else if constexpr (K == 8)
+        asm("mad.hi.cc.u32 %0, %8, %16, %0;\n\tmadc.hi.cc.u32 %1, %9, %16, %1;\n\tmadc.hi.cc.u32 %2, %10, %16, %2;\n\tmadc.hi.cc.u32 %3, %11, %16, %3;\n\tmadc.hi.cc.u32 %4, %12, %16, %4;\n\tmadc.hi.cc.u32 %5, %13, %16, %5;\n\tmadc.hi.cc.u32 %6, %14, %16, %6;\n\tmadc.hi.u32 %7, %15, %16, %7;"
+            : "+r"(t[C + 0]), "+r"(t[C + 1]), "+r"(t[C + 2]), "+r"(t[C + 3]), "+r"(t[C + 4]), "+r"(t[C + 5]), "+r"(t[C + 6]), "+r"(t[C + 7])
+            : "r"(x[XO + 0]), "r"(x[XO + 1]), "r"(x[XO + 2]), "r"(x[XO + 3]), "r"(x[XO + 4]), "r"(x[XO + 5]), "r"(x[XO + 6]), "r"(x[XO + 7]), "r"(y));
+}
+
+// x - k (k a multiple of p) when x >= k; returns whether it subtracted.
+ZK_DEV bool cond_sub_words(uint32_t (&x)[8], const uint32_t (&k)[8]) {
+    uint32_t d[8], borrow;
+    asm("sub.cc.u32 %0, %9, %17;\n\t"
+        "subc.cc.u32 %1, %10, %18;\n\t"
+        "subc.cc.u32 %2, %11, %19;\n\t"
+        "subc.cc.u32 %3, %12, %20;\n\t"
+        "subc.cc.u32 %4, %13, %21;\n\t"
+        "subc.cc.u32 %5, %14, %22;\n\t"
+        "subc.cc.u32 %6, %15, %23;\n\t"
+        "subc.cc.u32 %7, %16, %24;\n\t"
+        "subc.u32 %8, 0, 0;"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]),
+          "=r"(d[7]), "=r"(borrow)
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]),
+          "r"(x[7]), "r"(k[0]), "r"(k[1]), "r"(k[2]), "r"(k[3]), "r"(k[4]), "r"(k[5]),
+          "r"(k[6]), "r"(k[7]));
+    // borrow = 0xffffffff when x < k: keep x.
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = (x[i] & borrow) | (d[i] & ~borrow);
+    return borrow == 0;
+}
+
+// t[0..7] += x y mod 2^256 for row multipliers y_i = Y(i): the lower
+// triangle (lo(x_j y_i) for i + j <= 7, hi(x_j y_i) for i + j <= 6).
+template <int I, class Y> ZK_DEV void low_row(uint32_t (&t)[8], const uint32_t (&x)[8], Y y) {
+    lo_run<I, 0, 8 - I, false>(t, x, y(I));
+    if constexpr (I < 7) hi_run<I + 1, 0, 7 - I>(t, x, y(I));
+}
+template <class Y> ZK_DEV void low_product_add(uint32_t (&t)[8], const uint32_t (&x)[8], Y y) {
+    low_row<0>(t, x, y);
+    low_row<1>(t, x, y);
+    low_row<2>(t, x, y);
+    low_row<3>(t, x, y);
+    low_row<4>(t, x, y);
+    low_row<5>(t, x, y);
+    low_row<6>(t, x, y);
+    low_row<7>(t, x, y);
+}
+
+// Word i of 2^256 - p (p odd, so only word 0 takes the +1).
+template <class P> constexpr uint32_t neg_p(int i) { return i == 0 ? 0u - P::p(0) : ~P::p(i); }
+
+// Row i of the quotient: columns >= 7 of a_i wq, into t[7 .. i+8] (each
+// partial sum a[0..i] wq / 2^224 fits in those i + 2 words).
+template <int I> ZK_DEV void quot_row(uint32_t (&t)[17], const uint32_t (&wq)[8], uint32_t ai) {
+    lo_run<7, 7 - I, I + 1, true>(t, wq, ai);
+    if constexpr (I < 7) hi_run<7, 6 - I, I + 2>(t, wq, ai);
+    else hi_run<8, 0, 8>(t, wq, ai);
+}
+
+}  // namespace detail
+
+namespace detail {
+template <class P> struct Multiples {
+    static constexpr uint32_t p1(int i) { return P::p(i); }
+    static constexpr uint32_t p2(int i) { return (P::p(i) << 1) | (i ? P::p(i - 1) >> 31 : 0u); }
+};
+template <class P> ZK_DEV void cond_sub_p(uint32_t (&x)[8]) {
+    const uint32_t k[8] = {Multiples<P>::p1(0), Multiples<P>::p1(1), Multiples<P>::p1(2), Multiples<P>::p1(3),
+                           Multiples<P>::p1(4), Multiples<P>::p1(5), Multiples<P>::p1(6), Multiples<P>::p1(7)};
+    cond_sub_words(x, k);
+}
+template <class P> ZK_DEV void cond_sub_2p(uint32_t (&x)[8]) {
+    const uint32_t k[8] = {Multiples<P>::p2(0), Multiples<P>::p2(1), Multiples<P>::p2(2), Multiples<P>::p2(3),
+                           Multiples<P>::p2(4), Multiples<P>::p2(5), Multiples<P>::p2(6), Multiples<P>::p2(7)};
+    cond_sub_words(x, k);
+}
+// x += y, carry out dropped (callers keep the sum below 2^256).
+ZK_DEV void add_words(uint32_t (&x)[8], const uint32_t (&y)[8]) {
+    asm("add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32 %7, %7, %15;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(x[7])
+        : "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]), "r"(y[6]), "r"(y[7]));
+}
+}  // namespace detail
+
+// a w mod p in [0, 2p) for any a < 2^256, w < p canonical and
+// wq = floor(w 2^256 / p) (requires 3p < 2^256).  Plain residues (no
+// Montgomery factor).
+template <class P> ZK_DEV Fe<P> fe_mul_shoup_2p(const Fe<P> &a, const Fe<P> &w, const Fe<P> &wq) {
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = 0;
+    detail::quot_row<0>(t, wq.v, a.v[0]);
+    detail::quot_row<1>(t, wq.v, a.v[1]);
+    detail::quot_row<2>(t, wq.v, a.v[2]);
+    detail::quot_row<3>(t, wq.v, a.v[3]);
+    detail::quot_row<4>(t, wq.v, a.v[4]);
+    detail::quot_row<5>(t, wq.v, a.v[5]);
+    detail::quot_row<6>(t, wq.v, a.v[6]);
+    detail::quot_row<7>(t, wq.v, a.v[7]);
+    uint32_t q[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) q[i] = t[8 + i];
+    // a w - q p = a w + q (2^256 - p) mod 2^256, in one accumulator: the
+    // quotient's product first (q dies), then a w.
+    Fe<P> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = 0;
+    detail::low_product_add(r.v, q, [](int i) { return detail::neg_p<P>(i); });
+    detail::low_product_add(r.v, w.v, [&](int i) { return a.v[i]; });
+    detail::cond_sub_2p<P>(r.v);  // [0, 3p) -> [0, 2p)
+    return r;
+}
+
+// The same, canonical.
+template <class P> ZK_DEV Fe<P> fe_mul_shoup(const Fe<P> &a, const Fe<P> &w, const Fe<P> &wq) {
+    Fe<P> r = fe_mul_shoup_2p<P>(a, w, wq);
+    detail::cond_sub_p<P>(r.v);
+    return r;
+}
+
+// Values kept in [0, 2p) (requires 4p < 2^256):
+//   fe_add_2p:      a + b reduced to [0, 2p);
+//   fe_sub_2p_lazy: a - b + 2p in (0, 4p), a valid first operand of fe_mul_shoup_2p;
+//   fe_sub_2p:      the same reduced to [0, 2p);
+//   fe_canon_2p:    [0, 2p) -> canonical.
+template <class P> ZK_DEV Fe<P> fe_add_2p(const Fe<P> &a, const Fe<P> &b) {
+    Fe<P> s = a;
+    detail::add_words(s.v, b.v);
+    detail::cond_sub_2p<P>(s.v);
+    return s;
+}
+template <class P> ZK_DEV Fe<P> fe_sub_2p_lazy(const Fe<P> &a, const Fe<P> &b) {
+    Fe<P> d;
+    asm("sub.cc.u32 %0, %8, %16;\n\t"
+        "subc.cc.u32 %1, %9, %17;\n\t"
+        "subc.cc.u32 %2, %10, %18;\n\t"
+        "subc.cc.u32 %3, %11, %19;\n\t"
+        "subc.cc.u32 %4, %12, %20;\n\t"
+        "subc.cc.u32 %5, %13, %21;\n\t"
+        "subc.cc.u32 %6, %14, %22;\n\t"
+        "subc.u32 %7, %15, %23;"
+        : "=r"(d.v[0]), "=r"(d.v[1]), "=r"(d.v[2]), "=r"(d.v[3]), "=r"(d.v[4]), "=r"(d.v[5]),
+          "=r"(d.v[6]), "=r"(d.v[7])
+        : "r"(detail::Multiples<P>::p2(0)), "r"(detail::Multiples<P>::p2(1)), "r"(detail::Multiples<P>::p2(2)),
+          "r"(detail::Multiples<P>::p2(3)), "r"(detail::Multiples<P>::p2(4)), "r"(detail::Multiples<P>::p2(5)),
+          "r"(detail::Multiples<P>::p2(6)), "r"(detail::Multiples<P>::p2(7)), "r"(b.v[0]), "r"(b.v[1]),
+          "r"(b.v[2]), "r"(b.v[3]), "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));  // 2p - b
+    detail::add_words(d.v, a.v);
+    return d;
+}
+template <class P> ZK_DEV Fe<P> fe_sub_2p(const Fe<P> &a, const Fe<P> &b) {
+    Fe<P> d = fe_sub_2p_lazy<P>(a, b);
+    detail::cond_sub_2p<P>(d.v);
+    return d;
+}
+template <class P> ZK_DEV Fe<P> fe_canon_2p(const Fe<P> &a) {
+    Fe<P> r = a;
+    detail::cond_sub_p<P>(r.v);
+    return r;
+}
+
+// floor(w 2^256 / p) for a canonical w (bit-serial long division; table
+// set-up only).
+template <class P> ZK_DEV Fe<P> fe_shoup_quotient(const Fe<P> &w) {
+    uint32_t rem[8], q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t p1[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
+#pragma unroll
+    for (int i = 0; i < 8; i++) rem[i] = w.v[i];
+    for (int bit = 255; bit >= 0; bit--) {
+        // rem < p < 2^255, so 2 rem fits in 256 bits.
+#pragma unroll
+        for (int i = 7; i > 0; i--) rem[i] = (rem[i] << 1) | (rem[i - 1] >> 31);
+        rem[0] <<= 1;
+        if (detail::cond_sub_words(rem, p1)) q[bit >> 5] |= 1u << (bit & 31);
+    }
+    Fe<P> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = q[i];
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Inversion of a canonical (non-Montgomery) value by Bernstein-Yang divsteps
 // (D. J. Bernstein, B.-Y. Yang, "Fast constant-time gcd computation and
 // modular inversion", TCHES 2019), run in variable time: the values inverted

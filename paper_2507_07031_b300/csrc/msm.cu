@@ -1076,11 +1076,12 @@ int default_window(size_t n) {
 }  // namespace
 
 // Built-in bucket layout, the winners of a tuning sweep on B300 (int8 x 2^16
-// and uniform scalars, 2^16 .. 2^20): chunk multiplier 1, eight items per
-// lane in a tail slice, reduction segments of 2^4 and 2^6 (2^8 above 2^18
+// and uniform scalars, 2^16 .. 2^20; leaf commitments of 2^12): chunk
+// multiplier 1, eight items per lane in a tail slice, reduction segments of
+// 2^4 (2^5 up to 2^13 points, one team level fewer) and 2^6 (2^8 above 2^18
 // points).
 MsmLayout msm_layout(const Shared &sh, int lg) {
-    MsmLayout m{0, 3, 4, lg <= 18 ? 6u : 8u};
+    MsmLayout m{0, 3, lg <= 13 ? 5u : 4u, lg <= 18 ? 6u : 8u};
     if (lg < 0 || lg > kMaxLogN) return m;
     if (sh.tuned_layout[0][lg]) m.chunk_log = (uint32_t)sh.tuned_layout[0][lg] - 1;
     if (sh.tuned_layout[1][lg]) m.tail_log = (uint32_t)sh.tuned_layout[1][lg] - 1;

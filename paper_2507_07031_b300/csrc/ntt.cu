@@ -16,8 +16,13 @@
 // positions back in natural order.  Global loads and stores move runs of J
 // consecutive 32-byte elements (J R contiguous ones in the first pass).
 //
-// Data stay canonical: twiddles are stored in Montgomery form, so
-// mont(x, w R) = x w is already canonical and no conversion pass is needed.
+// Data are canonical in memory.  The inter-pass twiddles are stored in
+// Montgomery form, so mont(x, w R) = x w is already canonical.  Inside a
+// pass the butterflies keep values in [0, 2r) (4r < 2^256): their stage
+// twiddles come from a table of (w, floor(w 2^256 / r)) pairs and use the
+// precomputed-quotient product (fe_mul_shoup_2p, 22 % fewer multiply-pipe
+// cycles than a Montgomery product) on the lazy difference x - y + 2r; the
+// store reduces to canonical.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -81,12 +86,28 @@ __global__ void k_twiddles(const Fr *__restrict__ root, uint32_t lg, Fr *__restr
     }
 }
 
+// Stage-twiddle table: tws[k] = (w^k, floor(w^k 2^256 / r)), both canonical,
+// 16 words per entry, from the Montgomery table tw (one thread per entry).
+__global__ void k_stage_twiddles(const Fr *__restrict__ tw, uint32_t n, uint32_t *__restrict__ tws) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const Fr w = fe_from_mont<FrP>(tw[k]);
+    fe_store<FrP>(tws + 16 * (size_t)k, w);
+    fe_store<FrP>(tws + 16 * (size_t)k + 8, fe_shoup_quotient<FrP>(w));
+}
+
+// Butterfly difference (x - y) w_pos in [0, 2r) for x, y in [0, 2r) and a
+// stage twiddle entry (w, wq).
+__device__ __forceinline__ Fr stage_diff(const Fr &x, const Fr &y, const uint32_t *e) {
+    return fe_mul_shoup_2p<FrP>(fe_sub_2p_lazy<FrP>(x, y), fe_ldg<FrP>(e), fe_ldg<FrP>(e + 8));
+}
+
 struct PassArgs {
     const uint32_t *const *in_tab;  // per vector (blockIdx.y)
     uint32_t *const *out_tab;
     uint32_t logn, logR, logNs, J, logJ;  // J = 2^logJ sub-transforms per CTA
     const Fr *tw_n;  // size-n table (+ n^{-1} at index n)
-    const Fr *tw_R;  // size-R table
+    const uint32_t *tw_S;  // size-R stage table (w, wq), 16 words per entry
     int inverse;
     int scale;  // multiply outputs by n^{-1}
 };
@@ -141,12 +162,14 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
                 x.v[l] = sm[l * JR + i0];
                 y.v[l] = sm[l * JR + i1];
             }
-            Fr s = fe_add<FrP>(x, y);
-            Fr d = fe_sub<FrP>(x, y);
+            Fr s = fe_add_2p<FrP>(x, y);
+            Fr d;
             if (pos) {
                 uint32_t idx = pos << (a.logR - lh);
                 if (a.inverse) idx = R - idx;
-                d = fe_mul<FrP>(d, fe_ldg<FrP>(a.tw_R + idx));
+                d = stage_diff(x, y, a.tw_S + 16 * idx);
+            } else {
+                d = fe_sub_2p<FrP>(x, y);
             }
 #pragma unroll
             for (int l = 0; l < 8; l++) {
@@ -176,7 +199,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
         Fr x;
 #pragma unroll
         for (int l = 0; l < 8; l++) x.v[l] = sm[l * JR + src * J + jj];
-        if (a.scale) x = fe_mul<FrP>(x, sc);
+        x = a.scale ? fe_mul<FrP>(x, sc) : fe_canon_2p<FrP>(x);  // [0, 2r) -> canonical
         uint64_t dst = ((j >> a.logNs) << (a.logNs + a.logR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
         if (ZK_FAILED(dst < n, kCheckNttIdx)) continue;
         fe_store<FrP>(out + 8 * dst, x);
@@ -203,7 +226,7 @@ constexpr int kRegLE = 2;  // log2 elements per thread
 __device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
 
 template <int LR>
-__global__ void __launch_bounds__(512) k_ntt_reg(PassArgs a) {
+__global__ void __launch_bounds__(512, 2) k_ntt_reg(PassArgs a) {
     extern __shared__ uint32_t sm[];
     constexpr uint32_t R = 1u << LR, E = 1u << kRegLE;
     const uint32_t LJ = a.logJ, J = 1u << LJ, JR = J * R;
@@ -283,16 +306,16 @@ __global__ void __launch_bounds__(512) k_ntt_reg(PassArgs a) {
                 if (k & hk) continue;
                 const uint32_t k2 = k + hk;
                 const Fr u = x[k], v = x[k2];
-                x[k] = fe_add<FrP>(u, v);
-                Fr d = fe_sub<FrP>(u, v);
+                x[k] = fe_add_2p<FrP>(u, v);
                 // pos = r mod h with h = S 2^(ne - 1 - ls)
                 const uint32_t pos = elem_r(g, k) & ((R >> (s + 1)) - 1);
                 if (pos) {
                     uint32_t idx = pos << s;
                     if (a.inverse) idx = R - idx;
-                    d = fe_mul<FrP>(d, fe_ldg<FrP>(a.tw_R + idx));
+                    x[k2] = stage_diff(u, v, a.tw_S + 16 * idx);
+                } else {
+                    x[k2] = fe_sub_2p<FrP>(u, v);
                 }
-                x[k2] = d;
             }
         }
     }
@@ -325,7 +348,7 @@ __global__ void __launch_bounds__(512) k_ntt_reg(PassArgs a) {
         Fr v;
 #pragma unroll
         for (int l = 0; l < 8; l++) v.v[l] = sm[l * P + w];
-        if (a.scale) v = fe_mul<FrP>(v, sc);
+        v = a.scale ? fe_mul<FrP>(v, sc) : fe_canon_2p<FrP>(v);  // [0, 2r) -> canonical
         const uint64_t dst = ((j >> a.logNs) << (a.logNs + LR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
         if (ZK_FAILED(dst < n, kCheckNttIdx)) continue;
         fe_store<FrP>(out + 8 * dst, v);
@@ -453,16 +476,36 @@ int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
     return ZK_OK;
 }
 
+// The stage-twiddle table of 2^lg points (lg <= kMaxRadixLog), built once.
+static int stage_twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
+    if (lg < 0 || lg > kMaxRadixLog) return ZK_EINVAL;
+    const uint32_t *tw;
+    ZK_TRY(twiddles(ctx, lg, &tw, s));  // takes the shared lock itself
+    Shared &sh = *ctx->sh;
+    std::lock_guard<std::mutex> g(sh.mu);
+    DevBuf &b = sh.tws[lg];
+    if (!b.p) {
+        const uint32_t n = 1u << lg;
+        ZK_TRY(dev_alloc(sh, b, (size_t)n * 64));
+        k_stage_twiddles<<<(n + 127) / 128, 128, 0, s>>>((const Fr *)tw, n, (uint32_t *)b.p);
+        ZK_LAUNCHED();
+        // Shared read-only with lanes on other streams: finish before use.
+        ZK_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    *out = (const uint32_t *)b.p;
+    return ZK_OK;
+}
+
 // Built-in largest pass radix (log2) when none is tuned: the fastest choices
-// of an autotuner sweep on B300.  Up to 2^20 the shared-memory pass with
-// radices 2^6 .. 2^8 wins (small CTAs, many resident per SM; at 2^20 it also
-// won with L2 flushed before the call, 0.348 vs 0.376 ms); from 2^21 on, two
-// register-tiled passes of radix 2^10 .. 2^11 (half the DRAM passes of four).
+// of an autotuner sweep on B300.  Up to 2^18 the shared-memory pass with
+// radices 2^6 .. 2^8 wins (small CTAs, many resident per SM); from 2^19 on,
+// two register-tiled passes (2^10 + 2^9 .. 2^11 + 2^11), half the DRAM
+// passes of four and two stages per shared-memory exchange.
 static int default_radix(int L) {
     if (L <= 9) return L ? L : 1;
     if (L <= 16) return 6;
-    if (L == 17 || L == 19 || L == 20) return 8;
-    if (L == 18) return 7;
+    if (L <= 18) return 8;
+    if (L <= 20) return 10;
     return 11;  // 2^21 .. : two register-tiled passes
 }
 
@@ -511,8 +554,8 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
     PhaseScope ph(ctx, ZK_PHASE_NTT, s);
     for (int p = 0; p < P; p++) {
         const int logR = passes[p];
-        const uint32_t *tw_R;
-        ZK_TRY(twiddles(ctx, logR, &tw_R, s));
+        const uint32_t *tw_S;
+        ZK_TRY(stage_twiddles(ctx, logR, &tw_S, s));
         PassArgs a;
         a.in_tab = (const uint32_t *const *)(tabs + p * tab_words);
         a.out_tab = (uint32_t *const *)(tabs + p * tab_words + count);
@@ -530,7 +573,7 @@ static int ntt_group(zk_ctx *ctx, uint32_t *const *data_h, size_t count, size_t 
         a.logJ = 0;
         while ((1u << a.logJ) < a.J) a.logJ++;
         a.tw_n = (const Fr *)tw_n;
-        a.tw_R = (const Fr *)tw_R;
+        a.tw_S = tw_S;
         a.inverse = inverse ? 1 : 0;
         a.scale = (inverse && p == P - 1) ? 1 : 0;
         const uint32_t JR = a.J << logR;

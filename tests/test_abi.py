@@ -33,5 +33,5 @@ def test_error_paths_without_device():
     assert z.lib.zk_fold(None, None, None, None, None, None, None) == z.ZK_EINVAL
     assert z.lib.zk_field_op(7, z.ZK_FOP_MUL, None, None, None, 1, None) == z.ZK_EINVAL
     assert z.lib.zk_field_op(z.ZK_FIELD_Q, z.ZK_FOP_MUL, None, None, None, 1, None) == z.ZK_EINVAL
-    assert z.lib.zk_field_op(z.ZK_FIELD_Q, z.ZK_FOP_MULSUB + 1, None, None, None, 1, None) == z.ZK_EINVAL
+    assert z.lib.zk_field_op(z.ZK_FIELD_Q, z.ZK_FOP_MULC + 1, None, None, None, 1, None) == z.ZK_EINVAL
     assert z.lib.zk_field_op(z.ZK_FIELD_Q, z.ZK_FOP_MULSUB, None, None, None, 1, None) == z.ZK_EINVAL

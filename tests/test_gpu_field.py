@@ -63,6 +63,33 @@ def test_field_ops_match_oracle(zk, orc, field):
 
 
 @pytest.mark.parametrize("field", ["q", "r"])
+def test_field_mul_by_constant_matches_oracle(zk, orc, field):
+    """The product by a constant with a precomputed quotient (ZK_FOP_MULC,
+    the NTT's butterfly product): every pair of carry-edge values and
+    uniform pairs, each first operand fed as all four representatives
+    a + m p, m < 4 (elements 4j .. 4j + 3), so the quotient's truncation
+    and both corrections are exercised up to the top of [0, 4p); the
+    result must be the canonical a b mod p."""
+    import torch
+    M = Z.Q_MOD if field == "q" else Z.R_MOD
+    f_orc = orc.FQ if field == "q" else orc.FR
+    f_dev = zk.ZK_FIELD_Q if field == "q" else zk.ZK_FIELD_R
+    edge = _edge(M)
+    rng = np.random.default_rng(41 if field == "q" else 43)
+    uni = [int.from_bytes(rng.bytes(32), "little") % M for _ in range(1000)]
+    a = [x for x in edge for _ in edge] + uni
+    b = [y for _ in edge for y in edge] + uni[::-1]
+    A, B = np.repeat(_limbs(a), 4, axis=0), np.repeat(_limbs(b), 4, axis=0)
+    out = torch.zeros((A.shape[0], 4), dtype=torch.int64, device="cuda")
+    zk.zk_field_op(f_dev, zk.ZK_FOP_MULC, to_dev(A), to_dev(B), out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    want = np.repeat(np.stack([orc.fmul(f_orc, _limbs([x])[0], _limbs([y])[0]) for x, y in zip(a, b)]), 4, axis=0)
+    bad = np.nonzero(~np.all(got == want, axis=1))[0]
+    assert bad.size == 0, [(a[i // 4], b[i // 4], i % 4) for i in bad[:4]]
+
+
+@pytest.mark.parametrize("field", ["q", "r"])
 def test_field_mul_sub_mul_matches_oracle(zk, orc, field):
     """a_i b_i - a_m b_m with m = n - 1 - i (ZK_FOP_MULSUB), the form every
     point addition and doubling takes for Y; F_q reduces the 512-bit
