@@ -52,7 +52,7 @@ struct Shared {
     size_t srs_n = 0;
     DevBuf srs;  // affine Montgomery, srs_n points
     std::deque<WindowTable> tables;  // deque: references stay valid as tables are added
-    DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg
+    DevBuf tw[29];  // tw[lg][k] = omega_{2^lg}^k in Montgomery form, k < 2^lg; then n^-1 entries
     DevBuf tws[12];  // tws[lg][k] = (omega_{2^lg}^k, floor(omega_{2^lg}^k 2^256 / r)), canonical, k < 2^lg
     DevBuf lag[29];              // lag[lg][k] = [L_k(tau)]_1 over H of size 2^lg (affine Montgomery)
     int commit_route = 0;        // ZK_ROUTE_INTT or ZK_ROUTE_LAGRANGE for evaluation-form commitments

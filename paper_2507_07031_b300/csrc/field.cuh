@@ -22,7 +22,8 @@
 namespace zk {
 
 // Compile-time limb tables.  `p` is the modulus, `one` = R mod p, `r2` =
-// R^2 mod p, `r3` = R^3 mod p, `half` = (p - 1) / 2, `n0` = -p^{-1} mod 2^32.
+// R^2 mod p, `r3` = R^3 mod p, `half` = (p - 1) / 2, `ninv` = -p^{-1} mod
+// 2^256, `n0` = -p^{-1} mod 2^32 (its low word).
 struct FqP {
     static ZK_HD constexpr uint32_t p(int i) {
         constexpr uint32_t v[8] = {0xd87cfd47u, 0x3c208c16u, 0x6871ca8du, 0x97816a91u,
@@ -47,6 +48,11 @@ struct FqP {
     static ZK_HD constexpr uint32_t half(int i) {
         constexpr uint32_t v[8] = {0x6c3e7ea3u, 0x9e10460bu, 0xb438e546u, 0xcbc0b548u,
                                    0x40c0ac2eu, 0xdc2822dbu, 0x7098d014u, 0x18322739u};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t ninv(int i) {
+        constexpr uint32_t v[8] = {0xe4866389u, 0x87d20782u, 0x1eca6ac9u, 0x9ede7d65u,
+                                   0x1833da80u, 0xd8afcbd0u, 0x91888c6bu, 0xf57a22b7u};
         return v[i];
     }
     static constexpr uint32_t n0 = 0xe4866389u;
@@ -76,6 +82,11 @@ struct FrP {
     static ZK_HD constexpr uint32_t half(int i) {
         constexpr uint32_t v[8] = {0xf8000000u, 0xa1f0fac9u, 0x3cdcb848u, 0x9419f424u,
                                    0x40c0ac2eu, 0xdc2822dbu, 0x7098d014u, 0x18322739u};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t ninv(int i) {
+        constexpr uint32_t v[8] = {0xefffffffu, 0xc2e1f593u, 0x4c6911b3u, 0x6586864bu,
+                                   0x99062391u, 0xe39a9828u, 0x0d8341b2u, 0x73f82f1du};
         return v[i];
     }
     static constexpr uint32_t n0 = 0xefffffffu;
@@ -1012,24 +1023,21 @@ template <class P> ZK_DEV Fe<P> fe_canon_2p(const Fe<P> &a) {
     return r;
 }
 
-// floor(w 2^256 / p) for a canonical w (bit-serial long division; table
-// set-up only).
+// floor(w 2^256 / p) from w's Montgomery form m = w 2^256 mod p (w < p):
+// w 2^256 - m is an exact multiple of p, so the quotient is
+// (w 2^256 - m) p^-1 = -m p^-1 mod 2^256 (it is below 2^256 as w < p), one
+// lower-triangle product with the constant -p^-1 mod 2^256.
+template <class P> ZK_DEV Fe<P> fe_shoup_quotient_mont(const Fe<P> &m) {
+    Fe<P> q;
+#pragma unroll
+    for (int i = 0; i < 8; i++) q.v[i] = 0;
+    detail::low_product_add(q.v, m.v, [](int i) { return P::ninv(i); });
+    return q;
+}
+
+// The same from the canonical w.
 template <class P> ZK_DEV Fe<P> fe_shoup_quotient(const Fe<P> &w) {
-    uint32_t rem[8], q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const uint32_t p1[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
-#pragma unroll
-    for (int i = 0; i < 8; i++) rem[i] = w.v[i];
-    for (int bit = 255; bit >= 0; bit--) {
-        // rem < p < 2^255, so 2 rem fits in 256 bits.
-#pragma unroll
-        for (int i = 7; i > 0; i--) rem[i] = (rem[i] << 1) | (rem[i - 1] >> 31);
-        rem[0] <<= 1;
-        if (detail::cond_sub_words(rem, p1)) q[bit >> 5] |= 1u << (bit & 31);
-    }
-    Fe<P> r;
-#pragma unroll
-    for (int i = 0; i < 8; i++) r.v[i] = q[i];
-    return r;
+    return fe_shoup_quotient_mont<P>(fe_to_mont<P>(w));
 }
 
 // ---------------------------------------------------------------------------

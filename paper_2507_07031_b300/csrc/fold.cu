@@ -13,8 +13,10 @@
 // Degree 3 has two cross terms (the gamma^1 and gamma^2 coefficients of
 // R(gamma L + R)), e1 and e2, committed as E1, E2, and
 //   e'' = e' + gamma e1 + gamma^2 e2 + gamma^3 e,  E'' = E' + gamma E1 + gamma^2 E2 + gamma^3 E.
-// Field vectors are canonical; gamma and mu are moved into Montgomery form
-// once per thread so that mont(x, gamma R) = gamma x stays canonical.
+// Field vectors are canonical.  The per-fold constants (gamma and its powers
+// in Montgomery form, so that mont(x, gamma R) = gamma x stays canonical;
+// gamma's precomputed quotient for the witness RLC; the mu coefficients of
+// the cross terms) are computed once per fold by K4c, not by every thread.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +29,17 @@
 namespace zk {
 
 namespace {
+
+// Per-fold constants of the witness pass (device workspace, written by
+// k_fold_consts).  Montgomery form where marked, canonical otherwise.
+struct FoldConsts {
+    Fr g, g2, g3;  // gamma, gamma^2, gamma^3 (Montgomery)
+    Fr gc, gq;     // gamma and floor(gamma 2^256 / r): the RLC product m'' = gamma m + m'
+    Fr kc, kq;     // the cross terms' conversion factor (R mod r for degree 2, R^2 mod r
+                   // for degree 3) and its quotient
+    Fr c0, c1, c2;  // degree 2: r - mu, r - mu'; degree 3: -mu^2 R^-1, -mu'^2 R^-1,
+                    // -2 mu mu' R^-1
+};
 
 struct FoldDesc {
     const uint32_t *Lm[4];
@@ -44,40 +57,72 @@ struct FoldDesc {
     uint32_t *e2;           // degree 3: second cross term (workspace)
     uint32_t *E2;           // degree 3: its commitment
     uint32_t deg;           // 2 or 3
+    FoldConsts *fc;         // this fold's constants (device workspace)
 };
 
 constexpr int kInstMu = 40 * 2;  // word offset of mu in zk_acc_inst (5 points x 16 words)
 
+// K4c: the per-fold constants, one thread per fold.
+__global__ void k_fold_consts(const FoldDesc *__restrict__ descs, uint32_t F) {
+    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const FoldDesc &d = descs[f];
+    FoldConsts &c = *d.fc;
+    const Fr gc = fe_load<FrP>(d.gamma);
+    const Fr g = fe_to_mont<FrP>(gc);
+    const Fr g2 = fe_mul<FrP>(g, g);
+    fe_store<FrP>(c.g.v, g);
+    fe_store<FrP>(c.g2.v, g2);
+    fe_store<FrP>(c.g3.v, fe_mul<FrP>(g2, g));
+    fe_store<FrP>(c.gc.v, gc);
+    fe_store<FrP>(c.gq.v, fe_shoup_quotient_mont<FrP>(g));
+    const Fr uL = fe_load<FrP>(d.Lx + kInstMu), uR = fe_load<FrP>(d.Rx + kInstMu);
+    Fr kc;
+    if (d.deg == 3) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) kc.v[i] = FrP::r2(i);  // R^2 mod r as a plain residue
+        fe_store<FrP>(c.c0.v, fe_neg<FrP>(fe_mul<FrP>(uL, uL)));
+        fe_store<FrP>(c.c1.v, fe_neg<FrP>(fe_mul<FrP>(uR, uR)));
+        fe_store<FrP>(c.c2.v, fe_neg<FrP>(fe_dbl<FrP>(fe_mul<FrP>(uL, uR))));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; i++) kc.v[i] = FrP::one(i);  // R mod r as a plain residue
+        fe_store<FrP>(c.c0.v, fe_neg<FrP>(uL));
+        fe_store<FrP>(c.c1.v, fe_neg<FrP>(uR));
+        fe_store<FrP>(c.c2.v, fe_zero<FrP>());
+    }
+    fe_store<FrP>(c.kc.v, kc);
+    fe_store<FrP>(c.kq.v, fe_shoup_quotient<FrP>(kc));
+}
+
 // K4: cross terms and witness RLC, grid (elements, folds); one instance per
-// relation degree.  Both fit two blocks per SM (128 registers; degree 3 with
-// a 32-byte spill), twice the warps that one block at ~190-240 registers
-// gave, which the pass needs to keep its product chains issuing.
+// relation degree.  Both fit two blocks per SM (at most 128 registers, no
+// spill), twice the warps that one block at ~190-240 registers gave, which
+// the pass needs to keep its product chains issuing.  The RLC products by
+// gamma and the cross terms' conversion factor are products by a per-fold
+// constant, taken with its precomputed quotient (fe_mul_shoup).
 template <int DEG>
 __global__ void __launch_bounds__(256, 2)
     k_fold_witness(const FoldDesc *__restrict__ descs, uint32_t n) {
     const FoldDesc &d = descs[blockIdx.y];
-    const Fr r2 = fe_r2<FrP>();
-    const Fr g = fe_to_mont<FrP>(fe_load<FrP>(d.gamma));
-    const Fr g2 = fe_mul<FrP>(g, g);
-    const Fr muL = fe_to_mont<FrP>(fe_load<FrP>(d.Lx + kInstMu));
-    const Fr muR = fe_to_mont<FrP>(fe_load<FrP>(d.Rx + kInstMu));
+    const FoldConsts &c = *d.fc;
+    const Fr g = fe_ldg<FrP>(c.g.v), g2 = fe_ldg<FrP>(c.g2.v);
+    // gamma m + m' for one witness column (precomputed-quotient product)
+    auto rlc = [&](const Fr &a, const Fr &b) {
+        return fe_add<FrP>(fe_mul_shoup<FrP>(a, fe_ldg<FrP>(c.gc.v), fe_ldg<FrP>(c.gq.v)), b);
+    };
+    // the canonical cross term from its reduced lazy sum
+    auto convert = [&](const Fr &x) { return fe_mul_shoup<FrP>(x, fe_ldg<FrP>(c.kc.v), fe_ldg<FrP>(c.kq.v)); };
     if constexpr (DEG == 3) {
         // Sums of products share one Montgomery reduction (see the degree-2
         // branch).  The pair products enter as x R^-1 (a Montgomery product
         // of canonical values), so each cross term is a sum of four products
-        // of values below r whose reduction is e R^-2; a product with R^3
-        // gives the canonical e.  The mu coefficients are prepared the same
-        // way: -mu_L^2 R^-1, -2 mu_L mu_R R^-1, -mu_R^2 R^-1 (canonical).
+        // of values below r whose reduction is e R^-2; a product with R^2
+        // (convert) gives the canonical e.  The mu coefficients are prepared
+        // the same way: -mu_L^2 R^-1, -mu_R^2 R^-1, -2 mu_L mu_R R^-1.
         using namespace detail;
-        (void)muL;
-        (void)muR;
-        const Fr uL = fe_load<FrP>(d.Lx + kInstMu), uR = fe_load<FrP>(d.Rx + kInstMu);
-        const Fr cLL = fe_neg<FrP>(fe_mul<FrP>(uL, uL)), cRR = fe_neg<FrP>(fe_mul<FrP>(uR, uR));
-        const Fr cLR = fe_neg<FrP>(fe_dbl<FrP>(fe_mul<FrP>(uL, uR)));
-        const Fr g3 = fe_mul<FrP>(g2, g);
-        Fr r3;
-#pragma unroll
-        for (int i = 0; i < 8; i++) r3.v[i] = FrP::r3(i);
+        const Fr cLL = fe_ldg<FrP>(c.c0.v), cRR = fe_ldg<FrP>(c.c1.v), cLR = fe_ldg<FrP>(c.c2.v);
+        const Fr g3 = fe_ldg<FrP>(c.g3.v);
         for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
             const size_t o = 8 * (size_t)k;
             // Consumed in three groups, each finished (its RLC outputs
@@ -89,8 +134,8 @@ __global__ void __launch_bounds__(256, 2)
                 paa = fe_mul<FrP>(a1, a2);
                 pbb = fe_mul<FrP>(b1, b2);
                 sx = redc_wide<FrP>(wide_add<FrP>(wide_mul<FrP>(a1, b2), wide_mul<FrP>(b1, a2)));
-                fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
-                fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
+                fe_store<FrP>(d.Om[0] + o, rlc(a1, b1));
+                fe_store<FrP>(d.Om[1] + o, rlc(a2, b2));
             }
             Wide w2, w1;
             {
@@ -98,7 +143,7 @@ __global__ void __launch_bounds__(256, 2)
                 // gamma^2: a1 a2 b3 + (a1 b2 + b1 a2) a3;  gamma^1: (a1 b2 + b1 a2) b3 + b1 b2 a3
                 w2 = wide_add<FrP>(wide_mul<FrP>(paa, b3), wide_mul<FrP>(sx, a3));
                 w1 = wide_add<FrP>(wide_mul<FrP>(sx, b3), wide_mul<FrP>(pbb, a3));
-                fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
+                fe_store<FrP>(d.Om[2] + o, rlc(a3, b3));
             }
             Fr e1, e2;
             {
@@ -106,9 +151,9 @@ __global__ void __launch_bounds__(256, 2)
                 // - mu_L^2 b4 - 2 mu_L mu_R a4 (gamma^2), - 2 mu_L mu_R b4 - mu_R^2 a4 (gamma^1)
                 w2 = wide_add<FrP>(w2, wide_add<FrP>(wide_mul<FrP>(b4, cLL), wide_mul<FrP>(a4, cLR)));
                 w1 = wide_add<FrP>(w1, wide_add<FrP>(wide_mul<FrP>(b4, cLR), wide_mul<FrP>(a4, cRR)));
-                e2 = fe_mul<FrP>(redc_wide<FrP>(w2), r3);
-                e1 = fe_mul<FrP>(redc_wide<FrP>(w1), r3);
-                fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+                e2 = convert(redc_wide<FrP>(w2));
+                e1 = convert(redc_wide<FrP>(w1));
+                fe_store<FrP>(d.Om[3] + o, rlc(a4, b4));
             }
             fe_store<FrP>(d.e1 + o, e1);
             fe_store<FrP>(d.e2 + o, e2);
@@ -124,10 +169,7 @@ __global__ void __launch_bounds__(256, 2)
         // 4 r^2 < r 2^256, the reduction's bound.  The mu terms enter with
         // the canonical negations r - mu, so every term is a plain product.
         using namespace detail;
-        (void)muL;
-        (void)muR;
-        const Fr nmuL = fe_neg<FrP>(fe_load<FrP>(d.Lx + kInstMu));
-        const Fr nmuR = fe_neg<FrP>(fe_load<FrP>(d.Rx + kInstMu));
+        const Fr nmuL = fe_ldg<FrP>(c.c0.v), nmuR = fe_ldg<FrP>(c.c1.v);
         for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
             const size_t o = 8 * (size_t)k;
             Fr a1 = fe_load<FrP>(d.Lm[0] + o), a2 = fe_load<FrP>(d.Lm[1] + o);
@@ -136,15 +178,15 @@ __global__ void __launch_bounds__(256, 2)
             Fr b3 = fe_load<FrP>(d.Rm[2] + o), b4 = fe_load<FrP>(d.Rm[3] + o);
             Fr eL = fe_load<FrP>(d.Le + o), eR = fe_load<FrP>(d.Re + o);
             // e1 = m1 m2' + m1' m2 - mu m3' - mu' m3: one reduction gives
-            // e1 R^-1, a product with R^2 the canonical value.
+            // e1 R^-1, a product with R (convert) the canonical value.
             const Wide w = wide_add<FrP>(wide_add<FrP>(wide_mul<FrP>(a1, b2), wide_mul<FrP>(b1, a2)),
                                          wide_add<FrP>(wide_mul<FrP>(b3, nmuL), wide_mul<FrP>(a3, nmuR)));
-            const Fr e1 = fe_mul<FrP>(redc_wide<FrP>(w), r2);
+            const Fr e1 = convert(redc_wide<FrP>(w));
             fe_store<FrP>(d.e1 + o, e1);
-            fe_store<FrP>(d.Om[0] + o, fe_add<FrP>(fe_mul<FrP>(a1, g), b1));
-            fe_store<FrP>(d.Om[1] + o, fe_add<FrP>(fe_mul<FrP>(a2, g), b2));
-            fe_store<FrP>(d.Om[2] + o, fe_add<FrP>(fe_mul<FrP>(a3, g), b3));
-            fe_store<FrP>(d.Om[3] + o, fe_add<FrP>(fe_mul<FrP>(a4, g), b4));
+            fe_store<FrP>(d.Om[0] + o, rlc(a1, b1));
+            fe_store<FrP>(d.Om[1] + o, rlc(a2, b2));
+            fe_store<FrP>(d.Om[2] + o, rlc(a3, b3));
+            fe_store<FrP>(d.Om[3] + o, rlc(a4, b4));
             // e'' = e' + gamma e1 + gamma^2 e (g, g2 in Montgomery form)
             const Fr t = redc_wide<FrP>(wide_add<FrP>(wide_mul<FrP>(e1, g), wide_mul<FrP>(eL, g2)));
             fe_store<FrP>(d.Oe + o, fe_add<FrP>(eR, t));
@@ -307,10 +349,11 @@ bool acc_ok(const zk_acc *a, size_t n) {
 unsigned elem_blocks(uint32_t n) { return std::min<unsigned>((n + 255) / 256, 1024u); }
 
 // Runs a batch of folds that share the length n.  dd: device descriptor
-// slots (F), E1: device points (F); the instance pass runs on s_inst after the
-// batch's E1 commitments exist (s_inst may equal s).
-int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *dd, uint32_t *E1,
-               cudaStream_t s, cudaStream_t s_inst, cudaEvent_t ev) {
+// slots (F), fc: device constant slots (F), E1: device points (F); the
+// instance pass runs on s_inst after the batch's E1 commitments exist
+// (s_inst may equal s).
+int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *dd, FoldConsts *fc,
+               uint32_t *E1, cudaStream_t s, cudaStream_t s_inst, cudaEvent_t ev) {
     const size_t F = descs.size();
     if (F == 0) return ZK_OK;
     int err = ZK_OK;
@@ -330,6 +373,7 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     std::vector<size_t> lens(nx * F, n);
     std::vector<MsmJob> jobs(nx * F);
     for (size_t f = 0; f < F; f++) {
+        descs[f].fc = fc + f;
         descs[f].e1 = e1 + f * (size_t)n * 8;
         if (!descs[f].E1) descs[f].E1 = E1 + 16 * f;
         vecs[f] = descs[f].e1;
@@ -351,6 +395,8 @@ int fold_batch(zk_ctx *ctx, std::vector<FoldDesc> &descs, uint32_t n, FoldDesc *
     dim3 g(elem_blocks(n), (unsigned)F);
     {
         PhaseScope ph(ctx, ZK_PHASE_FOLD_WITNESS, s);
+        k_fold_consts<<<(unsigned)((F + 63) / 64), 64, 0, s>>>(dd, (uint32_t)F);
+        ZK_LAUNCHED();
         if (three) k_fold_witness<3><<<g, 256, 0, s>>>(dd, n);
         else k_fold_witness<2><<<g, 256, 0, s>>>(dd, n);
         ZK_LAUNCHED();
@@ -393,6 +439,7 @@ FoldDesc make_desc(const zk_acc *L, const zk_acc *R, const zk_acc *O, const uint
     d.e2 = nullptr;
     d.E2 = nullptr;
     d.deg = deg;
+    d.fc = nullptr;
     return d;
 }
 
@@ -418,8 +465,9 @@ int fold_impl(zk_ctx *ctx, const zk_acc *L, const zk_acc *R, const zk_fr *gamma,
     std::vector<FoldDesc> d(1, make_desc(L, R, out, g, deg));
     uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.E1", 128, &err);
     FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.descs", sizeof(FoldDesc), &err);
-    if (!E1 || !dd) return err;
-    ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd, E1, s, s, nullptr));
+    FoldConsts *fc = (FoldConsts *)scratch(ctx, "fold.consts", sizeof(FoldConsts), &err);
+    if (!E1 || !dd || !fc) return err;
+    ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd, fc, E1, s, s, nullptr));
     if (E1_out) {  // E1, then E2 for degree 3 (contiguous in the workspace)
         const size_t bytes = 64 * (deg - 1);
         if (is_device_ptr(E1_out)) {
@@ -460,7 +508,8 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
     // next level's witness work (main stream) runs.
     FoldDesc *dd = (FoldDesc *)scratch(ctx, "fold.treedescs", (count - 1) * sizeof(FoldDesc), &err);
     uint32_t *E1 = (uint32_t *)scratch(ctx, "fold.treeE1", (count - 1) * 128, &err);
-    if (!dd || !E1) return err;
+    FoldConsts *fc = (FoldConsts *)scratch(ctx, "fold.treeconsts", (count - 1) * sizeof(FoldConsts), &err);
+    if (!dd || !E1 || !fc) return err;
     if (!ctx->side) {
         // Highest priority: the instance pass's few blocks are dispatched
         // ahead of the next level's queued MSM blocks instead of after them.
@@ -485,7 +534,8 @@ int fold_tree_impl(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *gamma
             d.push_back(make_desc(Lp, Rp, Rp, g + 8 * (goff + j), (uint32_t)ctx->sh->fold_degree));
         }
         // the level's E1 points at 2 goff (E1 then E2 for degree 3): disjoint per level
-        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd + goff, E1 + 32 * goff, s, ctx->side, ctx->side_ev[0]));
+        ZK_TRY(fold_batch(ctx, d, (uint32_t)n, dd + goff, fc + goff, E1 + 32 * goff, s, ctx->side,
+                          ctx->side_ev[0]));
         goff += width / 2;
         width /= 2;
     }

@@ -65,7 +65,9 @@ __global__ void k_root(uint32_t lg, Fr *out) {
     *out = fe_pow<FrP>(fe_to_mont<FrP>(five), e);
 }
 
-// tw[k] = w^k for k < n (chunks of 64 per thread); tw[n] = n^{-1}.
+// tw[k] = w^k for k < n (chunks of 64 per thread); tw[n] = n^{-1} (Montgomery
+// form), tw[n + 1] = n^{-1} and tw[n + 2] = floor(n^{-1} 2^256 / r) (canonical:
+// the inverse transform's final scaling by a precomputed-quotient product).
 __global__ void k_twiddles(const Fr *__restrict__ root, uint32_t lg, Fr *__restrict__ tw) {
     const uint64_t n = 1ull << lg;
     uint64_t lo = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 64;
@@ -73,7 +75,10 @@ __global__ void k_twiddles(const Fr *__restrict__ root, uint32_t lg, Fr *__restr
         Fr nn = fe_zero<FrP>();
         nn.v[0] = (uint32_t)n;
         nn.v[1] = (uint32_t)(n >> 32);
-        tw[n] = fe_to_mont<FrP>(fe_inv_canonical<FrP>(nn));
+        const Fr ninv = fe_inv_canonical<FrP>(nn);
+        tw[n] = fe_to_mont<FrP>(ninv);
+        tw[n + 1] = ninv;
+        tw[n + 2] = fe_shoup_quotient<FrP>(ninv);
     }
     if (lo >= n) return;
     uint64_t hi = lo + 64 < n ? lo + 64 : n;
@@ -106,7 +111,7 @@ struct PassArgs {
     const uint32_t *const *in_tab;  // per vector (blockIdx.y)
     uint32_t *const *out_tab;
     uint32_t logn, logR, logNs, J, logJ;  // J = 2^logJ sub-transforms per CTA
-    const Fr *tw_n;  // size-n table (+ n^{-1} at index n)
+    const Fr *tw_n;  // size-n table (+ n^{-1} and its quotient at n + 1, n + 2)
     const uint32_t *tw_S;  // size-R stage table (w, wq), 16 words per entry
     int inverse;
     int scale;  // multiply outputs by n^{-1}
@@ -181,8 +186,11 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
     }
 
     // Store V_r (at bit-reversed position r) to its natural-order place.
-    Fr sc;
-    if (a.scale) sc = fe_ldg<FrP>(a.tw_n + n);
+    Fr sc, scq;
+    if (a.scale) {
+        sc = fe_ldg<FrP>(a.tw_n + n + 1);
+        scq = fe_ldg<FrP>(a.tw_n + n + 2);
+    }
     for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
         uint32_t r, jj;
         if (Ns >= J) {
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(PassArgs a) {
         Fr x;
 #pragma unroll
         for (int l = 0; l < 8; l++) x.v[l] = sm[l * JR + src * J + jj];
-        x = a.scale ? fe_mul<FrP>(x, sc) : fe_canon_2p<FrP>(x);  // [0, 2r) -> canonical
+        x = a.scale ? fe_mul_shoup<FrP>(x, sc, scq) : fe_canon_2p<FrP>(x);  // [0, 2r) -> canonical
         uint64_t dst = ((j >> a.logNs) << (a.logNs + a.logR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
         if (ZK_FAILED(dst < n, kCheckNttIdx)) continue;
         fe_store<FrP>(out + 8 * dst, x);
@@ -329,8 +337,11 @@ __global__ void __launch_bounds__(512, 2) k_ntt_reg(PassArgs a) {
         }
     }
     __syncthreads();
-    Fr sc;
-    if (a.scale) sc = fe_ldg<FrP>(a.tw_n + n);
+    Fr sc, scq;
+    if (a.scale) {
+        sc = fe_ldg<FrP>(a.tw_n + n + 1);
+        scq = fe_ldg<FrP>(a.tw_n + n + 2);
+    }
     for (uint32_t e = threadIdx.x; e < JR; e += blockDim.x) {
         uint32_t r, jx;
         if (Ns >= J) {
@@ -348,7 +359,7 @@ __global__ void __launch_bounds__(512, 2) k_ntt_reg(PassArgs a) {
         Fr v;
 #pragma unroll
         for (int l = 0; l < 8; l++) v.v[l] = sm[l * P + w];
-        v = a.scale ? fe_mul<FrP>(v, sc) : fe_canon_2p<FrP>(v);  // [0, 2r) -> canonical
+        v = a.scale ? fe_mul_shoup<FrP>(v, sc, scq) : fe_canon_2p<FrP>(v);  // [0, 2r) -> canonical
         const uint64_t dst = ((j >> a.logNs) << (a.logNs + LR)) + (j & (Ns - 1)) + ((uint64_t)r << a.logNs);
         if (ZK_FAILED(dst < n, kCheckNttIdx)) continue;
         fe_store<FrP>(out + 8 * dst, v);
@@ -460,7 +471,7 @@ int twiddles(zk_ctx *ctx, int lg, const uint32_t **out, cudaStream_t s) {
     DevBuf &b = sh.tw[lg];
     if (!b.p) {
         const size_t n = (size_t)1 << lg;
-        ZK_TRY(dev_alloc(sh, b, (n + 1) * sizeof(Fr)));
+        ZK_TRY(dev_alloc(sh, b, (n + 3) * sizeof(Fr)));
         int err = ZK_OK;
         Fr *root = (Fr *)scratch(ctx, "ntt.root", sizeof(Fr), &err);
         if (!root) return err;

@@ -65,6 +65,8 @@ def test_montgomery_constants_match_definitions(field_host, f):
     assert got[3] == R256 ** 3 % p
     assert got[4] == (p - 1) // 2
     assert got[5] == (-pow(p, -1, 1 << 32)) % (1 << 32)
+    assert got[6] == (-pow(p, -1, R256)) % R256
+    assert got[6] & W32 == got[5]
 
 
 @pytest.mark.parametrize("f", ["q", "r"])
