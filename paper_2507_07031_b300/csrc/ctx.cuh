@@ -27,8 +27,9 @@ struct DevBuf {
 };
 
 // Precomputed window table for window width c: entry (w, i) holds
-// 2^(c w) * SRS[i] as an affine point in Montgomery form (64 bytes), for
-// w < W = ceil(254 / c) and i < n.  With one table per c every window of a
+// 2^(c w) * SRS[i] as a window-table entry (AffineS: canonical x, y and
+// their precomputed quotients, 128 bytes), for w < W = ceil(254 / c) and
+// i < n; window 0 is the base points themselves.  With one table per c every window of a
 // scalar adds into the same bucket set, so the bucket reduction is done once
 // per MSM instead of once per window, and no Horner pass over windows is
 // needed.

@@ -88,6 +88,20 @@ ZK_DEV Xyzz xyzz_dbl(const Xyzz &p) {
     return r;
 }
 
+// The mixed addition after U2 = x2 ZZ1 and S2 = y2 ZZZ1 (madd-2008-s), with
+// P = U2 - X1 != 0 and R = S2 - Y1.
+ZK_DEV Xyzz madd_finish(const Xyzz &p, const Fq &P, const Fq &R) {
+    Fq PP = fe_sqr<FqP>(P);
+    Fq PPP = fe_mul<FqP>(P, PP);
+    Fq Q = fe_mul<FqP>(p.X, PP);
+    Xyzz r;
+    r.X = fe_sub<FqP>(fe_sub<FqP>(fe_sqr<FqP>(R), PPP), fe_dbl<FqP>(Q));
+    r.Y = fe_mul_sub_mul<FqP>(R, fe_sub<FqP>(Q, r.X), p.Y, PPP);
+    r.ZZ = fe_mul<FqP>(p.ZZ, PP);
+    r.ZZZ = fe_mul<FqP>(p.ZZZ, PPP);
+    return r;
+}
+
 // P + Q with Q affine (madd-2008-s), all exceptional cases handled.
 ZK_DEV Xyzz xyzz_add_affine(const Xyzz &p, const Affine &q) {
     if (xyzz_is_inf(p)) return xyzz_from_affine(q);
@@ -99,15 +113,88 @@ ZK_DEV Xyzz xyzz_add_affine(const Xyzz &p, const Affine &q) {
         if (fe_is_zero<FqP>(R)) return xyzz_dbl_affine(q);  // P = Q
         return xyzz_inf();                                   // P = -Q
     }
-    Fq PP = fe_sqr<FqP>(P);
-    Fq PPP = fe_mul<FqP>(P, PP);
-    Fq Q = fe_mul<FqP>(p.X, PP);
+    return madd_finish(p, P, R);
+}
+
+// ---------------------------------------------------------------------------
+// Window-table entries.  The bucket accumulation's mixed additions multiply
+// two accumulator coordinates by the table point's x and y, which are fixed
+// when the table is built.  An entry therefore holds them canonical with
+// their precomputed quotients (fe_mul_shoup): x ZZ1 with ZZ1 in Montgomery
+// form (ZZ1 R) is x ZZ1 R, the Montgomery form of U2, in 207 word products
+// instead of a Montgomery product's 264 (S2 likewise).  128 bytes, one
+// aligned line per entry; a 64-byte affine point cost the same 128-byte
+// fetch from DRAM.
+// ---------------------------------------------------------------------------
+
+struct AffineS {
+    Fq x, y;    // canonical coordinates
+    Fq xq, yq;  // floor(x 2^256 / q), floor(y 2^256 / q)
+};
+
+// The entry of an affine point in Montgomery form; the quotients come from
+// the Montgomery forms directly (fe_shoup_quotient_mont).
+ZK_DEV AffineS affines_from_affine(const Affine &a) {
+    AffineS e;
+    e.x = fe_from_mont<FqP>(a.x);
+    e.y = fe_from_mont<FqP>(a.y);
+    e.xq = fe_shoup_quotient_mont<FqP>(a.x);
+    e.yq = fe_shoup_quotient_mont<FqP>(a.y);
+    return e;
+}
+
+// One out-of-line copy of the product (the accumulation kernel's code stays
+// within the instruction cache, as for the F_q Montgomery product).
+static __device__ __noinline__ Fq fq_mul_shoup_call(const Fq a, const Fq w, const Fq wq) {
+    return fe_mul_shoup<FqP>(a, w, wq);
+}
+
+// The entry's point, negated when neg, in affine Montgomery form: the
+// product of the constant R mod q with x is x R.
+ZK_DEV Affine affines_point(const AffineS &e, bool neg) {
+    Fq one;
+#pragma unroll
+    for (int i = 0; i < 8; i++) one.v[i] = FqP::one(i);  // R mod q as a plain residue
+    Affine a;
+    a.x = fq_mul_shoup_call(one, e.x, e.xq);
+    a.y = fq_mul_shoup_call(one, e.y, e.yq);
+    if (neg) a.y = fe_neg<FqP>(a.y);
+    return a;
+}
+
+// The entry's point (negated when neg) as an XYZZ point without a full
+// product: any lambda != 0 gives the same point (lambda^2 x, lambda^3 y,
+// lambda^2, lambda^3), and lambda = 2^-128 makes the Montgomery words of
+// X and ZZ the stored x and the integer 1, ZZZ's the constant 2^-128 mod q,
+// and Y's y 2^-128 (four word reduction rounds).  An accumulator that starts
+// a bucket takes this, so the lanes of a warp that start one hold the others
+// up by 68 word products, not two full products.
+ZK_DEV Xyzz xyzz_from_entry(const AffineS &e, bool neg) {
     Xyzz r;
-    r.X = fe_sub<FqP>(fe_sub<FqP>(fe_sqr<FqP>(R), PPP), fe_dbl<FqP>(Q));
-    r.Y = fe_mul_sub_mul<FqP>(R, fe_sub<FqP>(Q, r.X), p.Y, PPP);
-    r.ZZ = fe_mul<FqP>(p.ZZ, PP);
-    r.ZZZ = fe_mul<FqP>(p.ZZZ, PPP);
+    r.X = e.x;
+    r.Y = fe_mul_2m128<FqP>(e.y);
+    if (neg) r.Y = fe_neg<FqP>(r.Y);
+    r.ZZ = fe_zero<FqP>();
+    r.ZZ.v[0] = 1;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.ZZZ.v[i] = FqP::rinvh(i);
     return r;
+}
+
+// P + Q, Q = +-(the entry's point) (neg selects -), madd-2008-s with every
+// exceptional case: -Q has S2 = -(y ZZZ1).
+ZK_DEV Xyzz xyzz_add_entry(const Xyzz &p, const AffineS &q, bool neg) {
+    if (xyzz_is_inf(p)) return xyzz_from_entry(q, neg);
+    Fq U2 = fq_mul_shoup_call(p.ZZ, q.x, q.xq);
+    Fq S2 = fq_mul_shoup_call(p.ZZZ, q.y, q.yq);
+    if (neg) S2 = fe_neg<FqP>(S2);
+    Fq P = fe_sub<FqP>(U2, p.X);
+    Fq R = fe_sub<FqP>(S2, p.Y);
+    if (fe_is_zero<FqP>(P)) {
+        if (fe_is_zero<FqP>(R)) return xyzz_dbl_affine(affines_point(q, neg));  // P = Q
+        return xyzz_inf();                                                     // P = -Q
+    }
+    return madd_finish(p, P, R);
 }
 
 // P + Q, both XYZZ (add-2008-s), all exceptional cases handled.
@@ -163,7 +250,9 @@ ZK_DEV bool affine_on_curve(const Affine &a) {
 
 // ---------------------------------------------------------------------------
 // Memory forms.
-//   * device table entry: affine Montgomery, 64 bytes (x then y);
+//   * device base points (SRS, Lagrange basis): affine Montgomery, 64 bytes
+//     (x then y);
+//   * window-table entry: AffineS, 128 bytes (x, y, xq, yq, canonical);
 //   * boundary form: canonical affine, 64 bytes; infinity = zeros.
 // ---------------------------------------------------------------------------
 
@@ -173,6 +262,24 @@ ZK_DEV Affine affine_ldg(const void *p) {
     a.x = fe_ldg<FqP>(c);
     a.y = fe_ldg<FqP>(c + 32);
     return a;
+}
+
+ZK_DEV AffineS affines_ldg(const void *p) {
+    const char *c = reinterpret_cast<const char *>(p);
+    AffineS a;
+    a.x = fe_ldg<FqP>(c);
+    a.y = fe_ldg<FqP>(c + 32);
+    a.xq = fe_ldg<FqP>(c + 64);
+    a.yq = fe_ldg<FqP>(c + 96);
+    return a;
+}
+
+ZK_DEV void affines_store(void *p, const AffineS &a) {
+    char *c = reinterpret_cast<char *>(p);
+    fe_store<FqP>(c, a.x);
+    fe_store<FqP>(c + 32, a.y);
+    fe_store<FqP>(c + 64, a.xq);
+    fe_store<FqP>(c + 96, a.yq);
 }
 
 ZK_DEV void affine_store(void *p, const Affine &a) {

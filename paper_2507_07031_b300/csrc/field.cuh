@@ -23,7 +23,7 @@ namespace zk {
 
 // Compile-time limb tables.  `p` is the modulus, `one` = R mod p, `r2` =
 // R^2 mod p, `r3` = R^3 mod p, `half` = (p - 1) / 2, `ninv` = -p^{-1} mod
-// 2^256, `n0` = -p^{-1} mod 2^32 (its low word).
+// 2^256, `n0` = -p^{-1} mod 2^32 (its low word), `rinvh` = 2^-128 mod p.
 struct FqP {
     static ZK_HD constexpr uint32_t p(int i) {
         constexpr uint32_t v[8] = {0xd87cfd47u, 0x3c208c16u, 0x6871ca8du, 0x97816a91u,
@@ -53,6 +53,11 @@ struct FqP {
     static ZK_HD constexpr uint32_t ninv(int i) {
         constexpr uint32_t v[8] = {0xe4866389u, 0x87d20782u, 0x1eca6ac9u, 0x9ede7d65u,
                                    0x1833da80u, 0xd8afcbd0u, 0x91888c6bu, 0xf57a22b7u};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t rinvh(int i) {
+        constexpr uint32_t v[8] = {0x34ade680u, 0x1da790e4u, 0xf9905883u, 0x27a2f342u,
+                                   0x0dfa3d61u, 0xb5ab3489u, 0x064ef9b1u, 0x1e07f71bu};
         return v[i];
     }
     static constexpr uint32_t n0 = 0xe4866389u;
@@ -87,6 +92,11 @@ struct FrP {
     static ZK_HD constexpr uint32_t ninv(int i) {
         constexpr uint32_t v[8] = {0xefffffffu, 0xc2e1f593u, 0x4c6911b3u, 0x6586864bu,
                                    0x99062391u, 0xe39a9828u, 0x0d8341b2u, 0x73f82f1du};
+        return v[i];
+    }
+    static ZK_HD constexpr uint32_t rinvh(int i) {
+        constexpr uint32_t v[8] = {0x76f9dc6fu, 0x18ee753cu, 0xa329e70fu, 0x54ad7e14u,
+                                   0x4f7684dfu, 0x2b16366fu, 0x1fdf3579u, 0x133100d7u};
         return v[i];
     }
     static constexpr uint32_t n0 = 0xefffffffu;
@@ -1019,6 +1029,25 @@ template <class P> ZK_DEV Fe<P> fe_sub_2p(const Fe<P> &a, const Fe<P> &b) {
 }
 template <class P> ZK_DEV Fe<P> fe_canon_2p(const Fe<P> &a) {
     Fe<P> r = a;
+    detail::cond_sub_p<P>(r.v);
+    return r;
+}
+
+// a 2^-128 mod p for a < 2^256: four word-level Montgomery reduction rounds
+// (68 word products) give t = (a + m p) / 2^128 < 2p, then one conditional
+// subtraction.
+template <class P> ZK_DEV Fe<P> fe_mul_2m128(const Fe<P> &a) {
+    uint32_t t[17];
+#pragma unroll
+    for (int i = 0; i < 17; i++) t[i] = i < 8 ? a.v[i] : 0u;
+    const uint32_t pm[8] = {P::p(0), P::p(1), P::p(2), P::p(3), P::p(4), P::p(5), P::p(6), P::p(7)};
+    detail::mac_row<0>(t, pm, t[0] * P::n0);  // t[0] becomes 0
+    detail::mac_row<1>(t, pm, t[1] * P::n0);
+    detail::mac_row<2>(t, pm, t[2] * P::n0);
+    detail::mac_row<3>(t, pm, t[3] * P::n0);
+    Fe<P> r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = t[4 + i];
     detail::cond_sub_p<P>(r.v);
     return r;
 }

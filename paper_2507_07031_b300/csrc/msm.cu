@@ -53,10 +53,10 @@ constexpr size_t kStatsMin = 4096;  // scalars below which the width scan is ski
 struct JobDesc {
     const uint32_t *scalars;  // n canonical scalars (device)
     void *out;                // canonical affine result (device)
-    const Affine *table;      // points the sorted entries index (window table, or `base`)
-    const Affine *base;       // base points: SRS, or the Lagrange basis of H
-    const Affine *wtable;     // window table of width c over the base points
-    const Affine *t16;        // window table of width 16 over the base points, or null
+    const AffineS *table;     // entries the sorted entries index (a window table, or its window 0)
+    const AffineS *wtable;    // window table of width c over the base points (SRS, or the
+                              // Lagrange basis of H); window 0 is the base points
+    const AffineS *t16;       // window table of width 16 over the base points, or null
     uint32_t t16n;            // its points per window
     uint32_t n;
     uint32_t logB;            // buckets in use: 2^logB (2^(c - 1), or fewer for short scalars)
@@ -438,7 +438,7 @@ __global__ void k_msm_plan(JobDesc *__restrict__ jobs, uint32_t count, const uin
         d.shift = 0;
         d.dbl = 0;
         d.logB = kMinWindow - 1;
-        d.table = d.base;
+        d.table = d.wtable;
     } else if (len < (uint32_t)kScalarBits - 1 || tz > 0) {
         const uint32_t sh = min(tz, len - 1);
         const uint32_t eff = len - sh;  // bits left after the shift
@@ -447,7 +447,7 @@ __global__ void k_msm_plan(JobDesc *__restrict__ jobs, uint32_t count, const uin
         if (eff + 1 <= c) {
             d.wins = 1;
             d.logB = max(eff + 1, (uint32_t)kMinWindow) - 1;
-            d.table = d.base;
+            d.table = d.wtable;  // window 0: the base points
             const uint32_t k16 = min(sh / 16, 15u);
             if (d.t16 && k16 && (sh & 15) <= 1 && eff + (sh & 15) + 1 <= c) {
                 d.shift = 16 * k16;
@@ -555,7 +555,7 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
     uint32_t b = upper_index(off0, nb, lo);  // bucket holding entry lo
     uint32_t end = off0[b + 1];
     uint32_t job = search(dj.bbase, 0, dj.count, b);
-    const Affine *table = dj.jobs[job].table;
+    const AffineS *table = dj.jobs[job].table;
     uint32_t jend = dj.bbase[job + 1];
     Xyzz acc = xyzz_inf();
     for (uint32_t j = lo; j < hi; j++) {
@@ -576,9 +576,7 @@ __global__ void k_pieces_first(const uint32_t *__restrict__ sorted, const uint32
             }
         }
         const uint32_t v = sorted[j];
-        Affine a = affine_ldg(table + (v >> 1));
-        if (v & 1) a = affine_neg(a);
-        acc = xyzz_add_affine(acc, a);
+        acc = xyzz_add_entry(acc, affines_ldg(table + (v >> 1)), v & 1);
     }
     const uint32_t plo = off1[b];
     piece_out(acc, b, plo + c - off0[b] / p0, off1[b + 1] - plo, pieces, buckets);
@@ -1167,7 +1165,7 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
     // (built on first use, outside timed loops).
     // (The jobs are sorted by width and basis, so each pair's jobs are
     // contiguous: one table lookup per group, sized for its longest job.)
-    std::vector<const Affine *> bases(count), tabs(count);
+    std::vector<const AffineS *> tabs(count);
     std::vector<uint32_t> tabn(count);
     for (size_t g0 = 0; g0 < count;) {
         const int basis = jv[g0].job.basis;
@@ -1179,22 +1177,21 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         const WindowTable *t;
         ZK_TRY(table_get(ctx, jv[g0].c, need, basis, &t, s));
         for (size_t k = g0; k < g1; k++) {
-            bases[k] = basis ? (const Affine *)sh.lag[basis].p : (const Affine *)sh.srs.p;
-            tabs[k] = (const Affine *)t->buf.p;
+            tabs[k] = (const AffineS *)t->buf.p;
             tabn[k] = (uint32_t)t->n;
         }
         g0 = g1;
     }
     // Width-16 tables that already exist (SRS loading builds the SRS's),
     // for the single-window path of scalars with 16 or more trailing zeros.
-    std::vector<const Affine *> t16s(count, nullptr);
+    std::vector<const AffineS *> t16s(count, nullptr);
     std::vector<uint32_t> t16n(count, 0);
     if (stats) {
         std::lock_guard<std::mutex> g(sh.mu);
         for (size_t k = 0; k < count; k++)
             for (auto &t : sh.tables)
                 if (t.c == 16 && t.basis == jv[k].job.basis && t.n >= jv[k].job.n) {
-                    t16s[k] = (const Affine *)t.buf.p;
+                    t16s[k] = (const AffineS *)t.buf.p;
                     t16n[k] = (uint32_t)t.n;
                     break;
                 }
@@ -1314,7 +1311,6 @@ int msm_batch_impl(zk_ctx *ctx, const MsmJob *jobs_in, size_t count, int c_fixed
         hd[k].scalars = jv[k].job.scalars;
         hd[k].out = jv[k].job.out;
         hd[k].table = tabs[k];
-        hd[k].base = bases[k];
         hd[k].wtable = tabs[k];
         hd[k].n = jv[k].job.n;
         hd[k].logB = (uint32_t)(jv[k].c - 1);
@@ -1469,13 +1465,12 @@ int noalloc_workspace(int device, unsigned char **out) {
 // Writes the one-job table (descriptor and prefix arrays) that the MSM
 // kernels read, without a host-to-device copy.
 __global__ void k_noalloc_jobs(unsigned char *ws, const uint32_t *scalars, uint32_t n, void *out,
-                               const Affine *table) {
+                               const AffineS *table) {
     if (threadIdx.x || blockIdx.x) return;
     JobDesc *d = reinterpret_cast<JobDesc *>(ws + kNaJobs);
     d->scalars = scalars;
     d->out = out;
-    d->table = table;
-    d->base = nullptr;  // no plan kernel runs: always the full-width shape
+    d->table = table;  // no plan kernel runs: always the full-width shape
     d->wtable = table;
     d->t16 = nullptr;
     d->t16n = 0;
@@ -1547,7 +1542,7 @@ extern "C" int zk_commit_noalloc(zk_ctx *ctx, const zk_fr *coeffs, size_t n, zk_
     void *scan_tmp = ws + kNaScan;
 
     k_noalloc_jobs<<<1, 1, 0, s>>>(ws, (const uint32_t *)coeffs, (uint32_t)n, out,
-                                   (const Affine *)tab->buf.p);
+                                   (const AffineS *)tab->buf.p);
     ZK_LAUNCHED();
     DevJobs dj;
     dj.jobs = (const JobDesc *)(ws + kNaJobs);

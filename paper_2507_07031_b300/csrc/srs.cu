@@ -141,8 +141,14 @@ __global__ void k_fixed_base(const uint32_t *__restrict__ powers, const Affine *
 }
 
 // ---------------------------------------------------------------------------
-// Window tables: dst[i] = 2^c * src[i].
+// Window tables: dst[i] = 2^c * src[i]; entries (AffineS) of a window.
 // ---------------------------------------------------------------------------
+__global__ void k_table_entries(const Affine *__restrict__ src, AffineS *__restrict__ dst, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    affines_store(dst + i, affines_from_affine(affine_ldg(src + i)));
+}
+
 __global__ void k_shift_window(const Affine *__restrict__ src, Xyzz *__restrict__ dst, size_t n,
                                int c) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -157,21 +163,25 @@ int build_table(zk_ctx *ctx, WindowTable &t, int c, size_t n, int basis, cudaStr
     const Affine *base = (const Affine *)sh.srs.p;
     if (basis) base = (const Affine *)sh.lag[basis].p;
     const int W = windows_for(c);
-    ZK_TRY(dev_alloc(sh, t.buf, (size_t)W * n * sizeof(Affine)));
+    ZK_TRY(dev_alloc(sh, t.buf, (size_t)W * n * sizeof(AffineS)));
     t.c = c;
     t.W = W;
     t.n = n;
     t.basis = basis;
-    Affine *tab = (Affine *)t.buf.p;
-    ZK_CUDA_TRY(cudaMemcpyAsync(tab, base, n * sizeof(Affine), cudaMemcpyDeviceToDevice, s));
+    AffineS *tab = (AffineS *)t.buf.p;
     int err = ZK_OK;
     Xyzz *tmp = (Xyzz *)scratch(ctx, "srs.xyzz", n * sizeof(Xyzz), &err);
-    if (!tmp) return err;
+    Affine *win = (Affine *)scratch(ctx, "srs.window", n * sizeof(Affine), &err);  // window w, Montgomery
+    if (!tmp || !win) return err;
     unsigned blocks = (unsigned)((n + 127) / 128);
+    k_table_entries<<<blocks, 128, 0, s>>>(base, tab, n);
+    ZK_LAUNCHED();
     for (int w = 1; w < W; w++) {
-        k_shift_window<<<blocks, 128, 0, s>>>(tab + (size_t)(w - 1) * n, tmp, n, c);
+        k_shift_window<<<blocks, 128, 0, s>>>(w == 1 ? base : win, tmp, n, c);
         ZK_LAUNCHED();
-        ZK_TRY(normalize(ctx, tmp, tab + (size_t)w * n, n, s));
+        ZK_TRY(normalize(ctx, tmp, win, n, s));
+        k_table_entries<<<blocks, 128, 0, s>>>(win, tab + (size_t)w * n, n);
+        ZK_LAUNCHED();
     }
     // Tables are shared read-only by lanes on other streams: finish now.
     ZK_CUDA_TRY(cudaStreamSynchronize(s));

@@ -2,7 +2,7 @@
 // the divstep inversion (run on the host, the same source the kernels use)
 // and the compile-time Montgomery constants of both BN254 fields.
 //
-//   field_host consts q|r     prints p, R mod p, R^2, R^3, (p - 1) / 2, n0 and -p^-1 mod R
+//   field_host consts q|r     prints p, R mod p, R^2, R^3, (p - 1) / 2, n0, -p^-1 mod R and 2^-128 mod p
 //   field_host inv q|r        reads one hex value per line, prints x^-1 mod p
 //
 // Values are printed as 64 hex digits, most significant word first.
@@ -50,6 +50,8 @@ void consts() {
     put(w);
     std::printf("%08x\n", P::n0);
     for (int i = 0; i < 8; i++) w[i] = P::ninv(i);
+    put(w);
+    for (int i = 0; i < 8; i++) w[i] = P::rinvh(i);
     put(w);
 }
 

@@ -67,6 +67,7 @@ def test_montgomery_constants_match_definitions(field_host, f):
     assert got[5] == (-pow(p, -1, 1 << 32)) % (1 << 32)
     assert got[6] == (-pow(p, -1, R256)) % R256
     assert got[6] & W32 == got[5]
+    assert got[7] == pow(2, -128, p)
 
 
 @pytest.mark.parametrize("f", ["q", "r"])
