@@ -52,7 +52,7 @@ HBM_FALLBACK = 6400.0        # GB/s, used only when MEASURED_PEAKS.json is absen
 # DRAM bytes (read + write) of one k_pieces_first launch, uniform 2^20, c = 17,
 # from an ncu capture of that launch (dram__bytes_read.sum +
 # dram__bytes_write.sum); None when the kernel has changed since.
-ACCUM_TRAFFIC = None
+ACCUM_TRAFFIC = 2.1457e9
 CPU_SAMPLE_LOG = 15  # oracle MSM sample: 2^15 points, ~10-15 s on 16 cores
 
 
