@@ -11,6 +11,16 @@
    during the reduction rows; the reduced value is below 2p.  The device
    routine itself is compared bit for bit with the oracle on the GPU
    (ZK_FOP_MULSUB).
+3. The product by a constant with a precomputed quotient (NTT butterflies,
+   fold RLC, products by a window-table point): a word-level model of its
+   truncated quotient checks the error bound (at most two units), the
+   carry windows and exactness for every first operand below 2^256; the
+   closed form of the quotient from the Montgomery form is checked against
+   floor division.  The device routine is compared with the oracle on the
+   GPU (ZK_FOP_MULC).
+4. The scaled bucket start of the MSM accumulation (lambda = 2^-128) is
+   checked to represent the same affine point, with a model of the
+   four-row reduction that forms y 2^-128.
 
 The moduli are the published BN254 primes (EIP-196), written out here."""
 import os
@@ -120,3 +130,131 @@ def test_product_difference_model_bounds(f):
     cases += [tuple(rng.randrange(p) for _ in range(4)) for _ in range(5000)]
     for a, b, c, d in cases:
         assert _mul_sub_mul_model(a, b, c, d, p) == (a * b - c * d) * rinv % p
+
+
+def _shoup_model(a, w, p):
+    """fe_mul_shoup's steps on 32-bit words, with the bounds its carry chains
+    rely on.  The quotient takes only the partial products of a wq in columns
+    >= 7 (lo(a_i wq_j) for i + j >= 7, hi for i + j >= 6), row by row into
+    the window of words 7 .. i + 8; then a w + q (2^256 - p) mod 2^256 and
+    two conditional subtractions (2p, then p)."""
+    wq = (w << 256) // p
+    A, WQ = _words(a, 8), _words(wq, 8)
+    acc = 0
+    for i in range(8):
+        for j in range(8):
+            prod = A[i] * WQ[j]
+            if i + j >= 7:
+                acc += (prod & W32) << (32 * (i + j))
+            if i + j >= 6:
+                acc += (prod >> 32) << (32 * (i + j + 1))
+        assert acc % (1 << 224) == 0  # nothing below word 7
+        assert acc >> 224 < 1 << (32 * (i + 2))  # the window t[7 .. i + 8] holds it
+    q = acc >> 256
+    Q = a * w // p
+    assert 0 <= Q - q <= 2  # the dropped columns sum to below 2^228
+    low = lambda x, y: sum(((X * Y) & W32) << (32 * (i + j)) for i, X in enumerate(_words(x, 8))
+                           for j, Y in enumerate(_words(y, 8)) if i + j <= 7) + \
+        sum(((X * Y) >> 32) << (32 * (i + j + 1)) for i, X in enumerate(_words(x, 8))
+            for j, Y in enumerate(_words(y, 8)) if i + j <= 6)
+    r = (low(q, (1 << 256) - p) + low(w, a)) % (1 << 256)  # lower triangles only
+    assert r == a * w - q * p < 3 * p < 1 << 256
+    if r >= 2 * p:
+        r -= 2 * p
+    if r >= p:
+        r -= p
+    return r
+
+
+@pytest.mark.parametrize("f", ["q", "r"])
+def test_precomputed_quotient_product_model(f):
+    """The product by a constant with a precomputed quotient (the NTT's
+    butterflies, the fold's RLC, the MSM's products by a table point): exact
+    for every first operand below 2^256, the range the lazy butterflies feed
+    it (values up to 4p), including its top 2^256 - 1."""
+    p = MODULI[f]
+    rng = random.Random(71 if f == "q" else 73)
+    edge = _edge(p)
+    firsts = edge + [(1 << 256) - 1, 4 * p - 1, 3 * p, 2 * p - 1] + [rng.randrange(1 << 256) for _ in range(300)]
+    consts = edge + [rng.randrange(p) for _ in range(60)]
+    for a in firsts[::2]:
+        for w in consts[::3]:
+            assert _shoup_model(a, w, p) == a * w % p, (hex(a), hex(w))
+    for _ in range(3000):
+        a, w = rng.randrange(1 << 256), rng.randrange(p)
+        assert _shoup_model(a, w, p) == a * w % p
+
+
+@pytest.mark.parametrize("f", ["q", "r"])
+def test_quotient_from_montgomery_form(f):
+    """floor(w 2^256 / p) = -(w R mod p) p^-1 mod 2^256 (R = 2^256): the
+    closed form the device takes the quotient from, one lower-triangle
+    product of w's Montgomery form with the constant -p^-1 mod 2^256."""
+    p = MODULI[f]
+    R = 1 << 256
+    ninv = (-pow(p, -1, R)) % R
+    rng = random.Random(79 if f == "q" else 83)
+    for w in _edge(p) + [rng.randrange(p) for _ in range(5000)]:
+        assert (w * R % p) * ninv % R == (w << 256) // p, hex(w)
+
+
+def _mul_2m128_model(a, p):
+    """fe_mul_2m128's steps: four word-level Montgomery reduction rows
+    t += m p 2^(32 i), m = t_i n0 mod 2^32, then words 4 .. 11 and one
+    conditional subtraction."""
+    n0 = (-pow(p, -1, 1 << 32)) % (1 << 32)
+    t = a
+    for i in range(4):
+        m = ((t >> (32 * i)) & W32) * n0 & W32
+        t += (m * p) << (32 * i)
+        assert (t >> (32 * i)) & W32 == 0
+        assert t < 1 << (32 * (i + 9))  # the row's window t[i .. i + 8]
+    r = t >> 128
+    assert r < 2 * p
+    return r - p if r >= p else r
+
+
+def test_scaled_bucket_start():
+    """A bucket's first table point enters the accumulator as the XYZZ point
+    with Montgomery words (x, y 2^-128, 1, 2^-128 mod q), x and y the entry's
+    canonical coordinates: the representation lambda = 2^-128 of the same
+    affine point.  Checked on the field values the words stand for (word R^-1),
+    with y 2^-128 from the four-row reduction model, on points of the curve."""
+    q = MODULI["q"]
+    R = 1 << 256
+    rinv = pow(R, -1, q)
+    rinvh = pow(2, -128, q)
+    rng = random.Random(89)
+    pts = []
+    x, y = 1, 2  # the generator of y^2 = x^3 + 3
+    for _ in range(40):
+        pts.append((x, y))
+        k = rng.randrange(1, 1 << 64)
+        # k P by double-and-add in affine coordinates (Python integers)
+        acc = None
+        base = (x, y)
+        while k:
+            if k & 1:
+                acc = base if acc is None else _affine_add(acc, base, q)
+            base = _affine_add(base, base, q)
+            k >>= 1
+        x, y = acc
+    for x, y in pts:
+        assert (y * y - x ** 3 - 3) % q == 0
+        words = (x, _mul_2m128_model(y, q), 1, rinvh)
+        X, Y, ZZ, ZZZ = (v * rinv % q for v in words)
+        assert ZZ ** 3 % q == ZZZ ** 2 % q
+        assert X * pow(ZZ, -1, q) % q == x
+        assert Y * pow(ZZZ, -1, q) % q == y
+    for a in _edge(q) + [R - 1]:
+        assert _mul_2m128_model(a, q) == a * rinvh % q
+
+
+def _affine_add(P, Q, p):
+    (x1, y1), (x2, y2) = P, Q
+    if P == Q:
+        lam = 3 * x1 * x1 * pow(2 * y1, -1, p) % p
+    else:
+        lam = (y2 - y1) * pow(x2 - x1, -1, p) % p
+    x3 = (lam * lam - x1 - x2) % p
+    return x3, (lam * (x1 - x3) - y1) % p
