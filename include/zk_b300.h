@@ -296,7 +296,7 @@ int zk_fold_tree_levels(zk_ctx *ctx, zk_acc *leaves, size_t count, const zk_fr *
  * B300); zk_tune_get returns the value in effect (tuned or built-in).
  * zk_tune_measure times one candidate on synthetic device data (median
  * of `reps` runs, ms) without changing the setting; the first use of a new
- * window width builds its window table (about W x 64 bytes per SRS point).
+ * window width builds its window table (about W x 128 bytes per SRS point).
  * paper_2507_07031_b300/autotune.py sweeps the candidates and stores the
  * winners in a JSON table. */
 #define ZK_TUNE_MSM_WINDOW 0
