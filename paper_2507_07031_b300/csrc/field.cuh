@@ -924,9 +924,8 @@ template <int I> ZK_DEV void quot_row(uint32_t (&t)[17], const uint32_t (&wq)[8]
     else hi_run<8, 0, 8>(t, wq, ai);
 }
 
-}  // namespace detail
 
-namespace detail {
+// Words of p and 2p, and conditional subtractions of them.
 template <class P> struct Multiples {
     static constexpr uint32_t p1(int i) { return P::p(i); }
     static constexpr uint32_t p2(int i) { return (P::p(i) << 1) | (i ? P::p(i - 1) >> 31 : 0u); }
